@@ -1,0 +1,183 @@
+/*
+ * bt.h -- C ABI of libbt: preconditioned conjugate gradient for symmetric
+ * positive definite block-tridiagonal systems S x = b on an NVIDIA GB300
+ * (sm_103a), preconditioned by the parametrised multi-splitting polynomial
+ * preconditioner of arXiv 2503.15269 at its optimal parameters.
+ *
+ * The matrix (Sec. 2.1, Eq. 1): N diagonal blocks D_i (n x n, SPD) and N-1
+ * off-diagonal blocks O_i = S[i, i+1], with S[i+1, i] = O_i^T; blocks are
+ * dense.  Indices are 0-based here (the paper counts from 1).
+ *
+ * The preconditioner (Sec. 3.1 and Sec. 3.5): with a = 1, b = -1,
+ *     M^-1 = (alpha_0 I + alpha_1 H + ... + alpha_{m-1} H^{m-1}) G,
+ * alpha_0 = 1, where G = G_opt (block tridiagonal) and H = H_opt (block
+ * pentadiagonal with zero +-1 blocks) have the closed forms of Sec. 4.1:
+ *     E_i = D_i^-1 O_i D_{i+1}^-1
+ *     G[i,i] = D_i^-1,  G[i,i+1] = -E_i,  G[i+1,i] = -E_i^T
+ *     H[i,i] = E_{i-1}^T O_{i-1} + E_i O_i^T,  H[i,i+2] = E_i O_{i+1},
+ *     H[i+2,i] = E_{i+1}^T O_i^T.
+ * It is applied as in Sec. 4.2: y_0 = G r, y_j = H y_{j-1}, z = sum alpha_j y_j.
+ *
+ * Conventions for every call below:
+ *   - Array arguments named D, O, b, x, r, z, y are DEVICE pointers to
+ *     float64 data, row-major within each block: D is [N][n][n], O is
+ *     [N-1][n][n], vectors are [N*n] (block i at offset i*n).  The caller
+ *     owns them; the library never frees them and keeps no pointer to D or
+ *     O after bt_setup* returns (it copies what it needs).
+ *   - Arrays named N, n, d_off, o_off, vec_off, iters, status are HOST
+ *     arrays.
+ *   - Work is queued on params->stream (a cudaStream_t; NULL = legacy
+ *     default stream).  Calls that return device-computed scalars through
+ *     host pointers (iters, status) synchronise that stream; the *_async
+ *     variants do not.
+ *   - Every call returns a bt_status.  On BT_ERR_ARG / BT_ERR_PARAM nothing
+ *     was launched.  bt_last_error gives the detail of the last failure.
+ *   - A handle is used by one host thread and one stream at a time.
+ */
+#ifndef BT_H_
+#define BT_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BT_OK = 0,
+  BT_ERR_ARG = 1,             /* bad pointer, size or layout                        */
+  BT_ERR_PARAM = 2,           /* parameter outside what the method admits (a, m, alpha) */
+  BT_ERR_NOT_SPD = 3,         /* a diagonal block D_i failed Cholesky (pivot <= 0)  */
+  BT_ERR_NO_CONVERGENCE = 4,  /* maxit (or max_outer) reached; x holds the last iterate */
+  BT_ERR_BREAKDOWN = 5,       /* p.q <= 0: S or M^-1 is not positive definite       */
+  BT_ERR_NONFINITE = 6,       /* NaN/Inf met in b or during the iteration           */
+  BT_ERR_TIMEOUT = 7,         /* the device loop ran past params->cycle_budget      */
+  BT_ERR_CUDA = 8,            /* a CUDA runtime call failed                         */
+  BT_ERR_ALLOC = 9,           /* device allocation failed                           */
+  BT_ERR_STATE = 10           /* call not valid for this handle (e.g. batched vs single) */
+} bt_status;
+
+typedef enum {
+  BT_FP64 = 0,   /* everything in float64                                            */
+  BT_MIXED = 1   /* float32 SpMV/preconditioner inside float64 iterative refinement   */
+} bt_precision;
+
+#define BT_MAX_M 8      /* largest polynomial order m accepted                 */
+#define BT_MAX_BLOCK 64 /* largest block size n accepted                       */
+
+typedef struct bt_params {
+  double a;            /* multi-splitting weight, b = 1 - 2a.  Admissible set C_g
+                          (Sec. 3.3) is a in [0,1]; this build implements the optimum
+                          a = 1 (Thm. 3.2) and rejects other values with BT_ERR_PARAM. */
+  int m;               /* polynomial order, 1..BT_MAX_M.                           */
+  const double* alpha; /* HOST array of m coefficients (Eq. with polynomial
+                          coefficients, Sec. 3.5); alpha[0] must be 1 and every
+                          alpha_j >= 0 (keeps M^-1 SPD, Thm. 3.3's setting).
+                          NULL = all ones (the "Optimal" preconditioner).           */
+  int precision;       /* bt_precision                                             */
+  double tol_inner;    /* BT_MIXED: relative tolerance of each float32 inner solve;
+                          0 = 1e-5.                                                 */
+  int max_outer;       /* BT_MIXED: refinement steps; 0 = 30.                      */
+  int use_x0;          /* 1: x holds the initial guess on entry; 0: start from 0.  */
+  long long cycle_budget; /* device clock cycles one solve may take before it stops
+                          with BT_ERR_TIMEOUT; 0 = 2^34 (about 8 s).                */
+  void* stream;        /* cudaStream_t                                             */
+  int ctas_per_sm;     /* persistent CTAs per SM; 0 = autotuned/default.           */
+  int group_ctas;      /* single-instance solves: CTAs that split the block rows;
+                          0 = chosen from N and n.                                  */
+  int stage_kb;        /* shared-memory pipeline stage size in KiB; 0 = default.   */
+} bt_params;
+
+typedef struct bt_ctx* bt_handle;
+
+/* Fill *p with the defaults: a = 1, m = 2, alpha = NULL, BT_FP64, everything
+ * else 0 (= automatic). */
+void bt_params_init(bt_params* p);
+
+/* Single instance setup (Sec. 4.1).  Copies D and O into the library's
+ * layout, factors every D_i by Cholesky in float64, forms D_i^-1, E_i and
+ * (m >= 2) the H blocks, in float64 (BT_FP64) or float32 from the float64
+ * Cholesky factor (BT_MIXED).  Returns BT_ERR_NOT_SPD if some D_i is not
+ * positive definite (bt_last_error gives the block and the failing pivot).
+ * Synchronises params->stream.  N >= 1, 1 <= n <= BT_MAX_BLOCK. */
+bt_status bt_setup(int N, int n, const double* D, const double* O,
+                   const bt_params* params, bt_handle* out);
+
+/* z = M^-1 r, one application of the preconditioner (Sec. 4.2), in the
+ * handle's working precision (float32 blocks for BT_MIXED).  r, z: [N*n]. */
+bt_status bt_apply_precond(bt_handle h, const double* r, double* z);
+
+/* y = S x (Eq. 1) with the float64 blocks.  x, y: [N*n]. */
+bt_status bt_spmv(bt_handle h, const double* x, double* y);
+
+/* y = S x with the float32 blocks of a BT_MIXED handle (the product the inner
+ * solve uses); float64 in and out.  BT_ERR_STATE on a BT_FP64 handle. */
+bt_status bt_spmv_f32(bt_handle h, const double* x, double* y);
+
+/* Solve S x = b by PCG (the textbook method the paper cites), stopping when
+ * ||r_k||_2 <= tol ||b||_2 on the recursive residual (BT_FP64) or on the
+ * float64 true residual b - S x (BT_MIXED).  One persistent kernel keeps the
+ * whole iteration on the device.  *iters = number of products S p (float32
+ * inner products summed over refinement steps for BT_MIXED).  b == 0 gives
+ * x = 0, iters = 0.  Synchronises the stream. */
+bt_status bt_pcg_solve(bt_handle h, const double* b, double* x, double tol, int maxit,
+                       int* iters);
+
+/* Details of the last bt_pcg_solve / batched solve of instance k (0 for a
+ * single instance): refinement steps taken and the final relative residual
+ * ||b - S x|| / ||b|| that the device measured (float64 true residual for
+ * BT_MIXED; the recursive residual for BT_FP64).  Host outputs. */
+bt_status bt_solve_info(bt_handle h, int k, int* outer, double* rel_residual);
+
+/* Batched setup: B independent instances of sizes N[k] x n[k], packed back
+ * to back: instance k's D starts at D + d_off[k], its O at O + o_off[k]
+ * (element offsets, HOST arrays).  Same work as bt_setup per instance. */
+bt_status bt_setup_batched(int B, const int* N, const int* n, const long long* d_off,
+                           const long long* o_off, const double* D, const double* O,
+                           const bt_params* params, bt_handle* out);
+
+/* Solve all B instances in one persistent launch: each CTA pulls instances
+ * from a device work queue ordered largest first and keeps per-instance
+ * convergence state.  Instance k's b and x start at b + vec_off[k] and
+ * x + vec_off[k]; vec_off == NULL means packed back to back in instance
+ * order.  iters[k], status[k] (HOST arrays of B) receive per-instance
+ * results; the call returns the first non-OK status, else BT_OK. */
+bt_status bt_pcg_solve_batched(bt_handle h, const double* b, double* x, const long long* vec_off,
+                               double tol, int maxit, int* iters, int* status);
+
+/* Same without any host synchronisation or host-side output (suitable for
+ * stream capture): per-instance iteration counts and statuses are written to
+ * the DEVICE arrays d_iters[B], d_status[B] (either may be NULL).  vec_off
+ * is the packing given at bt_setup_batched (back to back). */
+bt_status bt_pcg_solve_batched_async(bt_handle h, const double* b, double* x, double tol,
+                                     int maxit, int* d_iters, int* d_status);
+
+/* Capture bt_pcg_solve_batched_async(h, b, x, tol, maxit, d_iters, d_status)
+ * once into a CUDA graph owned by the handle; bt_graph_launch replays it on
+ * the handle's stream.  A new capture replaces the previous one. */
+bt_status bt_graph_capture_batched(bt_handle h, const double* b, double* x, double tol,
+                                   int maxit, int* d_iters, int* d_status);
+bt_status bt_graph_launch(bt_handle h);
+
+/* Adjoint of x = S^-1 b (kernel only): given x and g = S^-1 (dL/dx) for each
+ * instance (both packed like b), write dL/dD_i = -g_i x_i^T and
+ * dL/dO_i = -(g_i x_{i+1}^T + x_i g_{i+1}^T) into gD, gO (DEVICE, same
+ * packing as the D and O given at setup).  The caller obtains g with a second
+ * solve on the same handle (S is symmetric). */
+bt_status bt_adjoint_blocks(bt_handle h, const double* x, const double* g, double* gD,
+                            double* gO);
+
+/* Detail of the last failure on h: instance, block row and a value (the
+ * failing Cholesky pivot, or the offending p.q).  Any pointer may be NULL. */
+bt_status bt_last_error(bt_handle h, int* instance, int* block, double* value);
+
+/* Bytes of device memory the handle holds. */
+long long bt_device_bytes(bt_handle h);
+
+/* Release everything the handle owns.  NULL is ignored. */
+void bt_destroy(bt_handle h);
+
+const char* bt_status_string(bt_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BT_H_ */

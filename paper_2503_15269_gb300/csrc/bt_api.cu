@@ -1,0 +1,626 @@
+// C ABI of libbt (declared in include/bt.h): argument checks, memory layout,
+// instance scheduling order, launch configuration and the entry points.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "../../include/bt.h"
+#include "bt_common.cuh"
+
+extern "C" cudaError_t bt_launch_persistent(const bt::KParams* P, int grid, int smem_bytes, int mt_is_float,
+                                            int cooperative, cudaStream_t stream);
+extern "C" int bt_persistent_smem_fixed();
+extern "C" cudaError_t bt_persistent_occupancy(int mt_is_float, int smem_bytes, int* blocks_per_sm);
+extern "C" cudaError_t bt_launch_setup(const bt::SetupParams* P, int mixed, int m, int maxn, cudaStream_t st);
+extern "C" cudaError_t bt_launch_adjoint(const bt::AdjParams* P, cudaStream_t st);
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct bt_ctx {
+  bool batched = false;
+  int B = 0;
+  std::vector<int> N, n;
+  std::vector<long long> d_off, o_off, vec_off;
+  int maxN = 0, maxn = 0;
+  long long maxNn = 0, total_rows = 0, total_vec = 0;
+  bt_params prm{};
+  double alpha[BT_MAX_M];
+  cudaStream_t stream = nullptr;
+  int mixed = 0;
+  int dev = 0, sms = 0;
+  // device memory
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  double *D64 = nullptr, *O64 = nullptr, *Dinv64 = nullptr, *E64 = nullptr, *Hd64 = nullptr, *Hu64 = nullptr,
+         *Hl64 = nullptr;
+  float *D32 = nullptr, *O32 = nullptr, *Dinv32 = nullptr, *E32 = nullptr, *Hd32 = nullptr, *Hu32 = nullptr,
+        *Hl32 = nullptr;
+  bt::InstDesc* d_inst = nullptr;
+  bt::RowRef* d_rows = nullptr;
+  int* d_order = nullptr;
+  long long* d_doff = nullptr;
+  long long* d_ooff = nullptr;
+  int* d_ctl = nullptr;          // [0] queue, [1] abort, [2] barrier (as unsigned)
+  double* d_red = nullptr;
+  int *d_iters = nullptr, *d_status = nullptr, *d_outer = nullptr;
+  double *d_resid = nullptr, *d_errval = nullptr;
+  unsigned long long* d_fail_key = nullptr;
+  double* d_fail_piv = nullptr;
+  char* d_ws = nullptr;
+  long long ws_stride = 0, ws_vec = 0;
+  int ws_slots = 0;
+  // launch configuration
+  int stages = 0, stage_bytes = 0, smem = 0, grid = 0, G = 1;
+  // results of the last solve
+  std::vector<int> h_outer;
+  std::vector<double> h_resid;
+  // last error detail
+  int err_inst = -1, err_blk = -1;
+  double err_val = 0.0;
+  cudaGraphExec_t graph = nullptr;
+  cudaGraph_t graph_src = nullptr;
+};
+
+namespace {
+
+inline bt_status cuda_st(cudaError_t e) { return e == cudaSuccess ? BT_OK : BT_ERR_CUDA; }
+
+template <typename T>
+bt_status dalloc(bt_ctx* h, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  void* q = nullptr;
+  if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) return BT_ERR_ALLOC;
+  h->allocs.push_back(q);
+  h->bytes += count * sizeof(T);
+  *p = static_cast<T*>(q);
+  return BT_OK;
+}
+
+void free_all(bt_ctx* h) {
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->graph_src) cudaGraphDestroy(h->graph_src);
+  h->graph = nullptr;
+  h->graph_src = nullptr;
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+}
+
+bt_status check_params(const bt_params* p, double* alpha_out) {
+  if (!p) return BT_ERR_ARG;
+  // admissible set C_g is a in [0,1]; this build implements a = 1
+  if (!(p->a >= 0.0 && p->a <= 1.0)) return BT_ERR_PARAM;
+  if (p->a != 1.0) return BT_ERR_PARAM;
+  if (p->m < 1 || p->m > BT_MAX_M) return BT_ERR_PARAM;
+  for (int j = 0; j < p->m; ++j) {
+    const double a = p->alpha ? p->alpha[j] : 1.0;
+    if (!std::isfinite(a) || a < 0.0) return BT_ERR_PARAM;
+    alpha_out[j] = a;
+  }
+  if (alpha_out[0] != 1.0) return BT_ERR_PARAM;
+  if (p->precision != BT_FP64 && p->precision != BT_MIXED) return BT_ERR_PARAM;
+  if (p->tol_inner < 0.0 || p->tol_inner >= 1.0) return BT_ERR_PARAM;
+  if (p->max_outer < 0 || p->cycle_budget < 0 || p->ctas_per_sm < 0 || p->group_ctas < 0 || p->stage_kb < 0)
+    return BT_ERR_PARAM;
+  return BT_OK;
+}
+
+inline long long rup(long long v, long long a) { return (v + a - 1) / a * a; }
+
+// Common setup for one or many instances.
+bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
+  cudaStream_t st = h->stream;
+  cudaGetDevice(&h->dev);
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->dev);
+  const int B = h->B;
+  std::vector<bt::InstDesc> inst(B);
+  long long off32 = 0, off64 = 0, vec = 0, rows = 0;
+  for (int k = 0; k < B; ++k) {
+    const int N = h->N[k], n = h->n[k];
+    inst[k].N = N;
+    inst[k].n = n;
+    inst[k].bs32 = (int)rup((long long)n * n, 4);
+    inst[k].bs64 = (int)rup((long long)n * n, 2);
+    inst[k].off32 = off32;
+    inst[k].off64 = off64;
+    inst[k].vec = vec;  // natural packing: instances back to back
+    h->vec_off.push_back(vec);
+    off32 += (long long)N * inst[k].bs32;
+    off64 += (long long)N * inst[k].bs64;
+    vec += (long long)N * n;
+    rows += N;
+    h->maxN = std::max(h->maxN, N);
+    h->maxn = std::max(h->maxn, n);
+    h->maxNn = std::max(h->maxNn, (long long)N * n);
+  }
+  h->total_rows = rows;
+  h->total_vec = vec;
+  const bool mixed = h->mixed != 0;
+  const bool wantH = h->prm.m >= 2;
+  bt_status s;
+#define ALLOC(ptr, cnt) \
+  if ((s = dalloc(h, &(ptr), (cnt))) != BT_OK) return s
+  ALLOC(h->D64, off64);
+  ALLOC(h->O64, off64);
+  if (mixed) {
+    ALLOC(h->D32, off32);
+    ALLOC(h->O32, off32);
+    ALLOC(h->Dinv32, off32);
+    ALLOC(h->E32, off32);
+    if (wantH) {
+      ALLOC(h->Hd32, off32);
+      ALLOC(h->Hu32, off32);
+      ALLOC(h->Hl32, off32);
+    }
+  } else {
+    ALLOC(h->Dinv64, off64);
+    ALLOC(h->E64, off64);
+    if (wantH) {
+      ALLOC(h->Hd64, off64);
+      ALLOC(h->Hu64, off64);
+      ALLOC(h->Hl64, off64);
+    }
+  }
+  ALLOC(h->d_inst, B);
+  ALLOC(h->d_rows, rows);
+  ALLOC(h->d_order, B);
+  ALLOC(h->d_doff, B);
+  ALLOC(h->d_ooff, B);
+  ALLOC(h->d_ctl, 64);
+  ALLOC(h->d_iters, B);
+  ALLOC(h->d_status, B);
+  ALLOC(h->d_outer, B);
+  ALLOC(h->d_resid, B);
+  ALLOC(h->d_errval, B);
+  ALLOC(h->d_fail_key, 1);
+  ALLOC(h->d_fail_piv, rows);
+  // zero every block array once (padding slots must read as zero)
+  auto z64 = [&](double* p) { if (p) cudaMemsetAsync(p, 0, off64 * sizeof(double), st); };
+  auto z32 = [&](float* p) { if (p) cudaMemsetAsync(p, 0, off32 * sizeof(float), st); };
+  z64(h->D64); z64(h->O64); z64(h->Dinv64); z64(h->E64); z64(h->Hd64); z64(h->Hu64); z64(h->Hl64);
+  z32(h->D32); z32(h->O32); z32(h->Dinv32); z32(h->E32); z32(h->Hd32); z32(h->Hu32); z32(h->Hl32);
+  // row table and LPT order (largest N n^2 first)
+  std::vector<bt::RowRef> rr(rows);
+  {
+    long long t = 0;
+    for (int k = 0; k < B; ++k)
+      for (int i = 0; i < h->N[k]; ++i) rr[t++] = bt::RowRef{k, i};
+  }
+  std::vector<int> order(B);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (long long)h->N[a] * h->n[a] * h->n[a] > (long long)h->N[b] * h->n[b] * h->n[b];
+  });
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(h->d_inst, inst.data(), B * sizeof(bt::InstDesc), cudaMemcpyHostToDevice, st)) ||
+      (e = cudaMemcpyAsync(h->d_rows, rr.data(), rows * sizeof(bt::RowRef), cudaMemcpyHostToDevice, st)) ||
+      (e = cudaMemcpyAsync(h->d_order, order.data(), B * sizeof(int), cudaMemcpyHostToDevice, st)) ||
+      (e = cudaMemcpyAsync(h->d_doff, h->d_off.data(), B * sizeof(long long), cudaMemcpyHostToDevice, st)) ||
+      (e = cudaMemcpyAsync(h->d_ooff, h->o_off.data(), B * sizeof(long long), cudaMemcpyHostToDevice, st)))
+    return BT_ERR_CUDA;
+  if ((e = cudaMemsetAsync(h->d_fail_key, 0xff, sizeof(unsigned long long), st))) return BT_ERR_CUDA;
+  bt::SetupParams sp{};
+  sp.inst = h->d_inst;
+  sp.rows = h->d_rows;
+  sp.nrows = rows;
+  sp.D = D;
+  sp.O = O;
+  sp.d_off = h->d_doff;
+  sp.o_off = h->d_ooff;
+  sp.D64 = h->D64; sp.O64 = h->O64; sp.Dinv64 = h->Dinv64; sp.E64 = h->E64;
+  sp.Hd64 = h->Hd64; sp.Hu64 = h->Hu64; sp.Hl64 = h->Hl64;
+  sp.D32 = h->D32; sp.O32 = h->O32; sp.Dinv32 = h->Dinv32; sp.E32 = h->E32;
+  sp.Hd32 = h->Hd32; sp.Hu32 = h->Hu32; sp.Hl32 = h->Hl32;
+  sp.want32 = mixed ? 1 : 0;
+  sp.want64 = 1;
+  sp.fail_key = h->d_fail_key;
+  sp.fail_piv = h->d_fail_piv;
+  if ((e = bt_launch_setup(&sp, mixed ? 1 : 0, h->prm.m, h->maxn, st))) return BT_ERR_CUDA;
+
+  // ---- launch configuration of the persistent kernel ----
+  const int wbytes = mixed ? 4 : 8;
+  const long long bsb_max = rup((long long)h->maxn * h->maxn, mixed ? 4 : 2) * wbytes;
+  const long long bsb64_max = rup((long long)h->maxn * h->maxn, 2) * 8;
+  long long need = std::max(5 * bsb_max, 3 * bsb64_max);
+  long long sb = h->prm.stage_kb > 0 ? (long long)h->prm.stage_kb * 1024 : 48 * 1024;
+  sb = std::max(sb, rup(need, 128));
+  int smem_optin = 0;
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
+  const int fixed = bt_persistent_smem_fixed();
+  int cps = h->prm.ctas_per_sm > 0 ? h->prm.ctas_per_sm : 1;
+  const int per_cta = (int)std::min<long long>(smem_optin, (228 * 1024) / cps - 1024);
+  int S = (int)((per_cta - fixed) / sb);
+  if (S > bt::kMaxStages) S = bt::kMaxStages;
+  if (S < 2) return BT_ERR_ARG;  // block too large for the shared-memory pipeline
+  h->stages = S;
+  h->stage_bytes = (int)sb;
+  h->smem = fixed + S * (int)sb;
+  int occ = 0;
+  if (cuda_st(bt_persistent_occupancy(mixed ? 1 : 0, h->smem, &occ)) != BT_OK || occ < 1) return BT_ERR_CUDA;
+  cps = std::min(cps, occ);
+  if (h->batched) {
+    h->G = 1;
+    h->grid = std::min(h->sms * cps, std::max(1, B));
+    h->ws_slots = h->grid;
+  } else {
+    int G = h->prm.group_ctas;
+    if (G <= 0) {
+      const int rows_per = 4;
+      G = std::max(1, std::min(h->sms * cps, h->N[0] / rows_per));
+    }
+    G = std::min(G, h->sms * occ);
+    G = std::min(G, h->N[0]);
+    h->G = std::max(1, G);
+    h->grid = h->G;
+    h->ws_slots = 1;
+  }
+  h->ws_vec = rup(std::max<long long>(h->maxNn, 1), 64);
+  const int mts = mixed ? 4 : 8;
+  h->ws_stride = rup(10 * h->ws_vec * mts + h->ws_vec * 8, 256);
+  if ((s = dalloc(h, &h->d_ws, (size_t)h->ws_stride * h->ws_slots)) != BT_OK) return s;
+  if ((s = dalloc(h, &h->d_red, (size_t)2 * std::max(1, h->G) * 4)) != BT_OK) return s;
+  cudaMemsetAsync(h->d_ws, 0, (size_t)h->ws_stride * h->ws_slots, st);
+
+  // ---- setup status ----
+  unsigned long long key = 0;
+  if ((e = cudaMemcpyAsync(&key, h->d_fail_key, sizeof(key), cudaMemcpyDeviceToHost, st))) return BT_ERR_CUDA;
+  if ((e = cudaStreamSynchronize(st))) return BT_ERR_CUDA;
+  if (key != ~0ull) {
+    h->err_inst = (int)(key >> 32);
+    h->err_blk = (int)(key & 0xffffffffu);
+    long long grow = 0;
+    for (int k = 0; k < h->err_inst; ++k) grow += h->N[k];
+    grow += h->err_blk;
+    cudaMemcpy(&h->err_val, h->d_fail_piv + grow, sizeof(double), cudaMemcpyDeviceToHost);
+    return BT_ERR_NOT_SPD;
+  }
+  h->h_outer.assign(B, 0);
+  h->h_resid.assign(B, 0.0);
+  return BT_OK;
+}
+
+bt_ctx* new_ctx(const bt_params* p) {
+  bt_ctx* h = new bt_ctx();
+  h->prm = *p;
+  h->stream = static_cast<cudaStream_t>(p->stream);
+  h->mixed = p->precision == BT_MIXED;
+  return h;
+}
+
+bt::KParams base_kparams(bt_ctx* h) {
+  bt::KParams P{};
+  P.D64 = h->D64; P.O64 = h->O64; P.Dinv64 = h->Dinv64; P.E64 = h->E64;
+  P.Hd64 = h->Hd64; P.Hu64 = h->Hu64; P.Hl64 = h->Hl64;
+  P.D32 = h->D32; P.O32 = h->O32; P.Dinv32 = h->Dinv32; P.E32 = h->E32;
+  P.Hd32 = h->Hd32; P.Hu32 = h->Hu32; P.Hl32 = h->Hl32;
+  P.inst = h->d_inst;
+  P.order = h->d_order;
+  P.B = h->B;
+  P.queue = h->d_ctl;
+  P.abort_flag = h->d_ctl + 1;
+  P.bar = reinterpret_cast<unsigned*>(h->d_ctl + 2);
+  P.red = h->d_red;
+  P.mixed = h->mixed;
+  P.m = h->prm.m;
+  for (int j = 0; j < BT_MAX_M; ++j) P.alpha[j] = j < h->prm.m ? h->alpha[j] : 0.0;
+  P.tol_inner = h->prm.tol_inner > 0 ? h->prm.tol_inner : 1e-5;
+  P.max_outer = h->prm.max_outer > 0 ? h->prm.max_outer : 30;
+  P.use_x0 = h->prm.use_x0;
+  P.budget = h->prm.cycle_budget > 0 ? h->prm.cycle_budget : (1ll << 34);
+  P.ws = h->d_ws;
+  P.ws_stride = h->ws_stride;
+  P.ws_vec = h->ws_vec;
+  P.G = h->G;
+  P.iters = h->d_iters;
+  P.status = h->d_status;
+  P.outer = h->d_outer;
+  P.resid = h->d_resid;
+  P.errval = h->d_errval;
+  P.stages = h->stages;
+  P.stage_bytes = h->stage_bytes;
+  return P;
+}
+
+bt_status launch(bt_ctx* h, bt::KParams& P) {
+  cudaError_t e = cudaMemsetAsync(h->d_ctl, 0, 64 * sizeof(int), h->stream);
+  if (e) return BT_ERR_CUDA;
+  const bool coop = h->G > 1;
+  e = bt_launch_persistent(&P, h->grid, h->smem, h->mixed, coop ? 1 : 0, h->stream);
+  return cuda_st(e);
+}
+
+// Op launch with the batched grid or the group grid as configured.
+bt_status run_op(bt_ctx* h, int op, const double* in, double* out) {
+  bt::KParams P = base_kparams(h);
+  P.op = op;
+  P.bvec = in;
+  P.xvec = out;
+  P.tol = 0;
+  P.maxit = 0;
+  return launch(h, P);
+}
+
+bt_status collect(bt_ctx* h, int* iters, int* status_out, bool all) {
+  const int B = h->B;
+  std::vector<int> st(B), it(B);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(it.data(), h->d_iters, B * sizeof(int), cudaMemcpyDeviceToHost, h->stream)) ||
+      (e = cudaMemcpyAsync(st.data(), h->d_status, B * sizeof(int), cudaMemcpyDeviceToHost, h->stream)) ||
+      (e = cudaMemcpyAsync(h->h_outer.data(), h->d_outer, B * sizeof(int), cudaMemcpyDeviceToHost, h->stream)) ||
+      (e = cudaMemcpyAsync(h->h_resid.data(), h->d_resid, B * sizeof(double), cudaMemcpyDeviceToHost,
+                           h->stream)) ||
+      (e = cudaStreamSynchronize(h->stream)))
+    return BT_ERR_CUDA;
+  bt_status first = BT_OK;
+  for (int k = 0; k < B; ++k) {
+    if (iters) iters[k] = it[k];
+    if (status_out) status_out[k] = st[k];
+    if (st[k] != BT_OK && first == BT_OK) {
+      first = static_cast<bt_status>(st[k]);
+      h->err_inst = k;
+      h->err_blk = -1;
+      double v = 0;
+      cudaMemcpy(&v, h->d_errval + k, sizeof(double), cudaMemcpyDeviceToHost);
+      h->err_val = v;
+    }
+    if (!all) break;
+  }
+  return first;
+}
+
+}  // namespace
+
+extern "C" {
+
+void bt_params_init(bt_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->a = 1.0;
+  p->m = 2;
+  p->alpha = nullptr;
+  p->precision = BT_FP64;
+}
+
+const char* bt_status_string(bt_status s) {
+  switch (s) {
+    case BT_OK: return "ok";
+    case BT_ERR_ARG: return "invalid argument";
+    case BT_ERR_PARAM: return "parameter outside the admissible set";
+    case BT_ERR_NOT_SPD: return "diagonal block not positive definite";
+    case BT_ERR_NO_CONVERGENCE: return "no convergence within the iteration limit";
+    case BT_ERR_BREAKDOWN: return "CG breakdown (p.q <= 0)";
+    case BT_ERR_NONFINITE: return "non-finite value";
+    case BT_ERR_TIMEOUT: return "device loop exceeded its cycle budget";
+    case BT_ERR_CUDA: return "CUDA runtime error";
+    case BT_ERR_ALLOC: return "device allocation failed";
+    case BT_ERR_STATE: return "call not valid for this handle";
+  }
+  return "unknown status";
+}
+
+bt_status bt_setup(int N, int n, const double* D, const double* O, const bt_params* params, bt_handle* out) {
+  if (!out) return BT_ERR_ARG;
+  *out = nullptr;
+  if (N < 1 || n < 1 || n > BT_MAX_BLOCK || !D || (N > 1 && !O)) return BT_ERR_ARG;
+  double alpha[BT_MAX_M];
+  bt_status s = check_params(params, alpha);
+  if (s != BT_OK) return s;
+  bt_ctx* h = new_ctx(params);
+  std::memcpy(h->alpha, alpha, sizeof(alpha));
+  h->batched = false;
+  h->B = 1;
+  h->N = {N};
+  h->n = {n};
+  h->d_off = {0};
+  h->o_off = {0};
+  s = setup_common(h, D, O);
+  if (s != BT_OK && s != BT_ERR_NOT_SPD) {
+    free_all(h);
+    delete h;
+    return s;
+  }
+  *out = h;
+  return s;
+}
+
+bt_status bt_setup_batched(int B, const int* N, const int* n, const long long* d_off, const long long* o_off,
+                           const double* D, const double* O, const bt_params* params, bt_handle* out) {
+  if (!out) return BT_ERR_ARG;
+  *out = nullptr;
+  if (B < 1 || !N || !n || !d_off || !o_off || !D) return BT_ERR_ARG;
+  bool needO = false;
+  for (int k = 0; k < B; ++k) {
+    if (N[k] < 1 || n[k] < 1 || n[k] > BT_MAX_BLOCK || d_off[k] < 0 || o_off[k] < 0) return BT_ERR_ARG;
+    if (N[k] > 1) needO = true;
+  }
+  if (needO && !O) return BT_ERR_ARG;
+  double alpha[BT_MAX_M];
+  bt_status s = check_params(params, alpha);
+  if (s != BT_OK) return s;
+  bt_ctx* h = new_ctx(params);
+  std::memcpy(h->alpha, alpha, sizeof(alpha));
+  h->batched = true;
+  h->B = B;
+  h->N.assign(N, N + B);
+  h->n.assign(n, n + B);
+  h->d_off.assign(d_off, d_off + B);
+  h->o_off.assign(o_off, o_off + B);
+  s = setup_common(h, D, O);
+  if (s != BT_OK && s != BT_ERR_NOT_SPD) {
+    free_all(h);
+    delete h;
+    return s;
+  }
+  *out = h;
+  return s;
+}
+
+bt_status bt_apply_precond(bt_handle h, const double* r, double* z) {
+  if (!h || !r || !z) return BT_ERR_ARG;
+  bt_status s = run_op(h, bt::kOpApply, r, z);
+  if (s != BT_OK) return s;
+  return cuda_st(cudaStreamSynchronize(h->stream));
+}
+
+bt_status bt_spmv(bt_handle h, const double* x, double* y) {
+  if (!h || !x || !y) return BT_ERR_ARG;
+  bt_status s = run_op(h, bt::kOpSpmv64, x, y);
+  if (s != BT_OK) return s;
+  return cuda_st(cudaStreamSynchronize(h->stream));
+}
+
+bt_status bt_spmv_f32(bt_handle h, const double* x, double* y) {
+  if (!h || !x || !y) return BT_ERR_ARG;
+  if (!h->mixed) return BT_ERR_STATE;
+  bt_status s = run_op(h, bt::kOpSpmv32, x, y);
+  if (s != BT_OK) return s;
+  return cuda_st(cudaStreamSynchronize(h->stream));
+}
+
+static bt_status solve_launch(bt_handle h, const double* b, double* x, double tol, int maxit) {
+  if (!(tol >= 0.0) || maxit < 0) return BT_ERR_ARG;
+  bt::KParams P = base_kparams(h);
+  P.op = bt::kOpSolve;
+  P.bvec = b;
+  P.xvec = x;
+  P.tol = tol;
+  P.maxit = maxit;
+  return launch(h, P);
+}
+
+bt_status bt_pcg_solve(bt_handle h, const double* b, double* x, double tol, int maxit, int* iters) {
+  if (!h || !b || !x) return BT_ERR_ARG;
+  if (h->batched) return BT_ERR_STATE;
+  bt_status s = solve_launch(h, b, x, tol, maxit);
+  if (s != BT_OK) return s;
+  int it = 0;
+  s = collect(h, &it, nullptr, true);
+  if (iters) *iters = it;
+  return s;
+}
+
+bt_status bt_pcg_solve_batched(bt_handle h, const double* b, double* x, const long long* vec_off, double tol,
+                               int maxit, int* iters, int* status) {
+  if (!h || !b || !x) return BT_ERR_ARG;
+  if (!h->batched) return BT_ERR_STATE;
+  if (vec_off) {
+    bool same = true;
+    for (int k = 0; k < h->B; ++k) same &= (vec_off[k] == h->vec_off[k]);
+    if (!same) {
+      // re-pack the descriptors with the new vector offsets
+      std::vector<bt::InstDesc> inst(h->B);
+      cudaMemcpy(inst.data(), h->d_inst, h->B * sizeof(bt::InstDesc), cudaMemcpyDeviceToHost);
+      for (int k = 0; k < h->B; ++k) {
+        if (vec_off[k] < 0) return BT_ERR_ARG;
+        inst[k].vec = vec_off[k];
+        h->vec_off[k] = vec_off[k];
+      }
+      if (cudaMemcpy(h->d_inst, inst.data(), h->B * sizeof(bt::InstDesc), cudaMemcpyHostToDevice))
+        return BT_ERR_CUDA;
+    }
+  }
+  bt_status s = solve_launch(h, b, x, tol, maxit);
+  if (s != BT_OK) return s;
+  return collect(h, iters, status, true);
+}
+
+bt_status bt_pcg_solve_batched_async(bt_handle h, const double* b, double* x, double tol, int maxit,
+                                     int* d_iters, int* d_status) {
+  if (!h || !b || !x) return BT_ERR_ARG;
+  if (!h->batched) return BT_ERR_STATE;
+  bt_status s = solve_launch(h, b, x, tol, maxit);
+  if (s != BT_OK) return s;
+  if (d_iters &&
+      cudaMemcpyAsync(d_iters, h->d_iters, h->B * sizeof(int), cudaMemcpyDeviceToDevice, h->stream))
+    return BT_ERR_CUDA;
+  if (d_status &&
+      cudaMemcpyAsync(d_status, h->d_status, h->B * sizeof(int), cudaMemcpyDeviceToDevice, h->stream))
+    return BT_ERR_CUDA;
+  return BT_OK;
+}
+
+bt_status bt_graph_capture_batched(bt_handle h, const double* b, double* x, double tol, int maxit, int* d_iters,
+                                   int* d_status) {
+  if (!h) return BT_ERR_ARG;
+  if (!h->batched) return BT_ERR_STATE;
+  if (!h->stream) return BT_ERR_ARG;  // the legacy default stream cannot be captured
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->graph_src) cudaGraphDestroy(h->graph_src);
+  h->graph = nullptr;
+  h->graph_src = nullptr;
+  // make sure the kernel attributes are set before capture
+  int occ = 0;
+  bt_persistent_occupancy(h->mixed, h->smem, &occ);
+  if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal)) return BT_ERR_CUDA;
+  bt_status s = bt_pcg_solve_batched_async(h, b, x, tol, maxit, d_iters, d_status);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  if (s != BT_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e) return BT_ERR_CUDA;
+  h->graph_src = g;
+  if (cudaGraphInstantiate(&h->graph, g, 0)) return BT_ERR_CUDA;
+  return BT_OK;
+}
+
+bt_status bt_graph_launch(bt_handle h) {
+  if (!h || !h->graph) return BT_ERR_STATE;
+  return cuda_st(cudaGraphLaunch(h->graph, h->stream));
+}
+
+bt_status bt_solve_info(bt_handle h, int k, int* outer, double* rel_residual) {
+  if (!h || k < 0 || k >= h->B) return BT_ERR_ARG;
+  if ((int)h->h_outer.size() != h->B) return BT_ERR_STATE;
+  if (outer) *outer = h->h_outer[k];
+  if (rel_residual) *rel_residual = h->h_resid[k];
+  return BT_OK;
+}
+
+bt_status bt_adjoint_blocks(bt_handle h, const double* x, const double* g, double* gD, double* gO) {
+  if (!h || !x || !g || !gD) return BT_ERR_ARG;
+  if (!gO && h->maxN > 1) return BT_ERR_ARG;
+  bt::AdjParams a{};
+  a.inst = h->d_inst;
+  a.rows = h->d_rows;
+  a.nrows = h->total_rows;
+  a.d_off = h->d_doff;
+  a.o_off = h->d_ooff;
+  a.x = x;
+  a.g = g;
+  a.gD = gD;
+  a.gO = gO;
+  return cuda_st(bt_launch_adjoint(&a, h->stream));
+}
+
+bt_status bt_last_error(bt_handle h, int* instance, int* block, double* value) {
+  if (!h) return BT_ERR_ARG;
+  if (instance) *instance = h->err_inst;
+  if (block) *block = h->err_blk;
+  if (value) *value = h->err_val;
+  return BT_OK;
+}
+
+long long bt_device_bytes(bt_handle h) { return h ? (long long)h->bytes : 0; }
+
+void bt_destroy(bt_handle h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  free_all(h);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,161 @@
+// Shared definitions for the libbt CUDA sources (sm_103a).
+//
+// Library block layout.  Every block array (D, O, D^-1, E, Hd, Hu, Hl) holds,
+// per instance, N slots of `bs` elements, one slot per block row i (the
+// arrays with fewer real blocks -- O and E have N-1, Hu and Hl have N-2 --
+// keep zero-filled padding slots so that every array indexes by row).  `bs`
+// is n*n rounded up to 16 bytes so that each block starts on the 16-byte
+// boundary a bulk copy needs.  Inside a slot the block is stored
+// column-major: element (a, c) at c*n + a.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bt {
+
+constexpr int kMaxM = 8;
+constexpr int kMaxBlock = 64;
+constexpr int kMaxStages = 8;
+constexpr int kThreads = 256;           // threads per persistent CTA
+constexpr int kMaxChunkElems = 512;     // rows-per-chunk cap: R * n <= 512
+
+enum Status : int {
+  kOK = 0, kErrArg = 1, kErrParam = 2, kErrNotSPD = 3, kErrNoConv = 4,
+  kErrBreakdown = 5, kErrNonfinite = 6, kErrTimeout = 7
+};
+
+struct InstDesc {
+  int N, n;
+  int bs32, bs64;          // padded block stride in elements
+  long long off32, off64;  // element offset of block row 0 in every block array
+  long long vec;           // element offset of the instance's vectors in b / x
+};
+
+enum Op : int { kOpSolve = 0, kOpSpmv64 = 1, kOpSpmv32 = 2, kOpApply = 3 };
+
+struct KParams {
+  const double *D64, *O64, *Dinv64, *E64, *Hd64, *Hu64, *Hl64;
+  const float *D32, *O32, *Dinv32, *E32, *Hd32, *Hu32, *Hl32;
+  const InstDesc* inst;
+  const int* order;        // instance processing order (largest first)
+  int B;
+  int* queue;              // work counter, zeroed before launch
+  const double* bvec;      // SOLVE: b;  SPMV: x;  APPLY: r
+  double* xvec;            // SOLVE: x;  SPMV: y;  APPLY: z
+  int op, mixed, m;
+  double alpha[kMaxM];
+  double tol, tol_inner;
+  int maxit, max_outer, use_x0;
+  long long budget;        // clock cycles per instance solve
+  char* ws;                // workspace: one slot per CTA (batched) or one shared slot
+  long long ws_stride;     // bytes per slot
+  long long ws_vec;        // elements per vector in a slot (>= max N*n)
+  int G;                   // CTAs per instance (1 = batched mode)
+  unsigned* bar;           // group barrier counter (zeroed before launch)
+  double* red;             // group reduction slots [2][G][4]
+  int* abort_flag;
+  int* iters; int* status; int* outer; double* resid; double* errval;
+  int stages, stage_bytes;
+};
+
+struct RowRef {
+  int inst, row;
+};
+
+struct SetupParams {
+  const InstDesc* inst;
+  const RowRef* rows;
+  long long nrows;
+  const double* D;          // caller's D (row-major blocks)
+  const double* O;          // caller's O
+  const long long* d_off;   // per instance, element offsets in D / O
+  const long long* o_off;
+  double *D64, *O64, *Dinv64, *E64, *Hd64, *Hu64, *Hl64;
+  float *D32, *O32, *Dinv32, *E32, *Hd32, *Hu32, *Hl32;
+  int want32, want64;       // which precisions to produce
+  unsigned long long* fail_key;  // min over failing (inst << 32 | row)
+  double* fail_piv;         // per global row: the failing pivot
+};
+
+struct AdjParams {
+  const InstDesc* inst;
+  const RowRef* rows;
+  long long nrows;
+  const long long* d_off;
+  const long long* o_off;
+  const double* x;
+  const double* g;
+  double* gD;
+  double* gO;
+};
+
+
+// ---------------------------------------------------------------------------
+// PTX helpers: mbarrier, bulk global->shared copy through the TMA engine.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: returns false if `deadline` (clock64 cycles) passes first.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, long long deadline) {
+  while (!mbar_try_wait(b, parity)) {
+    if (clock64() > deadline) return false;
+  }
+  return true;
+}
+
+// bytes must be a multiple of 16; both addresses 16-byte aligned.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* b) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(b))
+      : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ int ld_volatile_i32(const int* p) {
+  return *reinterpret_cast<const volatile int*>(p);
+}
+
+template <typename T>
+__device__ __forceinline__ bool is_finite(T v) {
+  return isfinite(v);
+}
+
+}  // namespace bt

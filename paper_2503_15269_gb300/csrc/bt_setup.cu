@@ -1,0 +1,305 @@
+// Setup kernels: the preconditioner blocks of Sec. 4.1 for every block row of
+// every instance, plus the layout copies of D and O, and the adjoint's block
+// outer products.
+//
+//   K0  copy D_i, O_i (row-major, caller's) into the library layout
+//       (column-major, 16-byte padded slots) in float64 and/or float32
+//   K1  D_i = L_i L_i^T by Cholesky in float64, W = L_i^-1, D_i^-1 = W^T W
+//       (float64 for the float64 handle; float32 from the float64 factor for
+//       the mixed handle)
+//   K2  E_i = D_i^-1 O_i D_{i+1}^-1
+//   K3  Hd_i = E_{i-1}^T O_{i-1} + E_i O_i^T, Hu_i = E_i O_{i+1},
+//       Hl_i = E_{i+1}^T O_i^T          (only for polynomial order m >= 2)
+// One CTA per block row; block products run out of shared memory.
+#include "bt_common.cuh"
+
+namespace bt {
+
+// ---------------------------------------------------------------- K0
+__global__ void k_copy_blocks(const __grid_constant__ SetupParams P) {
+  const long long gr = blockIdx.x;
+  if (gr >= P.nrows) return;
+  const RowRef rr = P.rows[gr];
+  const InstDesc d = P.inst[rr.inst];
+  const int n = d.n, i = rr.row;
+  const double* Du = P.D + P.d_off[rr.inst] + (long long)i * n * n;
+  const bool hasO = i < d.N - 1;
+  const double* Ou = hasO ? P.O + P.o_off[rr.inst] + (long long)i * n * n : nullptr;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int a = t / n, c = t - a * n;  // row-major source element (a, c)
+    const double dv = Du[t];
+    const double ov = hasO ? Ou[t] : 0.0;
+    const long long o64 = d.off64 + (long long)i * d.bs64 + (long long)c * n + a;
+    const long long o32 = d.off32 + (long long)i * d.bs32 + (long long)c * n + a;
+    P.D64[o64] = dv;
+    P.O64[o64] = ov;
+    if (P.want32) {
+      P.D32[o32] = (float)dv;
+      P.O32[o32] = (float)ov;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- K1
+// Dense Cholesky of one block in shared memory, then the inverse.
+template <typename MT>
+__global__ void k_chol_inv(const __grid_constant__ SetupParams P) {
+  extern __shared__ __align__(16) char smraw[];
+  const long long gr = blockIdx.x;
+  if (gr >= P.nrows) return;
+  const RowRef rr = P.rows[gr];
+  const InstDesc d = P.inst[rr.inst];
+  const int n = d.n, i = rr.row;
+  double* A = reinterpret_cast<double*>(smraw);              // n*n, row-major lower factor
+  MT* W = reinterpret_cast<MT*>(smraw + (size_t)n * n * 8);  // n*n
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  const double* Du = P.D + P.d_off[rr.inst] + (long long)i * n * n;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) A[t] = Du[t];
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      const double piv = A[j * n + j];
+      if (!(piv > 0.0) || !isfinite(piv)) {
+        bad = 1;
+        P.fail_piv[gr] = piv;
+        atomicMin(P.fail_key, ((unsigned long long)rr.inst << 32) | (unsigned)i);
+      } else {
+        A[j * n + j] = sqrt(piv);
+      }
+    }
+    __syncthreads();
+    if (bad) return;
+    const double ljj = A[j * n + j];
+    for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) A[r * n + j] /= ljj;
+    __syncthreads();
+    // trailing update of the lower triangle: A[r][c] -= L[r][j] L[c][j], j < c <= r
+    const int m = n - j - 1;
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+      const int r = j + 1 + t / m, c = j + 1 + t % m;
+      if (c <= r) A[r * n + c] -= A[r * n + j] * A[c * n + j];
+    }
+    __syncthreads();
+  }
+  // W = L^-1, one column per thread (forward substitution in MT precision)
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    for (int r = 0; r < c; ++r) W[r * n + c] = MT(0);
+    W[c * n + c] = MT(1) / (MT)A[c * n + c];
+    for (int r = c + 1; r < n; ++r) {
+      MT acc = MT(0);
+      for (int t = c; t < r; ++t) acc = fma((MT)A[r * n + t], W[t * n + c], acc);
+      W[r * n + c] = -acc / (MT)A[r * n + r];
+    }
+  }
+  __syncthreads();
+  // D^-1 = W^T W (symmetric: compute a >= b and mirror)
+  MT* out = (sizeof(MT) == 8) ? reinterpret_cast<MT*>(P.Dinv64 + d.off64 + (long long)i * d.bs64)
+                              : reinterpret_cast<MT*>(P.Dinv32 + d.off32 + (long long)i * d.bs32);
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int a = t / n, b = t % n;
+    if (a < b) continue;
+    MT acc = MT(0);
+    for (int r = a; r < n; ++r) acc = fma(W[r * n + a], W[r * n + b], acc);
+    out[(long long)b * n + a] = acc;
+    out[(long long)a * n + b] = acc;
+  }
+}
+
+// Small dense products in shared memory: matrices are row-major n x n.
+// C (+)= op(A) op(B)
+template <typename MT>
+__device__ void sm_gemm(MT* C, const MT* A, bool tA, const MT* B, bool tB, int n, bool accumulate) {
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int a = t / n, b = t % n;
+    MT acc = accumulate ? C[t] : MT(0);
+    for (int c = 0; c < n; ++c) {
+      const MT av = tA ? A[c * n + a] : A[a * n + c];
+      const MT bv = tB ? B[b * n + c] : B[c * n + b];
+      acc = fma(av, bv, acc);
+    }
+    C[t] = acc;
+  }
+}
+
+// load a column-major library block into row-major shared memory
+template <typename MT>
+__device__ void sm_load(MT* dst, const MT* src, int n) {
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int a = t / n, c = t % n;
+    dst[t] = src[(long long)c * n + a];
+  }
+}
+template <typename MT>
+__device__ void sm_store(MT* dst, const MT* src, int n) {
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int a = t / n, c = t % n;
+    dst[(long long)c * n + a] = src[t];
+  }
+}
+
+template <typename MT>
+struct MatSet {
+  const MT *O, *Dinv;
+  MT *E, *Hd, *Hu, *Hl;
+  long long off;
+  int bs;
+};
+
+template <typename MT>
+__device__ MatSet<MT> matset(const SetupParams& P, const InstDesc& d) {
+  MatSet<MT> s;
+  if (sizeof(MT) == 8) {
+    s.O = (const MT*)P.O64; s.Dinv = (const MT*)P.Dinv64; s.E = (MT*)P.E64;
+    s.Hd = (MT*)P.Hd64; s.Hu = (MT*)P.Hu64; s.Hl = (MT*)P.Hl64; s.off = d.off64; s.bs = d.bs64;
+  } else {
+    s.O = (const MT*)P.O32; s.Dinv = (const MT*)P.Dinv32; s.E = (MT*)P.E32;
+    s.Hd = (MT*)P.Hd32; s.Hu = (MT*)P.Hu32; s.Hl = (MT*)P.Hl32; s.off = d.off32; s.bs = d.bs32;
+  }
+  return s;
+}
+
+// ---------------------------------------------------------------- K2
+template <typename MT>
+__global__ void k_E(const __grid_constant__ SetupParams P) {
+  extern __shared__ __align__(16) char smraw[];
+  const long long gr = blockIdx.x;
+  if (gr >= P.nrows) return;
+  const RowRef rr = P.rows[gr];
+  const InstDesc d = P.inst[rr.inst];
+  const int n = d.n, i = rr.row;
+  if (i >= d.N - 1) return;  // padding slot stays zero
+  MatSet<MT> M = matset<MT>(P, d);
+  MT* s0 = reinterpret_cast<MT*>(smraw);
+  MT* s1 = s0 + n * n;
+  MT* s2 = s1 + n * n;
+  const auto blk = [&](const MT* base, int row) { return base + M.off + (long long)row * M.bs; };
+  sm_load(s0, blk(M.O, i), n);
+  sm_load(s1, blk(M.Dinv, i + 1), n);
+  __syncthreads();
+  sm_gemm(s2, s0, false, s1, false, n, false);  // T = O_i D_{i+1}^-1
+  __syncthreads();
+  sm_load(s0, blk(M.Dinv, i), n);
+  __syncthreads();
+  sm_gemm(s1, s0, false, s2, false, n, false);  // E_i = D_i^-1 T
+  __syncthreads();
+  sm_store(const_cast<MT*>(blk(M.E, i)), s1, n);
+}
+
+// ---------------------------------------------------------------- K3
+template <typename MT>
+__global__ void k_H(const __grid_constant__ SetupParams P) {
+  extern __shared__ __align__(16) char smraw[];
+  const long long gr = blockIdx.x;
+  if (gr >= P.nrows) return;
+  const RowRef rr = P.rows[gr];
+  const InstDesc d = P.inst[rr.inst];
+  const int n = d.n, i = rr.row, N = d.N;
+  MatSet<MT> M = matset<MT>(P, d);
+  MT* sa = reinterpret_cast<MT*>(smraw);
+  MT* sb = sa + n * n;
+  MT* sc = sb + n * n;
+  const auto blk = [&](const MT* base, int row) { return base + M.off + (long long)row * M.bs; };
+  // Hd_i = E_{i-1}^T O_{i-1} + E_i O_i^T
+  bool acc = false;
+  if (i > 0) {
+    sm_load(sa, blk(M.E, i - 1), n);
+    sm_load(sb, blk(M.O, i - 1), n);
+    __syncthreads();
+    sm_gemm(sc, sa, true, sb, false, n, false);
+    acc = true;
+    __syncthreads();
+  }
+  if (i < N - 1) {
+    sm_load(sa, blk(M.E, i), n);
+    sm_load(sb, blk(M.O, i), n);
+    __syncthreads();
+    sm_gemm(sc, sa, false, sb, true, n, acc);
+    acc = true;
+    __syncthreads();
+  }
+  if (acc) sm_store(const_cast<MT*>(blk(M.Hd, i)), sc, n);
+  __syncthreads();
+  if (i < N - 2) {
+    // Hu_i = E_i O_{i+1}
+    sm_load(sa, blk(M.E, i), n);
+    sm_load(sb, blk(M.O, i + 1), n);
+    __syncthreads();
+    sm_gemm(sc, sa, false, sb, false, n, false);
+    __syncthreads();
+    sm_store(const_cast<MT*>(blk(M.Hu, i)), sc, n);
+    __syncthreads();
+    // Hl_i = E_{i+1}^T O_i^T
+    sm_load(sa, blk(M.E, i + 1), n);
+    sm_load(sb, blk(M.O, i), n);
+    __syncthreads();
+    sm_gemm(sc, sa, true, sb, true, n, false);
+    __syncthreads();
+    sm_store(const_cast<MT*>(blk(M.Hl, i)), sc, n);
+  }
+}
+
+// ---------------------------------------------------------------- adjoint
+// gD_i = -g_i x_i^T, gO_i = -(g_i x_{i+1}^T + x_i g_{i+1}^T), caller layout.
+__global__ void k_adjoint(const __grid_constant__ AdjParams P) {
+  const long long gr = blockIdx.x;
+  if (gr >= P.nrows) return;
+  const RowRef rr = P.rows[gr];
+  const InstDesc d = P.inst[rr.inst];
+  const int n = d.n, i = rr.row;
+  const double* x = P.x + d.vec;
+  const double* g = P.g + d.vec;
+  double* gD = P.gD + P.d_off[rr.inst] + (long long)i * n * n;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int a = t / n, c = t % n;
+    gD[t] = -g[(long long)i * n + a] * x[(long long)i * n + c];
+  }
+  if (i < d.N - 1) {
+    double* gO = P.gO + P.o_off[rr.inst] + (long long)i * n * n;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+      const int a = t / n, c = t % n;
+      gO[t] = -(g[(long long)i * n + a] * x[(long long)(i + 1) * n + c] +
+                x[(long long)i * n + a] * g[(long long)(i + 1) * n + c]);
+    }
+  }
+}
+
+}  // namespace bt
+
+// ---------------------------------------------------------------- host launchers
+extern "C" cudaError_t bt_launch_setup(const bt::SetupParams* P, int mixed, int m, int maxn, cudaStream_t st) {
+  const long long nb = P->nrows;
+  if (nb == 0) return cudaSuccess;
+  const dim3 grid((unsigned)nb);
+  bt::k_copy_blocks<<<grid, 128, 0, st>>>(*P);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  const int sm_chol = maxn * maxn * 8 + maxn * maxn * (mixed ? 4 : 8);
+  const int msz = mixed ? 4 : 8;
+  const int sm_prod = 3 * maxn * maxn * msz;
+  if (mixed) {
+    cudaFuncSetAttribute(bt::k_chol_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_chol);
+    cudaFuncSetAttribute(bt::k_E<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_prod);
+    cudaFuncSetAttribute(bt::k_H<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_prod);
+    bt::k_chol_inv<float><<<grid, 128, sm_chol, st>>>(*P);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    bt::k_E<float><<<grid, 128, sm_prod, st>>>(*P);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if (m >= 2) bt::k_H<float><<<grid, 128, sm_prod, st>>>(*P);
+  } else {
+    cudaFuncSetAttribute(bt::k_chol_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_chol);
+    cudaFuncSetAttribute(bt::k_E<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_prod);
+    cudaFuncSetAttribute(bt::k_H<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_prod);
+    bt::k_chol_inv<double><<<grid, 128, sm_chol, st>>>(*P);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    bt::k_E<double><<<grid, 128, sm_prod, st>>>(*P);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if (m >= 2) bt::k_H<double><<<grid, 128, sm_prod, st>>>(*P);
+  }
+  return cudaGetLastError();
+}
+
+extern "C" cudaError_t bt_launch_adjoint(const bt::AdjParams* P, cudaStream_t st) {
+  if (P->nrows == 0) return cudaSuccess;
+  bt::k_adjoint<<<(unsigned)P->nrows, 128, 0, st>>>(*P);
+  return cudaGetLastError();
+}

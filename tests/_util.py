@@ -1,0 +1,67 @@
+"""Helpers shared by the GPU tests (marshalling only)."""
+import numpy as np
+
+from paper_2503_15269_gb300 import binding as bb
+
+
+def dev(a):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda:0")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+class Single:
+    """One instance on the device: setup + entry points, raising on error."""
+
+    def __init__(self, inst, m=2, alpha=None, precision=bb.BT_FP64, **kw):
+        self.inst = inst
+        self.D = dev(inst.D)
+        self.O = dev(inst.O if inst.O.size else np.zeros((1, inst.n, inst.n)))
+        self.params, self._keep = bb.make_params(m=m, alpha=alpha, precision=precision, **kw)
+        self.st, self.h = bb.bt_setup(inst.N, inst.n, self.D, self.O, self.params)
+
+    def ok(self):
+        assert self.st == bb.BT_OK, bb.status_string(self.st)
+        return self
+
+    def apply(self, r):
+        z = dev(np.zeros(r.size))
+        st = bb.bt_apply_precond(self.h, dev(r.reshape(-1)), z)
+        assert st == bb.BT_OK, bb.status_string(st)
+        return host(z).reshape(r.shape)
+
+    def spmv(self, x, f32=False):
+        y = dev(np.zeros(x.size))
+        st = (bb.bt_spmv_f32 if f32 else bb.bt_spmv)(self.h, dev(x.reshape(-1)), y)
+        assert st == bb.BT_OK, bb.status_string(st)
+        return host(y).reshape(x.shape)
+
+    def solve(self, b, tol, maxit, x0=None):
+        x = dev(np.zeros(b.size) if x0 is None else x0.reshape(-1))
+        st, it = bb.bt_pcg_solve(self.h, dev(b.reshape(-1)), x, tol, maxit)
+        return st, it, host(x).reshape(b.shape)
+
+    def info(self):
+        return bb.bt_solve_info(self.h, 0)
+
+    def close(self):
+        if self.h:
+            bb.bt_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def maxrel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
