@@ -1,0 +1,447 @@
+#!/usr/bin/env python
+"""Benchmark of the block-tridiagonal PCG library on one GB300 (or N, weak).
+
+Workload (one step): 1024 LQR Schur-complement instances, horizon
+N ~ U{32..512}, block size n in {12, 24, 36}, input size n/3 -- setup of every
+instance's preconditioner blocks (Cholesky in float64, float32 blocks) and a
+mixed-precision PCG solve of all of them to relative residual 1e-8, in one
+persistent launch, with the optimal-parameter preconditioner at m = 2,
+alpha = (1, 7).  Inputs are larger than L2 (several GB), so no flush is
+needed between steps.
+
+Prints one JSON line (rank 0).  See --help for the options.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "solves/s at rel. residual 1e-8: mixed+batched vs plain FP64 PCG; HBM % of peak"
+UNIT = "solves/s"
+TOL = 1e-8
+ALPHA = (1.0, 7.0)
+M = 2
+KERNEL_SRC = os.path.join(ROOT, "paper_2503_15269_gb300", "csrc", "bt_pcg.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pcg_batched_ocp1024_traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--batch", type=int, default=1024, help="instances per step (1024 = the published workload)")
+    ap.add_argument("--profile", action="store_true", help="timed loop only (for ncu): no baselines, e2e or clocks")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 one-at-a-time comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--cpu-sample", type=int, default=48, help="instances in the oracle CPU sample")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+def _oracle_job(args):
+    idx, tol = args
+    from oracle import bt_oracle as orc
+    from paper_2503_15269_gb300 import workloads as wl
+    inst = wl.config2(indices=[idx])[0]
+    t0 = time.perf_counter()
+    res = orc.pcg_opt(inst.D, inst.O, inst.b, list(ALPHA), tol, 5000)
+    dt = time.perf_counter() - t0
+    return idx, dt, res.iters, res.status
+
+
+def sample_indices(batch: int, count: int):
+    step = max(1, batch // count)
+    return list(range(0, batch, step))[:count]
+
+
+def run_oracle(indices, procs):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        pool.map(_oracle_job, [(indices[0], TOL)])  # warm the workers (imports)
+        t0 = time.perf_counter()
+        out = pool.map(_oracle_job, [(i, TOL) for i in indices], chunksize=1)
+        wall = time.perf_counter() - t0
+    return wall, out
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def reference_arm(a):
+    """The oracle (numpy float64, as it stands) timed on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    procs = min(cpu_cores(), 16)
+    idx = sample_indices(a.batch, min(a.cpu_sample, 32))
+    for _ in range(a.warmup):
+        run_oracle(idx[:procs], procs)
+    walls = []
+    n_done = 0
+    for _ in range(a.steps):
+        wall, out = run_oracle(idx, procs)
+        walls.append(wall)
+        n_done += len(out)
+    value = n_done / sum(walls)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sum(walls) / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded LQR Schur complements)",
+        "config": {"workload": f"ocp batch of {a.batch}: N~U{{32..512}}, n in {{12,24,36}}, m=n/3; "
+                               f"each step solves a sample of {len(idx)}",
+                   "preconditioner": "a=1, m=2, alpha=(1,7)", "tol": TOL},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
+                         "sample": f"{len(idx)} of {a.batch} instances per step (every {a.batch // len(idx)}th)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# Algorithmic bytes of the persistent solve kernel
+# ---------------------------------------------------------------------------
+def alg_bytes(Ns, ns, iters, outers, m=M):
+    """Bytes the method must move (blocks at their size, no padding), per
+    instance:  each float32 inner iteration streams S (D, O), G (D^-1, E) and
+    H (Hd, Hu, Hl) once plus 14 vector passes; each inner restart applies
+    M^-1 once more (G, H) and each refinement step streams the float64 D, O
+    plus 3 float64 vector passes."""
+    tot = 0
+    for N, n, it, o in zip(Ns, ns, iters, outers):
+        n2 = n * n
+        s_blocks = (2 * N - 1) * n2
+        g_blocks = (2 * N - 1) * n2
+        h_blocks = max(3 * N - 4, 0) * n2 * (m - 1)
+        it_b = 4 * (s_blocks + g_blocks + h_blocks) + 14 * 4 * N * n
+        prec_b = 4 * (g_blocks + h_blocks) + 4 * 4 * N * n
+        a64_b = 8 * s_blocks + 3 * 8 * N * n
+        tot += it * it_b + o * (prec_b + a64_b)
+    return tot
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in (KERNEL_SRC, os.path.join(ROOT, "paper_2503_15269_gb300", "csrc", "bt_common.cuh")):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(batch):
+    try:
+        t = json.load(open(TRAFFIC_FILE))
+    except Exception:
+        return None
+    if t.get("kernel_hash") != kernel_hash():
+        return None
+    per = t.get("dram_bytes_per_instance")
+    return None if per is None else per * batch
+
+
+def measured_peak():
+    try:
+        p = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# Clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        self.gpu = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+        try:
+            self.f.close()
+        except Exception:
+            pass
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for j, nme in enumerate(names):
+                if len(r) > 5 + j and "Active" in r[5 + j] and "Not" not in r[5 + j]:
+                    reasons.add(nme)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+def main():
+    a = parse()
+    if a.impl == "reference":
+        reference_arm(a)
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import numpy as np
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2503_15269_gb300 import binding as bb
+    from paper_2503_15269_gb300 import build
+    from paper_2503_15269_gb300 import workloads as wl
+    build.build()
+    bb.lib()
+
+    insts = wl.config2(count=max(a.batch, 1)) if a.batch == 1024 else wl.config2(indices=list(range(a.batch)))
+    Ns, ns, d_off, o_off, v_off, D, O, b = wl.pack_batch(insts)
+    B = len(insts)
+    del insts
+    stream = torch.cuda.Stream(device=dev)
+    hD = torch.from_numpy(D).pin_memory()
+    hO = torch.from_numpy(O).pin_memory()
+    hb = torch.from_numpy(b).pin_memory()
+    hx = torch.empty_like(hb).pin_memory()
+    hst = torch.empty(2 * B, dtype=torch.int32).pin_memory()
+    dD = hD.to(dev)
+    dO = hO.to(dev)
+    db = hb.to(dev)
+    dx = torch.zeros_like(db)
+    d_it = torch.zeros(2 * B, dtype=torch.int32, device=dev)
+
+    p, keep = bb.make_params(m=M, alpha=ALPHA, precision=bb.BT_MIXED, stream=stream)
+    st, h = bb.bt_setup_batched(Ns, ns, d_off, o_off, dD, dO, p)
+    assert st == bb.BT_OK, bb.status_string(st)
+
+    def step():
+        s1 = bb.bt_refactor(h, dD, dO)
+        s2 = bb.bt_pcg_solve_batched_async(h, db, dx, TOL, 5000, d_it[:B], d_it[B:])
+        assert s1 == bb.BT_OK and s2 == bb.BT_OK
+
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for _ in range(a.warmup):
+            step()
+    torch.cuda.synchronize()
+    # per-instance iteration counts (bitwise-deterministic, same in every step)
+    st, iters, sts = bb.bt_pcg_solve_batched(h, db, dx, B, TOL, 5000)
+    outers = [bb.bt_solve_info(h, k)[1] for k in range(B)]
+    resid = [bb.bt_solve_info(h, k)[2] for k in range(B)]
+    assert st == bb.BT_OK and (sts == 0).all(), (st, np.unique(sts))
+    assert max(resid) <= TOL, max(resid)
+
+    # ---- device-timed steps ----
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(local) if not a.profile else None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.__enter__()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for k in range(a.steps):
+            ev[k][0].record(stream)
+            assert bb.bt_refactor(h, dD, dO) == bb.BT_OK
+            ev[k][1].record(stream)
+            assert bb.bt_pcg_solve_batched_async(h, db, dx, TOL, 5000, d_it[:B], d_it[B:]) == bb.BT_OK
+            ev[k][2].record(stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.__exit__()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    ms_setup = sum(x[0].elapsed_time(x[1]) for x in ev) / a.steps
+    ms_solve = sum(x[1].elapsed_time(x[2]) for x in ev) / a.steps
+    t = torch.tensor([ms], device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    value = world * B * a.steps / (ms / 1e3)
+
+    if a.profile:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms / a.steps,
+                              "ms_solve": ms_solve, "ms_setup": ms_setup}), flush=True)
+        return
+
+    # ---- end to end through host buffers ----
+    for _ in range(1):
+        pass
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        # one warm end-to-end step
+        dD.copy_(hD, non_blocking=True); dO.copy_(hO, non_blocking=True); db.copy_(hb, non_blocking=True)
+        step()
+        hx.copy_(dx, non_blocking=True); hst.copy_(d_it, non_blocking=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        f0.record(stream)
+        for _ in range(a.steps):
+            dD.copy_(hD, non_blocking=True); dO.copy_(hO, non_blocking=True); db.copy_(hb, non_blocking=True)
+            step()
+            hx.copy_(dx, non_blocking=True); hst.copy_(d_it, non_blocking=True)
+        f1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = f0.elapsed_time(f1)
+    te = torch.tensor([ms_e2e], device=dev)
+    if dist:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * B * a.steps / (float(te.item()) / 1e3)
+    assert (hst[B:].numpy() == 0).all()
+    h2d = hD.numel() * 8 + hO.numel() * 8 + hb.numel() * 8
+    d2h = hx.numel() * 8 + hst.numel() * 4
+
+    # ---- roofline of the persistent solve kernel ----
+    abytes = alg_bytes(Ns, ns, iters, outers)
+    achieved = abytes / (ms_solve / 1e3) / 1e9
+    peak, peak_kind = measured_peak()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": stored_traffic(B), "peak_source": peak_kind,
+            "kernel": "bt_persistent_kernel<float> (batched mixed solve)",
+            "alg_bytes_per_launch": abytes, "ms_per_launch": ms_solve}
+
+    # ---- plain FP64 single-instance PCG, one instance at a time ----
+    fp64 = None
+    if rank == 0 and world == 1 and not a.no_fp64:
+        fp64 = fp64_one_at_a_time(bb, torch, dev, stream, Ns, ns, d_off, o_off, v_off, dD, dO, db)
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        procs = min(cpu_cores(), 16)
+        idx = sample_indices(B, min(a.cpu_sample, B))
+        wall, out = run_oracle(idx, procs)
+        cpu = {"value": len(out) / wall, "unit": UNIT, "cores": procs, "kind": "oracle",
+               "sample": f"{len(idx)} of the {B} instances (every {max(1, B // len(idx))}th), "
+                         f"numpy float64 oracle PCG incl. its setup, {procs} spawn processes",
+               "wall_s": wall, "oracle_iters_mean": float(np.mean([o[2] for o in out]))}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (seeded LQR Schur complements)",
+            "config": {"workload": f"ocp batch of {B}: N~U{{32..512}}, n in {{12,24,36}}, m=n/3, "
+                                   "mixed precision, one persistent launch",
+                       "preconditioner": "a=1, m=2, alpha=(1,7)", "tol": TOL,
+                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": 5 * a.steps,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clocks.summary() if clocks else None,
+            "detail": {"ms_setup": ms_setup, "ms_solve": ms_solve, "iters_mean": float(np.mean(iters)),
+                       "iters_max": int(np.max(iters)), "outer_mean": float(np.mean(outers)),
+                       "max_true_rel_residual": float(max(resid)), "fp64_one_at_a_time": fp64,
+                       "device_bytes": bb.bt_device_bytes(h)},
+        }
+        print(json.dumps(line), flush=True)
+    bb.bt_destroy(h)
+    if dist:
+        dist.destroy_process_group()
+
+
+def fp64_one_at_a_time(bb, torch, dev, stream, Ns, ns, d_off, o_off, v_off, dD, dO, db):
+    """The same instances solved by the plain float64 PCG, one persistent
+    launch per instance (setup refactor + solve), back to back on one stream."""
+    B = len(Ns)
+    hs = []
+    p, keep = bb.make_params(m=M, alpha=ALPHA, precision=bb.BT_FP64, stream=stream)
+    views = []
+    for k in range(B):
+        N, n = int(Ns[k]), int(ns[k])
+        Dk = dD[d_off[k]:d_off[k] + N * n * n]
+        Ok = dO[o_off[k]:o_off[k] + max(N - 1, 1) * n * n] if N > 1 else dO[:n * n]
+        bk = db[v_off[k]:v_off[k] + N * n]
+        xk = torch.zeros_like(bk)
+        st, h = bb.bt_setup(N, n, Dk, Ok, p)
+        assert st == bb.BT_OK
+        hs.append(h)
+        views.append((Dk, Ok, bk, xk))
+    dits = torch.zeros(2 * B, dtype=torch.int32, device=dev)
+
+    def run():
+        for k in range(B):
+            Dk, Ok, bk, xk = views[k]
+            assert bb.bt_refactor(hs[k], Dk, Ok) == bb.BT_OK
+            assert bb.bt_pcg_solve_async(hs[k], bk, xk, TOL, 5000, dits[k:k + 1], dits[B + k:B + k + 1]) == bb.BT_OK
+
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        run()
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        g0.record(stream)
+        run()
+        g1.record(stream)
+    torch.cuda.synchronize()
+    ms = g0.elapsed_time(g1)
+    its = dits[:B].cpu().numpy()
+    sts = dits[B:].cpu().numpy()
+    for h in hs:
+        bb.bt_destroy(h)
+    return {"value": B / (ms / 1e3), "unit": UNIT, "ms": ms, "iters_mean": float(its.mean()),
+            "all_ok": bool((sts == 0).all())}
+
+
+if __name__ == "__main__":
+    main()

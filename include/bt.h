@@ -101,6 +101,17 @@ void bt_params_init(bt_params* p);
 bt_status bt_setup(int N, int n, const double* D, const double* O,
                    const bt_params* params, bt_handle* out);
 
+/* Recompute every per-block factor of an existing handle (single or batched)
+ * from new values of D and O with the same sizes and packing as at setup: the
+ * same kernels as bt_setup*, no allocation, queued on the handle's stream
+ * without synchronisation (so it can sit inside a timed or captured region).
+ * A non-SPD block is reported by the next bt_setup_status call. */
+bt_status bt_refactor(bt_handle h, const double* D, const double* O);
+
+/* Synchronise the handle's stream; BT_ERR_NOT_SPD if the last setup or
+ * refactor met a diagonal block that is not positive definite, else BT_OK. */
+bt_status bt_setup_status(bt_handle h);
+
 /* z = M^-1 r, one application of the preconditioner (Sec. 4.2), in the
  * handle's working precision (float32 blocks for BT_MIXED).  r, z: [N*n]. */
 bt_status bt_apply_precond(bt_handle h, const double* r, double* z);
@@ -120,6 +131,11 @@ bt_status bt_spmv_f32(bt_handle h, const double* x, double* y);
  * x = 0, iters = 0.  Synchronises the stream. */
 bt_status bt_pcg_solve(bt_handle h, const double* b, double* x, double tol, int maxit,
                        int* iters);
+
+/* bt_pcg_solve without host synchronisation: the iteration count and status
+ * go to the DEVICE ints d_iters[0], d_status[0] (either may be NULL). */
+bt_status bt_pcg_solve_async(bt_handle h, const double* b, double* x, double tol, int maxit,
+                             int* d_iters, int* d_status);
 
 /* Details of the last bt_pcg_solve / batched solve of instance k (0 for a
  * single instance): refinement steps taken and the final relative residual

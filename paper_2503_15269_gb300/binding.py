@@ -62,6 +62,9 @@ def lib() -> C.CDLL:
     sig = {
         "bt_params_init": (None, [C.POINTER(bt_params)]),
         "bt_setup": (C.c_int, [C.c_int, C.c_int, dp, dp, C.POINTER(bt_params), C.POINTER(H)]),
+        "bt_refactor": (C.c_int, [H, dp, dp]),
+        "bt_setup_status": (C.c_int, [H]),
+        "bt_pcg_solve_async": (C.c_int, [H, dp, dp, C.c_double, C.c_int, vp, vp]),
         "bt_apply_precond": (C.c_int, [H, dp, dp]),
         "bt_spmv": (C.c_int, [H, dp, dp]),
         "bt_spmv_f32": (C.c_int, [H, dp, dp]),
@@ -169,6 +172,18 @@ def bt_setup_batched(Ns, ns, d_off, o_off, D, O, params: bt_params):
     st = lib().bt_setup_batched(B, Na, na, da, oa, _ptr(D), _ptr(O) if O is not None and O.numel() else C.c_void_p(0),
                                 C.byref(params), C.byref(h))
     return st, h
+
+
+def bt_refactor(h, D, O) -> int:
+    return lib().bt_refactor(h, _ptr(D), _ptr(O) if O is not None and O.numel() else C.c_void_p(0))
+
+
+def bt_setup_status(h) -> int:
+    return lib().bt_setup_status(h)
+
+
+def bt_pcg_solve_async(h, b, x, tol: float, maxit: int, d_iters=None, d_status=None) -> int:
+    return lib().bt_pcg_solve_async(h, _ptr(b), _ptr(x), float(tol), int(maxit), _ptr(d_iters), _ptr(d_status))
 
 
 def bt_apply_precond(h, r, z) -> int:

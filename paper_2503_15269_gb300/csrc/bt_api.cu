@@ -118,6 +118,44 @@ bt_status check_params(const bt_params* p, double* alpha_out) {
 
 inline long long rup(long long v, long long a) { return (v + a - 1) / a * a; }
 
+// Queue the setup kernels (K0..K3) for D, O on the handle's stream.
+bt_status launch_setup_kernels(bt_ctx* h, const double* D, const double* O) {
+  cudaStream_t st = h->stream;
+  if (cudaMemsetAsync(h->d_fail_key, 0xff, sizeof(unsigned long long), st)) return BT_ERR_CUDA;
+  bt::SetupParams sp{};
+  sp.inst = h->d_inst;
+  sp.rows = h->d_rows;
+  sp.nrows = h->total_rows;
+  sp.D = D;
+  sp.O = O;
+  sp.d_off = h->d_doff;
+  sp.o_off = h->d_ooff;
+  sp.D64 = h->D64; sp.O64 = h->O64; sp.Dinv64 = h->Dinv64; sp.E64 = h->E64;
+  sp.Hd64 = h->Hd64; sp.Hu64 = h->Hu64; sp.Hl64 = h->Hl64;
+  sp.D32 = h->D32; sp.O32 = h->O32; sp.Dinv32 = h->Dinv32; sp.E32 = h->E32;
+  sp.Hd32 = h->Hd32; sp.Hu32 = h->Hu32; sp.Hl32 = h->Hl32;
+  sp.want32 = h->mixed ? 1 : 0;
+  sp.want64 = 1;
+  sp.fail_key = h->d_fail_key;
+  sp.fail_piv = h->d_fail_piv;
+  return cuda_st(bt_launch_setup(&sp, h->mixed ? 1 : 0, h->prm.m, h->maxn, st));
+}
+
+// Read the setup failure key (synchronises); fills the error detail.
+bt_status read_setup_status(bt_ctx* h) {
+  unsigned long long key = 0;
+  if (cudaMemcpyAsync(&key, h->d_fail_key, sizeof(key), cudaMemcpyDeviceToHost, h->stream)) return BT_ERR_CUDA;
+  if (cudaStreamSynchronize(h->stream)) return BT_ERR_CUDA;
+  if (key == ~0ull) return BT_OK;
+  h->err_inst = (int)(key >> 32);
+  h->err_blk = (int)(key & 0xffffffffu);
+  long long grow = 0;
+  for (int k = 0; k < h->err_inst; ++k) grow += h->N[k];
+  grow += h->err_blk;
+  cudaMemcpy(&h->err_val, h->d_fail_piv + grow, sizeof(double), cudaMemcpyDeviceToHost);
+  return BT_ERR_NOT_SPD;
+}
+
 // Common setup for one or many instances.
 bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
   cudaStream_t st = h->stream;
@@ -209,24 +247,7 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
       (e = cudaMemcpyAsync(h->d_doff, h->d_off.data(), B * sizeof(long long), cudaMemcpyHostToDevice, st)) ||
       (e = cudaMemcpyAsync(h->d_ooff, h->o_off.data(), B * sizeof(long long), cudaMemcpyHostToDevice, st)))
     return BT_ERR_CUDA;
-  if ((e = cudaMemsetAsync(h->d_fail_key, 0xff, sizeof(unsigned long long), st))) return BT_ERR_CUDA;
-  bt::SetupParams sp{};
-  sp.inst = h->d_inst;
-  sp.rows = h->d_rows;
-  sp.nrows = rows;
-  sp.D = D;
-  sp.O = O;
-  sp.d_off = h->d_doff;
-  sp.o_off = h->d_ooff;
-  sp.D64 = h->D64; sp.O64 = h->O64; sp.Dinv64 = h->Dinv64; sp.E64 = h->E64;
-  sp.Hd64 = h->Hd64; sp.Hu64 = h->Hu64; sp.Hl64 = h->Hl64;
-  sp.D32 = h->D32; sp.O32 = h->O32; sp.Dinv32 = h->Dinv32; sp.E32 = h->E32;
-  sp.Hd32 = h->Hd32; sp.Hu32 = h->Hu32; sp.Hl32 = h->Hl32;
-  sp.want32 = mixed ? 1 : 0;
-  sp.want64 = 1;
-  sp.fail_key = h->d_fail_key;
-  sp.fail_piv = h->d_fail_piv;
-  if ((e = bt_launch_setup(&sp, mixed ? 1 : 0, h->prm.m, h->maxn, st))) return BT_ERR_CUDA;
+  if (launch_setup_kernels(h, D, O) != BT_OK) return BT_ERR_CUDA;
 
   // ---- launch configuration of the persistent kernel ----
   const int wbytes = mixed ? 4 : 8;
@@ -273,21 +294,9 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
   cudaMemsetAsync(h->d_ws, 0, (size_t)h->ws_stride * h->ws_slots, st);
 
   // ---- setup status ----
-  unsigned long long key = 0;
-  if ((e = cudaMemcpyAsync(&key, h->d_fail_key, sizeof(key), cudaMemcpyDeviceToHost, st))) return BT_ERR_CUDA;
-  if ((e = cudaStreamSynchronize(st))) return BT_ERR_CUDA;
-  if (key != ~0ull) {
-    h->err_inst = (int)(key >> 32);
-    h->err_blk = (int)(key & 0xffffffffu);
-    long long grow = 0;
-    for (int k = 0; k < h->err_inst; ++k) grow += h->N[k];
-    grow += h->err_blk;
-    cudaMemcpy(&h->err_val, h->d_fail_piv + grow, sizeof(double), cudaMemcpyDeviceToHost);
-    return BT_ERR_NOT_SPD;
-  }
   h->h_outer.assign(B, 0);
   h->h_resid.assign(B, 0.0);
-  return BT_OK;
+  return read_setup_status(h);
 }
 
 bt_ctx* new_ctx(const bt_params* p) {
@@ -466,6 +475,16 @@ bt_status bt_setup_batched(int B, const int* N, const int* n, const long long* d
   return s;
 }
 
+bt_status bt_refactor(bt_handle h, const double* D, const double* O) {
+  if (!h || !D || (h->maxN > 1 && !O)) return BT_ERR_ARG;
+  return launch_setup_kernels(h, D, O);
+}
+
+bt_status bt_setup_status(bt_handle h) {
+  if (!h) return BT_ERR_ARG;
+  return read_setup_status(h);
+}
+
 bt_status bt_apply_precond(bt_handle h, const double* r, double* z) {
   if (!h || !r || !z) return BT_ERR_ARG;
   bt_status s = run_op(h, bt::kOpApply, r, z);
@@ -508,6 +527,19 @@ bt_status bt_pcg_solve(bt_handle h, const double* b, double* x, double tol, int 
   s = collect(h, &it, nullptr, true);
   if (iters) *iters = it;
   return s;
+}
+
+bt_status bt_pcg_solve_async(bt_handle h, const double* b, double* x, double tol, int maxit, int* d_iters,
+                             int* d_status) {
+  if (!h || !b || !x) return BT_ERR_ARG;
+  if (h->batched) return BT_ERR_STATE;
+  bt_status s = solve_launch(h, b, x, tol, maxit);
+  if (s != BT_OK) return s;
+  if (d_iters && cudaMemcpyAsync(d_iters, h->d_iters, sizeof(int), cudaMemcpyDeviceToDevice, h->stream))
+    return BT_ERR_CUDA;
+  if (d_status && cudaMemcpyAsync(d_status, h->d_status, sizeof(int), cudaMemcpyDeviceToDevice, h->stream))
+    return BT_ERR_CUDA;
+  return BT_OK;
 }
 
 bt_status bt_pcg_solve_batched(bt_handle h, const double* b, double* x, const long long* vec_off, double tol,
