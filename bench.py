@@ -35,6 +35,18 @@ KERNEL_SRC = os.path.join(ROOT, "paper_2503_15269_gb300", "csrc", "bt_pcg.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pcg_batched_ocp1024_traffic.json")
 
 
+def _jsonable(o):
+    if hasattr(o, "item"):
+        return o.item()
+    if hasattr(o, "tolist"):
+        return o.tolist()
+    return str(o)
+
+
+def emit(line):
+    print(json.dumps(line, default=_jsonable), flush=True)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -114,7 +126,7 @@ def reference_arm(a):
                          "sample": f"{len(idx)} of {a.batch} instances per step (every {a.batch // len(idx)}th)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line), flush=True)
+    emit(line)
 
 
 # ---------------------------------------------------------------------------
@@ -318,8 +330,8 @@ def main():
 
     if a.profile:
         if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms / a.steps,
-                              "ms_solve": ms_solve, "ms_setup": ms_setup}), flush=True)
+            emit({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms / a.steps,
+                  "ms_solve": ms_solve, "ms_setup": ms_setup})
         return
 
     # ---- end to end through host buffers ----
@@ -351,7 +363,7 @@ def main():
     d2h = hx.numel() * 8 + hst.numel() * 4
 
     # ---- roofline of the persistent solve kernel ----
-    abytes = alg_bytes(Ns, ns, iters, outers)
+    abytes = int(alg_bytes([int(v) for v in Ns], [int(v) for v in ns], [int(v) for v in iters], outers))
     achieved = abytes / (ms_solve / 1e3) / 1e9
     peak, peak_kind = measured_peak()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -393,7 +405,7 @@ def main():
                        "max_true_rel_residual": float(max(resid)), "fp64_one_at_a_time": fp64,
                        "device_bytes": bb.bt_device_bytes(h)},
         }
-        print(json.dumps(line), flush=True)
+        emit(line)
     bb.bt_destroy(h)
     if dist:
         dist.destroy_process_group()
