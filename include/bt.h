@@ -181,6 +181,36 @@ bt_status bt_graph_launch(bt_handle h);
 bt_status bt_adjoint_blocks(bt_handle h, const double* x, const double* g, double* gD,
                             double* gO);
 
+/* bt_pcg_solve_noalloc -- a solve for callers that cannot allocate device
+ * memory (the paper has no counterpart; this is a property of the library).
+ * Some callers may not call cudaMalloc: a real-time control loop whose
+ * memory is fixed at start-up (cudaMalloc can synchronise the device and has
+ * no latency bound), or a plug-in inside a host application that owns the
+ * GPU's memory budget.  This entry point runs the same setup kernels and
+ * persistent PCG kernel as bt_setup + bt_pcg_solve on one instance, but every
+ * buffer they need besides the caller's D, O, b and x (block copies, D_i^-1,
+ * E_i, H blocks, work vectors, control words) lives in one static device
+ * array of BT_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds
+ * until the process exits.  Nothing is allocated and no handle is created.
+ *   - Arguments as for bt_setup and bt_pcg_solve (D, O, b, x device float64,
+ *     row-major blocks; params as for bt_setup, including params->stream);
+ *     *iters (host, may be NULL) receives the iteration count.
+ *   - Sizes whose buffers do not fit in the array are rejected with
+ *     BT_ERR_ARG before anything runs: for BT_FP64 with m = 2 the limit is
+ *     about 56 N n^2 + 88 N n bytes <= 16 MiB (N = 128, n = 32 fits).
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before any
+ *     stream capture.
+ *   - Every call shares the array, which keeps the last call's contents; each
+ *     call clears what must start at zero.  Calls that overlap on the GPU race
+ *     on the array: issue them one after another.
+ *   - Synchronises params->stream; returns the solve status (as bt_pcg_solve)
+ *     or BT_ERR_NOT_SPD from the setup. */
+#define BT_NOALLOC_SCRATCH_BYTES (16u << 20)
+bt_status bt_pcg_solve_noalloc(int N, int n, const double* D, const double* O, const double* b,
+                               double* x, double tol, int maxit, const bt_params* params,
+                               int* iters);
+
 /* Detail of the last failure on h: instance, block row and a value (the
  * failing Cholesky pivot, or the offending p.q).  Any pointer may be NULL. */
 bt_status bt_last_error(bt_handle h, int* instance, int* block, double* value);

@@ -76,6 +76,8 @@ def lib() -> C.CDLL:
         "bt_graph_capture_batched": (C.c_int, [H, dp, dp, C.c_double, C.c_int, vp, vp]),
         "bt_graph_launch": (C.c_int, [H]),
         "bt_adjoint_blocks": (C.c_int, [H, dp, dp, dp, dp]),
+        "bt_pcg_solve_noalloc": (C.c_int, [C.c_int, C.c_int, dp, dp, dp, dp, C.c_double, C.c_int,
+                                           C.POINTER(bt_params), ip]),
         "bt_last_error": (C.c_int, [H, ip, ip, C.POINTER(C.c_double)]),
         "bt_device_bytes": (C.c_longlong, [H]),
         "bt_destroy": (None, [H]),
@@ -235,6 +237,13 @@ def bt_graph_launch(h) -> int:
 
 def bt_adjoint_blocks(h, x, g, gD, gO) -> int:
     return lib().bt_adjoint_blocks(h, _ptr(x), _ptr(g), _ptr(gD), _ptr(gO))
+
+
+def bt_pcg_solve_noalloc(N: int, n: int, D, O, b, x, tol: float, maxit: int, params: bt_params):
+    it = C.c_int(0)
+    st = lib().bt_pcg_solve_noalloc(N, n, _ptr(D), _ptr(O) if O is not None and O.numel() else C.c_void_p(0),
+                                    _ptr(b), _ptr(x), float(tol), int(maxit), C.byref(params), C.byref(it))
+    return st, it.value
 
 
 def bt_last_error(h):
