@@ -61,7 +61,8 @@ typedef enum {
 } bt_precision;
 
 #define BT_MAX_M 8      /* largest polynomial order m accepted                 */
-#define BT_MAX_BLOCK 64 /* largest block size n accepted                       */
+#define BT_MAX_BLOCK 64 /* largest block size n accepted (BT_FP64 handles: n <= 48, the
+                           shared-memory pipeline needs two stages of five blocks) */
 
 typedef struct bt_params {
   double a;            /* multi-splitting weight, b = 1 - 2a.  Admissible set C_g
@@ -142,6 +143,22 @@ bt_status bt_pcg_solve_async(bt_handle h, const double* b, double* x, double tol
  * ||b - S x|| / ||b|| that the device measured (float64 true residual for
  * BT_MIXED; the recursive residual for BT_FP64).  Host outputs. */
 bt_status bt_solve_info(bt_handle h, int k, int* outer, double* rel_residual);
+
+/* Many right-hand sides (a BT_MIXED single-instance handle): solve
+ * S X = B for nrhs <= 64 columns at once.  The columns run independent PCG
+ * recurrences (own alpha, beta, stopping test) that share every block sweep,
+ * so each block product becomes an n x n by n x 64 contraction; float32
+ * inner solves inside float64 refinement on each column's true residual, as
+ * in bt_pcg_solve.  B, X: DEVICE [N*n][nrhs] float64, row-major.  iters and
+ * status (HOST arrays of nrhs, may be NULL) receive per-column results; the
+ * call returns the first non-OK status.  Requires n % 4 == 0.  The first call
+ * allocates the many-RHS workspace on the handle.  Synchronises the stream. */
+bt_status bt_pcg_solve_multi(bt_handle h, const double* B, double* X, int nrhs, double tol,
+                             int maxit, int* iters, int* status);
+
+/* Refinement steps and final relative true residual of column j of the last
+ * bt_pcg_solve_multi. */
+bt_status bt_multi_info(bt_handle h, int j, int* outer, double* rel_residual);
 
 /* Batched setup: B independent instances of sizes N[k] x n[k], packed back
  * to back: instance k's D starts at D + d_off[k], its O at O + o_off[k]

@@ -78,6 +78,8 @@ def lib() -> C.CDLL:
         "bt_adjoint_blocks": (C.c_int, [H, dp, dp, dp, dp]),
         "bt_pcg_solve_noalloc": (C.c_int, [C.c_int, C.c_int, dp, dp, dp, dp, C.c_double, C.c_int,
                                            C.POINTER(bt_params), ip]),
+        "bt_pcg_solve_multi": (C.c_int, [H, dp, dp, C.c_int, C.c_double, C.c_int, ip, ip]),
+        "bt_multi_info": (C.c_int, [H, C.c_int, ip, C.POINTER(C.c_double)]),
         "bt_last_error": (C.c_int, [H, ip, ip, C.POINTER(C.c_double)]),
         "bt_device_bytes": (C.c_longlong, [H]),
         "bt_destroy": (None, [H]),
@@ -244,6 +246,20 @@ def bt_pcg_solve_noalloc(N: int, n: int, D, O, b, x, tol: float, maxit: int, par
     st = lib().bt_pcg_solve_noalloc(N, n, _ptr(D), _ptr(O) if O is not None and O.numel() else C.c_void_p(0),
                                     _ptr(b), _ptr(x), float(tol), int(maxit), C.byref(params), C.byref(it))
     return st, it.value
+
+
+def bt_pcg_solve_multi(h, B, X, nrhs: int, tol: float, maxit: int):
+    it = (C.c_int * nrhs)()
+    ss = (C.c_int * nrhs)()
+    st = lib().bt_pcg_solve_multi(h, _ptr(B), _ptr(X), int(nrhs), float(tol), int(maxit), it, ss)
+    return st, np.array(it[:], dtype=np.int64), np.array(ss[:], dtype=np.int64)
+
+
+def bt_multi_info(h, j: int):
+    o = C.c_int(0)
+    r = C.c_double(0.0)
+    st = lib().bt_multi_info(h, int(j), C.byref(o), C.byref(r))
+    return st, o.value, r.value
 
 
 def bt_last_error(h):

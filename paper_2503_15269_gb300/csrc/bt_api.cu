@@ -17,6 +17,14 @@ extern "C" int bt_persistent_smem_fixed();
 extern "C" cudaError_t bt_persistent_occupancy(int mt_is_float, int smem_bytes, int* blocks_per_sm);
 extern "C" cudaError_t bt_launch_setup(const bt::SetupParams* P, int mixed, int m, int maxn, cudaStream_t st);
 extern "C" cudaError_t bt_launch_adjoint(const bt::AdjParams* P, cudaStream_t st);
+namespace bt { struct MParams; }
+extern "C" int bt_mrhs_smem_bytes(int n);
+extern "C" cudaError_t bt_mrhs_occupancy(int smem, int* blocks);
+extern "C" cudaError_t bt_mrhs_solve_launch(int N, int n, int m, const double* alpha, const float* const* blk32,
+                                            const double* D64, const double* O64, int bs32, int bs64,
+                                            void* const* vec, double tol, double tol_inner, int maxit,
+                                            int max_outer, long long budget, int G, int nrhs, const double* B,
+                                            double* X, int smem, cudaStream_t st);
 
 namespace {
 
@@ -61,7 +69,7 @@ struct bt_ctx {
   long long ws_stride = 0, ws_vec = 0;
   int ws_slots = 0;
   // launch configuration
-  int stages = 0, stage_bytes = 0, smem = 0, grid = 0, G = 1;
+  int stages = 0, stage_bytes = 0, smem = 0, grid = 0, G = 1, vec_slot_bytes = 0;
   // results of the last solve
   std::vector<int> h_outer;
   std::vector<double> h_resid;
@@ -70,6 +78,10 @@ struct bt_ctx {
   double err_val = 0.0;
   cudaGraphExec_t graph = nullptr;
   cudaGraph_t graph_src = nullptr;
+  // many-right-hand-side workspace (allocated on the first bt_pcg_solve_multi)
+  void* mr_vec[16] = {};
+  int mr_G = 0, mr_smem = 0, mr_outer = 0;
+  std::vector<double> mr_resid;
 };
 
 namespace {
@@ -254,19 +266,25 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
   const long long bsb_max = rup((long long)h->maxn * h->maxn, mixed ? 4 : 2) * wbytes;
   const long long bsb64_max = rup((long long)h->maxn * h->maxn, 2) * 8;
   long long need = std::max(5 * bsb_max, 3 * bsb64_max);
-  long long sb = h->prm.stage_kb > 0 ? (long long)h->prm.stage_kb * 1024 : 48 * 1024;
+  long long sb = h->prm.stage_kb > 0 ? (long long)h->prm.stage_kb * 1024 : 80 * 1024;
   sb = std::max(sb, rup(need, 128));
   int smem_optin = 0;
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
   const int fixed = bt_persistent_smem_fixed();
+  int vslot = mixed ? 12 * 1024 : 24 * 1024;  // one vector-ring slot
   int cps = h->prm.ctas_per_sm > 0 ? h->prm.ctas_per_sm : 1;
   const int per_cta = (int)std::min<long long>(smem_optin, (228 * 1024) / cps - 1024);
-  int S = (int)((per_cta - fixed) / sb);
+  int S = (int)((per_cta - fixed - 3 * vslot) / sb);
+  if (S < 2) {  // large blocks: keep two block stages, stage vectors directly
+    vslot = 0;
+    S = (int)((per_cta - fixed) / sb);
+  }
+  h->vec_slot_bytes = vslot;
   if (S > bt::kMaxStages) S = bt::kMaxStages;
   if (S < 2) return BT_ERR_ARG;  // block too large for the shared-memory pipeline
   h->stages = S;
   h->stage_bytes = (int)sb;
-  h->smem = fixed + S * (int)sb;
+  h->smem = fixed + 3 * vslot + S * (int)sb;
   int occ = 0;
   if (cuda_st(bt_persistent_occupancy(mixed ? 1 : 0, h->smem, &occ)) != BT_OK || occ < 1) return BT_ERR_CUDA;
   cps = std::min(cps, occ);
@@ -338,6 +356,7 @@ bt::KParams base_kparams(bt_ctx* h) {
   P.errval = h->d_errval;
   P.stages = h->stages;
   P.stage_bytes = h->stage_bytes;
+  P.vec_slot_bytes = h->vec_slot_bytes;
   return P;
 }
 
@@ -635,6 +654,78 @@ bt_status bt_adjoint_blocks(bt_handle h, const double* x, const double* g, doubl
   a.gD = gD;
   a.gO = gO;
   return cuda_st(bt_launch_adjoint(&a, h->stream));
+}
+
+bt_status bt_pcg_solve_multi(bt_handle h, const double* B, double* X, int nrhs, double tol, int maxit, int* iters,
+                             int* status) {
+  if (!h || !B || !X) return BT_ERR_ARG;
+  if (h->batched) return BT_ERR_STATE;
+  if (!h->mixed) return BT_ERR_STATE;
+  if (nrhs < 1 || nrhs > 64 || !(tol >= 0.0) || maxit < 0) return BT_ERR_ARG;
+  const int N = h->N[0], n = h->n[0];
+  if (n % 4 != 0) return BT_ERR_ARG;
+  const int kJ = 64;
+  if (!h->mr_vec[0]) {
+    const size_t cnt = (size_t)N * n * kJ;
+    bt_status s;
+    double* d = nullptr;
+    float* f = nullptr;
+    for (int i = 0; i < 3; ++i) {  // B64, X64, R64
+      if ((s = dalloc(h, &d, cnt)) != BT_OK) return s;
+      h->mr_vec[i] = d;
+    }
+    for (int i = 3; i < 11; ++i) {  // Xin, R, P, Q, Y0, Ya, Yb, Z
+      if ((s = dalloc(h, &f, cnt)) != BT_OK) return s;
+      h->mr_vec[i] = f;
+    }
+    h->mr_smem = bt_mrhs_smem_bytes(n);
+    int occ = 0;
+    if (bt_mrhs_occupancy(h->mr_smem, &occ) != cudaSuccess || occ < 1) return BT_ERR_CUDA;
+    h->mr_G = std::max(1, std::min(h->sms * occ, N));
+    double* red = nullptr;
+    if ((s = dalloc(h, &red, (size_t)2 * h->mr_G * kJ)) != BT_OK) return s;
+    h->mr_vec[11] = red;
+    int* ctl = nullptr;
+    if ((s = dalloc(h, &ctl, 64)) != BT_OK) return s;
+    h->mr_vec[12] = ctl;
+    int* res_i = nullptr;
+    if ((s = dalloc(h, &res_i, 3 * kJ)) != BT_OK) return s;
+    h->mr_vec[13] = res_i;
+    double* res_d = nullptr;
+    if ((s = dalloc(h, &res_d, kJ)) != BT_OK) return s;
+    h->mr_vec[14] = res_d;
+  }
+  if (cudaMemsetAsync(h->mr_vec[12], 0, 64 * sizeof(int), h->stream)) return BT_ERR_CUDA;
+  const float* blk32[7] = {h->D32, h->O32, h->Dinv32, h->E32, h->Hd32, h->Hu32, h->Hl32};
+  const double tin = h->prm.tol_inner > 0 ? h->prm.tol_inner : 1e-5;
+  const int mo = h->prm.max_outer > 0 ? h->prm.max_outer : 30;
+  const long long budget = h->prm.cycle_budget > 0 ? h->prm.cycle_budget : (1ll << 36);
+  const int bs32 = (int)rup((long long)n * n, 4), bs64 = (int)rup((long long)n * n, 2);
+  cudaError_t e = bt_mrhs_solve_launch(N, n, h->prm.m, h->alpha, blk32, h->D64, h->O64, bs32, bs64, h->mr_vec, tol,
+                                       tin, maxit, mo, budget, h->mr_G, nrhs, B, X, h->mr_smem, h->stream);
+  if (e != cudaSuccess) return BT_ERR_CUDA;
+  std::vector<int> ri(3 * kJ);
+  std::vector<double> rd(kJ);
+  if (cudaMemcpyAsync(ri.data(), h->mr_vec[13], 3 * kJ * sizeof(int), cudaMemcpyDeviceToHost, h->stream) ||
+      cudaMemcpyAsync(rd.data(), h->mr_vec[14], kJ * sizeof(double), cudaMemcpyDeviceToHost, h->stream) ||
+      cudaStreamSynchronize(h->stream))
+    return BT_ERR_CUDA;
+  bt_status first = BT_OK;
+  for (int j = 0; j < nrhs; ++j) {
+    if (iters) iters[j] = ri[j];
+    if (status) status[j] = ri[kJ + j];
+    if (ri[kJ + j] != BT_OK && first == BT_OK) first = static_cast<bt_status>(ri[kJ + j]);
+  }
+  h->mr_resid.assign(rd.begin(), rd.begin() + nrhs);
+  h->mr_outer = ri[2 * kJ];
+  return first;
+}
+
+bt_status bt_multi_info(bt_handle h, int j, int* outer, double* rel_residual) {
+  if (!h || j < 0 || j >= (int)h->mr_resid.size()) return BT_ERR_ARG;
+  if (outer) *outer = h->mr_outer;
+  if (rel_residual) *rel_residual = h->mr_resid[j];
+  return BT_OK;
 }
 
 bt_status bt_last_error(bt_handle h, int* instance, int* block, double* value) {

@@ -56,6 +56,7 @@ struct KParams {
   int* abort_flag;
   int* iters; int* status; int* outer; double* resid; double* errval;
   int stages, stage_bytes;
+  int vec_slot_bytes;      // bytes of one vector-ring slot
 };
 
 struct RowRef {
@@ -107,6 +108,12 @@ __device__ __forceinline__ void fence_mbar_init() {
 
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Order this thread's earlier generic-proxy global writes before later
+// async-proxy (bulk copy) reads of the same addresses.
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* b, unsigned bytes) {

@@ -1,0 +1,674 @@
+// Many right-hand sides: J = 64 independent PCG recurrences on one SPD
+// block-tridiagonal matrix, sharing every block sweep (the block products
+// become n x n by n x J contractions).  Float32 inner PCG inside float64
+// iterative refinement, the optimal-parameter preconditioner of Sec. 3-4
+// (a = 1, polynomial coefficients alpha), textbook PCG per column.
+//
+// One cooperative launch; G CTAs split the block rows.  Rows are processed
+// in gather form, so every output row is independent (no carries between
+// CTAs):
+//   A   Q_i  = D_i P_i + O_i P_{i+1} + O_{i-1}^T P_{i-1}                 (Eq. 1)
+//   B1  Y0_i = D_i^-1 R_i - E_i R_{i+1} - E_{i-1}^T R_{i-1}              (Sec. 4.1)
+//   B2  Yj_i = Hd_i Y_i + Hu_i Y_{i+2} + Hl_{i-2} Y_{i-2},  Z += alpha_j Yj (Sec. 4.2)
+// with per-column scalars alpha_j, beta_j, rho_j and a per-column active mask;
+// grid barriers (bounded) separate the phases.  Vectors are [N][n][J]
+// (block row i, then its n rows, then the J columns), J = 64.
+//
+// Each row job stages its three blocks and three vector blocks in shared
+// memory with cp.async (double-buffered: the next row loads while the current
+// one computes); the block products are register-tiled, 4 rows x 4 columns of
+// the output per thread.
+#include <cstdint>
+
+#include "../../include/bt.h"
+#include "bt_common.cuh"
+
+namespace bt {
+
+constexpr int kJ = 64;              // right-hand-side columns per solve
+constexpr int kMThreads = 256;
+
+struct MParams {
+  const float *D32, *O32, *Dinv32, *E32, *Hd32, *Hu32, *Hl32;  // library layout (column-major, padded)
+  const double *D64, *O64;
+  int N, n, bs32, bs64, m;
+  float alpha[kMaxM];
+  // float64 vectors [N][n][J]
+  const double* B64;
+  double* X64;
+  double* R64;
+  // float32 vectors [N][n][J]
+  float *Xin, *R, *P, *Q, *Y0, *Ya, *Yb, *Z;
+  double* red;          // [2][G][kJ]
+  unsigned* bar;
+  int* abort_flag;
+  double tol, tol_inner;
+  int maxit, max_outer;
+  long long budget;
+  int G;
+  int nrhs;
+  // results per column
+  int* iters;
+  int* status;
+  double* resid;
+  int* outer;
+};
+
+__device__ __forceinline__ void cp16(void* smem, const void* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// copy `count` floats (multiple of 4, 16-byte aligned) global -> shared
+__device__ __forceinline__ void cp_block(float* dst, const float* src, int count) {
+  for (int t = threadIdx.x * 4; t < count; t += kMThreads * 4) cp16(dst + t, src + t);
+}
+__device__ __forceinline__ void cp_blockd(double* dst, const double* src, int count) {
+  for (int t = threadIdx.x * 2; t < count; t += kMThreads * 2) cp16(dst + t, src + t);
+}
+
+// acc[r][c] += sum_k M(a0+r, k) X(k, j0+c): M column-major n x n, X n x J.
+template <typename T>
+__device__ __forceinline__ void prod_direct(const T* __restrict__ M, const T* __restrict__ X, int n, int a0, int j0,
+                                            T acc[4][4]) {
+#pragma unroll 4
+  for (int k = 0; k < n; ++k) {
+    const T* mc = M + k * n + a0;
+    const T* xr = X + k * kJ + j0;
+    const T m0 = mc[0], m1 = mc[1], m2 = mc[2], m3 = mc[3];
+    const T x0 = xr[0], x1 = xr[1], x2 = xr[2], x3 = xr[3];
+    acc[0][0] = fma(m0, x0, acc[0][0]); acc[0][1] = fma(m0, x1, acc[0][1]);
+    acc[0][2] = fma(m0, x2, acc[0][2]); acc[0][3] = fma(m0, x3, acc[0][3]);
+    acc[1][0] = fma(m1, x0, acc[1][0]); acc[1][1] = fma(m1, x1, acc[1][1]);
+    acc[1][2] = fma(m1, x2, acc[1][2]); acc[1][3] = fma(m1, x3, acc[1][3]);
+    acc[2][0] = fma(m2, x0, acc[2][0]); acc[2][1] = fma(m2, x1, acc[2][1]);
+    acc[2][2] = fma(m2, x2, acc[2][2]); acc[2][3] = fma(m2, x3, acc[2][3]);
+    acc[3][0] = fma(m3, x0, acc[3][0]); acc[3][1] = fma(m3, x1, acc[3][1]);
+    acc[3][2] = fma(m3, x2, acc[3][2]); acc[3][3] = fma(m3, x3, acc[3][3]);
+  }
+}
+
+// acc[r][c] += sum_k M(k, a0+r) X(k, j0+c): the transposed block.
+template <typename T>
+__device__ __forceinline__ void prod_trans(const T* __restrict__ M, const T* __restrict__ X, int n, int a0, int j0,
+                                           T acc[4][4]) {
+#pragma unroll 2
+  for (int k = 0; k < n; ++k) {
+    const T* xr = X + k * kJ + j0;
+    const T x0 = xr[0], x1 = xr[1], x2 = xr[2], x3 = xr[3];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const T mv = M[(a0 + r) * n + k];
+      acc[r][0] = fma(mv, x0, acc[r][0]);
+      acc[r][1] = fma(mv, x1, acc[r][1]);
+      acc[r][2] = fma(mv, x2, acc[r][2]);
+      acc[r][3] = fma(mv, x3, acc[r][3]);
+    }
+  }
+}
+
+struct MSolver {
+  const MParams& P;
+  char* sm;
+  int g, G, N, n, s, e;
+  long long deadline;
+  int bar_count;
+  bool fail;
+  double* colbuf;   // smem [kJ] scratch for reduced values
+  double* colred;   // smem [kMThreads/16... ] partials
+
+  __device__ MSolver(const MParams& P_, char* sm_) : P(P_), sm(sm_) {}
+
+  // Grid barrier with a per-column reduction of v (one value per column,
+  // held by threads tid < kJ after an in-CTA reduction).  Bounded.
+  __device__ void grid_reduce(double* colv /* smem [kJ], CTA partials in, totals out */) {
+    if (fail) return;
+    __syncthreads();
+    int* flag = reinterpret_cast<int*>(sm);
+    if (threadIdx.x == 0) {
+      const int par = bar_count & 1;
+      double* slot = P.red + ((size_t)par * G + g) * kJ;
+      for (int j = 0; j < kJ; ++j) slot[j] = colv[j];
+      __threadfence();
+      atomicAdd(P.bar, 1u);
+      ++bar_count;
+      const unsigned target = (unsigned)G * (unsigned)bar_count;
+      int bad = 0;
+      while (ld_acquire_u32(P.bar) < target) {
+        if (ld_volatile_i32(P.abort_flag) || clock64() > deadline) {
+          bad = 1;
+          break;
+        }
+      }
+      if (bad) atomicExch(P.abort_flag, 1);
+      flag[0] = bad;
+    }
+    __syncthreads();
+    if (flag[0]) {
+      fail = true;
+      return;
+    }
+    if (threadIdx.x < kJ) {
+      const int par = (bar_count - 1) & 1;
+      double t = 0.0;
+      for (int gg = 0; gg < G; ++gg) t += reinterpret_cast<volatile double*>(P.red)[((size_t)par * G + gg) * kJ + threadIdx.x];
+      colv[threadIdx.x] = t;
+    }
+    __syncthreads();
+  }
+
+  __device__ void barrier() {
+    double* cv = colbuf;
+    if (threadIdx.x < kJ) cv[threadIdx.x] = 0.0;
+    grid_reduce(cv);
+  }
+};
+
+// Reduce per-thread column partials part[jg][4] (threads laid out t = ag*16 + jg)
+// into colv[kJ] over the CTA, fixed order.
+__device__ __forceinline__ void cta_col_reduce(const double (&pv)[4], double* scratch /* [kMThreads/16][kJ] */,
+                                               double* colv, int ngroups) {
+  const int t = threadIdx.x;
+  const int jg = t & 15, ag = t >> 4;
+  if (ag < ngroups)
+    for (int c = 0; c < 4; ++c) scratch[ag * kJ + 4 * jg + c] = pv[c];
+  __syncthreads();
+  if (t < kJ) {
+    double s = 0.0;
+    for (int a = 0; a < ngroups; ++a) s += scratch[a * kJ + t];
+    colv[t] = s;
+  }
+  __syncthreads();
+}
+
+}  // namespace bt
+
+using namespace bt;
+
+// Shared memory layout (bytes):
+//   [0, 256)          flags
+//   [256, +512)       colA  (double[kJ])   per-column scalars / reductions
+//   ... colB, colC, colD, rho, alpha, beta, act, nbv, nrv, tin
+//   then scratch [16][kJ] doubles (column partials)
+//   then two job buffers of kJobBytes
+constexpr int kColBytes = kJ * 8;
+constexpr int kMSmScalars = 256;
+constexpr int kMNumCols = 12;
+constexpr int kMSmScratch = kMSmScalars + kMNumCols * kColBytes;
+constexpr int kMSmJobs = kMSmScratch + 16 * kJ * 8;
+
+__host__ __device__ constexpr int mrhs_job_bytes(int n) {
+  // float32 job: 3 blocks + 3 vector blocks; float64 job: same in doubles
+  return 3 * n * n * 8 + 3 * n * kJ * 8;
+}
+
+namespace bt {
+
+enum MPhase : int { MP_A = 0, MP_B1 = 1, MP_B2 = 2, MP_A64 = 3 };
+
+// One sweep over the owned rows of float32 (T = float) or the float64
+// refinement residual (T = double).  The finalize functor receives the 4x4
+// tile (rows a0.., columns j0..) of row i.
+template <typename T, typename Fin>
+__device__ void msweep(MSolver& Sv, int phase, const T* v_in, Fin fin) {
+  const MParams& P = Sv.P;
+  const int n = Sv.n, N = Sv.N;
+  const int tid = threadIdx.x;
+  const int ngroups = n / 4;
+  const int jg = tid & 15, ag = tid >> 4;
+  const bool active = ag < ngroups;
+  const int a0 = 4 * ag, j0 = 4 * jg;
+  const int bb = n * n, vb = n * kJ;
+  char* jobs = Sv.sm + kMSmJobs;
+  const bool dbl = sizeof(T) == 8;
+  // one float64 job or two float32 jobs (double buffer) in the same region
+  const int jbytes = dbl ? mrhs_job_bytes(n) : mrhs_job_bytes(n) / 2;
+  const int nbuf = dbl ? 1 : 2;   // float64 jobs use one buffer spanning both
+  const int k = (phase == MP_B2) ? 2 : 1;
+  auto blk = [&](int which, int row) -> const T* {
+    // which: 0 = first (D, D^-1, Hd), 1 = second (O, E, Hu), 2 = third (O, E, Hl)
+    if (dbl) {
+      const double* A = (which == 0) ? P.D64 : P.O64;
+      return reinterpret_cast<const T*>(A + (size_t)row * P.bs64);
+    }
+    const float* A;
+    if (phase == MP_A) A = (which == 0) ? P.D32 : P.O32;
+    else if (phase == MP_B1) A = (which == 0) ? P.Dinv32 : P.E32;
+    else A = (which == 0) ? P.Hd32 : (which == 1 ? P.Hu32 : P.Hl32);
+    return reinterpret_cast<const T*>(A + (size_t)row * P.bs32);
+  };
+  auto issue = [&](int row, int buf) {
+    T* base = reinterpret_cast<T*>(jobs + (size_t)buf * jbytes);
+    T* m0 = base;
+    T* m1 = base + bb;
+    T* m2 = base + 2 * bb;
+    T* x0 = base + 3 * bb;   // vector rows row-k, row, row+k
+    // blocks: first(row), second(row), third(row-k) [transposed O/E or Hl]
+    auto cpb = [&](T* dst, const T* src, int cnt) {
+      if (dbl) cp_blockd(reinterpret_cast<double*>(dst), reinterpret_cast<const double*>(src), cnt);
+      else cp_block(reinterpret_cast<float*>(dst), reinterpret_cast<const float*>(src), cnt);
+    };
+    cpb(m0, blk(0, row), bb);
+    if (row + k < N) cpb(m1, blk(1, row), bb);
+    if (row - k >= 0) cpb(m2, blk(2, row - k), bb);
+    for (int d = -1; d <= 1; ++d) {
+      const int r = row + d * k;
+      if (r >= 0 && r < N) cpb(x0 + (d + 1) * vb, v_in + (size_t)r * vb, vb);
+    }
+    cp_commit();
+  };
+  const int nrows = Sv.e - Sv.s;
+  if (nrows <= 0) return;
+  if (nbuf == 2) issue(Sv.s, 0);
+  for (int it = 0; it < nrows; ++it) {
+    const int row = Sv.s + it;
+    const int buf = (nbuf == 2) ? (it & 1) : 0;
+    if (nbuf == 2) {
+      if (it + 1 < nrows) {
+        issue(row + 1, (it + 1) & 1);
+        cp_wait<1>();
+      } else {
+        cp_wait<0>();
+      }
+    } else {
+      issue(row, 0);
+      cp_wait<0>();
+    }
+    __syncthreads();
+    const T* base = reinterpret_cast<const T*>(jobs + (size_t)buf * jbytes);
+    const T* m0 = base;
+    const T* m1 = base + bb;
+    const T* m2 = base + 2 * bb;
+    const T* xl = base + 3 * bb;
+    const T* xc = xl + vb;
+    const T* xr = xc + vb;
+    T acc[4][4] = {};
+    T acc2[4][4] = {};  // off-diagonal terms (sign -1 for G)
+    if (active) {
+      prod_direct(m0, xc, n, a0, j0, acc);
+      if (row + k < N) prod_direct(m1, xr, n, a0, j0, acc2);
+      if (row - k >= 0) {
+        if (phase == MP_B2) prod_direct(m2, xl, n, a0, j0, acc2);   // Hl_{i-2} Y_{i-2}
+        else prod_trans(m2, xl, n, a0, j0, acc2);                    // O_{i-1}^T / E_{i-1}^T
+      }
+    }
+    const T sg = (phase == MP_B1) ? T(-1) : T(1);
+    T out[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) out[r][c] = acc[r][c] + sg * acc2[r][c];
+    if (active) fin(row, a0, j0, out, xc);
+    __syncthreads();
+  }
+}
+
+// The kernel: mixed-precision refinement around float32 PCG, all columns.
+__global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_constant__ MParams P) {
+  extern __shared__ __align__(128) char smem[];
+  MSolver Sv(P, smem);
+  Sv.g = blockIdx.x;
+  Sv.G = P.G;
+  Sv.N = P.N;
+  Sv.n = P.n;
+  Sv.s = (int)((long long)Sv.g * P.N / P.G);
+  Sv.e = (int)((long long)(Sv.g + 1) * P.N / P.G);
+  Sv.deadline = clock64() + P.budget;
+  Sv.bar_count = 0;
+  Sv.fail = false;
+  double* col = reinterpret_cast<double*>(smem + kMSmScalars);
+  double* colR = col + 0 * kJ;     // reduction buffer
+  double* rho = col + 1 * kJ;
+  double* alp = col + 2 * kJ;
+  double* bet = col + 3 * kJ;
+  double* actv = col + 4 * kJ;     // 1 active in the inner solve, 0 frozen
+  double* nbv = col + 5 * kJ;      // ||b_j||
+  double* nrv = col + 6 * kJ;      // ||r64_j||
+  double* tin = col + 7 * kJ;      // inner tolerance per column (squared)
+  double* outer_act = col + 8 * kJ;  // 1 while the column needs refinement
+  double* itc = col + 9 * kJ;      // inner iterations per column
+  double* scl = col + 10 * kJ;     // 1 / ||r64_j||
+  double* rrv = col + 11 * kJ;
+  double* scratch = reinterpret_cast<double*>(smem + kMSmScratch);
+  Sv.colbuf = colR;
+  const int n = P.n, N = P.N;
+  const int tid = threadIdx.x;
+  const int ngroups = n / 4;
+  const size_t vb = (size_t)n * kJ;
+  const int J = kJ;
+  const int m = P.m;
+
+  // ||b_j||^2 and x64 = 0 over the owned rows
+  {
+    double pv[4] = {0, 0, 0, 0};
+    const int jg = tid & 15, ag = tid >> 4;
+    if (ag < ngroups)
+      for (int row = Sv.s; row < Sv.e; ++row)
+        for (int r = 0; r < 4; ++r)
+          for (int c = 0; c < 4; ++c) {
+            const size_t idx = (size_t)row * vb + (size_t)(4 * ag + r) * J + 4 * jg + c;
+            const double bv = P.B64[idx];
+            pv[c] += bv * bv;
+            P.X64[idx] = 0.0;
+          }
+    cta_col_reduce(pv, scratch, colR, ngroups);
+    Sv.grid_reduce(colR);
+    if (tid < J) {
+      nbv[tid] = sqrt(colR[tid]);
+      const bool live = tid < P.nrhs && nbv[tid] > 0.0;
+      outer_act[tid] = live ? 1.0 : 0.0;
+      itc[tid] = 0.0;
+      nrv[tid] = nbv[tid];
+    }
+    __syncthreads();
+  }
+  int outer = 0;
+  int total_it = 0;
+  for (outer = 0; outer <= P.max_outer && !Sv.fail; ++outer) {
+    // ---- refinement residual r64 = b - S x64 (float64), skipped at x = 0
+    if (outer > 0) {
+      double pv[4] = {0, 0, 0, 0};
+      msweep<double>(Sv, MP_A64, P.X64, [&](int row, int a0, int j0, double (&o)[4][4], const double*) {
+        for (int r = 0; r < 4; ++r)
+          for (int c = 0; c < 4; ++c) {
+            const size_t idx = (size_t)row * vb + (size_t)(a0 + r) * J + j0 + c;
+            const double rv = P.B64[idx] - o[r][c];
+            P.R64[idx] = rv;
+            pv[c] += rv * rv;
+          }
+      });
+      cta_col_reduce(pv, scratch, colR, ngroups);
+      Sv.grid_reduce(colR);
+      if (tid < J) nrv[tid] = sqrt(colR[tid]);
+      __syncthreads();
+    }
+    // convergence of the true residual per column
+    if (tid < J) {
+      const bool live = outer_act[tid] > 0.0 && !(nrv[tid] <= P.tol * nbv[tid]);
+      if (outer_act[tid] > 0.0 && !isfinite(nrv[tid])) outer_act[tid] = -1.0;  // non-finite
+      else outer_act[tid] = live ? 1.0 : (outer_act[tid] < 0.0 ? -1.0 : 0.0);
+      const bool a = outer_act[tid] > 0.0;
+      scl[tid] = a ? 1.0 / nrv[tid] : 0.0;
+      double t = P.tol_inner;
+      if (a) {
+        const double need = 0.5 * P.tol * nbv[tid] / nrv[tid];
+        if (need > t) t = need;
+        if (t > 0.5) t = 0.5;
+      }
+      tin[tid] = t * t;
+      actv[tid] = a ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    int any = 0;
+    for (int j = 0; j < J; ++j) any |= (actv[j] > 0.0);
+    if (!any || outer == P.max_outer || total_it >= P.maxit) break;
+    // ---- inner float32 PCG: r = rhs, x_in = 0
+    {
+      double pv[4] = {0, 0, 0, 0};
+      const int jg = tid & 15, ag = tid >> 4;
+      if (ag < ngroups)
+        for (int row = Sv.s; row < Sv.e; ++row)
+          for (int r = 0; r < 4; ++r)
+            for (int c = 0; c < 4; ++c) {
+              const int j = 4 * jg + c;
+              const size_t idx = (size_t)row * vb + (size_t)(4 * ag + r) * J + j;
+              const double src = (outer > 0) ? P.R64[idx] : P.B64[idx];
+              const float rv = (float)(src * scl[j]);
+              P.R[idx] = rv;
+              P.Xin[idx] = 0.0f;
+            }
+      (void)pv;
+      Sv.barrier();
+    }
+    // z0 = M^-1 r0 ; rho = r.z
+    auto apply_precond = [&](double* rzout) {
+      // B1: y0 = G r
+      msweep<float>(Sv, MP_B1, P.R, [&](int row, int a0, int j0, float (&o)[4][4], const float*) {
+        for (int r = 0; r < 4; ++r)
+          for (int c = 0; c < 4; ++c) {
+            const size_t idx = (size_t)row * vb + (size_t)(a0 + r) * J + j0 + c;
+            P.Y0[idx] = o[r][c];
+            if (m == 1) P.Z[idx] = o[r][c];
+          }
+      });
+      Sv.barrier();
+      for (int jp = 1; jp < m && !Sv.fail; ++jp) {
+        const float* yin = (jp == 1) ? P.Y0 : ((jp - 1) % 2 == 1 ? P.Ya : P.Yb);
+        float* yout = (jp % 2 == 1) ? P.Ya : P.Yb;
+        const float aj = P.alpha[jp];
+        msweep<float>(Sv, MP_B2, yin, [&](int row, int a0, int j0, float (&o)[4][4], const float*) {
+          for (int r = 0; r < 4; ++r)
+            for (int c = 0; c < 4; ++c) {
+              const size_t idx = (size_t)row * vb + (size_t)(a0 + r) * J + j0 + c;
+              yout[idx] = o[r][c];
+              const float zp = (jp == 1) ? P.Y0[idx] : P.Z[idx];
+              P.Z[idx] = fmaf(aj, o[r][c], zp);
+            }
+        });
+        Sv.barrier();
+      }
+      // rz per column
+      double pv[4] = {0, 0, 0, 0};
+      const int jg = tid & 15, ag = tid >> 4;
+      if (ag < ngroups)
+        for (int row = Sv.s; row < Sv.e; ++row)
+          for (int r = 0; r < 4; ++r)
+            for (int c = 0; c < 4; ++c) {
+              const size_t idx = (size_t)row * vb + (size_t)(4 * ag + r) * J + 4 * jg + c;
+              pv[c] += (double)P.R[idx] * (double)P.Z[idx];
+            }
+      cta_col_reduce(pv, scratch, colR, ngroups);
+      Sv.grid_reduce(colR);
+      if (tid < J) rzout[tid] = colR[tid];
+      __syncthreads();
+    };
+    apply_precond(rho);
+    // p = z
+    {
+      const int jg = tid & 15, ag = tid >> 4;
+      if (ag < ngroups)
+        for (int row = Sv.s; row < Sv.e; ++row)
+          for (int r = 0; r < 4; ++r)
+            for (int c = 0; c < 4; ++c) {
+              const size_t idx = (size_t)row * vb + (size_t)(4 * ag + r) * J + 4 * jg + c;
+              P.P[idx] = P.Z[idx];
+            }
+      Sv.barrier();
+    }
+    // inner iterations
+    for (int kit = 1; !Sv.fail; ++kit) {
+      int anyact = 0;
+      for (int j = 0; j < J; ++j) anyact |= (actv[j] > 0.0);
+      if (!anyact || total_it >= P.maxit) break;
+      ++total_it;
+      // A: q = S p, pq per column
+      double pv[4] = {0, 0, 0, 0};
+      msweep<float>(Sv, MP_A, P.P, [&](int row, int a0, int j0, float (&o)[4][4], const float* pc) {
+        for (int r = 0; r < 4; ++r)
+          for (int c = 0; c < 4; ++c) {
+            const size_t idx = (size_t)row * vb + (size_t)(a0 + r) * J + j0 + c;
+            P.Q[idx] = o[r][c];
+            pv[c] += (double)pc[(a0 + r) * J + j0 + c] * (double)o[r][c];
+          }
+      });
+      cta_col_reduce(pv, scratch, colR, ngroups);
+      Sv.grid_reduce(colR);
+      if (tid < J) {
+        const double pq = colR[tid];
+        if (actv[tid] > 0.0) {
+          if (!isfinite(pq)) { actv[tid] = 0.0; outer_act[tid] = -1.0; alp[tid] = 0.0; }
+          else if (!(pq > 0.0)) { actv[tid] = 0.0; outer_act[tid] = -2.0; alp[tid] = 0.0; }
+          else alp[tid] = rho[tid] / pq;
+        } else {
+          alp[tid] = 0.0;
+        }
+        if (actv[tid] > 0.0) itc[tid] += 1.0;
+      }
+      __syncthreads();
+      // x += alpha p, r -= alpha q, rr per column
+      {
+        double pr[4] = {0, 0, 0, 0};
+        const int jg = tid & 15, ag = tid >> 4;
+        if (ag < ngroups)
+          for (int row = Sv.s; row < Sv.e; ++row)
+            for (int r = 0; r < 4; ++r)
+              for (int c = 0; c < 4; ++c) {
+                const int j = 4 * jg + c;
+                const size_t idx = (size_t)row * vb + (size_t)(4 * ag + r) * J + j;
+                const float a = (float)alp[j];
+                P.Xin[idx] = fmaf(a, P.P[idx], P.Xin[idx]);
+                const float rv = fmaf(-a, P.Q[idx], P.R[idx]);
+                P.R[idx] = rv;
+                pr[c] += (double)rv * (double)rv;
+              }
+        cta_col_reduce(pr, scratch, colR, ngroups);
+        Sv.grid_reduce(colR);
+        if (tid < J) {
+          rrv[tid] = colR[tid];
+          if (actv[tid] > 0.0 && rrv[tid] <= tin[tid]) actv[tid] = 0.0;  // converged column
+        }
+        __syncthreads();
+      }
+      int still = 0;
+      for (int j = 0; j < J; ++j) still |= (actv[j] > 0.0);
+      if (!still) break;
+      apply_precond(bet);   // bet temporarily holds the new r.z
+      if (tid < J) {
+        const double rzn = bet[tid];
+        const double b = (actv[tid] > 0.0) ? rzn / rho[tid] : 0.0;
+        rho[tid] = rzn;
+        bet[tid] = b;
+      }
+      __syncthreads();
+      // p = z + beta p
+      {
+        const int jg = tid & 15, ag = tid >> 4;
+        if (ag < ngroups)
+          for (int row = Sv.s; row < Sv.e; ++row)
+            for (int r = 0; r < 4; ++r)
+              for (int c = 0; c < 4; ++c) {
+                const int j = 4 * jg + c;
+                const size_t idx = (size_t)row * vb + (size_t)(4 * ag + r) * J + j;
+                P.P[idx] = fmaf((float)bet[j], P.P[idx], P.Z[idx]);
+              }
+        Sv.barrier();
+      }
+    }
+    // x64 += ||r64|| * x_in
+    {
+      const int jg = tid & 15, ag = tid >> 4;
+      if (ag < ngroups)
+        for (int row = Sv.s; row < Sv.e; ++row)
+          for (int r = 0; r < 4; ++r)
+            for (int c = 0; c < 4; ++c) {
+              const int j = 4 * jg + c;
+              const size_t idx = (size_t)row * vb + (size_t)(4 * ag + r) * J + j;
+              if (scl[j] > 0.0) P.X64[idx] = fma(nrv[j], (double)P.Xin[idx], P.X64[idx]);
+            }
+      Sv.barrier();
+    }
+  }
+  if (Sv.g == 0 && tid < J && tid < P.nrhs) {
+    int st = kOK;
+    if (Sv.fail) st = kErrTimeout;
+    else if (outer_act[tid] == -1.0) st = kErrNonfinite;
+    else if (outer_act[tid] == -2.0) st = kErrBreakdown;
+    else if (outer_act[tid] > 0.0) st = kErrNoConv;
+    else if (!isfinite(nbv[tid])) st = kErrNonfinite;
+    P.status[tid] = st;
+    P.iters[tid] = (int)itc[tid];
+    P.resid[tid] = nbv[tid] > 0.0 ? nrv[tid] / nbv[tid] : 0.0;
+    P.outer[tid] = outer;
+  }
+}
+
+// Layout conversion: caller [N*n][nrhs] (row-major) <-> internal [N][n][kJ].
+__global__ void k_mrhs_in(const double* B, double* B64, long long rows, int nrhs) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= rows * kJ) return;
+  const long long r = t / kJ;
+  const int j = (int)(t % kJ);
+  B64[t] = (j < nrhs) ? B[r * nrhs + j] : 0.0;
+}
+__global__ void k_mrhs_out(const double* X64, double* X, long long rows, int nrhs) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= rows * nrhs) return;
+  const long long r = t / nrhs;
+  const int j = (int)(t % nrhs);
+  X[t] = X64[r * kJ + j];
+}
+
+}  // namespace bt
+
+extern "C" int bt_mrhs_smem_bytes(int n) { return kMSmJobs + mrhs_job_bytes(n); }
+
+extern "C" cudaError_t bt_launch_mrhs(const bt::MParams* P, const double* B, double* X, int smem, cudaStream_t st) {
+  const long long rows = (long long)P->N * P->n;
+  const int tb = 256;
+  bt::k_mrhs_in<<<(unsigned)((rows * bt::kJ + tb - 1) / tb), tb, 0, st>>>(B, const_cast<double*>(P->B64), rows,
+                                                                         P->nrhs);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(bt::bt_mrhs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)P};
+  e = cudaLaunchCooperativeKernel((const void*)bt::bt_mrhs_kernel, dim3(P->G), dim3(bt::kMThreads), args, smem, st);
+  if (e != cudaSuccess) return e;
+  bt::k_mrhs_out<<<(unsigned)((rows * P->nrhs + tb - 1) / tb), tb, 0, st>>>(P->X64, X, rows, P->nrhs);
+  return cudaGetLastError();
+}
+
+extern "C" cudaError_t bt_mrhs_occupancy(int smem, int* blocks) {
+  cudaError_t e = cudaFuncSetAttribute(bt::bt_mrhs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, bt::bt_mrhs_kernel, bt::kMThreads, smem);
+}
+
+// Host launcher: fills the kernel parameters from plain pointers (the
+// workspace vector list is B64, X64, R64, Xin, R, P, Q, Y0, Ya, Yb, Z, red,
+// ctl, int results [iters | status | outer], double results [resid]).
+extern "C" cudaError_t bt_mrhs_solve_launch(int N, int n, int m, const double* alpha, const float* const* blk32,
+                                            const double* D64, const double* O64, int bs32, int bs64,
+                                            void* const* vec, double tol, double tol_inner, int maxit,
+                                            int max_outer, long long budget, int G, int nrhs, const double* B,
+                                            double* X, int smem, cudaStream_t st) {
+  bt::MParams P{};
+  P.D32 = blk32[0]; P.O32 = blk32[1]; P.Dinv32 = blk32[2]; P.E32 = blk32[3];
+  P.Hd32 = blk32[4]; P.Hu32 = blk32[5]; P.Hl32 = blk32[6];
+  P.D64 = D64;
+  P.O64 = O64;
+  P.N = N; P.n = n; P.bs32 = bs32; P.bs64 = bs64; P.m = m;
+  for (int j = 0; j < bt::kMaxM; ++j) P.alpha[j] = j < m ? (float)alpha[j] : 0.0f;
+  P.B64 = static_cast<const double*>(vec[0]);
+  P.X64 = static_cast<double*>(vec[1]);
+  P.R64 = static_cast<double*>(vec[2]);
+  P.Xin = static_cast<float*>(vec[3]);
+  P.R = static_cast<float*>(vec[4]);
+  P.P = static_cast<float*>(vec[5]);
+  P.Q = static_cast<float*>(vec[6]);
+  P.Y0 = static_cast<float*>(vec[7]);
+  P.Ya = static_cast<float*>(vec[8]);
+  P.Yb = static_cast<float*>(vec[9]);
+  P.Z = static_cast<float*>(vec[10]);
+  P.red = static_cast<double*>(vec[11]);
+  int* ctl = static_cast<int*>(vec[12]);
+  P.abort_flag = ctl + 1;
+  P.bar = reinterpret_cast<unsigned*>(ctl + 2);
+  int* ri = static_cast<int*>(vec[13]);
+  P.iters = ri;
+  P.status = ri + bt::kJ;
+  P.outer = ri + 2 * bt::kJ;
+  P.resid = static_cast<double*>(vec[14]);
+  P.tol = tol;
+  P.tol_inner = tol_inner;
+  P.maxit = maxit;
+  P.max_outer = max_outer;
+  P.budget = budget;
+  P.G = G;
+  P.nrhs = nrhs;
+  return bt_launch_mrhs(&P, B, X, smem, st);
+}

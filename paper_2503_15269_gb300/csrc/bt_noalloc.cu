@@ -120,13 +120,19 @@ extern "C" bt_status bt_pcg_solve_noalloc(int N, int n, const double* D, const d
   const int bs32 = (int)rup((long long)n * n, 4);
   const int bs64 = (int)rup((long long)n * n, 2);
   const long long bsb = mixed ? (long long)bs32 * 4 : (long long)bs64 * 8;
-  long long sb = p->stage_kb > 0 ? (long long)p->stage_kb * 1024 : 48 * 1024;
+  long long sb = p->stage_kb > 0 ? (long long)p->stage_kb * 1024 : 80 * 1024;
   sb = std::max(sb, rup(std::max(5 * bsb, 3 * (long long)bs64 * 8), 128));
   const int fixed = bt_persistent_smem_fixed();
-  int S = (int)((std::min<long long>(smem_optin, 228 * 1024 - 1024) - fixed) / sb);
+  int vslot = mixed ? 12 * 1024 : 24 * 1024;
+  const long long per_cta = std::min<long long>(smem_optin, 228 * 1024 - 1024);
+  int S = (int)((per_cta - fixed - 3 * vslot) / sb);
+  if (S < 2) {
+    vslot = 0;
+    S = (int)((per_cta - fixed) / sb);
+  }
   S = std::min(S, bt::kMaxStages);
   if (S < 2) return BT_ERR_ARG;
-  const int smem = fixed + S * (int)sb;
+  const int smem = fixed + 3 * vslot + S * (int)sb;
   int occ = 0;
   if (bt_persistent_occupancy(mixed ? 1 : 0, smem, &occ) != cudaSuccess || occ < 1) return BT_ERR_CUDA;
   int G = p->group_ctas > 0 ? p->group_ctas : std::max(1, N / 4);
@@ -236,6 +242,7 @@ extern "C" bt_status bt_pcg_solve_noalloc(int N, int n, const double* D, const d
   P.errval = d_errval;
   P.stages = S;
   P.stage_bytes = (int)sb;
+  P.vec_slot_bytes = vslot;
 
   unsigned long long key = 0;
   if (cudaMemcpyAsync(&key, fail_key, sizeof(key), cudaMemcpyDeviceToHost, st)) return BT_ERR_CUDA;

@@ -57,13 +57,17 @@ __device__ __forceinline__ Geo geo_of(int kind, int stage_bytes, int bs_bytes, i
 constexpr int kSmCtl = 0;                               // ints
 constexpr int kSmRed = 128;                             // double [8 warps][4]
 constexpr int kSmBc = kSmRed + 8 * 4 * 8;               // double bcast[8]
-constexpr int kSmRing = kSmBc + 8 * 8;                  // T ring[2][64]
-constexpr int kSmVs = kSmRing + 2 * kMaxBlock * 8;      // T vs[kMaxChunkElems + 4*64]
-constexpr int kSmParts = kSmVs + (kMaxChunkElems + 4 * kMaxBlock) * 8;  // T p1[512], p2[512], push[512+128]
+constexpr int kVsElems = kMaxChunkElems + 4 * kMaxBlock;
+constexpr int kSmRing = kSmBc + 8 * 8;                  // T ring[2 buffers][2][64]
+constexpr int kSmVs = kSmRing + 2 * 2 * kMaxBlock * 8;  // T vs[2 buffers][kVsElems]
+constexpr int kSmParts = kSmVs + 2 * kVsElems * 8;      // T p1[512], p2[512], push[512+128]
 constexpr int kSmFull = kSmParts + (3 * kMaxChunkElems + 2 * kMaxBlock) * 8;  // uint64 full[kMaxStages]
-constexpr int kSmStages = ((kSmFull + kMaxStages * 8 + 127) / 128) * 128;
+constexpr int kVecSlots = 3;                                   // vector ring depth
+constexpr int kSmVbar = kSmFull + kMaxStages * 8;              // uint64 vbar[kVecSlots]
+constexpr int kSmVring = ((kSmVbar + kVecSlots * 8 + 127) / 128) * 128;  // vector ring, then the stages
 
-__host__ __device__ constexpr int smem_fixed_bytes() { return kSmStages; }
+// fixed part; the host adds kVecSlots * vec_slot_bytes + stages * stage_bytes
+__host__ __device__ constexpr int smem_fixed_bytes() { return kSmVring; }
 
 template <typename T>
 __device__ __forceinline__ T dot_col(const T* __restrict__ M, int n, int a, const T* __restrict__ v) {
@@ -113,6 +117,126 @@ struct Sweep {
   T sgn;
 };
 
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+// Two outputs (a, a+1) of M v, M column-major NB x NB, a even.
+template <int NB, typename T>
+__device__ __forceinline__ void dcol2(const T* __restrict__ M, int a, const T* __restrict__ v, T& o0, T& o1) {
+  using V = typename Vec2<T>::type;
+  T a0 = T(0), a1 = T(0), b0 = T(0), b1 = T(0);
+#pragma unroll
+  for (int c = 0; c < NB; c += 2) {
+    const V m0 = *reinterpret_cast<const V*>(M + c * NB + a);
+    const V m1 = *reinterpret_cast<const V*>(M + (c + 1) * NB + a);
+    const V vv = *reinterpret_cast<const V*>(v + c);
+    a0 = fma(m0.x, vv.x, a0);
+    a1 = fma(m0.y, vv.x, a1);
+    b0 = fma(m1.x, vv.y, b0);
+    b1 = fma(m1.y, vv.y, b1);
+  }
+  o0 = a0 + b0;
+  o1 = a1 + b1;
+}
+
+// One output of M^T v: column a of M (contiguous) dotted with v.  The walk
+// along the column starts at a lane-dependent offset so that the 8 lanes of a
+// shared-memory phase fall in different banks.
+template <int NB, typename T>
+__device__ __forceinline__ T dtr1(const T* __restrict__ M, int a, const T* __restrict__ v, int rot) {
+  using V = typename Vec2<T>::type;
+  constexpr int Q = NB / 4;
+  const T* col = M + a * NB;
+  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    int qq = q + rot;
+    if (qq >= Q) qq -= Q;
+    const V m0 = *reinterpret_cast<const V*>(col + 4 * qq);
+    const V m1 = *reinterpret_cast<const V*>(col + 4 * qq + 2);
+    const V v0 = *reinterpret_cast<const V*>(v + 4 * qq);
+    const V v1 = *reinterpret_cast<const V*>(v + 4 * qq + 2);
+    s0 = fma(m0.x, v0.x, s0);
+    s1 = fma(m0.y, v0.y, s1);
+    s2 = fma(m1.x, v1.x, s2);
+    s3 = fma(m1.y, v1.y, s3);
+  }
+  return (s0 + s1) + (s2 + s3);
+}
+
+// All block-vector products of one chunk: part1 = M1 v_i, part2 = M2 v_{i+k},
+// push = (M2^T v_i) for S and G, (Hl_i v_i) for H.  NB = 0: runtime n.
+template <int KIND, int NB, typename T>
+__device__ __forceinline__ void chunk_products(const T* __restrict__ stg, int R, int bse, int n_rt, int N, int nr,
+                                               int h, int r0, int base, const T* __restrict__ vs, T* part1, T* part2,
+                                               T* push) {
+  constexpr int k = (KIND == kKB2) ? 2 : 1;
+  const int tid = threadIdx.x;
+  const T* a0 = stg;
+  const T* a1 = stg + (size_t)R * bse;
+  const T* a2 = stg + (size_t)2 * R * bse;
+  if constexpr (NB > 0) {
+    constexpr int n = NB;
+    constexpr int hp = NB / 2;
+    const int nd2 = nr * hp;                          // pairs of direct outputs
+    const int np = (KIND == kKB2) ? (nr + h) * hp : (nr + h) * n;
+    const int ntask = 2 * nd2 + np;
+    const int rot = (tid & 7) % (NB / 4);
+    for (int t = tid; t < ntask; t += kThreads) {
+      if (t < nd2) {
+        const int jj = t / hp, a = 2 * (t - jj * hp);
+        dcol2<NB>(a0 + (size_t)jj * bse, a, vs + (r0 + jj - base) * n, part1[jj * n + a], part1[jj * n + a + 1]);
+      } else if (t < 2 * nd2) {
+        const int t2 = t - nd2;
+        const int jj = t2 / hp, a = 2 * (t2 - jj * hp);
+        if (r0 + jj + k < N) {
+          const T* M2 = (KIND == kKB2) ? a1 + (size_t)jj * bse : a1 + (size_t)(jj + h) * bse;
+          dcol2<NB>(M2, a, vs + (r0 + jj + k - base) * n, part2[jj * n + a], part2[jj * n + a + 1]);
+        } else {
+          part2[jj * n + a] = T(0);
+          part2[jj * n + a + 1] = T(0);
+        }
+      } else {
+        const int t3 = t - 2 * nd2;
+        if constexpr (KIND == kKB2) {
+          const int jj = t3 / hp, a = 2 * (t3 - jj * hp);
+          dcol2<NB>(a2 + (size_t)jj * bse, a, vs + jj * n, push[jj * n + a], push[jj * n + a + 1]);
+        } else {
+          const int jj = t3 / n, a = t3 - jj * n;
+          push[jj * n + a] = dtr1<NB>(a1 + (size_t)jj * bse, a, vs + jj * n, rot);
+        }
+      }
+    }
+  } else {
+    // runtime block size (any n)
+    const int n = n_rt;
+    const int nd = nr * n;
+    const int ntask = 2 * nd + (nr + h) * n;
+    for (int t = tid; t < ntask; t += kThreads) {
+      if (t < nd) {
+        const int jj = t / n, a = t - jj * n;
+        part1[t] = dot_col(a0 + (size_t)jj * bse, n, a, vs + (r0 + jj - base) * n);
+      } else if (t < 2 * nd) {
+        const int t2 = t - nd;
+        const int jj = t2 / n, a = t2 - jj * n;
+        T val = T(0);
+        if (r0 + jj + k < N) {
+          const T* M2 = (KIND == kKB2) ? a1 + (size_t)jj * bse : a1 + (size_t)(jj + h) * bse;
+          val = dot_col(M2, n, a, vs + (r0 + jj + k - base) * n);
+        }
+        part2[t2] = val;
+      } else {
+        const int t3 = t - 2 * nd;
+        const int jj = t3 / n, a = t3 - jj * n;
+        if (KIND == kKB2) push[t3] = dot_col(a2 + (size_t)jj * bse, n, a, vs + jj * n);
+        else push[t3] = dot_tr(a1 + (size_t)jj * bse, n, a, vs + jj * n);
+      }
+    }
+  }
+}
+
 template <typename MT>
 struct Solver {
   const KParams& P;
@@ -131,8 +255,13 @@ struct Solver {
   uint64_t* full;
   char* stages;
   unsigned issued, consumed;
-  int pat[kMaxM + 2];
-  int pat_len, p_slot, p_chunk;
+  // vector ring (bulk copies of the vector rows of a chunk, within a sweep)
+  uint64_t* vbar;
+  char* vring;
+  int VSB;
+  unsigned vissued, vcons;
+  int pat_len, pat_first, p_slot, p_chunk;  // predicted sweep sequence (see kind_at)
+  int ncA, ncB1, ncB2, ncA64;                // chunks per sweep kind for this instance
   const double* mats64[7];
   const MT* mats[7];
   int bs, bs64;
@@ -142,8 +271,12 @@ struct Solver {
     S = P.stages;
     SB = P.stage_bytes;
     full = reinterpret_cast<uint64_t*>(sm + kSmFull);
-    stages = sm + kSmStages;
+    vbar = reinterpret_cast<uint64_t*>(sm + kSmVbar);
+    vring = sm + kSmVring;
+    VSB = P.vec_slot_bytes;
+    stages = vring + (size_t)kVecSlots * VSB;
     issued = consumed = 0;
+    vissued = vcons = 0;
     bar_count = 0;
   }
 
@@ -155,54 +288,107 @@ struct Solver {
     return (e - s + gg.R - 1) / gg.R;
   }
 
-  // ---- producer (thread 0 only) ------------------------------------------
-  __device__ void issue(int kind, int c) {
-    const Geo gg = geo(kind);
-    const int r0 = s + c * gg.R;
-    const int r1 = min(e, r0 + gg.R);
-    const int h = (c == 0) ? min(gg.halo, s) : 0;
-    const int bsb = bsb_of(kind);
-    const int st = issued % S;
-    char* dst = stages + (size_t)st * SB;
-    uint64_t* bar = &full[st];
-    const int nr = r1 - r0;
-    unsigned total;
-    if (kind == kKB2) total = (unsigned)(3 * nr + h) * bsb;
-    else total = (unsigned)(2 * nr + h) * bsb;
-    fence_proxy_async_smem();
-    mbar_arrive_expect_tx(bar, total);
-    if (kind == kKA64) {
-      const double* D = mats64[0];
-      const double* O = mats64[1];
-      bulk_g2s(dst, D + (size_t)r0 * bs64, nr * bsb, bar);
-      bulk_g2s(dst + (size_t)gg.R * bsb, O + (size_t)(r0 - h) * bs64, (nr + h) * bsb, bar);
-    } else {
-      const MT* A0 = kind == kKA ? mats[0] : (kind == kKB1 ? mats[2] : mats[4]);
-      const MT* A1 = kind == kKA ? mats[1] : (kind == kKB1 ? mats[3] : mats[5]);
-      bulk_g2s(dst, A0 + (size_t)r0 * bs, nr * bsb, bar);
-      if (kind == kKB2) {
-        bulk_g2s(dst + (size_t)gg.R * bsb, A1 + (size_t)r0 * bs, nr * bsb, bar);
-        bulk_g2s(dst + (size_t)2 * gg.R * bsb, mats[6] + (size_t)(r0 - h) * bs, (nr + h) * bsb, bar);
-      } else {
-        bulk_g2s(dst + (size_t)gg.R * bsb, A1 + (size_t)(r0 - h) * bs, (nr + h) * bsb, bar);
+  // ---- producer ------------------------------------------------------------
+  // The pipeline state lives in a Producer value: sweeps copy it into
+  // registers on entry and back on exit, so the per-chunk bookkeeping never
+  // touches local memory.  The predicted sweep sequence is either a single
+  // kind repeated (len 1) or the PCG iteration pattern A, B1, B2 x (m-1).
+  struct Producer {
+    int s, e, n, S, SB, bs, bs64;
+    char* stages;
+    uint64_t* full;
+    const char *m0, *m1, *m2, *m3, *m4, *m5, *m6;  // D, O, D^-1, E, Hd, Hu, Hl (working precision)
+    const char *d64, *o64;                          // float64 D, O
+    int pat_len, pat_first, p_slot, p_chunk;
+    int ncA, ncB1, ncB2, ncA64;
+    int RA, RB1, RB2, RA64;
+    unsigned issued;
+
+    __device__ __forceinline__ int kind_at(int slot) const {
+      return pat_len == 1 ? pat_first : (slot == 0 ? kKA : (slot == 1 ? kKB1 : kKB2));
+    }
+    __device__ __forceinline__ int nch(int kind) const {
+      return kind == kKA ? ncA : (kind == kKB1 ? ncB1 : (kind == kKB2 ? ncB2 : ncA64));
+    }
+    __device__ __forceinline__ int rows(int kind) const {
+      return kind == kKA ? RA : (kind == kKB1 ? RB1 : (kind == kKB2 ? RB2 : RA64));
+    }
+    // thread 0 issues the bulk copies of chunk c of `kind`; every thread
+    // advances the cursor identically.
+    __device__ __forceinline__ void step(bool leader) {
+      const int kind = kind_at(p_slot);
+      if (leader) {
+        const int R = rows(kind);
+        const int c = p_chunk;
+        const int r0 = s + c * R;
+        const int r1 = min(e, r0 + R);
+        const int halo = (kind == kKB2) ? 2 : 1;
+        const int h = (c == 0) ? min(halo, s) : 0;
+        const int bse = (kind == kKA64) ? bs64 : bs;
+        const int esz = (kind == kKA64) ? 8 : (int)sizeof(MT);
+        const int bsb = bse * esz;
+        const int st = issued % S;
+        char* dst = stages + (size_t)st * SB;
+        uint64_t* bar = &full[st];
+        const int nr = r1 - r0;
+        const unsigned total = (unsigned)((kind == kKB2 ? 3 * nr : 2 * nr) + h) * bsb;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar, total);
+        const char* A0 = kind == kKA ? m0 : (kind == kKB1 ? m2 : (kind == kKB2 ? m4 : d64));
+        const char* A1 = kind == kKA ? m1 : (kind == kKB1 ? m3 : (kind == kKB2 ? m5 : o64));
+        bulk_g2s(dst, A0 + (size_t)r0 * bsb, nr * bsb, bar);
+        if (kind == kKB2) {
+          bulk_g2s(dst + (size_t)R * bsb, A1 + (size_t)r0 * bsb, nr * bsb, bar);
+          bulk_g2s(dst + (size_t)2 * R * bsb, m6 + (size_t)(r0 - h) * bsb, (nr + h) * bsb, bar);
+        } else {
+          bulk_g2s(dst + (size_t)R * bsb, A1 + (size_t)(r0 - h) * bsb, (nr + h) * bsb, bar);
+        }
+      }
+      ++issued;
+      if (++p_chunk >= nch(kind)) {
+        p_chunk = 0;
+        p_slot = (p_slot + 1 == pat_len) ? 0 : p_slot + 1;
       }
     }
-    ++issued;
+  };
+
+  __device__ __forceinline__ Producer producer() const {
+    Producer q;
+    q.s = s; q.e = e; q.n = n; q.S = S; q.SB = SB; q.bs = bs; q.bs64 = bs64;
+    q.stages = stages; q.full = full;
+    q.m0 = (const char*)mats[0]; q.m1 = (const char*)mats[1]; q.m2 = (const char*)mats[2];
+    q.m3 = (const char*)mats[3]; q.m4 = (const char*)mats[4]; q.m5 = (const char*)mats[5];
+    q.m6 = (const char*)mats[6];
+    q.d64 = (const char*)mats64[0]; q.o64 = (const char*)mats64[1];
+    q.pat_len = pat_len; q.pat_first = pat_first; q.p_slot = p_slot; q.p_chunk = p_chunk;
+    q.ncA = ncA; q.ncB1 = ncB1; q.ncB2 = ncB2; q.ncA64 = ncA64;
+    q.RA = geo(kKA).R; q.RB1 = geo(kKB1).R; q.RB2 = geo(kKB2).R; q.RA64 = geo(kKA64).R;
+    q.issued = issued;
+    return q;
+  }
+  __device__ __forceinline__ void store_producer(const Producer& q) {
+    p_slot = q.p_slot;
+    p_chunk = q.p_chunk;
+    issued = q.issued;
   }
 
-  __device__ void issue_next() {
-    // thread 0: issue the chunk at the producer cursor, then advance it.
-    const int kind = pat[p_slot];
-    issue(kind, p_chunk);
-    if (++p_chunk >= nchunks(kind)) {
-      p_chunk = 0;
-      p_slot = (p_slot + 1) % pat_len;
-    }
+  // chunk counts of the current instance (call after s, e, n, bs are set)
+  __device__ void set_chunk_counts() {
+    ncA = nchunks(kKA);
+    ncB1 = nchunks(kKB1);
+    ncB2 = nchunks(kKB2);
+    ncA64 = nchunks(kKA64);
   }
 
   // Drain every chunk in flight (bounded) so that the ring is idle.
   __device__ void flush() {
     bool ok = true;
+    while (vcons < vissued) {
+      const int st = vcons % kVecSlots;
+      const unsigned par = (vcons / kVecSlots) & 1u;
+      if (ok && !mbar_wait(&vbar[st], par, deadline + (1ll << 31))) ok = false;
+      ++vcons;
+    }
     while (consumed < issued) {
       const int st = consumed % S;
       const unsigned par = (consumed / S) & 1u;
@@ -213,31 +399,17 @@ struct Solver {
     if (!ok) fail = true;
   }
 
-  // Start a new predicted sweep sequence: pattern `p[0..len)`, starting slot.
-  __device__ void restart(const int* p, int len, int start_slot) {
+  // Start a new predicted sweep sequence: either `first` repeated (len 1) or
+  // the iteration pattern (len m + 1), from `start_slot`; prefill the ring.
+  __device__ void restart(int first, int len, int start_slot) {
     flush();
     pat_len = len;
-    for (int i = 0; i < len; ++i) pat[i] = p[i];
+    pat_first = first;
     p_slot = start_slot;
     p_chunk = 0;
-    if (tid == 0) {
-      for (int i = 0; i < S; ++i) issue_next();
-    } else {
-      // keep the uniform copies of the cursor in step with thread 0
-      for (int i = 0; i < S; ++i) {
-        ++issued;
-        if (++p_chunk >= nchunks(pat[p_slot])) { p_chunk = 0; p_slot = (p_slot + 1) % pat_len; }
-      }
-    }
-  }
-
-  __device__ void advance_producer_after_release() {
-    if (tid == 0) {
-      issue_next();
-    } else {
-      ++issued;
-      if (++p_chunk >= nchunks(pat[p_slot])) { p_chunk = 0; p_slot = (p_slot + 1) % pat_len; }
-    }
+    Producer q = producer();
+    for (int i = 0; i < S; ++i) q.step(tid == 0);
+    store_producer(q);
   }
 
   // ---- reductions & group barrier ----------------------------------------
@@ -245,6 +417,8 @@ struct Solver {
   // order, so results are bitwise reproducible).  v[3] carries a timeout flag.
   __device__ void group_reduce(double v[4]) {
     if (fail) return;
+    // vector rows written so far are read by bulk copies after this barrier
+    fence_proxy_async_global();
     double* red = reinterpret_cast<double*>(sm + kSmRed);
     double* bc = reinterpret_cast<double*>(sm + kSmBc);
     int* ctl = reinterpret_cast<int*>(sm + kSmCtl);
@@ -294,167 +468,308 @@ struct Solver {
     __syncthreads();
   }
 
+  // ---- vector rows of a chunk ---------------------------------------------
+  // The vector arrays a sweep reads for one chunk, in a fixed order; `own`
+  // arrays cover the chunk's owned rows [r0, r1), the others [base, vend).
+  struct VecPlan {
+    const char *src0, *src1, *src2, *src3;
+    int esz0, esz1, esz2, esz3;
+    int own0, own1, own2, own3;
+    int cnt;
+    __device__ __forceinline__ void add(const void* ptr, int esz, int own) {
+      const char* c = static_cast<const char*>(ptr);
+      if (cnt == 0) { src0 = c; esz0 = esz; own0 = own; }
+      else if (cnt == 1) { src1 = c; esz1 = esz; own1 = own; }
+      else if (cnt == 2) { src2 = c; esz2 = esz; own2 = own; }
+      else { src3 = c; esz3 = esz; own3 = own; }
+      ++cnt;
+    }
+    __device__ __forceinline__ const char* src(int i) const { return i == 0 ? src0 : (i == 1 ? src1 : (i == 2 ? src2 : src3)); }
+    __device__ __forceinline__ int esz(int i) const { return i == 0 ? esz0 : (i == 1 ? esz1 : (i == 2 ? esz2 : esz3)); }
+    __device__ __forceinline__ int own(int i) const { return i == 0 ? own0 : (i == 1 ? own1 : (i == 2 ? own2 : own3)); }
+  };
+
+  template <int STG, int FIN, typename T>
+  static __device__ __forceinline__ VecPlan vec_plan(const Sweep<T>& sw) {
+    VecPlan v{};
+    v.cnt = 0;
+    if constexpr (STG == SV_P) {
+      v.add(sw.z, sizeof(T), 0);
+      if (!sw.first) v.add(sw.p_old, sizeof(T), 0);
+    } else if constexpr (STG == SV_VEC || STG == SV_R_FIRST) {
+      v.add(sw.src64, 8, 0);
+    } else if constexpr (STG == SV_R_UPD) {
+      v.add(sw.r_old, sizeof(T), 0);
+      v.add(sw.q, sizeof(T), 0);
+      v.add(sw.x, sizeof(T), 1);
+      v.add(sw.p_in, sizeof(T), 1);
+    } else if constexpr (STG == SV_R_X0) {
+      v.add(sw.src64, 8, 0);
+      v.add(sw.q, sizeof(T), 0);
+    } else {
+      v.add(sw.yprev, sizeof(T), 0);
+    }
+    if constexpr (FIN == FN_YJ) {
+      if (sw.j > 1) v.add(sw.zv, sizeof(T), 1);
+      if (sw.last) v.add(sw.rcur_for_dot, sizeof(T), 1);
+    } else if constexpr (FIN == FN_R64) {
+      v.add(sw.bsub, 8, 1);
+    }
+    return v;
+  }
+
+  // Can the plan be moved by bulk copies (16-byte aligned rows, fits a slot)?
+  static __device__ __forceinline__ bool vec_plan_ok(const VecPlan& v, int n, int R, int k, int halo, int VSB) {
+    int bytes = 0;
+    for (int i = 0; i < v.cnt; ++i) {
+      if ((reinterpret_cast<uintptr_t>(v.src(i)) & 15u) != 0) return false;
+      if (((long long)n * v.esz(i)) % 16 != 0) return false;
+      const int rows = v.own(i) ? R : R + halo + k;
+      bytes += rows * n * v.esz(i);
+    }
+    return bytes <= VSB;
+  }
+
+  // leader thread: bulk-copy the vector rows [base, vend) / [r0, r1) of a chunk
+  static __device__ __forceinline__ void issue_vec(const VecPlan& v, int n, int r0, int r1, int base, int vend,
+                                                   char* dst, uint64_t* bar) {
+    unsigned total = 0;
+    for (int i = 0; i < v.cnt; ++i) total += (unsigned)((v.own(i) ? (r1 - r0) : (vend - base)) * n * v.esz(i));
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(bar, total);
+    unsigned off = 0;
+    for (int i = 0; i < v.cnt; ++i) {
+      const int rows = v.own(i) ? (r1 - r0) : (vend - base);
+      const int row0 = v.own(i) ? r0 : base;
+      const unsigned bytes = (unsigned)(rows * n * v.esz(i));
+      bulk_g2s(dst + off, v.src(i) + (size_t)row0 * n * v.esz(i), bytes, bar);
+      off += bytes;
+    }
+  }
+
   // ---- one sweep -----------------------------------------------------------
-  template <typename T>
-  __device__ void run_sweep(const Sweep<T>& sw, double acc[4]) {
-    const int kind = sw.kind;
-    const Geo gg = geo(kind);
-    const int R = gg.R, k = gg.k;
-    const int bse = (kind == kKA64) ? bs64 : bs;  // element stride of a block
-    T* ring = reinterpret_cast<T*>(sm + kSmRing);
-    T* vs = reinterpret_cast<T*>(sm + kSmVs);
+  // KIND / STG / FIN are compile-time: each instantiation carries only the
+  // staging and finalize code it uses.  The block products dispatch once per
+  // chunk on n to compile-time block sizes (unrolled, vector loads).  The
+  // vector rows each chunk reads arrive by bulk copies issued kVecSlots-1
+  // chunks ahead inside the sweep (they are final once the sweep starts).
+  // All pipeline state is held in registers for the duration of the sweep.
+  template <int KIND, int STG, int FIN, typename T>
+  __device__ __noinline__ void sweep(const Sweep<T> sw, double acc[4]) {
+    constexpr int kHalo = (KIND == kKB2) ? 2 : 1;
+    constexpr int k = (KIND == kKB2) ? 2 : 1;
+    Producer q = producer();
+    const int n = this->n, N = this->N, s = this->s, e = this->e;
+    const int S = this->S, SB = this->SB, VSB = this->VSB;
+    const long long dl = deadline + (1ll << 31);
+    uint64_t* const full = this->full;
+    uint64_t* const vbar = this->vbar;
+    char* const stages = this->stages;
+    char* const vring = this->vring;
+    unsigned consumed = this->consumed, vissued = this->vissued, vcons = this->vcons;
+    const bool leader = (threadIdx.x == 0);
+    const int tid = threadIdx.x;
+    const int R = q.rows(KIND);
+    const int bse = (KIND == kKA64) ? bs64 : bs;
+    T* ringb = reinterpret_cast<T*>(sm + kSmRing);           // [2][k][n]
+    T* vsb = reinterpret_cast<T*>(sm + kSmVs);               // [2][kVsElems]
     T* part1 = reinterpret_cast<T*>(sm + kSmParts);
     T* part2 = part1 + kMaxChunkElems;
     T* push = part2 + kMaxChunkElems;
+    const T sgn = (KIND == kKB1) ? T(-1) : T(1);
     const int nc = (e - s + R - 1) / R;
+    const VecPlan vp = vec_plan<STG, FIN, T>(sw);
+    const bool va = vec_plan_ok(vp, n, R, k, kHalo, VSB);
+    // staged inputs, copied to registers
+    const T alpha = sw.alpha, beta = sw.beta, alpha_j = sw.alpha_j;
+    const bool first = sw.first, m1 = sw.m1, last = sw.last, out_to_user = sw.out_to_user;
+    const bool write_r = sw.write_r, zero_x = sw.zero_x;
+    const int jpow = sw.j;
+    const double scale = sw.scale;
+    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
+    auto chunk_rows = [&](int c, int& r0, int& r1, int& base, int& vend) {
+      r0 = s + c * R;
+      r1 = min(e, r0 + R);
+      base = r0 - ((c == 0) ? min(kHalo, s) : 0);
+      vend = min(N, r1 + k);
+    };
+    if (va) {
+      const int pre = min(kVecSlots - 1, nc);
+      for (int c = 0; c < pre; ++c) {
+        if (leader) {
+          int r0, r1, base, vend;
+          chunk_rows(c, r0, r1, base, vend);
+          const int slot = vissued % kVecSlots;
+          issue_vec(vp, n, r0, r1, base, vend, vring + (size_t)slot * VSB, &vbar[slot]);
+        }
+        ++vissued;
+      }
+    }
+    bool failed = false;
     for (int c = 0; c < nc; ++c) {
-      const int r0 = s + c * R;
-      const int r1 = min(e, r0 + R);
+      int r0, r1, base, vend;
+      chunk_rows(c, r0, r1, base, vend);
       const int nr = r1 - r0;
-      const int h = (c == 0) ? min(gg.halo, s) : 0;
-      const int base = r0 - h;
-      const int vend = min(N, r1 + k);
+      const int h = r0 - base;
       const int st = consumed % S;
       const unsigned par = (consumed / S) & 1u;
-      // 1. wait for the chunk's blocks (every thread observes the mbarrier)
-      const bool ok = mbar_wait(&full[st], par, deadline + (1ll << 31));
+      const int buf = consumed & 1u;
+      T* vs = vsb + buf * kVsElems;
+      const T* ring_in = ringb + (buf ^ 1) * (2 * kMaxBlock);
+      T* ring_out = ringb + buf * (2 * kMaxBlock);
+      // 1. wait for the chunk's blocks and vector rows
+      bool ok = mbar_wait(&full[st], par, dl);
       ++consumed;
+      const char* vslot = vring + (size_t)(vcons % kVecSlots) * VSB;
+      if (va) {
+        ok = ok && mbar_wait(&vbar[vcons % kVecSlots], (vcons / kVecSlots) & 1u, dl);
+        ++vcons;
+      }
+      // byte offsets of the vector arrays inside the slot
+      int voff1 = 0, voff2 = 0, voff3 = 0;
+      {
+        const int rng = (vend - base) * n, ow = nr * n;
+        const int b0 = (vp.cnt > 0) ? (vp.own0 ? ow : rng) * vp.esz0 : 0;
+        const int b1 = (vp.cnt > 1) ? (vp.own1 ? ow : rng) * vp.esz1 : 0;
+        const int b2 = (vp.cnt > 2) ? (vp.own2 ? ow : rng) * vp.esz2 : 0;
+        voff1 = b0;
+        voff2 = b0 + b1;
+        voff3 = b0 + b1 + b2;
+      }
+      const T* sv0 = reinterpret_cast<const T*>(vslot);
+      const T* sv1 = reinterpret_cast<const T*>(vslot + voff1);
+      const T* sv2 = reinterpret_cast<const T*>(vslot + voff2);
+      const T* sv3 = reinterpret_cast<const T*>(vslot + voff3);
+      const double* sd0 = reinterpret_cast<const double*>(vslot);
       // 2. stage the vector rows [base, vend) with the fused PCG updates
       const int nv = (vend - base) * n;
       for (int t = tid; t < nv; t += kThreads) {
-        const int row = base + t / n;
-        const long long idx = (long long)row * n + (t % n);
+        const int rr = t / n;
+        const int a = t - rr * n;
+        const int row = base + rr;
+        const long long idx = (long long)row * n + a;
         const bool own = row >= r0 && row < r1;
+        const int lo = t - h * n;  // index among the owned rows
         T v;
-        switch (sw.stg) {
-          case SV_P: {
-            v = sw.first ? sw.z[idx] : fma(sw.beta, sw.p_old[idx], sw.z[idx]);
-            if (own) sw.p_cur[idx] = v;
-          } break;
-          case SV_VEC:
-            v = static_cast<T>(sw.src64[idx]);
-            break;
-          case SV_R_UPD: {
-            v = fma(-sw.alpha, sw.q[idx], sw.r_old[idx]);
-            if (own) {
-              sw.r_cur[idx] = v;
-              sw.x[idx] = fma(sw.alpha, sw.p_in[idx], sw.x[idx]);
-              acc[2] += (double)v * (double)v;
-            }
-          } break;
-          case SV_R_FIRST: {
-            v = static_cast<T>(sw.src64[idx] * sw.scale);
-            if (own) {
-              if (sw.write_r) sw.r_cur[idx] = v;
-              if (sw.zero_x) sw.x[idx] = T(0);
-              acc[2] += (double)v * (double)v;
-            }
-          } break;
-          case SV_R_X0: {
-            v = static_cast<T>(sw.src64[idx] - (double)sw.q[idx]);
-            if (own) {
-              sw.r_cur[idx] = v;
-              acc[2] += (double)v * (double)v;
-            }
-          } break;
-          default:
-            v = sw.yprev[idx];
-            break;
+        if constexpr (STG == SV_P) {
+          const T zz = va ? sv0[t] : sw.z[idx];
+          if (first) v = zz;
+          else v = fma(beta, va ? sv1[t] : sw.p_old[idx], zz);
+          if (own) sw.p_cur[idx] = v;
+        } else if constexpr (STG == SV_VEC) {
+          v = static_cast<T>(va ? sd0[t] : sw.src64[idx]);
+        } else if constexpr (STG == SV_R_UPD) {
+          v = fma(-alpha, va ? sv1[t] : sw.q[idx], va ? sv0[t] : sw.r_old[idx]);
+          if (own) {
+            sw.r_cur[idx] = v;
+            sw.x[idx] = fma(alpha, va ? sv3[lo] : sw.p_in[idx], va ? sv2[lo] : sw.x[idx]);
+            acc2 += (double)v * (double)v;
+          }
+        } else if constexpr (STG == SV_R_FIRST) {
+          v = static_cast<T>((va ? sd0[t] : sw.src64[idx]) * scale);
+          if (own) {
+            if (write_r) sw.r_cur[idx] = v;
+            if (zero_x) sw.x[idx] = T(0);
+            acc2 += (double)v * (double)v;
+          }
+        } else if constexpr (STG == SV_R_X0) {
+          v = static_cast<T>((va ? sd0[t] : sw.src64[idx]) - (double)(va ? sv1[t] : sw.q[idx]));
+          if (own) {
+            sw.r_cur[idx] = v;
+            acc2 += (double)v * (double)v;
+          }
+        } else {
+          v = va ? sv0[t] : sw.yprev[idx];
         }
         vs[t] = v;
       }
       if (__syncthreads_or(!ok)) {
-        fail = true;
-        if (G > 1 && tid == 0) atomicExch(P.abort_flag, 1);
-        return;
+        if (G > 1 && leader) atomicExch(P.abort_flag, 1);
+        failed = true;
+        break;
+      }
+      // the vector slot of chunk c-1 is free now: prefetch chunk c + kVecSlots - 1
+      if (va && c + kVecSlots - 1 < nc) {
+        if (leader) {
+          int pr0, pr1, pbase, pvend;
+          chunk_rows(c + kVecSlots - 1, pr0, pr1, pbase, pvend);
+          const int slot = vissued % kVecSlots;
+          issue_vec(vp, n, pr0, pr1, pbase, pvend, vring + (size_t)slot * VSB, &vbar[slot]);
+        }
+        ++vissued;
       }
       // 3. block-vector products out of shared memory
       const T* stg = reinterpret_cast<const T*>(stages + (size_t)st * SB);
-      const T* a0 = stg;
-      const T* a1 = stg + (size_t)R * bse;
-      const T* a2 = stg + (size_t)2 * R * bse;
-      const int nd = nr * n;
-      const int ntask = 2 * nd + (nr + h) * n;
-      for (int t = tid; t < ntask; t += kThreads) {
-        if (t < nd) {
-          const int jj = t / n, a = t - jj * n;
-          const int row = r0 + jj;
-          part1[t] = dot_col(a0 + (size_t)jj * bse, n, a, vs + (row - base) * n);
-        } else if (t < 2 * nd) {
-          const int t2 = t - nd;
-          const int jj = t2 / n, a = t2 - jj * n;
-          const int row = r0 + jj;
-          T val = T(0);
-          if (row + k < N) {
-            const T* M2 = (kind == kKB2) ? a1 + (size_t)jj * bse : a1 + (size_t)(jj + h) * bse;
-            val = dot_col(M2, n, a, vs + (row + k - base) * n);
-          }
-          part2[t2] = val;
-        } else {
-          const int t3 = t - 2 * nd;
-          const int jj = t3 / n, a = t3 - jj * n;
-          const int src = base + jj;
-          T val = T(0);
-          if (src + k < N) {
-            if (kind == kKB2) val = dot_col(a2 + (size_t)jj * bse, n, a, vs + jj * n);
-            else val = dot_tr(a1 + (size_t)jj * bse, n, a, vs + jj * n);
-          }
-          push[t3] = val;
-        }
+      switch (n) {
+        case 12: chunk_products<KIND, 12, T>(stg, R, bse, n, N, nr, h, r0, base, vs, part1, part2, push); break;
+        case 24: chunk_products<KIND, 24, T>(stg, R, bse, n, N, nr, h, r0, base, vs, part1, part2, push); break;
+        case 36: chunk_products<KIND, 36, T>(stg, R, bse, n, N, nr, h, r0, base, vs, part1, part2, push); break;
+        case 48: chunk_products<KIND, 48, T>(stg, R, bse, n, N, nr, h, r0, base, vs, part1, part2, push); break;
+        default: chunk_products<KIND, 0, T>(stg, R, bse, n, N, nr, h, r0, base, vs, part1, part2, push); break;
       }
       __syncthreads();
       // 4. the stage is free: refill it with the next predicted chunk
-      advance_producer_after_release();
+      q.step(leader);
       // 5. finalize owned rows
+      const int nd = nr * n;
+      // slot of the finalize-only arrays (after the staging arrays)
+      const int ns = (STG == SV_P) ? (first ? 1 : 2) : ((STG == SV_R_UPD) ? 4 : ((STG == SV_R_X0) ? 2 : 1));
+      const int iz = ns, ir = ns + ((FIN == FN_YJ && jpow > 1) ? 1 : 0);
+      const T* fz = (iz == 1) ? sv1 : ((iz == 2) ? sv2 : sv3);
+      const T* fr = (ir == 1) ? sv1 : ((ir == 2) ? sv2 : sv3);
+      const double* fb = reinterpret_cast<const double*>((const char*)fz);
       for (int t = tid; t < nd; t += kThreads) {
         const int jj = t / n, a = t - jj * n;
         const int row = r0 + jj;
         const int src = row - k;
         T carry = T(0);
-        if (src >= 0) carry = (src >= base) ? push[(src - base) * n + a] : ring[(src % k) * n + a];
-        const T out = part1[t] + sw.sgn * (part2[t] + carry);
+        if (src >= 0) carry = (src >= base) ? push[(src - base) * n + a] : ring_in[(src % k) * n + a];
+        const T out = part1[t] + sgn * (part2[t] + carry);
         const long long idx = (long long)row * n + a;
         const T vi = vs[(row - base) * n + a];
-        switch (sw.fin) {
-          case FN_Q:
-            sw.qout[idx] = out;
-            acc[0] += (double)vi * (double)out;
-            break;
-          case FN_OUT64:
-            sw.out64[idx] = (double)out;
-            break;
-          case FN_R64: {
-            const double r = sw.bsub[idx] - (double)out;
-            sw.r64[idx] = r;
-            acc[0] += r * r;
-          } break;
-          case FN_Y0:
-            if (sw.m1) {
-              if (sw.out_to_user) sw.out64[idx] = (double)out;
-              else sw.zv[idx] = out;
-              acc[1] += (double)vi * (double)out;
-            } else {
-              sw.y0[idx] = out;
-            }
-            break;
-          default: {  // FN_YJ
-            const T zprev = (sw.j == 1) ? vi : sw.zv[idx];
-            const T zz = fma(sw.alpha_j, out, zprev);
-            if (!sw.last) sw.ynext[idx] = out;
-            if (sw.last && sw.out_to_user) sw.out64[idx] = (double)zz;
-            else sw.zv[idx] = zz;
-            if (sw.last) acc[1] += (double)sw.rcur_for_dot[idx] * (double)zz;
-          } break;
+        if constexpr (FIN == FN_Q) {
+          sw.qout[idx] = out;
+          acc0 += (double)vi * (double)out;
+        } else if constexpr (FIN == FN_OUT64) {
+          sw.out64[idx] = (double)out;
+        } else if constexpr (FIN == FN_R64) {
+          const double r = (va ? fb[t] : sw.bsub[idx]) - (double)out;
+          sw.r64[idx] = r;
+          acc0 += r * r;
+        } else if constexpr (FIN == FN_Y0) {
+          if (m1) {
+            if (out_to_user) sw.out64[idx] = (double)out;
+            else sw.zv[idx] = out;
+            acc1 += (double)vi * (double)out;
+          } else {
+            sw.y0[idx] = out;
+          }
+        } else {  // FN_YJ
+          const T zprev = (jpow == 1) ? vi : (va ? fz[t] : sw.zv[idx]);
+          const T zz = fma(alpha_j, out, zprev);
+          if (!last) sw.ynext[idx] = out;
+          if (last && out_to_user) sw.out64[idx] = (double)zz;
+          else sw.zv[idx] = zz;
+          if (last) acc1 += (double)(va ? fr[t] : sw.rcur_for_dot[idx]) * (double)zz;
         }
       }
-      __syncthreads();
-      // 6. keep the last k pushes for the next chunk
+      // 6. carry the pushes of the last k source rows into the other ring
+      //    buffer (read by the next chunk after its barriers)
       for (int t = tid; t < k * n; t += kThreads) {
         const int w = t / n, a = t - w * n;
         const int src = r1 - k + w;
-        if (src >= base && src >= 0) ring[(src % k) * n + a] = push[(src - base) * n + a];
+        if (src < 0) continue;
+        ring_out[(src % k) * n + a] = (src >= base) ? push[(src - base) * n + a] : ring_in[(src % k) * n + a];
       }
     }
+    this->consumed = consumed;
+    this->vissued = vissued;
+    this->vcons = vcons;
+    store_producer(q);
+    acc[0] += acc0;
+    acc[1] += acc1;
+    acc[2] += acc2;
+    if (failed) fail = true;
   }
 
   // ---- vector-only passes over the owned rows ------------------------------
@@ -472,11 +787,12 @@ template <typename MT>
 __device__ void solve_instance(Solver<MT>& Sv, int inst_id);
 
 template <typename MT>
-__global__ void __launch_bounds__(kThreads, 2) bt_persistent_kernel(const __grid_constant__ KParams P) {
+__global__ void __launch_bounds__(kThreads, 1) bt_persistent_kernel(const __grid_constant__ KParams P) {
   extern __shared__ __align__(128) char smem[];
   Solver<MT> Sv(P, smem);
   if (threadIdx.x == 0) {
     for (int i = 0; i < P.stages; ++i) mbar_init(&Sv.full[i], 1);
+    for (int i = 0; i < kVecSlots; ++i) mbar_init(&Sv.vbar[i], 1);
     fence_mbar_init();
   }
   __syncthreads();
@@ -536,6 +852,7 @@ __device__ void solve_instance(Solver<MT>& Sv, int inst_id) {
   }
   Sv.mats64[0] = P.D64 + d.off64;
   Sv.mats64[1] = P.O64 + d.off64;
+  Sv.set_chunk_counts();
 
   // workspace slot
   const int slot = (Sv.G > 1) ? 0 : (int)blockIdx.x;
@@ -557,11 +874,6 @@ __device__ void solve_instance(Solver<MT>& Sv, int inst_id) {
   const bool mixed = P.mixed != 0;
 
   // pattern of the inner iteration: A, B1, B2 x (m-1)
-  int pat_it[kMaxM + 2];
-  pat_it[0] = kKA;
-  pat_it[1] = kKB1;
-  for (int j = 1; j < m; ++j) pat_it[1 + j] = kKB2;
-  const int pat_it_len = m + 1;
 
   double acc[4];
   auto zero_acc = [&]() { acc[0] = acc[1] = acc[2] = acc[3] = 0.0; };
@@ -579,7 +891,7 @@ __device__ void solve_instance(Solver<MT>& Sv, int inst_id) {
       sw.zv = z; sw.j = j; sw.m = m; sw.alpha_j = (MT)P.alpha[j]; sw.last = (j == m - 1);
       sw.rcur_for_dot = rcur; sw.out_to_user = to_user; sw.out64 = xu;
       zero_acc();
-      Sv.run_sweep(sw, acc);
+      Sv.template sweep<kKB2, SV_Y, FN_YJ>(sw, acc);
       Sv.group_reduce(acc);
       if (Sv.fail) return;
     }
@@ -589,31 +901,29 @@ __device__ void solve_instance(Solver<MT>& Sv, int inst_id) {
   double resid = 0.0, errv = 0.0;
 
   if (P.op == kOpSpmv64 || (P.op == kOpSpmv32 && sizeof(MT) == 8)) {
-    const int pat[1] = {kKA64};
-    Sv.restart(pat, 1, 0);
+    Sv.restart(kKA64, 1, 0);
     Sweep<double> sw = {};
     sw.kind = kKA64; sw.stg = SV_VEC; sw.fin = FN_OUT64; sw.sgn = 1.0;
     sw.src64 = bu; sw.out64 = xu;
     zero_acc();
-    Sv.run_sweep(sw, acc);
+    Sv.template sweep<kKA64, SV_VEC, FN_OUT64>(sw, acc);
     Sv.group_reduce(acc);
   } else if (P.op == kOpSpmv32) {
-    const int pat[1] = {kKA};
-    Sv.restart(pat, 1, 0);
+    Sv.restart(kKA, 1, 0);
     Sweep<MT> sw = {};
     sw.kind = kKA; sw.stg = SV_VEC; sw.fin = FN_OUT64; sw.sgn = MT(1);
     sw.src64 = bu; sw.out64 = xu;
     zero_acc();
-    Sv.run_sweep(sw, acc);
+    Sv.template sweep<kKA, SV_VEC, FN_OUT64>(sw, acc);
     Sv.group_reduce(acc);
   } else if (P.op == kOpApply) {
-    Sv.restart(pat_it, pat_it_len, 1);
+    Sv.restart(kKA, m + 1, 1);
     Sweep<MT> sw = {};
     sw.kind = kKB1; sw.stg = SV_R_FIRST; sw.fin = FN_Y0; sw.sgn = MT(-1);
     sw.src64 = bu; sw.scale = 1.0; sw.r_cur = rb[0]; sw.write_r = true; sw.zero_x = false;
     sw.y0 = y0; sw.m1 = (m == 1); sw.out_to_user = true; sw.out64 = xu; sw.zv = z;
     zero_acc();
-    Sv.run_sweep(sw, acc);
+    Sv.template sweep<kKB1, SV_R_FIRST, FN_Y0>(sw, acc);
     Sv.group_reduce(acc);
     if (!Sv.fail) precond_sweeps_after_b1(rb[0], true);
   } else {
@@ -625,14 +935,14 @@ __device__ void solve_instance(Solver<MT>& Sv, int inst_id) {
       it_out = 0;
       st_out = kOK;
       // initial residual and z0 = M^-1 r0
-      Sv.restart(pat_it, pat_it_len, from_x0 ? 0 : 1);
+      Sv.restart(kKA, m + 1, from_x0 ? 0 : 1);
       if (from_x0) {
         Sweep<MT> sa = {};
         sa.kind = kKA; sa.stg = SV_VEC; sa.fin = FN_Q; sa.sgn = MT(1);
         sa.src64 = reinterpret_cast<const double*>(xv);  // float64 path only
         sa.qout = q;
         zero_acc();
-        Sv.run_sweep(sa, acc);
+        Sv.template sweep<kKA, SV_VEC, FN_Q>(sa, acc);
         Sv.group_reduce(acc);
         if (Sv.fail) { st_out = kErrTimeout; return; }
       }
@@ -643,7 +953,8 @@ __device__ void solve_instance(Solver<MT>& Sv, int inst_id) {
       else { s1.stg = SV_R_FIRST; s1.src64 = src64; s1.scale = scale; s1.zero_x = true; }
       s1.y0 = y0; s1.m1 = (m == 1); s1.out_to_user = false; s1.zv = z;
       zero_acc();
-      Sv.run_sweep(s1, acc);
+      if (from_x0) Sv.template sweep<kKB1, SV_R_X0, FN_Y0>(s1, acc);
+      else Sv.template sweep<kKB1, SV_R_FIRST, FN_Y0>(s1, acc);
       Sv.group_reduce(acc);
       if (Sv.fail) { st_out = kErrTimeout; return; }
       if (acc[3] > 0) { st_out = kErrTimeout; return; }
@@ -677,7 +988,7 @@ __device__ void solve_instance(Solver<MT>& Sv, int inst_id) {
         sa.z = z; sa.p_old = pb[(k + 1) & 1]; sa.p_cur = pb[k & 1];
         sa.beta = (MT)beta; sa.first = (k == 1); sa.qout = q;
         zero_acc();
-        Sv.run_sweep(sa, acc);
+        Sv.template sweep<kKA, SV_P, FN_Q>(sa, acc);
         Sv.group_reduce(acc);
         if (Sv.fail || acc[3] > 0) { st_out = kErrTimeout; it_out = k - 1; return; }
         const double pq = acc[0];
@@ -691,7 +1002,7 @@ __device__ void solve_instance(Solver<MT>& Sv, int inst_id) {
         sb.x = xv; sb.p_in = pb[k & 1];
         sb.y0 = y0; sb.m1 = (m == 1); sb.out_to_user = false; sb.zv = z;
         zero_acc();
-        Sv.run_sweep(sb, acc);
+        Sv.template sweep<kKB1, SV_R_UPD, FN_Y0>(sb, acc);
         Sv.group_reduce(acc);
         if (Sv.fail || acc[3] > 0) { st_out = kErrTimeout; it_out = k; return; }
         rr = acc[2];
@@ -741,13 +1052,12 @@ __device__ void solve_instance(Solver<MT>& Sv, int inst_id) {
         for (outer = 0;; ++outer) {
           const bool have_r64 = (outer > 0) || P.use_x0;
           if (have_r64) {
-            const int pat[1] = {kKA64};
-            Sv.restart(pat, 1, 0);
+            Sv.restart(kKA64, 1, 0);
             Sweep<double> sw = {};
             sw.kind = kKA64; sw.stg = SV_VEC; sw.fin = FN_R64; sw.sgn = 1.0;
             sw.src64 = xu; sw.bsub = bu; sw.r64 = r64;
             zero_acc();
-            Sv.run_sweep(sw, acc);
+            Sv.template sweep<kKA64, SV_VEC, FN_R64>(sw, acc);
             Sv.group_reduce(acc);
             if (Sv.fail || acc[3] > 0) { st = kErrTimeout; break; }
             nr = sqrt(acc[0]);
