@@ -16,7 +16,14 @@ namespace bt {
 constexpr int kMaxM = 8;
 constexpr int kMaxBlock = 64;
 constexpr int kMaxStages = 8;
-constexpr int kThreads = 256;           // threads per persistent CTA
+#ifndef BT_THREADS
+#define BT_THREADS 256
+#endif
+#ifndef BT_LEADER_WARP
+#define BT_LEADER_WARP 0
+#endif
+constexpr int kThreads = BT_THREADS;    // threads per persistent CTA
+constexpr int kLeaderTid = 32 * BT_LEADER_WARP;  // thread that issues the bulk copies
 constexpr int kMaxChunkElems = 512;     // rows-per-chunk cap: R * n <= 512
 
 enum Status : int {

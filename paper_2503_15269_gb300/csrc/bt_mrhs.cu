@@ -129,13 +129,13 @@ struct MSolver {
     if (fail) return;
     __syncthreads();
     int* flag = reinterpret_cast<int*>(sm);
+    const int par = bar_count & 1;  // every thread keeps the barrier count
+    ++bar_count;
     if (threadIdx.x == 0) {
-      const int par = bar_count & 1;
       double* slot = P.red + ((size_t)par * G + g) * kJ;
       for (int j = 0; j < kJ; ++j) slot[j] = colv[j];
       __threadfence();
       atomicAdd(P.bar, 1u);
-      ++bar_count;
       const unsigned target = (unsigned)G * (unsigned)bar_count;
       int bad = 0;
       while (ld_acquire_u32(P.bar) < target) {
@@ -153,7 +153,6 @@ struct MSolver {
       return;
     }
     if (threadIdx.x < kJ) {
-      const int par = (bar_count - 1) & 1;
       double t = 0.0;
       for (int gg = 0; gg < G; ++gg) t += reinterpret_cast<volatile double*>(P.red)[((size_t)par * G + gg) * kJ + threadIdx.x];
       colv[threadIdx.x] = t;

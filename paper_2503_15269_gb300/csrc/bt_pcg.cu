@@ -56,7 +56,7 @@ __device__ __forceinline__ Geo geo_of(int kind, int stage_bytes, int bs_bytes, i
 // Smem carve-up (bytes).  Fixed part first, then the stages (128-aligned).
 constexpr int kSmCtl = 0;                               // ints
 constexpr int kSmRed = 128;                             // double [8 warps][4]
-constexpr int kSmBc = kSmRed + 8 * 4 * 8;               // double bcast[8]
+constexpr int kSmBc = kSmRed + (kThreads / 32) * 4 * 8;  // double bcast[8]
 constexpr int kVsElems = kMaxChunkElems + 4 * kMaxBlock;
 constexpr int kSmRing = kSmBc + 8 * 8;                  // T ring[2 buffers][2][64]
 constexpr int kSmVs = kSmRing + 2 * 2 * kMaxBlock * 8;  // T vs[2 buffers][kVsElems]
@@ -408,7 +408,7 @@ struct Solver {
     p_slot = start_slot;
     p_chunk = 0;
     Producer q = producer();
-    for (int i = 0; i < S; ++i) q.step(tid == 0);
+    for (int i = 0; i < S; ++i) q.step(tid == kLeaderTid);
     store_producer(q);
   }
 
@@ -567,7 +567,7 @@ struct Solver {
     char* const stages = this->stages;
     char* const vring = this->vring;
     unsigned consumed = this->consumed, vissued = this->vissued, vcons = this->vcons;
-    const bool leader = (threadIdx.x == 0);
+    const bool leader = (threadIdx.x == kLeaderTid);
     const int tid = threadIdx.x;
     const int R = q.rows(KIND);
     const int bse = (KIND == kKA64) ? bs64 : bs;
@@ -790,7 +790,7 @@ template <typename MT>
 __global__ void __launch_bounds__(kThreads, 1) bt_persistent_kernel(const __grid_constant__ KParams P) {
   extern __shared__ __align__(128) char smem[];
   Solver<MT> Sv(P, smem);
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == kLeaderTid) {
     for (int i = 0; i < P.stages; ++i) mbar_init(&Sv.full[i], 1);
     for (int i = 0; i < kVecSlots; ++i) mbar_init(&Sv.vbar[i], 1);
     fence_mbar_init();

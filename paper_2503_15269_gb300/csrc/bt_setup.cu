@@ -2,87 +2,87 @@
 // every instance, plus the layout copies of D and O, and the adjoint's block
 // outer products.
 //
-//   K0  copy D_i, O_i (row-major, caller's) into the library layout
-//       (column-major, 16-byte padded slots) in float64 and/or float32
-//   K1  D_i = L_i L_i^T by Cholesky in float64, W = L_i^-1, D_i^-1 = W^T W
-//       (float64 for the float64 handle; float32 from the float64 factor for
-//       the mixed handle)
+//   K1  (one warp per block row) copy D_i, O_i (row-major, caller's) into the
+//       library layout (column-major, 16-byte padded slots) in float64 and/or
+//       float32; D_i = L_i L_i^T by Cholesky in float64, W = L_i^-1,
+//       D_i^-1 = W^T W (float64 for the float64 handle; float32 from the
+//       float64 factor for the mixed handle)
 //   K2  E_i = D_i^-1 O_i D_{i+1}^-1
 //   K3  Hd_i = E_{i-1}^T O_{i-1} + E_i O_i^T, Hu_i = E_i O_{i+1},
 //       Hl_i = E_{i+1}^T O_i^T          (only for polynomial order m >= 2)
-// One CTA per block row; block products run out of shared memory.
+// K2, K3: one CTA per block row; block products out of shared memory with
+// 4 x 4 register tiles.
 #include "bt_common.cuh"
 
 namespace bt {
 
-// ---------------------------------------------------------------- K0
-__global__ void k_copy_blocks(const __grid_constant__ SetupParams P) {
-  const long long gr = blockIdx.x;
-  if (gr >= P.nrows) return;
-  const RowRef rr = P.rows[gr];
-  const InstDesc d = P.inst[rr.inst];
-  const int n = d.n, i = rr.row;
-  const double* Du = P.D + P.d_off[rr.inst] + (long long)i * n * n;
-  const bool hasO = i < d.N - 1;
-  const double* Ou = hasO ? P.O + P.o_off[rr.inst] + (long long)i * n * n : nullptr;
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-    const int a = t / n, c = t - a * n;  // row-major source element (a, c)
-    const double dv = Du[t];
-    const double ov = hasO ? Ou[t] : 0.0;
-    const long long o64 = d.off64 + (long long)i * d.bs64 + (long long)c * n + a;
-    const long long o32 = d.off32 + (long long)i * d.bs32 + (long long)c * n + a;
-    P.D64[o64] = dv;
-    P.O64[o64] = ov;
-    if (P.want32) {
-      P.D32[o32] = (float)dv;
-      P.O32[o32] = (float)ov;
-    }
-  }
-}
-
-// ---------------------------------------------------------------- K1
-// Dense Cholesky of one block in shared memory, then the inverse.
+// ---------------------------------------------------------------- K0+K1
+// One warp per block row: load D_i (and O_i) once, write the library copies
+// (column-major; float64 and, for mixed handles, float32), factor D_i by
+// Cholesky in float64, invert the factor and form D_i^-1 = W^T W in MT.
+// Warp-synchronous: no CTA barriers, so a CTA hosts several block rows.
 template <typename MT>
-__global__ void k_chol_inv(const __grid_constant__ SetupParams P) {
+__global__ void k_factor(const __grid_constant__ SetupParams P, int wpc, int warp_bytes) {
   extern __shared__ __align__(16) char smraw[];
-  const long long gr = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long gr = (long long)blockIdx.x * wpc + warp;
   if (gr >= P.nrows) return;
   const RowRef rr = P.rows[gr];
   const InstDesc d = P.inst[rr.inst];
-  const int n = d.n, i = rr.row;
-  double* A = reinterpret_cast<double*>(smraw);              // n*n, row-major lower factor
-  MT* W = reinterpret_cast<MT*>(smraw + (size_t)n * n * 8);  // n*n
-  __shared__ int bad;
-  if (threadIdx.x == 0) bad = 0;
-  const double* Du = P.D + P.d_off[rr.inst] + (long long)i * n * n;
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) A[t] = Du[t];
-  __syncthreads();
-  for (int j = 0; j < n; ++j) {
-    if (threadIdx.x == 0) {
-      const double piv = A[j * n + j];
-      if (!(piv > 0.0) || !isfinite(piv)) {
-        bad = 1;
-        P.fail_piv[gr] = piv;
-        atomicMin(P.fail_key, ((unsigned long long)rr.inst << 32) | (unsigned)i);
-      } else {
-        A[j * n + j] = sqrt(piv);
+  const int n = d.n, i = rr.row, nn = n * n;
+  double* A = reinterpret_cast<double*>(smraw + (size_t)warp * warp_bytes);  // 16 maxn^2 bytes per warp
+  double* T = A + nn;
+  const double* Du = P.D + P.d_off[rr.inst] + (long long)i * nn;
+  const bool hasO = i < d.N - 1;
+  for (int t = lane; t < nn; t += 32) A[t] = Du[t];
+  if (hasO) {
+    const double* Ou = P.O + P.o_off[rr.inst] + (long long)i * nn;
+    for (int t = lane; t < nn; t += 32) T[t] = Ou[t];
+  }
+  __syncwarp();
+  {
+    double* D64 = P.D64 + d.off64 + (long long)i * d.bs64;
+    double* O64 = P.O64 + d.off64 + (long long)i * d.bs64;
+    float* D32 = P.want32 ? P.D32 + d.off32 + (long long)i * d.bs32 : nullptr;
+    float* O32 = P.want32 ? P.O32 + d.off32 + (long long)i * d.bs32 : nullptr;
+    for (int t = lane; t < nn; t += 32) {  // destination column-major index t = c*n + a
+      const int c = t / n, a = t - c * n;
+      const double dv = A[a * n + c];
+      D64[t] = dv;
+      if (D32) D32[t] = (float)dv;
+      if (hasO) {
+        const double ov = T[a * n + c];
+        O64[t] = ov;
+        if (O32) O32[t] = (float)ov;
       }
     }
-    __syncthreads();
-    if (bad) return;
-    const double ljj = A[j * n + j];
-    for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) A[r * n + j] /= ljj;
-    __syncthreads();
-    // trailing update of the lower triangle: A[r][c] -= L[r][j] L[c][j], j < c <= r
-    const int m = n - j - 1;
-    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-      const int r = j + 1 + t / m, c = j + 1 + t % m;
-      if (c <= r) A[r * n + c] -= A[r * n + j] * A[c * n + j];
-    }
-    __syncthreads();
   }
-  // W = L^-1, one column per thread (forward substitution in MT precision)
-  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+  __syncwarp();
+  // Cholesky D = L L^T in place (lower triangle of A, row-major), float64
+  for (int j = 0; j < n; ++j) {
+    const double piv = A[j * n + j];
+    if (!(piv > 0.0) || !isfinite(piv)) {
+      if (lane == 0) {
+        P.fail_piv[gr] = piv;
+        atomicMin(P.fail_key, ((unsigned long long)rr.inst << 32) | (unsigned)i);
+      }
+      return;
+    }
+    const double ljj = sqrt(piv);
+    __syncwarp();
+    for (int r = j + 1 + lane; r < n; r += 32) A[r * n + j] /= ljj;
+    if (lane == 0) A[j * n + j] = ljj;
+    __syncwarp();
+    const int m = n - j - 1;
+    for (int t = lane; t < m * m; t += 32) {
+      const int r = j + 1 + t / m, c = j + 1 + t % m;
+      if (c <= r) A[r * n + c] = fma(-A[r * n + j], A[c * n + j], A[r * n + c]);
+    }
+    __syncwarp();
+  }
+  // W = L^-1 (one column per lane, forward substitution in MT)
+  MT* W = reinterpret_cast<MT*>(T);
+  for (int c = lane; c < n; c += 32) {
     for (int r = 0; r < c; ++r) W[r * n + c] = MT(0);
     W[c * n + c] = MT(1) / (MT)A[c * n + c];
     for (int r = c + 1; r < n; ++r) {
@@ -91,12 +91,11 @@ __global__ void k_chol_inv(const __grid_constant__ SetupParams P) {
       W[r * n + c] = -acc / (MT)A[r * n + r];
     }
   }
-  __syncthreads();
-  // D^-1 = W^T W (symmetric: compute a >= b and mirror)
+  __syncwarp();
   MT* out = (sizeof(MT) == 8) ? reinterpret_cast<MT*>(P.Dinv64 + d.off64 + (long long)i * d.bs64)
                               : reinterpret_cast<MT*>(P.Dinv32 + d.off32 + (long long)i * d.bs32);
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-    const int a = t / n, b = t % n;
+  for (int t = lane; t < nn; t += 32) {
+    const int a = t / n, b = t - a * n;
     if (a < b) continue;
     MT acc = MT(0);
     for (int r = a; r < n; ++r) acc = fma(W[r * n + a], W[r * n + b], acc);
@@ -118,6 +117,39 @@ __device__ void sm_gemm(MT* C, const MT* A, bool tA, const MT* B, bool tB, int n
       acc = fma(av, bv, acc);
     }
     C[t] = acc;
+  }
+}
+
+// 4 x 4 register tiles when n % 4 == 0 (else the plain loop above).
+template <typename MT>
+__device__ void sm_gemm4(MT* C, const MT* A, bool tA, const MT* B, bool tB, int n, bool accumulate) {
+  if (n % 4 != 0) {
+    sm_gemm(C, A, tA, B, tB, n, accumulate);
+    return;
+  }
+  const int q = n / 4;
+  for (int t = threadIdx.x; t < q * q; t += blockDim.x) {
+    const int a0 = (t / q) * 4, b0 = (t % q) * 4;
+    MT acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[r][c] = accumulate ? C[(a0 + r) * n + b0 + c] : MT(0);
+    for (int k = 0; k < n; ++k) {
+      MT av[4], bv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) av[r] = tA ? A[k * n + a0 + r] : A[(a0 + r) * n + k];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) bv[c] = tB ? B[(b0 + c) * n + k] : B[k * n + b0 + c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) C[(a0 + r) * n + b0 + c] = acc[r][c];
   }
 }
 
@@ -176,11 +208,11 @@ __global__ void k_E(const __grid_constant__ SetupParams P) {
   sm_load(s0, blk(M.O, i), n);
   sm_load(s1, blk(M.Dinv, i + 1), n);
   __syncthreads();
-  sm_gemm(s2, s0, false, s1, false, n, false);  // T = O_i D_{i+1}^-1
+  sm_gemm4(s2, s0, false, s1, false, n, false);  // T = O_i D_{i+1}^-1
   __syncthreads();
   sm_load(s0, blk(M.Dinv, i), n);
   __syncthreads();
-  sm_gemm(s1, s0, false, s2, false, n, false);  // E_i = D_i^-1 T
+  sm_gemm4(s1, s0, false, s2, false, n, false);  // E_i = D_i^-1 T
   __syncthreads();
   sm_store(const_cast<MT*>(blk(M.E, i)), s1, n);
 }
@@ -205,7 +237,7 @@ __global__ void k_H(const __grid_constant__ SetupParams P) {
     sm_load(sa, blk(M.E, i - 1), n);
     sm_load(sb, blk(M.O, i - 1), n);
     __syncthreads();
-    sm_gemm(sc, sa, true, sb, false, n, false);
+    sm_gemm4(sc, sa, true, sb, false, n, false);
     acc = true;
     __syncthreads();
   }
@@ -213,7 +245,7 @@ __global__ void k_H(const __grid_constant__ SetupParams P) {
     sm_load(sa, blk(M.E, i), n);
     sm_load(sb, blk(M.O, i), n);
     __syncthreads();
-    sm_gemm(sc, sa, false, sb, true, n, acc);
+    sm_gemm4(sc, sa, false, sb, true, n, acc);
     acc = true;
     __syncthreads();
   }
@@ -224,7 +256,7 @@ __global__ void k_H(const __grid_constant__ SetupParams P) {
     sm_load(sa, blk(M.E, i), n);
     sm_load(sb, blk(M.O, i + 1), n);
     __syncthreads();
-    sm_gemm(sc, sa, false, sb, false, n, false);
+    sm_gemm4(sc, sa, false, sb, false, n, false);
     __syncthreads();
     sm_store(const_cast<MT*>(blk(M.Hu, i)), sc, n);
     __syncthreads();
@@ -232,7 +264,7 @@ __global__ void k_H(const __grid_constant__ SetupParams P) {
     sm_load(sa, blk(M.E, i + 1), n);
     sm_load(sb, blk(M.O, i), n);
     __syncthreads();
-    sm_gemm(sc, sa, true, sb, true, n, false);
+    sm_gemm4(sc, sa, true, sb, true, n, false);
     __syncthreads();
     sm_store(const_cast<MT*>(blk(M.Hl, i)), sc, n);
   }
@@ -270,26 +302,29 @@ extern "C" cudaError_t bt_launch_setup(const bt::SetupParams* P, int mixed, int 
   const long long nb = P->nrows;
   if (nb == 0) return cudaSuccess;
   const dim3 grid((unsigned)nb);
-  bt::k_copy_blocks<<<grid, 128, 0, st>>>(*P);
-  cudaError_t err = cudaGetLastError();
-  if (err != cudaSuccess) return err;
-  const int sm_chol = maxn * maxn * 8 + maxn * maxn * (mixed ? 4 : 8);
+  cudaError_t err;
+  const int per_warp = 16 * maxn * maxn;
+  int wpc = (200 * 1024) / per_warp;
+  if (wpc > 8) wpc = 8;
+  if (wpc < 1) wpc = 1;
+  const dim3 fgrid((unsigned)((nb + wpc - 1) / wpc));
+  const int sm_fac = wpc * per_warp;
   const int msz = mixed ? 4 : 8;
   const int sm_prod = 3 * maxn * maxn * msz;
   if (mixed) {
-    cudaFuncSetAttribute(bt::k_chol_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_chol);
+    cudaFuncSetAttribute(bt::k_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_fac);
     cudaFuncSetAttribute(bt::k_E<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_prod);
     cudaFuncSetAttribute(bt::k_H<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_prod);
-    bt::k_chol_inv<float><<<grid, 128, sm_chol, st>>>(*P);
+    bt::k_factor<float><<<fgrid, 32 * wpc, sm_fac, st>>>(*P, wpc, per_warp);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     bt::k_E<float><<<grid, 128, sm_prod, st>>>(*P);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     if (m >= 2) bt::k_H<float><<<grid, 128, sm_prod, st>>>(*P);
   } else {
-    cudaFuncSetAttribute(bt::k_chol_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_chol);
+    cudaFuncSetAttribute(bt::k_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_fac);
     cudaFuncSetAttribute(bt::k_E<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_prod);
     cudaFuncSetAttribute(bt::k_H<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_prod);
-    bt::k_chol_inv<double><<<grid, 128, sm_chol, st>>>(*P);
+    bt::k_factor<double><<<fgrid, 32 * wpc, sm_fac, st>>>(*P, wpc, per_warp);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     bt::k_E<double><<<grid, 128, sm_prod, st>>>(*P);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
