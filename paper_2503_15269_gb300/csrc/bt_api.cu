@@ -271,7 +271,7 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
   int smem_optin = 0;
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
   const int fixed = bt_persistent_smem_fixed();
-  int vslot = mixed ? 12 * 1024 : 24 * 1024;  // one vector-ring slot
+  int vslot = mixed ? 9 * 1024 : 18 * 1024;  // one vector-ring slot (largest chunk plan)
   int cps = h->prm.ctas_per_sm > 0 ? h->prm.ctas_per_sm : 1;
   const int per_cta = (int)std::min<long long>(smem_optin, (228 * 1024) / cps - 1024);
   int S = (int)((per_cta - fixed - 3 * vslot) / sb);

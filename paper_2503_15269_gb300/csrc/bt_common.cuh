@@ -167,6 +167,13 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p) {
   return *reinterpret_cast<const volatile int*>(p);
 }
 
+// floor(t / d) for 0 <= t < 16384 and 1 <= d <= 64 without an integer divide:
+// (t + 1/2) / d is at least 1/(2d) away from an integer, far more than the
+// float rounding error at these sizes.
+__device__ __forceinline__ int qdiv(int t, float inv_d) {
+  return __float2int_rz(__fmul_rn(__int2float_rn(t) + 0.5f, inv_d));
+}
+
 template <typename T>
 __device__ __forceinline__ bool is_finite(T v) {
   return isfinite(v);

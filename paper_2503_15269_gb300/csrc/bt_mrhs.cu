@@ -71,43 +71,50 @@ __device__ __forceinline__ void cp_blockd(double* dst, const double* src, int co
   for (int t = threadIdx.x * 2; t < count; t += kMThreads * 2) cp16(dst + t, src + t);
 }
 
+// 4 consecutive elements from shared memory (16-byte aligned for float,
+// two 16-byte loads for double).
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+  const double2 q0 = *reinterpret_cast<const double2*>(p);
+  const double2 q1 = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+}
+
 // acc[r][c] += sum_k M(a0+r, k) X(k, j0+c): M column-major n x n, X n x J.
 template <typename T>
 __device__ __forceinline__ void prod_direct(const T* __restrict__ M, const T* __restrict__ X, int n, int a0, int j0,
                                             T acc[4][4]) {
 #pragma unroll 4
   for (int k = 0; k < n; ++k) {
-    const T* mc = M + k * n + a0;
-    const T* xr = X + k * kJ + j0;
-    const T m0 = mc[0], m1 = mc[1], m2 = mc[2], m3 = mc[3];
-    const T x0 = xr[0], x1 = xr[1], x2 = xr[2], x3 = xr[3];
-    acc[0][0] = fma(m0, x0, acc[0][0]); acc[0][1] = fma(m0, x1, acc[0][1]);
-    acc[0][2] = fma(m0, x2, acc[0][2]); acc[0][3] = fma(m0, x3, acc[0][3]);
-    acc[1][0] = fma(m1, x0, acc[1][0]); acc[1][1] = fma(m1, x1, acc[1][1]);
-    acc[1][2] = fma(m1, x2, acc[1][2]); acc[1][3] = fma(m1, x3, acc[1][3]);
-    acc[2][0] = fma(m2, x0, acc[2][0]); acc[2][1] = fma(m2, x1, acc[2][1]);
-    acc[2][2] = fma(m2, x2, acc[2][2]); acc[2][3] = fma(m2, x3, acc[2][3]);
-    acc[3][0] = fma(m3, x0, acc[3][0]); acc[3][1] = fma(m3, x1, acc[3][1]);
-    acc[3][2] = fma(m3, x2, acc[3][2]); acc[3][3] = fma(m3, x3, acc[3][3]);
+    T mv[4], xv[4];
+    ld4(M + k * n + a0, mv);
+    ld4(X + k * kJ + j0, xv);
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[r][c] = fma(mv[r], xv[c], acc[r][c]);
   }
 }
 
-// acc[r][c] += sum_k M(k, a0+r) X(k, j0+c): the transposed block.
+// acc[r][c] += sum_k M(k, a0+r) X(k, j0+c): the transposed block (n % 4 == 0).
 template <typename T>
 __device__ __forceinline__ void prod_trans(const T* __restrict__ M, const T* __restrict__ X, int n, int a0, int j0,
                                            T acc[4][4]) {
-#pragma unroll 2
-  for (int k = 0; k < n; ++k) {
-    const T* xr = X + k * kJ + j0;
-    const T x0 = xr[0], x1 = xr[1], x2 = xr[2], x3 = xr[3];
+  for (int k = 0; k < n; k += 4) {
+    T mr[4][4], xr[4][4];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const T mv = M[(a0 + r) * n + k];
-      acc[r][0] = fma(mv, x0, acc[r][0]);
-      acc[r][1] = fma(mv, x1, acc[r][1]);
-      acc[r][2] = fma(mv, x2, acc[r][2]);
-      acc[r][3] = fma(mv, x3, acc[r][3]);
-    }
+    for (int r = 0; r < 4; ++r) ld4(M + (a0 + r) * n + k, mr[r]);   // M(k..k+3, a0+r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ld4(X + (k + q) * kJ + j0, xr[q]);  // X(k+q, j0..j0+3)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fma(mr[r][q], xr[q][c], acc[r][c]);
   }
 }
 

@@ -123,7 +123,7 @@ extern "C" bt_status bt_pcg_solve_noalloc(int N, int n, const double* D, const d
   long long sb = p->stage_kb > 0 ? (long long)p->stage_kb * 1024 : 80 * 1024;
   sb = std::max(sb, rup(std::max(5 * bsb, 3 * (long long)bs64 * 8), 128));
   const int fixed = bt_persistent_smem_fixed();
-  int vslot = mixed ? 12 * 1024 : 24 * 1024;
+  int vslot = mixed ? 9 * 1024 : 18 * 1024;
   const long long per_cta = std::min<long long>(smem_optin, 228 * 1024 - 1024);
   int S = (int)((per_cta - fixed - 3 * vslot) / sb);
   if (S < 2) {

@@ -142,26 +142,45 @@ __device__ __forceinline__ void dcol2(const T* __restrict__ M, int a, const T* _
 }
 
 // One output of M^T v: column a of M (contiguous) dotted with v.  The walk
-// along the column starts at a lane-dependent offset so that the 8 lanes of a
-// shared-memory phase fall in different banks.
+// along the column starts at an offset chosen per lane so that the 8 lanes
+// of a 128-bit shared-memory phase (consecutive a) fall in distinct bank
+// groups: word n*a + 4*q sits in bank group (n/4*a + q) mod 8, already
+// distinct for n = 4 mod 8; n = 24 adds (a >> 2) & 1 and n = 48 (a >> 1) & 3.
+template <int NB>
+__device__ __forceinline__ int tr_rot(int a) {
+  if constexpr (NB % 8 == 4) return 0;
+  else if constexpr (NB % 32 == 24 || NB % 32 == 8) return (a >> 2) & 1;
+  else return (a >> 1) & 3;
+}
+
 template <int NB, typename T>
-__device__ __forceinline__ T dtr1(const T* __restrict__ M, int a, const T* __restrict__ v, int rot) {
-  using V = typename Vec2<T>::type;
+__device__ __forceinline__ T dtr1(const T* __restrict__ M, int a, const T* __restrict__ v, int /*unused*/) {
   constexpr int Q = NB / 4;
   const T* col = M + a * NB;
+  const int rot = tr_rot<NB>(a) % Q;
   T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     int qq = q + rot;
     if (qq >= Q) qq -= Q;
-    const V m0 = *reinterpret_cast<const V*>(col + 4 * qq);
-    const V m1 = *reinterpret_cast<const V*>(col + 4 * qq + 2);
-    const V v0 = *reinterpret_cast<const V*>(v + 4 * qq);
-    const V v1 = *reinterpret_cast<const V*>(v + 4 * qq + 2);
-    s0 = fma(m0.x, v0.x, s0);
-    s1 = fma(m0.y, v0.y, s1);
-    s2 = fma(m1.x, v1.x, s2);
-    s3 = fma(m1.y, v1.y, s3);
+    if constexpr (sizeof(T) == 4) {
+      const float4 m = *reinterpret_cast<const float4*>(col + 4 * qq);
+      const float4 w = *reinterpret_cast<const float4*>(v + 4 * qq);
+      s0 = fma(m.x, w.x, s0);
+      s1 = fma(m.y, w.y, s1);
+      s2 = fma(m.z, w.z, s2);
+      s3 = fma(m.w, w.w, s3);
+    } else {
+      using V = typename Vec2<T>::type;
+      const V m0 = *reinterpret_cast<const V*>(col + 4 * qq);
+      const V m1 = *reinterpret_cast<const V*>(col + 4 * qq + 2);
+      const V v0 = *reinterpret_cast<const V*>(v + 4 * qq);
+      const V v1 = *reinterpret_cast<const V*>(v + 4 * qq + 2);
+      s0 = fma(m0.x, v0.x, s0);
+      s1 = fma(m0.y, v0.y, s1);
+      s2 = fma(m1.x, v1.x, s2);
+      s3 = fma(m1.y, v1.y, s3);
+    }
   }
   return (s0 + s1) + (s2 + s3);
 }
@@ -183,7 +202,6 @@ __device__ __forceinline__ void chunk_products(const T* __restrict__ stg, int R,
     const int nd2 = nr * hp;                          // pairs of direct outputs
     const int np = (KIND == kKB2) ? (nr + h) * hp : (nr + h) * n;
     const int ntask = 2 * nd2 + np;
-    const int rot = (tid & 7) % (NB / 4);
     for (int t = tid; t < ntask; t += kThreads) {
       if (t < nd2) {
         const int jj = t / hp, a = 2 * (t - jj * hp);
@@ -205,7 +223,7 @@ __device__ __forceinline__ void chunk_products(const T* __restrict__ stg, int R,
           dcol2<NB>(a2 + (size_t)jj * bse, a, vs + jj * n, push[jj * n + a], push[jj * n + a + 1]);
         } else {
           const int jj = t3 / n, a = t3 - jj * n;
-          push[jj * n + a] = dtr1<NB>(a1 + (size_t)jj * bse, a, vs + jj * n, rot);
+          push[jj * n + a] = dtr1<NB>(a1 + (size_t)jj * bse, a, vs + jj * n, 0);
         }
       }
     }
@@ -235,6 +253,15 @@ __device__ __forceinline__ void chunk_products(const T* __restrict__ stg, int R,
       }
     }
   }
+}
+
+__device__ __forceinline__ float4 ld4f(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4f(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float4 fma4(float a, float4 x, float4 y) {
+  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+__device__ __forceinline__ double dot4d(float4 a, float4 b) {
+  return (double)a.x * (double)b.x + (double)a.y * (double)b.y + (double)a.z * (double)b.z + (double)a.w * (double)b.w;
 }
 
 template <typename MT>
@@ -571,6 +598,7 @@ struct Solver {
     const int tid = threadIdx.x;
     const int R = q.rows(KIND);
     const int bse = (KIND == kKA64) ? bs64 : bs;
+    const float inv_n = 1.0f / (float)n;
     T* ringb = reinterpret_cast<T*>(sm + kSmRing);           // [2][k][n]
     T* vsb = reinterpret_cast<T*>(sm + kSmVs);               // [2][kVsElems]
     T* part1 = reinterpret_cast<T*>(sm + kSmParts);
@@ -580,6 +608,7 @@ struct Solver {
     const int nc = (e - s + R - 1) / R;
     const VecPlan vp = vec_plan<STG, FIN, T>(sw);
     const bool va = vec_plan_ok(vp, n, R, k, kHalo, VSB);
+    const bool vec4 = (sizeof(T) == 4) && va && ((n & 3) == 0);
     // staged inputs, copied to registers
     const T alpha = sw.alpha, beta = sw.beta, alpha_j = sw.alpha_j;
     const bool first = sw.first, m1 = sw.m1, last = sw.last, out_to_user = sw.out_to_user;
@@ -643,8 +672,39 @@ struct Solver {
       const double* sd0 = reinterpret_cast<const double*>(vslot);
       // 2. stage the vector rows [base, vend) with the fused PCG updates
       const int nv = (vend - base) * n;
+      bool staged4 = false;
+      if constexpr (sizeof(T) == 4 && (STG == SV_P || STG == SV_R_UPD || STG == SV_Y)) {
+        if (vec4) {  // 4 consecutive elements of one row per iteration
+          staged4 = true;
+          for (int t = 4 * tid; t < nv; t += 4 * kThreads) {
+            const int rr = qdiv(t, inv_n);
+            const int a = t - rr * n;
+            const int row = base + rr;
+            const long long idx = (long long)row * n + a;
+            const bool own = row >= r0 && row < r1;
+            const int lo = t - h * n;
+            float4 v;
+            if constexpr (STG == SV_P) {
+              const float4 zz = ld4f(sv0 + t);
+              v = first ? zz : fma4(beta, ld4f(sv1 + t), zz);
+              if (own) st4f(sw.p_cur + idx, v);
+            } else if constexpr (STG == SV_R_UPD) {
+              v = fma4(-alpha, ld4f(sv1 + t), ld4f(sv0 + t));
+              if (own) {
+                st4f(sw.r_cur + idx, v);
+                st4f(sw.x + idx, fma4(alpha, ld4f(sv3 + lo), ld4f(sv2 + lo)));
+                acc2 += dot4d(v, v);
+              }
+            } else {
+              v = ld4f(sv0 + t);
+            }
+            st4f(vs + t, v);
+          }
+        }
+      }
+      if (!staged4)
       for (int t = tid; t < nv; t += kThreads) {
-        const int rr = t / n;
+        const int rr = qdiv(t, inv_n);
         const int a = t - rr * n;
         const int row = base + rr;
         const long long idx = (long long)row * n + a;
@@ -718,8 +778,44 @@ struct Solver {
       const T* fz = (iz == 1) ? sv1 : ((iz == 2) ? sv2 : sv3);
       const T* fr = (ir == 1) ? sv1 : ((ir == 2) ? sv2 : sv3);
       const double* fb = reinterpret_cast<const double*>((const char*)fz);
+      bool fin4 = false;
+      if constexpr (sizeof(T) == 4 && (FIN == FN_Q || FIN == FN_Y0 || FIN == FN_YJ)) {
+        if (vec4 && !out_to_user) {
+          fin4 = true;
+          for (int t = 4 * tid; t < nd; t += 4 * kThreads) {
+            const int jj = qdiv(t, inv_n), a = t - jj * n;
+            const int row = r0 + jj;
+            const int src = row - k;
+            float4 carry = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (src >= 0) carry = (src >= base) ? ld4f(push + (src - base) * n + a) : ld4f(ring_in + (src % k) * n + a);
+            const float4 p1 = ld4f(part1 + t), p2 = ld4f(part2 + t);
+            const float4 out = make_float4(p1.x + sgn * (p2.x + carry.x), p1.y + sgn * (p2.y + carry.y),
+                                           p1.z + sgn * (p2.z + carry.z), p1.w + sgn * (p2.w + carry.w));
+            const long long idx = (long long)row * n + a;
+            const float4 vi = ld4f(vs + (row - base) * n + a);
+            if constexpr (FIN == FN_Q) {
+              st4f(sw.qout + idx, out);
+              acc0 += dot4d(vi, out);
+            } else if constexpr (FIN == FN_Y0) {
+              if (m1) {
+                st4f(sw.zv + idx, out);
+                acc1 += dot4d(vi, out);
+              } else {
+                st4f(sw.y0 + idx, out);
+              }
+            } else {
+              const float4 zprev = (jpow == 1) ? vi : ld4f(fz + t);
+              const float4 zz = fma4(alpha_j, out, zprev);
+              if (!last) st4f(sw.ynext + idx, out);
+              st4f(sw.zv + idx, zz);
+              if (last) acc1 += dot4d(ld4f(fr + t), zz);
+            }
+          }
+        }
+      }
+      if (!fin4)
       for (int t = tid; t < nd; t += kThreads) {
-        const int jj = t / n, a = t - jj * n;
+        const int jj = qdiv(t, inv_n), a = t - jj * n;
         const int row = r0 + jj;
         const int src = row - k;
         T carry = T(0);
@@ -756,7 +852,7 @@ struct Solver {
       // 6. carry the pushes of the last k source rows into the other ring
       //    buffer (read by the next chunk after its barriers)
       for (int t = tid; t < k * n; t += kThreads) {
-        const int w = t / n, a = t - w * n;
+        const int w = qdiv(t, inv_n), a = t - w * n;
         const int src = r1 - k + w;
         if (src < 0) continue;
         ring_out[(src % k) * n + a] = (src >= base) ? push[(src - base) * n + a] : ring_in[(src % k) * n + a];

@@ -30,7 +30,7 @@ __global__ void k_factor(const __grid_constant__ SetupParams P, int wpc, int war
   const RowRef rr = P.rows[gr];
   const InstDesc d = P.inst[rr.inst];
   const int n = d.n, i = rr.row, nn = n * n;
-  double* A = reinterpret_cast<double*>(smraw + (size_t)warp * warp_bytes);  // 16 maxn^2 bytes per warp
+  double* A = reinterpret_cast<double*>(smraw + (size_t)warp * warp_bytes);  // 16 maxn^2 + 512 bytes per warp
   double* T = A + nn;
   const double* Du = P.D + P.d_off[rr.inst] + (long long)i * nn;
   const bool hasO = i < d.N - 1;
@@ -40,13 +40,14 @@ __global__ void k_factor(const __grid_constant__ SetupParams P, int wpc, int war
     for (int t = lane; t < nn; t += 32) T[t] = Ou[t];
   }
   __syncwarp();
+  const float inv_n = 1.0f / (float)n;
   {
     double* D64 = P.D64 + d.off64 + (long long)i * d.bs64;
     double* O64 = P.O64 + d.off64 + (long long)i * d.bs64;
     float* D32 = P.want32 ? P.D32 + d.off32 + (long long)i * d.bs32 : nullptr;
     float* O32 = P.want32 ? P.O32 + d.off32 + (long long)i * d.bs32 : nullptr;
     for (int t = lane; t < nn; t += 32) {  // destination column-major index t = c*n + a
-      const int c = t / n, a = t - c * n;
+      const int c = qdiv(t, inv_n), a = t - c * n;
       const double dv = A[a * n + c];
       D64[t] = dv;
       if (D32) D32[t] = (float)dv;
@@ -58,7 +59,12 @@ __global__ void k_factor(const __grid_constant__ SetupParams P, int wpc, int war
     }
   }
   __syncwarp();
-  // Cholesky D = L L^T in place (lower triangle of A, row-major), float64
+  // Cholesky D = L L^T in place (lower triangle of A, row-major), float64.
+  // Float64 runs at 1/58 of the float32 rate here, so every float64
+  // warp-instruction counts: one rsqrt per column gives both the pivot
+  // (piv * rsqrt(piv)) and its reciprocal, and the trailing update walks
+  // only the lower triangle (triangular index t -> (rr, cc), rr >= cc).
+  double* rinv_col = T + nn;  // reciprocals of the diagonal of L (warp tail)
   for (int j = 0; j < n; ++j) {
     const double piv = A[j * n + j];
     if (!(piv > 0.0) || !isfinite(piv)) {
@@ -68,34 +74,48 @@ __global__ void k_factor(const __grid_constant__ SetupParams P, int wpc, int war
       }
       return;
     }
-    const double ljj = sqrt(piv);
+    const double rinv = rsqrt(piv);
     __syncwarp();
-    for (int r = j + 1 + lane; r < n; r += 32) A[r * n + j] /= ljj;
-    if (lane == 0) A[j * n + j] = ljj;
+    for (int r = j + 1 + lane; r < n; r += 32) A[r * n + j] *= rinv;
+    if (lane == 0) {
+      A[j * n + j] = piv * rinv;
+      rinv_col[j] = rinv;
+    }
     __syncwarp();
     const int m = n - j - 1;
-    for (int t = lane; t < m * m; t += 32) {
-      const int r = j + 1 + t / m, c = j + 1 + t % m;
-      if (c <= r) A[r * n + c] = fma(-A[r * n + j], A[c * n + j], A[r * n + c]);
+    const int tri = m * (m + 1) / 2;
+    for (int t = lane; t < tri; t += 32) {
+      int rq = __float2int_rz((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+      if ((rq + 1) * (rq + 2) / 2 <= t) ++rq;   // guard the float estimate
+      if (rq * (rq + 1) / 2 > t) --rq;
+      const int cq = t - rq * (rq + 1) / 2;
+      const int r = j + 1 + rq, c = j + 1 + cq;
+      A[r * n + c] = fma(-A[r * n + j], A[c * n + j], A[r * n + c]);
     }
     __syncwarp();
   }
-  // W = L^-1 (one column per lane, forward substitution in MT)
+  // W = L^-1 (one column per lane, forward substitution in MT); the
+  // reciprocals of the diagonal are formed once, into the warp's tail region.
   MT* W = reinterpret_cast<MT*>(T);
+  // 1 / L[r][r] from the Cholesky; float32 copies sit behind W's float32 data
+  MT* dv = (sizeof(MT) == 4) ? reinterpret_cast<MT*>(T) + nn : reinterpret_cast<MT*>(rinv_col);
+  if (sizeof(MT) == 4)
+    for (int r = lane; r < n; r += 32) dv[r] = (MT)rinv_col[r];
+  __syncwarp();
   for (int c = lane; c < n; c += 32) {
     for (int r = 0; r < c; ++r) W[r * n + c] = MT(0);
-    W[c * n + c] = MT(1) / (MT)A[c * n + c];
+    W[c * n + c] = dv[c];
     for (int r = c + 1; r < n; ++r) {
       MT acc = MT(0);
       for (int t = c; t < r; ++t) acc = fma((MT)A[r * n + t], W[t * n + c], acc);
-      W[r * n + c] = -acc / (MT)A[r * n + r];
+      W[r * n + c] = -acc * dv[r];
     }
   }
   __syncwarp();
   MT* out = (sizeof(MT) == 8) ? reinterpret_cast<MT*>(P.Dinv64 + d.off64 + (long long)i * d.bs64)
                               : reinterpret_cast<MT*>(P.Dinv32 + d.off32 + (long long)i * d.bs32);
   for (int t = lane; t < nn; t += 32) {
-    const int a = t / n, b = t - a * n;
+    const int a = qdiv(t, inv_n), b = t - a * n;
     if (a < b) continue;
     MT acc = MT(0);
     for (int r = a; r < n; ++r) acc = fma(W[r * n + a], W[r * n + b], acc);
@@ -108,8 +128,9 @@ __global__ void k_factor(const __grid_constant__ SetupParams P, int wpc, int war
 // C (+)= op(A) op(B)
 template <typename MT>
 __device__ void sm_gemm(MT* C, const MT* A, bool tA, const MT* B, bool tB, int n, bool accumulate) {
+  const float inv_n = 1.0f / (float)n;
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-    const int a = t / n, b = t % n;
+    const int a = qdiv(t, inv_n), b = t - a * n;
     MT acc = accumulate ? C[t] : MT(0);
     for (int c = 0; c < n; ++c) {
       const MT av = tA ? A[c * n + a] : A[a * n + c];
@@ -128,8 +149,10 @@ __device__ void sm_gemm4(MT* C, const MT* A, bool tA, const MT* B, bool tB, int 
     return;
   }
   const int q = n / 4;
+  const float inv_q = 1.0f / (float)q;
   for (int t = threadIdx.x; t < q * q; t += blockDim.x) {
-    const int a0 = (t / q) * 4, b0 = (t % q) * 4;
+    const int tq = qdiv(t, inv_q);
+    const int a0 = tq * 4, b0 = (t - tq * q) * 4;
     MT acc[4][4];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
@@ -156,16 +179,18 @@ __device__ void sm_gemm4(MT* C, const MT* A, bool tA, const MT* B, bool tB, int 
 // load a column-major library block into row-major shared memory
 template <typename MT>
 __device__ void sm_load(MT* dst, const MT* src, int n) {
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-    const int a = t / n, c = t % n;
-    dst[t] = src[(long long)c * n + a];
+  const float inv_n = 1.0f / (float)n;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {  // coalesced read of the column-major block
+    const int c = qdiv(t, inv_n), a = t - c * n;
+    dst[a * n + c] = src[t];
   }
 }
 template <typename MT>
 __device__ void sm_store(MT* dst, const MT* src, int n) {
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-    const int a = t / n, c = t % n;
-    dst[(long long)c * n + a] = src[t];
+  const float inv_n = 1.0f / (float)n;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {  // coalesced write of the column-major block
+    const int c = qdiv(t, inv_n), a = t - c * n;
+    dst[t] = src[a * n + c];
   }
 }
 
@@ -303,7 +328,7 @@ extern "C" cudaError_t bt_launch_setup(const bt::SetupParams* P, int mixed, int 
   if (nb == 0) return cudaSuccess;
   const dim3 grid((unsigned)nb);
   cudaError_t err;
-  const int per_warp = 16 * maxn * maxn;
+  const int per_warp = 16 * maxn * maxn + 8 * bt::kMaxBlock;  // A | T | diagonal reciprocals
   int wpc = (200 * 1024) / per_warp;
   if (wpc > 8) wpc = 8;
   if (wpc < 1) wpc = 1;
