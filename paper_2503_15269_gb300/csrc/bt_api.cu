@@ -65,6 +65,9 @@ struct bt_ctx {
   double *d_resid = nullptr, *d_errval = nullptr;
   unsigned long long* d_fail_key = nullptr;
   double* d_fail_piv = nullptr;
+  int* d_retry = nullptr;  // mixed: float64 refactor list (count + rows)
+  bt::SegRef* d_segs = nullptr;  // mixed: row segments of the fused E/H kernel
+  long long nsegs = 0;
   char* d_ws = nullptr;
   long long ws_stride = 0, ws_vec = 0;
   int ws_slots = 0;
@@ -150,6 +153,9 @@ bt_status launch_setup_kernels(bt_ctx* h, const double* D, const double* O) {
   sp.want64 = 1;
   sp.fail_key = h->d_fail_key;
   sp.fail_piv = h->d_fail_piv;
+  sp.retry = h->d_retry;
+  sp.segs = h->d_segs;
+  sp.nsegs = h->nsegs;
   return cuda_st(bt_launch_setup(&sp, h->mixed ? 1 : 0, h->prm.m, h->maxn, st));
 }
 
@@ -224,6 +230,12 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
   }
   ALLOC(h->d_inst, B);
   ALLOC(h->d_rows, rows);
+  constexpr int kSegRows = 32;  // block rows per fused E/H segment
+  if (mixed) {
+    h->nsegs = 0;
+    for (int k = 0; k < B; ++k) h->nsegs += (h->N[k] + kSegRows - 1) / kSegRows;
+    ALLOC(h->d_segs, h->nsegs);
+  }
   ALLOC(h->d_order, B);
   ALLOC(h->d_doff, B);
   ALLOC(h->d_ooff, B);
@@ -235,6 +247,7 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
   ALLOC(h->d_errval, B);
   ALLOC(h->d_fail_key, 1);
   ALLOC(h->d_fail_piv, rows);
+  if (h->mixed) ALLOC(h->d_retry, rows + 1);
   // zero every block array once (padding slots must read as zero)
   auto z64 = [&](double* p) { if (p) cudaMemsetAsync(p, 0, off64 * sizeof(double), st); };
   auto z32 = [&](float* p) { if (p) cudaMemsetAsync(p, 0, off32 * sizeof(float), st); };
@@ -247,6 +260,12 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
     for (int k = 0; k < B; ++k)
       for (int i = 0; i < h->N[k]; ++i) rr[t++] = bt::RowRef{k, i};
   }
+  std::vector<bt::SegRef> segs;
+  if (mixed) {
+    segs.reserve(h->nsegs);
+    for (int k = 0; k < B; ++k)
+      for (int a = 0; a < h->N[k]; a += kSegRows) segs.push_back(bt::SegRef{k, a, std::min(h->N[k], a + kSegRows), 0});
+  }
   std::vector<int> order(B);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
@@ -257,7 +276,9 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
       (e = cudaMemcpyAsync(h->d_rows, rr.data(), rows * sizeof(bt::RowRef), cudaMemcpyHostToDevice, st)) ||
       (e = cudaMemcpyAsync(h->d_order, order.data(), B * sizeof(int), cudaMemcpyHostToDevice, st)) ||
       (e = cudaMemcpyAsync(h->d_doff, h->d_off.data(), B * sizeof(long long), cudaMemcpyHostToDevice, st)) ||
-      (e = cudaMemcpyAsync(h->d_ooff, h->o_off.data(), B * sizeof(long long), cudaMemcpyHostToDevice, st)))
+      (e = cudaMemcpyAsync(h->d_ooff, h->o_off.data(), B * sizeof(long long), cudaMemcpyHostToDevice, st)) ||
+      (mixed && (e = cudaMemcpyAsync(h->d_segs, segs.data(), segs.size() * sizeof(bt::SegRef),
+                                     cudaMemcpyHostToDevice, st))))
     return BT_ERR_CUDA;
   if (launch_setup_kernels(h, D, O) != BT_OK) return BT_ERR_CUDA;
 

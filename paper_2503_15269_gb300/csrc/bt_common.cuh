@@ -20,10 +20,13 @@ constexpr int kMaxStages = 8;
 #define BT_THREADS 256
 #endif
 #ifndef BT_LEADER_WARP
-#define BT_LEADER_WARP 0
+#define BT_LEADER_WARP (BT_THREADS / 32 - 1)
 #endif
 constexpr int kThreads = BT_THREADS;    // threads per persistent CTA
-constexpr int kLeaderTid = 32 * BT_LEADER_WARP;  // thread that issues the bulk copies
+// Thread that issues the bulk copies: lane 0 of the last warp.  Per-chunk
+// work is spread from thread 0 upwards, so the last warp is the idlest one
+// and the copy issue stays off the chunk's critical path.
+constexpr int kLeaderTid = 32 * BT_LEADER_WARP;
 constexpr int kMaxChunkElems = 512;     // rows-per-chunk cap: R * n <= 512
 
 enum Status : int {
@@ -69,6 +72,9 @@ struct KParams {
 struct RowRef {
   int inst, row;
 };
+struct SegRef {  // block rows [a, b) of one instance
+  int inst, a, b, pad;
+};
 
 struct SetupParams {
   const InstDesc* inst;
@@ -83,6 +89,10 @@ struct SetupParams {
   int want32, want64;       // which precisions to produce
   unsigned long long* fail_key;  // min over failing (inst << 32 | row)
   double* fail_piv;         // per global row: the failing pivot
+  int* retry;               // mixed only, optional: [0] = count, [1..] = rows whose
+                            // float32 factor was refused (refactored in float64)
+  const SegRef* segs;       // mixed only, optional: row segments for the fused E/H kernel
+  long long nsegs;
 };
 
 struct AdjParams {

@@ -156,6 +156,7 @@ extern "C" bt_status bt_pcg_solve_noalloc(int N, int n, const double* D, const d
   int* order = c.take<int>(base, 1);
   bt::RowRef* rows = c.take<bt::RowRef>(base, N);
   double* fail_piv = c.take<double>(base, N);
+  int* retry = mixed ? c.take<int>(base, (size_t)N + 1) : nullptr;
   double* red = c.take<double>(base, (size_t)2 * G * 4);
   const size_t blocks_begin = c.off;
   const size_t n64 = (size_t)N * bs64, n32 = (size_t)N * bs32;
@@ -207,6 +208,7 @@ extern "C" bt_status bt_pcg_solve_noalloc(int N, int n, const double* D, const d
   sp.want64 = 1;
   sp.fail_key = fail_key;
   sp.fail_piv = fail_piv;
+  sp.retry = retry;
   if (bt_launch_setup(&sp, mixed ? 1 : 0, m, n, st) != cudaSuccess) return BT_ERR_CUDA;
 
   bt::KParams P{};

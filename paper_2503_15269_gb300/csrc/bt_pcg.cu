@@ -260,9 +260,34 @@ __device__ __forceinline__ void st4f(float* p, float4 v) { *reinterpret_cast<flo
 __device__ __forceinline__ float4 fma4(float a, float4 x, float4 y) {
   return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
 }
-__device__ __forceinline__ double dot4d(float4 a, float4 b) {
-  return (double)a.x * (double)b.x + (double)a.y * (double)b.y + (double)a.z * (double)b.z + (double)a.w * (double)b.w;
+// Dot-product partials.  Float64 issues at 1/64 of the float32 rate on this
+// part, so the float32 sweeps keep float64 off the per-chunk path: each
+// thread sums its float32 products (4-term dots) with a compensated float32
+// sum (TwoSum: the rounding error of every addition is carried in c, so the
+// partial is accurate to a few float32 ulps whatever the number of terms)
+// and widens it once per sweep.  The float64 sweeps sum in float64.
+__device__ __forceinline__ float dot4f(float4 a, float4 b) {
+  return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)));
 }
+template <typename T>
+struct Accum;
+template <>
+struct Accum<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    const float bp = t - s;
+    c += (s - (t - bp)) + (x - bp);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+template <>
+struct Accum<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
 
 template <typename MT>
 struct Solver {
@@ -451,7 +476,7 @@ struct Solver {
     int* ctl = reinterpret_cast<int*>(sm + kSmCtl);
     const int lane = tid & 31, w = tid >> 5;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 3; ++i) {  // v[3] is set below (timeout flag)
       double x = v[i];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -461,7 +486,7 @@ struct Solver {
     if (tid == 0) {
       double t[4] = {0, 0, 0, 0};
       for (int ww = 0; ww < kThreads / 32; ++ww)
-        for (int i = 0; i < 4; ++i) t[i] += red[ww * 4 + i];
+        for (int i = 0; i < 3; ++i) t[i] += red[ww * 4 + i];
       t[3] = (clock64() > deadline) ? 1.0 : 0.0;
       int bad = 0;
       if (G > 1) {
@@ -615,7 +640,7 @@ struct Solver {
     const bool write_r = sw.write_r, zero_x = sw.zero_x;
     const int jpow = sw.j;
     const double scale = sw.scale;
-    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
+    Accum<T> acc0, acc1, acc2;
     auto chunk_rows = [&](int c, int& r0, int& r1, int& base, int& vend) {
       r0 = s + c * R;
       r1 = min(e, r0 + R);
@@ -693,7 +718,7 @@ struct Solver {
               if (own) {
                 st4f(sw.r_cur + idx, v);
                 st4f(sw.x + idx, fma4(alpha, ld4f(sv3 + lo), ld4f(sv2 + lo)));
-                acc2 += dot4d(v, v);
+                acc2.add(dot4f(v, v));
               }
             } else {
               v = ld4f(sv0 + t);
@@ -723,20 +748,20 @@ struct Solver {
           if (own) {
             sw.r_cur[idx] = v;
             sw.x[idx] = fma(alpha, va ? sv3[lo] : sw.p_in[idx], va ? sv2[lo] : sw.x[idx]);
-            acc2 += (double)v * (double)v;
+            acc2.add(v * v);
           }
         } else if constexpr (STG == SV_R_FIRST) {
           v = static_cast<T>((va ? sd0[t] : sw.src64[idx]) * scale);
           if (own) {
             if (write_r) sw.r_cur[idx] = v;
             if (zero_x) sw.x[idx] = T(0);
-            acc2 += (double)v * (double)v;
+            acc2.add(v * v);
           }
         } else if constexpr (STG == SV_R_X0) {
           v = static_cast<T>((va ? sd0[t] : sw.src64[idx]) - (double)(va ? sv1[t] : sw.q[idx]));
           if (own) {
             sw.r_cur[idx] = v;
-            acc2 += (double)v * (double)v;
+            acc2.add(v * v);
           }
         } else {
           v = va ? sv0[t] : sw.yprev[idx];
@@ -795,11 +820,11 @@ struct Solver {
             const float4 vi = ld4f(vs + (row - base) * n + a);
             if constexpr (FIN == FN_Q) {
               st4f(sw.qout + idx, out);
-              acc0 += dot4d(vi, out);
+              acc0.add(dot4f(vi, out));
             } else if constexpr (FIN == FN_Y0) {
               if (m1) {
                 st4f(sw.zv + idx, out);
-                acc1 += dot4d(vi, out);
+                acc1.add(dot4f(vi, out));
               } else {
                 st4f(sw.y0 + idx, out);
               }
@@ -808,7 +833,7 @@ struct Solver {
               const float4 zz = fma4(alpha_j, out, zprev);
               if (!last) st4f(sw.ynext + idx, out);
               st4f(sw.zv + idx, zz);
-              if (last) acc1 += dot4d(ld4f(fr + t), zz);
+              if (last) acc1.add(dot4f(ld4f(fr + t), zz));
             }
           }
         }
@@ -825,18 +850,18 @@ struct Solver {
         const T vi = vs[(row - base) * n + a];
         if constexpr (FIN == FN_Q) {
           sw.qout[idx] = out;
-          acc0 += (double)vi * (double)out;
+          acc0.add(vi * out);
         } else if constexpr (FIN == FN_OUT64) {
           sw.out64[idx] = (double)out;
         } else if constexpr (FIN == FN_R64) {
           const double r = (va ? fb[t] : sw.bsub[idx]) - (double)out;
           sw.r64[idx] = r;
-          acc0 += r * r;
+          acc0.add(r * r);
         } else if constexpr (FIN == FN_Y0) {
           if (m1) {
             if (out_to_user) sw.out64[idx] = (double)out;
             else sw.zv[idx] = out;
-            acc1 += (double)vi * (double)out;
+            acc1.add(vi * out);
           } else {
             sw.y0[idx] = out;
           }
@@ -846,7 +871,7 @@ struct Solver {
           if (!last) sw.ynext[idx] = out;
           if (last && out_to_user) sw.out64[idx] = (double)zz;
           else sw.zv[idx] = zz;
-          if (last) acc1 += (double)(va ? fr[t] : sw.rcur_for_dot[idx]) * (double)zz;
+          if (last) acc1.add((va ? fr[t] : sw.rcur_for_dot[idx]) * zz);
         }
       }
       // 6. carry the pushes of the last k source rows into the other ring
@@ -862,9 +887,9 @@ struct Solver {
     this->vissued = vissued;
     this->vcons = vcons;
     store_producer(q);
-    acc[0] += acc0;
-    acc[1] += acc1;
-    acc[2] += acc2;
+    acc[0] += acc0.value();
+    acc[1] += acc1.value();
+    acc[2] += acc2.value();
     if (failed) fail = true;
   }
 
@@ -973,6 +998,13 @@ __device__ void solve_instance(Solver<MT>& Sv, int inst_id) {
 
   double acc[4];
   auto zero_acc = [&]() { acc[0] = acc[1] = acc[2] = acc[3] = 0.0; };
+  // PCG step scalars: the float32 inner iteration uses them rounded to float,
+  // so it divides in float32 (a float64 division is a dozen float64
+  // instructions on every thread); the float64 path divides in float64.
+  auto sdiv = [](double a, double b) -> double {
+    if constexpr (sizeof(MT) == 4) return (double)__fdiv_rn((float)a, (float)b);
+    else return a / b;
+  };
 
   // Apply z = M^-1 rhs into the inner vectors (or to the user array).
   // Runs B1 then B2 x (m-1); rz accumulates in acc[1] of the last sweep.
@@ -1068,7 +1100,9 @@ __device__ void solve_instance(Solver<MT>& Sv, int inst_id) {
         nrhs = sqrt(rr);
       }
       if (nrhs == 0.0) { return; }  // x = 0 already
-      if (sqrt(rr) <= tol_rel * nrhs) { return; }
+      // ||r|| <= tol ||rhs||, squared (no per-iteration square root)
+      const double thr2 = (tol_rel * nrhs) * (tol_rel * nrhs);
+      if (rr <= thr2) { return; }
       if (m > 1) {
         precond_sweeps_after_b1(rb[0], false);
         if (Sv.fail) { st_out = kErrTimeout; return; }
@@ -1090,7 +1124,7 @@ __device__ void solve_instance(Solver<MT>& Sv, int inst_id) {
         const double pq = acc[0];
         if (!isfinite(pq)) { st_out = kErrNonfinite; it_out = k - 1; return; }
         if (!(pq > 0.0)) { st_out = kErrBreakdown; it_out = k - 1; errv = pq; return; }
-        const double alpha = rho / pq;
+        const double alpha = sdiv(rho, pq);
         // B1: r -= alpha q, x += alpha p, y0 = G r
         Sweep<MT> sb = {};
         sb.kind = kKB1; sb.stg = SV_R_UPD; sb.fin = FN_Y0; sb.sgn = MT(-1);
@@ -1105,13 +1139,13 @@ __device__ void solve_instance(Solver<MT>& Sv, int inst_id) {
         rr_out = rr;
         it_out = k;
         if (!isfinite(rr)) { st_out = kErrNonfinite; return; }
-        if (sqrt(rr) <= tol_rel * nrhs) return;
+        if (rr <= thr2) return;
         if (m > 1) {
           precond_sweeps_after_b1(rb[k & 1], false);
           if (Sv.fail) { st_out = kErrTimeout; return; }
         }
         const double rz_new = acc[1];
-        beta = rz_new / rho;
+        beta = sdiv(rz_new, rho);
         rho = rz_new;
       }
     };

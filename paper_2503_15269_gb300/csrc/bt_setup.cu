@@ -12,6 +12,8 @@
 //       Hl_i = E_{i+1}^T O_i^T          (only for polynomial order m >= 2)
 // K2, K3: one CTA per block row; block products out of shared memory with
 // 4 x 4 register tiles.
+#include <algorithm>
+
 #include "bt_common.cuh"
 
 namespace bt {
@@ -22,15 +24,12 @@ namespace bt {
 // Cholesky in float64, invert the factor and form D_i^-1 = W^T W in MT.
 // Warp-synchronous: no CTA barriers, so a CTA hosts several block rows.
 template <typename MT>
-__global__ void k_factor(const __grid_constant__ SetupParams P, int wpc, int warp_bytes) {
-  extern __shared__ __align__(16) char smraw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long gr = (long long)blockIdx.x * wpc + warp;
-  if (gr >= P.nrows) return;
+__device__ void factor_row64(const SetupParams& P, long long gr, char* wsm) {
+  const int lane = threadIdx.x & 31;
   const RowRef rr = P.rows[gr];
   const InstDesc d = P.inst[rr.inst];
   const int n = d.n, i = rr.row, nn = n * n;
-  double* A = reinterpret_cast<double*>(smraw + (size_t)warp * warp_bytes);  // 16 maxn^2 + 512 bytes per warp
+  double* A = reinterpret_cast<double*>(wsm);  // 16 maxn^2 + 512 bytes per warp
   double* T = A + nn;
   const double* Du = P.D + P.d_off[rr.inst] + (long long)i * nn;
   const bool hasO = i < d.N - 1;
@@ -121,6 +120,132 @@ __global__ void k_factor(const __grid_constant__ SetupParams P, int wpc, int war
     for (int r = a; r < n; ++r) acc = fma(W[r * n + a], W[r * n + b], acc);
     out[(long long)b * n + a] = acc;
     out[(long long)a * n + b] = acc;
+  }
+}
+
+template <typename MT>
+__global__ void k_factor(const __grid_constant__ SetupParams P, int wpc, int warp_bytes) {
+  extern __shared__ __align__(16) char smraw[];
+  const int warp = threadIdx.x >> 5;
+  const long long gr = (long long)blockIdx.x * wpc + warp;
+  if (gr >= P.nrows) return;
+  factor_row64<MT>(P, gr, smraw + (size_t)warp * warp_bytes);
+}
+
+// Float64 refactor of the rows whose float32 factor was refused (list in
+// P.retry); a float64 failure here is the handle's NOT_SPD.
+__global__ void k_factor_retry(const __grid_constant__ SetupParams P, int wpc, int warp_bytes) {
+  extern __shared__ __align__(16) char smraw[];
+  const int warp = threadIdx.x >> 5;
+  const int count = *(volatile const int*)P.retry;
+  for (long long k = (long long)blockIdx.x * wpc + warp; k < count; k += (long long)gridDim.x * wpc)
+    factor_row64<float>(P, P.retry[1 + k], smraw + (size_t)warp * warp_bytes);
+}
+
+// ---------------------------------------------------------------- K1 (mixed)
+// Float32 factor for mixed handles, one warp per block row in a 4 n (n+1)
+// byte shared region (+ 64 floats):
+//   1. D_i, O_i -> library copies (float64 and float32, column-major), staged
+//      through shared memory half a block at a time;
+//   2. D_i = L L^T by Cholesky in float32, column-major in place (lane = row);
+//   3. W = L^-1 (lane = column), its strict lower part kept in the unused
+//      upper triangle and its diagonal (1 / L_jj) in the 64-float tail;
+//   4. D_i^-1 = W^T W, one column per step (lane = row), coalesced stores.
+// A pivot below 1e-3 of its original diagonal means kappa(D_i) > 1e3 (the
+// pivot is at least lambda_min, the diagonal at most lambda_max); such rows
+// and non-positive or non-finite pivots go to the float64 retry list, so a
+// poorly conditioned block costs float64 time only where it occurs.
+__global__ void k_factor32(const __grid_constant__ SetupParams P, int wpc, int warp_bytes) {
+  extern __shared__ __align__(16) char smraw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long gr = (long long)blockIdx.x * wpc + warp;
+  if (gr >= P.nrows) return;
+  const RowRef rr = P.rows[gr];
+  const InstDesc d = P.inst[rr.inst];
+  const int n = d.n, i = rr.row, nn = n * n;
+  char* wsm = smraw + (size_t)warp * warp_bytes;
+  float* A = reinterpret_cast<float*>(wsm);
+  float* dv = reinterpret_cast<float*>(wsm + warp_bytes - 64 * sizeof(float));
+  double* stg = reinterpret_cast<double*>(wsm);
+  float* D32 = P.D32 + d.off32 + (long long)i * d.bs32;
+  // 1. layout copies: rows [a0, a0 + h) of the caller's row-major block
+  const auto copy_block = [&](const double* src, double* dst64, float* dst32) {
+    for (int a0 = 0; a0 < n; a0 += (n + 1) / 2) {
+      const int h = min((n + 1) / 2, n - a0), cnt = h * n;
+      const float inv_h = 1.0f / (float)h;
+      for (int t = lane; t < cnt; t += 32) stg[t] = src[(long long)a0 * n + t];
+      __syncwarp();
+      for (int t = lane; t < cnt; t += 32) {  // t = c * h + (a - a0)
+        const int c = qdiv(t, inv_h), ar = t - c * h;
+        const double v = stg[ar * n + c];
+        dst64[(long long)c * n + a0 + ar] = v;
+        dst32[(long long)c * n + a0 + ar] = (float)v;
+      }
+      __syncwarp();
+    }
+  };
+  if (i < d.N - 1)
+    copy_block(P.O + P.o_off[rr.inst] + (long long)i * nn, P.O64 + d.off64 + (long long)i * d.bs64,
+               P.O32 + d.off32 + (long long)i * d.bs32);
+  copy_block(P.D + P.d_off[rr.inst] + (long long)i * nn, P.D64 + d.off64 + (long long)i * d.bs64, D32);
+  // this warp's own float32 copy, column-major: A[c n + r] = D(r, c)
+  for (int t = lane; t < nn; t += 32) A[t] = __ldcg(D32 + t);
+  __syncwarp();
+  for (int r = lane; r < n; r += 32) dv[r] = A[r * n + r];
+  __syncwarp();
+  // 2. Cholesky, lane owns rows r0 = lane and r1 = lane + 32
+  const int r0 = lane, r1 = lane + 32;
+  for (int j = 0; j < n; ++j) {
+    const float piv = A[j * n + j];
+    const float dj = dv[j];
+    if (!(piv > 0.f && piv > 1e-3f * dj) || !(piv < INFINITY)) {
+      if (lane == 0) P.retry[1 + atomicAdd(P.retry, 1)] = (int)gr;
+      return;
+    }
+    const float rinv = rsqrtf(piv);
+    __syncwarp();
+    if (r0 > j && r0 < n) A[j * n + r0] *= rinv;
+    if (r1 > j && r1 < n) A[j * n + r1] *= rinv;
+    if (lane == 0) {
+      A[j * n + j] = piv * rinv;
+      dv[j] = rinv;
+    }
+    __syncwarp();
+    const float l0 = (r0 > j && r0 < n) ? A[j * n + r0] : 0.f;
+    const float l1 = (r1 > j && r1 < n) ? A[j * n + r1] : 0.f;
+    for (int c = j + 1; c < n; ++c) {
+      const float bc = A[j * n + c];
+      if (c <= r0 && r0 < n) A[c * n + r0] = fmaf(-l0, bc, A[c * n + r0]);
+      if (c <= r1 && r1 < n) A[c * n + r1] = fmaf(-l1, bc, A[c * n + r1]);
+    }
+    __syncwarp();
+  }
+  // 3. W = L^-1: W(r, c) = -(1/L_rr) sum_{t=c}^{r-1} L(r, t) W(t, c), with
+  //    L(r, t) = A[t n + r], W(t, c) = A[t n + c] for t > c, W(c, c) = dv[c]
+  for (int c = lane; c < n; c += 32) {
+    const float wcc = dv[c];
+    for (int r = c + 1; r < n; ++r) {
+      float acc = A[c * n + r] * wcc;
+      for (int t = c + 1; t < r; ++t) acc = fmaf(A[t * n + r], A[t * n + c], acc);
+      A[r * n + c] = -acc * dv[r];
+    }
+  }
+  __syncwarp();
+  // 4. D_i^-1(a, b) = sum_{r >= max(a, b)} W(r, a) W(r, b), column b per step
+  float* out = P.Dinv32 + d.off32 + (long long)i * d.bs32;
+  for (int b = 0; b < n; ++b) {
+    float acc0 = 0.f, acc1 = 0.f;
+    for (int r = b; r < n; ++r) {
+      const float wrb = (r == b) ? dv[b] : A[r * n + b];
+      const float w0 = (r > r0) ? A[r * n + r0] : (r == r0 ? dv[r0] : 0.f);
+      acc0 = fmaf(w0, wrb, acc0);
+      if (n > 32) {
+        const float w1 = (r > r1) ? A[r * n + r1] : (r == r1 ? dv[r1 & 63] : 0.f);
+        acc1 = fmaf(w1, wrb, acc1);
+      }
+    }
+    if (r0 < n) out[(long long)b * n + r0] = acc0;
+    if (r1 < n) out[(long long)b * n + r1] = acc1;
   }
 }
 
@@ -295,6 +420,152 @@ __global__ void k_H(const __grid_constant__ SetupParams P) {
   }
 }
 
+// ---------------------------------------------------------------- K2+K3 (mixed)
+// E and H fused over a segment of consecutive block rows [a, b) of one
+// instance, all blocks column-major float32 in shared-memory rings.  Step j
+// (j = a-2 .. b+1) forms, as independent tile tasks,
+//   T_{j+1} = O_{j+1} D_{j+2}^-1            (kept for the next step)
+//   E_j     = D_j^-1 T_j                    (rows a-1 .. b; stored for j in [a, b))
+//   H_{j-2}: Hd = E^T_{i-1} O_{i-1} + E_i O_i^T, Hu = E_i O_{i+1},
+//            Hl = E_{i+1}^T O_i^T           (i = j-2 in [a, b))
+// while cp.async prefetches O_{j+2} and D_{j+3}^-1 for the next step.  Ring
+// sizes follow the block lifetimes: O 6, D^-1 4, T 2, E 4 slots.  Every
+// output element is one fma chain over k = 0 .. n-1 (two chains in a row for
+// Hd), the same arithmetic as K2/K3.
+template <int TS, bool TA, bool TB>
+__device__ __forceinline__ void tile_acc(float (&acc)[TS][TS], const float* __restrict__ A,
+                                         const float* __restrict__ B, int n, int a0, int b0) {
+  // acc(r, c) += sum_k opA(a0 + r, k) opB(k, b0 + c); X(a, c) at X[c n + a]
+  for (int k = 0; k < n; ++k) {
+    float av[TS], bv[TS];
+    if constexpr (!TA && TS == 4) {
+      const float4 v = *reinterpret_cast<const float4*>(A + k * n + a0);
+      av[0] = v.x; av[1] = v.y; av[2] = v.z; av[3] = v.w;
+    } else {
+#pragma unroll
+      for (int r = 0; r < TS; ++r) av[r] = TA ? A[(a0 + r) * n + k] : A[k * n + a0 + r];
+    }
+    if constexpr (TB && TS == 4) {
+      const float4 v = *reinterpret_cast<const float4*>(B + k * n + b0);
+      bv[0] = v.x; bv[1] = v.y; bv[2] = v.z; bv[3] = v.w;
+    } else {
+#pragma unroll
+      for (int c = 0; c < TS; ++c) bv[c] = TB ? B[k * n + b0 + c] : B[(b0 + c) * n + k];
+    }
+#pragma unroll
+    for (int r = 0; r < TS; ++r)
+#pragma unroll
+      for (int c = 0; c < TS; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+  }
+}
+
+template <int TS>
+__device__ __forceinline__ void tile_store(float* C, const float (&acc)[TS][TS], int n, int a0, int b0) {
+#pragma unroll
+  for (int c = 0; c < TS; ++c) {
+    if constexpr (TS == 4) {
+      *reinterpret_cast<float4*>(C + (b0 + c) * n + a0) = make_float4(acc[0][c], acc[1][c], acc[2][c], acc[3][c]);
+    } else {
+#pragma unroll
+      for (int r = 0; r < TS; ++r) C[(b0 + c) * n + a0 + r] = acc[r][c];
+    }
+  }
+}
+
+__device__ __forceinline__ void cp16(void* smem, const void* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem)), "l"(g)
+               : "memory");
+}
+
+template <int TS>
+__device__ void eh_segment(const SetupParams& P, const SegRef sg, bool want_h, float* fsm) {
+  const InstDesc d = P.inst[sg.inst];
+  const int n = d.n, N = d.N, a = sg.a, b = sg.b, bs = d.bs32;
+  const float* Og = P.O32 + d.off32;
+  const float* Dg = P.Dinv32 + d.off32;
+  float* Eg = P.E32 + d.off32;
+  float* sO = fsm;
+  float* sD = sO + 6 * bs;
+  float* sT = sD + 4 * bs;
+  float* sE = sT + 2 * bs;
+  // slot of block k (k >= -3 here, so k + 12 > 0)
+  const auto O_ = [&](int k) { return sO + ((k + 12) % 6) * bs; };
+  const auto D_ = [&](int k) { return sD + ((k + 12) % 4) * bs; };
+  const auto T_ = [&](int k) { return sT + ((k + 12) % 2) * bs; };
+  const auto E_ = [&](int k) { return sE + ((k + 12) % 4) * bs; };
+  const auto load = [&](float* dst, const float* src) {
+    for (int t = threadIdx.x * 4; t < bs; t += blockDim.x * 4) cp16(dst + t, src + t);
+  };
+  // O_k is read up to k = b, D_k^-1 up to k = b + 1
+  const auto wantO = [&](int k) { return k >= 0 && k <= N - 2 && k >= a - 1 && k <= b; };
+  const auto wantD = [&](int k) { return k >= 0 && k <= N - 1 && k >= a - 1 && k <= b + 1; };
+  if (wantO(a - 1)) load(O_(a - 1), Og + (long long)(a - 1) * bs);
+  if (wantD(a - 1)) load(D_(a - 1), Dg + (long long)(a - 1) * bs);
+  if (wantD(a)) load(D_(a), Dg + (long long)a * bs);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  const int q = n / TS, tq = q * q;
+  const float inv_q = 1.0f / (float)q;
+  for (int j = a - 2; j <= b + 1; ++j) {
+    if (wantO(j + 2)) load(O_(j + 2), Og + (long long)(j + 2) * bs);
+    if (wantD(j + 3)) load(D_(j + 3), Dg + (long long)(j + 3) * bs);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    const int i = j - 2;
+    const bool doT = (j + 1 >= 0) && (j + 1 <= N - 2) && (j + 1 >= a - 1) && (j + 1 <= b);
+    const bool doE = (j >= 0) && (j <= N - 2) && (j >= a - 1) && (j <= b);
+    const bool doH = want_h && i >= a && i < b;
+    const bool doHd = doH && (i > 0 || i < N - 1);
+    const bool doHu = doH && i <= N - 3;
+    const unsigned mask = (doT ? 1u : 0u) | (doE ? 2u : 0u) | (doHd ? 4u : 0u) | (doHu ? 24u : 0u);
+    const int njobs = __popc(mask);
+    for (int idx = threadIdx.x; idx < njobs * tq; idx += blockDim.x) {
+      const int js = idx / tq;
+      const int tile = idx - js * tq;
+      // job = position of the (js+1)-th set bit of mask
+      unsigned mm = mask;
+      for (int t = 0; t < js; ++t) mm &= mm - 1;
+      const int job = __ffs(mm) - 1;
+      const int tb = qdiv(tile, inv_q), ta = tile - tb * q;
+      const int a0 = ta * TS, b0 = tb * TS;
+      float acc[TS][TS];
+#pragma unroll
+      for (int r = 0; r < TS; ++r)
+#pragma unroll
+        for (int c = 0; c < TS; ++c) acc[r][c] = 0.f;
+      if (job == 0) {
+        tile_acc<TS, false, false>(acc, O_(j + 1), D_(j + 2), n, a0, b0);
+        tile_store<TS>(T_(j + 1), acc, n, a0, b0);
+      } else if (job == 1) {
+        tile_acc<TS, false, false>(acc, D_(j), T_(j), n, a0, b0);
+        tile_store<TS>(E_(j), acc, n, a0, b0);
+        if (j >= a && j < b) tile_store<TS>(Eg + (long long)j * bs, acc, n, a0, b0);
+      } else if (job == 2) {
+        if (i > 0) tile_acc<TS, true, false>(acc, E_(i - 1), O_(i - 1), n, a0, b0);
+        if (i < N - 1) tile_acc<TS, false, true>(acc, E_(i), O_(i), n, a0, b0);
+        tile_store<TS>(P.Hd32 + d.off32 + (long long)i * bs, acc, n, a0, b0);
+      } else if (job == 3) {
+        tile_acc<TS, false, false>(acc, E_(i), O_(i + 1), n, a0, b0);
+        tile_store<TS>(P.Hu32 + d.off32 + (long long)i * bs, acc, n, a0, b0);
+      } else {
+        tile_acc<TS, true, true>(acc, E_(i + 1), O_(i), n, a0, b0);
+        tile_store<TS>(P.Hl32 + d.off32 + (long long)i * bs, acc, n, a0, b0);
+      }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256, 2) k_EH(const __grid_constant__ SetupParams P, int want_h) {
+  extern __shared__ __align__(16) float fsm[];
+  const SegRef sg = P.segs[blockIdx.x];
+  const int n = P.inst[sg.inst].n;
+  if ((n & 3) == 0 && n >= 24) eh_segment<4>(P, sg, want_h != 0, fsm);
+  else if ((n & 1) == 0) eh_segment<2>(P, sg, want_h != 0, fsm);
+  else eh_segment<1>(P, sg, want_h != 0, fsm);
+}
+
 // ---------------------------------------------------------------- adjoint
 // gD_i = -g_i x_i^T, gO_i = -(g_i x_{i+1}^T + x_i g_{i+1}^T), caller layout.
 __global__ void k_adjoint(const __grid_constant__ AdjParams P) {
@@ -336,7 +607,31 @@ extern "C" cudaError_t bt_launch_setup(const bt::SetupParams* P, int mixed, int 
   const int sm_fac = wpc * per_warp;
   const int msz = mixed ? 4 : 8;
   const int sm_prod = 3 * maxn * maxn * msz;
-  if (mixed) {
+  if (mixed && P->retry) {
+    const int per_warp32 = (4 * maxn * (maxn + 1) + 15) / 16 * 16 + 64 * (int)sizeof(float);
+    const int wpc32 = 8;
+    const int sm32 = wpc32 * per_warp32;
+    cudaFuncSetAttribute(bt::k_factor32, cudaFuncAttributeMaxDynamicSharedMemorySize, sm32);
+    cudaFuncSetAttribute(bt::k_factor_retry, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_fac);
+    cudaFuncSetAttribute(bt::k_E<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_prod);
+    cudaFuncSetAttribute(bt::k_H<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_prod);
+    if ((err = cudaMemsetAsync(P->retry, 0, sizeof(int), st)) != cudaSuccess) return err;
+    bt::k_factor32<<<(unsigned)((nb + wpc32 - 1) / wpc32), 32 * wpc32, sm32, st>>>(*P, wpc32, per_warp32);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    const long long rgrid = std::min<long long>((nb + wpc - 1) / wpc, 304);
+    bt::k_factor_retry<<<(unsigned)rgrid, 32 * wpc, sm_fac, st>>>(*P, wpc, per_warp);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    const int maxbs = (maxn * maxn + 3) / 4 * 4;
+    const int sm_eh = 16 * maxbs * (int)sizeof(float);
+    if (P->segs && P->nsegs > 0 && sm_eh <= 200 * 1024) {
+      cudaFuncSetAttribute(bt::k_EH, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_eh);
+      bt::k_EH<<<(unsigned)P->nsegs, 256, sm_eh, st>>>(*P, m >= 2 ? 1 : 0);
+      return cudaGetLastError();
+    }
+    bt::k_E<float><<<grid, 128, sm_prod, st>>>(*P);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if (m >= 2) bt::k_H<float><<<grid, 128, sm_prod, st>>>(*P);
+  } else if (mixed) {
     cudaFuncSetAttribute(bt::k_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_fac);
     cudaFuncSetAttribute(bt::k_E<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_prod);
     cudaFuncSetAttribute(bt::k_H<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_prod);
