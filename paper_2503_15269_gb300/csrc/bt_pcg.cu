@@ -957,7 +957,7 @@ __device__ void solve_instance(Solver<MT>& Sv, int inst_id) {
   Sv.fail = false;
   Sv.status = kOK;
   Sv.deadline = clock64() + P.budget;
-  const int N = d.N, n = d.n, m = P.m;
+  const int n = d.n, m = P.m;
   if (sizeof(MT) == 4) {
     const long long o = d.off32;
     Sv.mats[0] = (const MT*)(P.D32 + o); Sv.mats[1] = (const MT*)(P.O32 + o);

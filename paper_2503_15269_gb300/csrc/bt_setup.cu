@@ -142,6 +142,100 @@ __global__ void k_factor_retry(const __grid_constant__ SetupParams P, int wpc, i
     factor_row64<float>(P, P.retry[1 + k], smraw + (size_t)warp * warp_bytes);
 }
 
+// ---------------------------------------------------------------- K1 (mixed), registers
+// Register-resident float32 factor for compile-time block sizes: lane l owns
+// rows (and, for W, columns) l and l + 32.  Cholesky right-looking by rows,
+// W = L^-1 by columns (forward substitution), D^-1 = W^T W by columns; the
+// operands another lane owns arrive by warp shuffle.  Returns false when a
+// pivot is refused (same rule as the shared-memory path).  The upper parts of
+// the row registers take harmless updates (each stays a finite combination of
+// entries of D and L) and are never read.
+template <int NB>
+__device__ __forceinline__ bool factor_regs(const float* __restrict__ D32, float* __restrict__ out, int lane) {
+  constexpr int H = (NB + 31) / 32;
+  constexpr unsigned FULL = 0xffffffffu;
+  float a[H][NB];
+#pragma unroll
+  for (int h = 0; h < H; ++h) {
+    const int r = lane + 32 * h;
+#pragma unroll
+    for (int c = 0; c < NB; ++c) a[h][c] = (r < NB) ? __ldcg(D32 + c * NB + r) : 0.f;
+  }
+  float rown[H];  // 1 / L_rr of the lane's own rows
+#pragma unroll
+  for (int h = 0; h < H; ++h) rown[h] = 0.f;
+  bool ok = true;  // a refused pivot is replaced by 1 and reported at the end
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    float piv = __shfl_sync(FULL, a[j / 32][j], j % 32);
+    const float dj = __ldcg(D32 + j * NB + j);
+    if (!(piv > 0.f && piv > 1e-3f * dj) || !(piv < INFINITY)) {
+      ok = false;
+      piv = 1.f;
+    }
+    const float ri = rsqrtf(piv);
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      const int r = lane + 32 * h;
+      a[h][j] = (r > j) ? a[h][j] * ri : ((r == j) ? piv * ri : a[h][j]);
+      rown[h] = (r == j) ? ri : rown[h];
+    }
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {  // constant bounds: the compiler unrolls both loops
+      if (c <= j) continue;
+      const float lc = __shfl_sync(FULL, a[c / 32][j], c % 32);  // L(c, j)
+#pragma unroll
+      for (int h = 0; h < H; ++h) a[h][c] = fmaf(-a[h][j], lc, a[h][c]);
+    }
+  }
+  if (!ok) return false;
+  // W(r, c), lane column c = lane + 32 h: W(c, c) = 1/L_cc, zero above
+  float w[H][NB];
+#pragma unroll
+  for (int r = 0; r < NB; ++r) {
+    float acc0[H], acc1[H];
+#pragma unroll
+    for (int h = 0; h < H; ++h) acc0[h] = acc1[h] = 0.f;
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+      if (t >= r) continue;
+      const float lrt = __shfl_sync(FULL, a[r / 32][t], r % 32);  // L(r, t)
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        if (t & 1) acc1[h] = fmaf(lrt, w[h][t], acc1[h]);
+        else acc0[h] = fmaf(lrt, w[h][t], acc0[h]);
+      }
+    }
+    const float dr = __shfl_sync(FULL, rown[r / 32], r % 32);  // 1 / L_rr
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      const int c = lane + 32 * h;
+      w[h][r] = (r > c) ? -(acc0[h] + acc1[h]) * dr : ((r == c) ? dr : 0.f);
+    }
+  }
+  // D^-1(a, b) = sum_{r >= b} W(r, a) W(r, b) (terms with r < a vanish)
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    float acc0[H], acc1[H];
+#pragma unroll
+    for (int h = 0; h < H; ++h) acc0[h] = acc1[h] = 0.f;
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+      if (r < b) continue;
+      const float wrb = __shfl_sync(FULL, w[b / 32][r], b % 32);  // W(r, b)
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        if (r & 1) acc1[h] = fmaf(w[h][r], wrb, acc1[h]);
+        else acc0[h] = fmaf(w[h][r], wrb, acc0[h]);
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < H; ++h)
+      if (lane + 32 * h < NB) out[b * NB + lane + 32 * h] = acc0[h] + acc1[h];
+  }
+  return true;
+}
+
 // ---------------------------------------------------------------- K1 (mixed)
 // Float32 factor for mixed handles, one warp per block row in a 4 n (n+1)
 // byte shared region (+ 64 floats):
@@ -188,6 +282,18 @@ __global__ void k_factor32(const __grid_constant__ SetupParams P, int wpc, int w
     copy_block(P.O + P.o_off[rr.inst] + (long long)i * nn, P.O64 + d.off64 + (long long)i * d.bs64,
                P.O32 + d.off32 + (long long)i * d.bs32);
   copy_block(P.D + P.d_off[rr.inst] + (long long)i * nn, P.D64 + d.off64 + (long long)i * d.bs64, D32);
+  float* out = P.Dinv32 + d.off32 + (long long)i * d.bs32;
+  {
+    int done = -1;  // -1: no register variant for this n
+    switch (n) {
+      case 12: done = factor_regs<12>(D32, out, lane) ? 1 : 0; break;
+      case 24: done = factor_regs<24>(D32, out, lane) ? 1 : 0; break;
+      case 36: done = factor_regs<36>(D32, out, lane) ? 1 : 0; break;
+      default: break;
+    }
+    if (done == 0 && lane == 0) P.retry[1 + atomicAdd(P.retry, 1)] = (int)gr;
+    if (done >= 0) return;
+  }
   // this warp's own float32 copy, column-major: A[c n + r] = D(r, c)
   for (int t = lane; t < nn; t += 32) A[t] = __ldcg(D32 + t);
   __syncwarp();
@@ -232,7 +338,6 @@ __global__ void k_factor32(const __grid_constant__ SetupParams P, int wpc, int w
   }
   __syncwarp();
   // 4. D_i^-1(a, b) = sum_{r >= max(a, b)} W(r, a) W(r, b), column b per step
-  float* out = P.Dinv32 + d.off32 + (long long)i * d.bs32;
   for (int b = 0; b < n; ++b) {
     float acc0 = 0.f, acc1 = 0.f;
     for (int r = b; r < n; ++r) {
@@ -428,47 +533,74 @@ __global__ void k_H(const __grid_constant__ SetupParams P) {
 //   E_j     = D_j^-1 T_j                    (rows a-1 .. b; stored for j in [a, b))
 //   H_{j-2}: Hd = E^T_{i-1} O_{i-1} + E_i O_i^T, Hu = E_i O_{i+1},
 //            Hl = E_{i+1}^T O_i^T           (i = j-2 in [a, b))
-// while cp.async prefetches O_{j+2} and D_{j+3}^-1 for the next step.  Ring
-// sizes follow the block lifetimes: O 6, D^-1 4, T 2, E 4 slots.  Every
-// output element is one fma chain over k = 0 .. n-1 (two chains in a row for
-// Hd), the same arithmetic as K2/K3.
-template <int TS, bool TA, bool TB>
+// while cp.async prefetches O_{j+2} and D_{j+3}^-1 for the next step.  E_j is
+// also kept transposed, so that every product reads its left operand along a
+// column (no strided shared-memory reads).  Ring sizes follow the block
+// lifetimes: O 6, D^-1 4, T 2, E 4, E^T 4 slots.  Every output element is one
+// fma chain over k = 0 .. n-1 (two chains in a row for Hd), the same
+// arithmetic as K2/K3.
+constexpr int kEHSlots = 20;
+
+// acc(r, c) += sum_k A(a0 + r, k) opB(k, b0 + c); X(a, c) at X[c n + a];
+// TB: opB = B^T.
+template <int TS, bool TB>
 __device__ __forceinline__ void tile_acc(float (&acc)[TS][TS], const float* __restrict__ A,
                                          const float* __restrict__ B, int n, int a0, int b0) {
-  // acc(r, c) += sum_k opA(a0 + r, k) opB(k, b0 + c); X(a, c) at X[c n + a]
-  for (int k = 0; k < n; ++k) {
-    float av[TS], bv[TS];
-    if constexpr (!TA && TS == 4) {
-      const float4 v = *reinterpret_cast<const float4*>(A + k * n + a0);
-      av[0] = v.x; av[1] = v.y; av[2] = v.z; av[3] = v.w;
-    } else {
+  if constexpr (TS == 4) {  // n % 4 == 0: 4-deep k steps, 128-bit loads of both operands
+    for (int k = 0; k < n; k += 4) {
+      float4 av[4], bv[4];
 #pragma unroll
-      for (int r = 0; r < TS; ++r) av[r] = TA ? A[(a0 + r) * n + k] : A[k * n + a0 + r];
+      for (int kk = 0; kk < 4; ++kk) av[kk] = *reinterpret_cast<const float4*>(A + (k + kk) * n + a0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        bv[q] = TB ? *reinterpret_cast<const float4*>(B + (k + q) * n + b0)     // row k+q of B^T: b0..b0+3
+                   : *reinterpret_cast<const float4*>(B + (b0 + q) * n + k);    // column b0+q of B: k..k+3
+      const float* af = reinterpret_cast<const float*>(av);
+      const float* bf = reinterpret_cast<const float*>(bv);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const float bkc = TB ? bf[kk * 4 + c] : bf[c * 4 + kk];
+            acc[r][c] = fmaf(af[kk * 4 + r], bkc, acc[r][c]);
+          }
     }
-    if constexpr (TB && TS == 4) {
-      const float4 v = *reinterpret_cast<const float4*>(B + k * n + b0);
-      bv[0] = v.x; bv[1] = v.y; bv[2] = v.z; bv[3] = v.w;
-    } else {
+  } else {
+    for (int k = 0; k < n; ++k) {
+      float av[TS], bv[TS];
+#pragma unroll
+      for (int r = 0; r < TS; ++r) av[r] = A[k * n + a0 + r];
 #pragma unroll
       for (int c = 0; c < TS; ++c) bv[c] = TB ? B[k * n + b0 + c] : B[(b0 + c) * n + k];
+#pragma unroll
+      for (int r = 0; r < TS; ++r)
+#pragma unroll
+        for (int c = 0; c < TS; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
     }
-#pragma unroll
-    for (int r = 0; r < TS; ++r)
-#pragma unroll
-      for (int c = 0; c < TS; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
   }
 }
 
-template <int TS>
+// C(a0 + r, b0 + c) = acc(r, c); TR: store C^T instead.
+template <int TS, bool TR = false>
 __device__ __forceinline__ void tile_store(float* C, const float (&acc)[TS][TS], int n, int a0, int b0) {
+  if constexpr (TS == 4) {
 #pragma unroll
-  for (int c = 0; c < TS; ++c) {
-    if constexpr (TS == 4) {
-      *reinterpret_cast<float4*>(C + (b0 + c) * n + a0) = make_float4(acc[0][c], acc[1][c], acc[2][c], acc[3][c]);
-    } else {
-#pragma unroll
-      for (int r = 0; r < TS; ++r) C[(b0 + c) * n + a0 + r] = acc[r][c];
+    for (int q = 0; q < 4; ++q) {
+      if constexpr (TR)
+        *reinterpret_cast<float4*>(C + (a0 + q) * n + b0) = make_float4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]);
+      else
+        *reinterpret_cast<float4*>(C + (b0 + q) * n + a0) = make_float4(acc[0][q], acc[1][q], acc[2][q], acc[3][q]);
     }
+  } else {
+#pragma unroll
+    for (int c = 0; c < TS; ++c)
+#pragma unroll
+      for (int r = 0; r < TS; ++r) {
+        if constexpr (TR) C[(a0 + r) * n + b0 + c] = acc[r][c];
+        else C[(b0 + c) * n + a0 + r] = acc[r][c];
+      }
   }
 }
 
@@ -488,11 +620,13 @@ __device__ void eh_segment(const SetupParams& P, const SegRef sg, bool want_h, f
   float* sD = sO + 6 * bs;
   float* sT = sD + 4 * bs;
   float* sE = sT + 2 * bs;
+  float* sET = sE + 4 * bs;
   // slot of block k (k >= -3 here, so k + 12 > 0)
   const auto O_ = [&](int k) { return sO + ((k + 12) % 6) * bs; };
   const auto D_ = [&](int k) { return sD + ((k + 12) % 4) * bs; };
   const auto T_ = [&](int k) { return sT + ((k + 12) % 2) * bs; };
   const auto E_ = [&](int k) { return sE + ((k + 12) % 4) * bs; };
+  const auto ET_ = [&](int k) { return sET + ((k + 12) % 4) * bs; };
   const auto load = [&](float* dst, const float* src) {
     for (int t = threadIdx.x * 4; t < bs; t += blockDim.x * 4) cp16(dst + t, src + t);
   };
@@ -534,21 +668,22 @@ __device__ void eh_segment(const SetupParams& P, const SegRef sg, bool want_h, f
 #pragma unroll
         for (int c = 0; c < TS; ++c) acc[r][c] = 0.f;
       if (job == 0) {
-        tile_acc<TS, false, false>(acc, O_(j + 1), D_(j + 2), n, a0, b0);
+        tile_acc<TS, false>(acc, O_(j + 1), D_(j + 2), n, a0, b0);
         tile_store<TS>(T_(j + 1), acc, n, a0, b0);
       } else if (job == 1) {
-        tile_acc<TS, false, false>(acc, D_(j), T_(j), n, a0, b0);
+        tile_acc<TS, false>(acc, D_(j), T_(j), n, a0, b0);
         tile_store<TS>(E_(j), acc, n, a0, b0);
+        tile_store<TS, true>(ET_(j), acc, n, a0, b0);
         if (j >= a && j < b) tile_store<TS>(Eg + (long long)j * bs, acc, n, a0, b0);
       } else if (job == 2) {
-        if (i > 0) tile_acc<TS, true, false>(acc, E_(i - 1), O_(i - 1), n, a0, b0);
-        if (i < N - 1) tile_acc<TS, false, true>(acc, E_(i), O_(i), n, a0, b0);
+        if (i > 0) tile_acc<TS, false>(acc, ET_(i - 1), O_(i - 1), n, a0, b0);
+        if (i < N - 1) tile_acc<TS, true>(acc, E_(i), O_(i), n, a0, b0);
         tile_store<TS>(P.Hd32 + d.off32 + (long long)i * bs, acc, n, a0, b0);
       } else if (job == 3) {
-        tile_acc<TS, false, false>(acc, E_(i), O_(i + 1), n, a0, b0);
+        tile_acc<TS, false>(acc, E_(i), O_(i + 1), n, a0, b0);
         tile_store<TS>(P.Hu32 + d.off32 + (long long)i * bs, acc, n, a0, b0);
       } else {
-        tile_acc<TS, true, true>(acc, E_(i + 1), O_(i), n, a0, b0);
+        tile_acc<TS, true>(acc, ET_(i + 1), O_(i), n, a0, b0);
         tile_store<TS>(P.Hl32 + d.off32 + (long long)i * bs, acc, n, a0, b0);
       }
     }
@@ -609,7 +744,7 @@ extern "C" cudaError_t bt_launch_setup(const bt::SetupParams* P, int mixed, int 
   const int sm_prod = 3 * maxn * maxn * msz;
   if (mixed && P->retry) {
     const int per_warp32 = (4 * maxn * (maxn + 1) + 15) / 16 * 16 + 64 * (int)sizeof(float);
-    const int wpc32 = 8;
+    const int wpc32 = 4;  // register-resident factor: ~170 registers per thread
     const int sm32 = wpc32 * per_warp32;
     cudaFuncSetAttribute(bt::k_factor32, cudaFuncAttributeMaxDynamicSharedMemorySize, sm32);
     cudaFuncSetAttribute(bt::k_factor_retry, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_fac);
@@ -622,7 +757,7 @@ extern "C" cudaError_t bt_launch_setup(const bt::SetupParams* P, int mixed, int 
     bt::k_factor_retry<<<(unsigned)rgrid, 32 * wpc, sm_fac, st>>>(*P, wpc, per_warp);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     const int maxbs = (maxn * maxn + 3) / 4 * 4;
-    const int sm_eh = 16 * maxbs * (int)sizeof(float);
+    const int sm_eh = bt::kEHSlots * maxbs * (int)sizeof(float);
     if (P->segs && P->nsegs > 0 && sm_eh <= 200 * 1024) {
       cudaFuncSetAttribute(bt::k_EH, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_eh);
       bt::k_EH<<<(unsigned)P->nsegs, 256, sm_eh, st>>>(*P, m >= 2 ? 1 : 0);
