@@ -186,7 +186,7 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
     const int N = h->N[k], n = h->n[k];
     inst[k].N = N;
     inst[k].n = n;
-    inst[k].bs32 = (int)rup((long long)n * n, 4);
+    inst[k].bs32 = bt::slot32(n);
     inst[k].bs64 = (int)rup((long long)n * n, 2);
     inst[k].off32 = off32;
     inst[k].off64 = off64;
@@ -284,7 +284,9 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
 
   // ---- launch configuration of the persistent kernel ----
   const int wbytes = mixed ? 4 : 8;
-  const long long bsb_max = rup((long long)h->maxn * h->maxn, mixed ? 4 : 2) * wbytes;
+  long long bsb_max = rup((long long)h->maxn * h->maxn, 2) * wbytes;
+  if (mixed)
+    for (int q = 1; q <= h->maxn; ++q) bsb_max = std::max<long long>(bsb_max, (long long)bt::slot32(q) * wbytes);
   const long long bsb64_max = rup((long long)h->maxn * h->maxn, 2) * 8;
   long long need = std::max(5 * bsb_max, 3 * bsb64_max);
   long long sb = h->prm.stage_kb > 0 ? (long long)h->prm.stage_kb * 1024 : 80 * 1024;
@@ -721,7 +723,7 @@ bt_status bt_pcg_solve_multi(bt_handle h, const double* B, double* X, int nrhs, 
   const double tin = h->prm.tol_inner > 0 ? h->prm.tol_inner : 1e-5;
   const int mo = h->prm.max_outer > 0 ? h->prm.max_outer : 30;
   const long long budget = h->prm.cycle_budget > 0 ? h->prm.cycle_budget : (1ll << 36);
-  const int bs32 = (int)rup((long long)n * n, 4), bs64 = (int)rup((long long)n * n, 2);
+  const int bs32 = bt::slot32(n), bs64 = (int)rup((long long)n * n, 2);
   cudaError_t e = bt_mrhs_solve_launch(N, n, h->prm.m, h->alpha, blk32, h->D64, h->O64, bs32, bs64, h->mr_vec, tol,
                                        tin, maxit, mo, budget, h->mr_G, nrhs, B, X, h->mr_smem, h->stream);
   if (e != cudaSuccess) return BT_ERR_CUDA;

@@ -69,6 +69,19 @@ struct KParams {
   int vec_slot_bytes;      // bytes of one vector-ring slot
 };
 
+// Slot stride (in floats) of a float32 n x n block in the library layout.
+// A multiple of 4 (16-byte aligned slots for bulk copies); for n % 4 == 0 also
+// congruent to n modulo 32, so that consecutive blocks continue the bank
+// sequence of one column-major matrix: a warp whose lanes read column c of two
+// neighbouring blocks touches 32 consecutive banks (no shared-memory bank
+// conflicts in the chunk products) at the price of <= 31 padding floats.
+__host__ __device__ inline int slot32(int n) {
+  int s = (n * n + 3) / 4 * 4;
+  if (n % 4 == 0)
+    while (s % 32 != n % 32) s += 4;
+  return s;
+}
+
 struct RowRef {
   int inst, row;
 };
@@ -136,6 +149,10 @@ __device__ __forceinline__ void fence_proxy_async_global() {
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* b, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
                : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, unsigned parity) {

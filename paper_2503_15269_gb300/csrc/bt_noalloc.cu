@@ -117,7 +117,7 @@ extern "C" bt_status bt_pcg_solve_noalloc(int N, int n, const double* D, const d
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
 
   // launch configuration (same rules as a handle made by bt_setup)
-  const int bs32 = (int)rup((long long)n * n, 4);
+  const int bs32 = bt::slot32(n);
   const int bs64 = (int)rup((long long)n * n, 2);
   const long long bsb = mixed ? (long long)bs32 * 4 : (long long)bs64 * 8;
   long long sb = p->stage_kb > 0 ? (long long)p->stage_kb * 1024 : 80 * 1024;

@@ -127,15 +127,34 @@ template <int NB, typename T>
 __device__ __forceinline__ void dcol2(const T* __restrict__ M, int a, const T* __restrict__ v, T& o0, T& o1) {
   using V = typename Vec2<T>::type;
   T a0 = T(0), a1 = T(0), b0 = T(0), b1 = T(0);
+  if constexpr (sizeof(T) == 4 && NB % 4 == 0) {  // v four words per load
 #pragma unroll
-  for (int c = 0; c < NB; c += 2) {
-    const V m0 = *reinterpret_cast<const V*>(M + c * NB + a);
-    const V m1 = *reinterpret_cast<const V*>(M + (c + 1) * NB + a);
-    const V vv = *reinterpret_cast<const V*>(v + c);
-    a0 = fma(m0.x, vv.x, a0);
-    a1 = fma(m0.y, vv.x, a1);
-    b0 = fma(m1.x, vv.y, b0);
-    b1 = fma(m1.y, vv.y, b1);
+    for (int c = 0; c < NB; c += 4) {
+      const float4 vv = *reinterpret_cast<const float4*>(v + c);
+      const V m0 = *reinterpret_cast<const V*>(M + c * NB + a);
+      const V m1 = *reinterpret_cast<const V*>(M + (c + 1) * NB + a);
+      const V m2 = *reinterpret_cast<const V*>(M + (c + 2) * NB + a);
+      const V m3 = *reinterpret_cast<const V*>(M + (c + 3) * NB + a);
+      a0 = fma(m0.x, vv.x, a0);
+      a1 = fma(m0.y, vv.x, a1);
+      b0 = fma(m1.x, vv.y, b0);
+      b1 = fma(m1.y, vv.y, b1);
+      a0 = fma(m2.x, vv.z, a0);
+      a1 = fma(m2.y, vv.z, a1);
+      b0 = fma(m3.x, vv.w, b0);
+      b1 = fma(m3.y, vv.w, b1);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < NB; c += 2) {
+      const V m0 = *reinterpret_cast<const V*>(M + c * NB + a);
+      const V m1 = *reinterpret_cast<const V*>(M + (c + 1) * NB + a);
+      const V vv = *reinterpret_cast<const V*>(v + c);
+      a0 = fma(m0.x, vv.x, a0);
+      a1 = fma(m0.y, vv.x, a1);
+      b0 = fma(m1.x, vv.y, b0);
+      b1 = fma(m1.y, vv.y, b1);
+    }
   }
   o0 = a0 + b0;
   o1 = a1 + b1;

@@ -756,7 +756,8 @@ extern "C" cudaError_t bt_launch_setup(const bt::SetupParams* P, int mixed, int 
     const long long rgrid = std::min<long long>((nb + wpc - 1) / wpc, 304);
     bt::k_factor_retry<<<(unsigned)rgrid, 32 * wpc, sm_fac, st>>>(*P, wpc, per_warp);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    const int maxbs = (maxn * maxn + 3) / 4 * 4;
+    int maxbs = 0;  // largest float32 slot of any block size up to maxn
+    for (int q = 1; q <= maxn; ++q) maxbs = std::max(maxbs, bt::slot32(q));
     const int sm_eh = bt::kEHSlots * maxbs * (int)sizeof(float);
     if (P->segs && P->nsegs > 0 && sm_eh <= 200 * 1024) {
       cudaFuncSetAttribute(bt::k_EH, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_eh);
