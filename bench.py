@@ -158,15 +158,20 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def stored_traffic(batch):
+def stored_traffic(abytes):
+    """DRAM bytes (read + write) of one solve launch, from an ncu capture of a
+    smaller batch of the same workload: its measured DRAM bytes per
+    algorithmic byte, times this launch's algorithmic bytes (traffic grows
+    with the bytes the solves stream).  None once the kernel sources differ
+    from the captured ones."""
     try:
         t = json.load(open(TRAFFIC_FILE))
     except Exception:
         return None
     if t.get("kernel_hash") != kernel_hash():
         return None
-    per = t.get("dram_bytes_per_instance")
-    return None if per is None else per * batch
+    ratio = t.get("dram_bytes_per_alg_byte")
+    return None if ratio is None else int(ratio * abytes)
 
 
 def measured_peak():
@@ -330,13 +335,13 @@ def main():
 
     if a.profile:
         if rank == 0:
+            ab = int(alg_bytes([int(v) for v in Ns], [int(v) for v in ns], [int(v) for v in iters], outers))
             emit({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms / a.steps,
-                  "ms_solve": ms_solve, "ms_setup": ms_setup})
+                  "ms_solve": ms_solve, "ms_setup": ms_setup, "alg_bytes_per_solve_launch": ab,
+                  "kernel_hash": kernel_hash()})
         return
 
     # ---- end to end through host buffers ----
-    for _ in range(1):
-        pass
     torch.cuda.synchronize()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
@@ -367,7 +372,7 @@ def main():
     achieved = abytes / (ms_solve / 1e3) / 1e9
     peak, peak_kind = measured_peak()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": stored_traffic(B), "peak_source": peak_kind,
+            "traffic": stored_traffic(abytes), "peak_source": peak_kind,
             "kernel": "bt_persistent_kernel<float> (batched mixed solve)",
             "alg_bytes_per_launch": abytes, "ms_per_launch": ms_solve}
 
