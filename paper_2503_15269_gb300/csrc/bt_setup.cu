@@ -267,7 +267,14 @@ __global__ void k_factor32(const __grid_constant__ SetupParams P, int wpc, int w
     for (int a0 = 0; a0 < n; a0 += (n + 1) / 2) {
       const int h = min((n + 1) / 2, n - a0), cnt = h * n;
       const float inv_h = 1.0f / (float)h;
-      for (int t = lane; t < cnt; t += 32) stg[t] = src[(long long)a0 * n + t];
+      // asynchronous 8-byte copies: every element of the half block in flight
+      // at once instead of one global round trip per loop iteration
+      for (int t = lane; t < cnt; t += 32)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(stg + t)),
+                     "l"(src + (long long)a0 * n + t)
+                     : "memory");
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
       __syncwarp();
       for (int t = lane; t < cnt; t += 32) {  // t = c * h + (a - a0)
         const int c = qdiv(t, inv_h), ar = t - c * h;

@@ -261,6 +261,29 @@ def test_mixed_ill_conditioned_block_apply(decades):
     assert err <= 2e-5, err
 
 
+def test_float32_copies_round_to_nearest_even():
+    # D = diag(d), O = 0: the float32 SpMV with x = 1 returns exactly the
+    # float32 copy of each d_i, which must be d_i rounded to nearest even
+    # (values at, just above and just below float32 midpoints, and random)
+    rng = np.random.default_rng(81)
+    N, n = 40, 36
+    f = rng.uniform(0.5, 4.0, N * n).astype(np.float32)
+    ulp = np.spacing(f).astype(np.float64)
+    d = f.astype(np.float64)
+    d[0::5] += ulp[0::5] / 2
+    d[1::5] -= ulp[1::5] / 2
+    d[2::5] += ulp[2::5] * 0.5000001
+    d[3::5] += ulp[3::5] * 0.4999999
+    d[4::5] = rng.uniform(1e-3, 1e3, d[4::5].size)
+    D = np.zeros((N, n, n))
+    D[:, np.arange(n), np.arange(n)] = d.reshape(N, n)
+    inst = wl.Instance(D=D, O=np.zeros((N - 1, n, n)), b=np.zeros((N, n)))
+    with Single(inst, m=2, alpha=[1.0, 7.0], precision=bb.BT_MIXED) as s:
+        s.ok()
+        y = s.spmv(np.ones((N, n)), f32=True)
+    assert np.array_equal(y.reshape(-1), d.astype(np.float32).astype(np.float64))
+
+
 def test_maxit_gives_no_convergence_and_last_iterate():
     inst = wl.config1()
     with Single(inst, m=2, alpha=[1.0, 7.0]) as s:
