@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 one-at-a-time comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-sample", type=int, default=48, help="instances in the oracle CPU sample")
+    ap.add_argument("--workload", choices=["ocp_batch", "many_rhs", "adjoint"], default="ocp_batch",
+                    help="ocp_batch: the headline workload (default); many_rhs: one LL^T system, N=2048, "
+                         "n=48, 64 right-hand sides; adjoint: 256 LQR instances, N=256, n=24, forward + adjoint")
     return ap.parse_args()
 
 
@@ -244,6 +247,9 @@ def main():
     a = parse()
     if a.impl == "reference":
         reference_arm(a)
+        return
+    if a.workload != "ocp_batch":
+        other_workload(a)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -452,6 +458,91 @@ def main():
     bb.bt_destroy(h)
     if dist:
         dist.destroy_process_group()
+
+
+def other_workload(a):
+    """The other measured rows, one GPU, inputs resident in HBM, CUDA events on
+    the launching stream, steps after warm-ups:
+      many_rhs  bt_pcg_solve_multi on the LL^T system N = 2048, n = 48 with 64
+                right-hand sides to 1e-8 (setup excluded; roofline of the
+                many-RHS kernel from its algorithmic bytes);
+      adjoint   bt_solve forward + backward (second solve + gradient blocks)
+                on 256 LQR instances, N = 256, n = 24, mixed, tol 1e-8."""
+    import numpy as np
+    import torch
+    from paper_2503_15269_gb300 import binding as bb
+    from paper_2503_15269_gb300 import workloads as wl
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if a.workload == "many_rhs":
+        inst = wl.config3()
+        N, n, J = inst.N, inst.n, 64
+        dD = torch.tensor(inst.D, device=dev)
+        dO = torch.tensor(inst.O, device=dev)
+        dB = torch.tensor(inst.b.reshape(N * n, J), device=dev)
+        dX = torch.zeros_like(dB)
+        p, keep = bb.make_params(m=M, alpha=ALPHA, precision=bb.BT_MIXED)
+        st, h = bb.bt_setup(N, n, dD, dO, p)
+        assert st == bb.BT_OK, bb.status_string(st)
+        for _ in range(a.warmup):
+            st, its, sts = bb.bt_pcg_solve_multi(h, dB, dX, J, TOL, 20000)
+            assert st == bb.BT_OK and (sts == 0).all()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(a.steps):
+            st, its, sts = bb.bt_pcg_solve_multi(h, dB, dX, J, TOL, 20000)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.steps
+        outers = [bb.bt_multi_info(h, j)[1] for j in range(J)]
+        bb.bt_destroy(h)
+        # bytes: every shared sweep streams the blocks once for all 64 columns;
+        # the sweeps of an outer step run until its slowest column converges
+        n2 = n * n
+        it_b = 4 * ((2 * N - 1) + (2 * N - 1) + (3 * N - 4) * (M - 1)) * n2 + 14 * 4 * N * n * J
+        prec_b = 4 * ((2 * N - 1) + (3 * N - 4) * (M - 1)) * n2 + 4 * 4 * N * n * J
+        a64_b = 8 * (2 * N - 1) * n2 + 3 * 8 * N * n * J
+        it_max, o_max = int(np.max(its)), int(np.max(outers))
+        abytes = it_max * it_b + o_max * (prec_b + a64_b)
+        peak, kind = measured_peak()
+        achieved = abytes / (ms / 1e3) / 1e9
+        emit({"metric": "right-hand sides solved per second to rel. residual 1e-8 (64 per call)",
+              "value": J / (ms / 1e3), "unit": "rhs/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+              "ms_per_step": ms, "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic (seeded LL^T)",
+              "config": {"workload": "LL^T N=2048 n=48, 64 right-hand sides, mixed, a=1 m=2 alpha=(1,7)"},
+              "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                           "frac": achieved / peak, "traffic": None, "peak_source": kind,
+                           "kernel": "bt_mrhs_kernel", "alg_bytes_per_launch": abytes},
+              "detail": {"iters_max": it_max, "iters_mean": float(np.mean(its)), "outer_max": o_max}})
+        return
+    from paper_2503_15269_gb300.autograd import bt_solve
+    insts = wl.config4()
+    Ns, ns, d_off, o_off, v_off, D, O, b = wl.pack_batch(insts)
+    D = torch.tensor(D, device=dev, requires_grad=True)
+    O = torch.tensor(O, device=dev, requires_grad=True)
+    b = torch.tensor(b, device=dev, requires_grad=True)
+    w = torch.tensor(np.random.default_rng(5).standard_normal(b.numel()), device=dev)
+
+    def step():
+        D.grad = O.grad = b.grad = None
+        x = bt_solve(D, O, b, Ns, ns, d_off, o_off, precision=bb.BT_MIXED, tol=TOL)
+        (x * w).sum().backward()
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(a.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.steps
+    B = len(insts)
+    emit({"metric": "forward + adjoint solves per second (x = S^-1 b and dL/d(D, O, b)), rel. residual 1e-8",
+          "value": B / (ms / 1e3), "unit": "instances/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+          "ms_per_step": ms, "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic (seeded LQR)",
+          "config": {"workload": "256 LQR instances N=256 n=24 (input size 8), setup + forward + adjoint per step"}})
 
 
 def fp64_one_at_a_time(bb, torch, dev, stream, Ns, ns, d_off, o_off, v_off, dD, dO, db):

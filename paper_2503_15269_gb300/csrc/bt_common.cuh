@@ -69,6 +69,30 @@ struct KParams {
   int vec_slot_bytes;      // bytes of one vector-ring slot
 };
 
+// Per-thread dot-product partials: float32 products summed with a compensated
+// float32 sum (TwoSum: each addition's rounding error is carried in c, so the
+// partial stays within a few float32 ulps whatever the number of terms),
+// widened to float64 once; float64 partials sum plainly.
+template <typename T>
+struct Accum;
+template <>
+struct Accum<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    const float bp = t - s;
+    c += (s - (t - bp)) + (x - bp);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+template <>
+struct Accum<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
 // Slot stride (in floats) of a float32 n x n block in the library layout.
 // A multiple of 4 (16-byte aligned slots for bulk copies); for n % 4 == 0 also
 // congruent to n modulo 32, so that consecutive blocks continue the bank

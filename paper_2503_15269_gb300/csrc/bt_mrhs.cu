@@ -174,6 +174,13 @@ struct MSolver {
   }
 };
 
+// Element (row, a, j0..j0+3) of an [N][n][kJ] vector: 4 consecutive columns.
+__device__ __forceinline__ float4 ldv4(const float* v, size_t idx) { return *reinterpret_cast<const float4*>(v + idx); }
+__device__ __forceinline__ void stv4(float* v, size_t idx, float4 x) { *reinterpret_cast<float4*>(v + idx) = x; }
+__device__ __forceinline__ void widen(const Accum<float> (&a)[4], double (&d)[4]) {
+  for (int c = 0; c < 4; ++c) d[c] = a[c].value();
+}
+
 // Reduce per-thread column partials part[jg][4] (threads laid out t = ag*16 + jg)
 // into colv[kJ] over the CTA, fixed order.
 __device__ __forceinline__ void cta_col_reduce(const double (&pv)[4], double* scratch /* [kMThreads/16][kJ] */,
@@ -203,7 +210,7 @@ using namespace bt;
 //   then two job buffers of kJobBytes
 constexpr int kColBytes = kJ * 8;
 constexpr int kMSmScalars = 256;
-constexpr int kMNumCols = 12;
+constexpr int kMNumCols = 13;  // 12 double columns + float alpha/beta copies
 constexpr int kMSmScratch = kMSmScalars + kMNumCols * kColBytes;
 constexpr int kMSmJobs = kMSmScratch + 16 * kJ * 8;
 
@@ -339,6 +346,8 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
   double* itc = col + 9 * kJ;      // inner iterations per column
   double* scl = col + 10 * kJ;     // 1 / ||r64_j||
   double* rrv = col + 11 * kJ;
+  float* alpf = reinterpret_cast<float*>(col + 12 * kJ);  // float copies of alpha_j, beta_j
+  float* betf = alpf + kJ;
   double* scratch = reinterpret_cast<double*>(smem + kMSmScratch);
   Sv.colbuf = colR;
   const int n = P.n, N = P.N;
@@ -434,12 +443,12 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
     auto apply_precond = [&](double* rzout) {
       // B1: y0 = G r
       msweep<float>(Sv, MP_B1, P.R, [&](int row, int a0, int j0, float (&o)[4][4], const float*) {
-        for (int r = 0; r < 4; ++r)
-          for (int c = 0; c < 4; ++c) {
-            const size_t idx = (size_t)row * vb + (size_t)(a0 + r) * J + j0 + c;
-            P.Y0[idx] = o[r][c];
-            if (m == 1) P.Z[idx] = o[r][c];
-          }
+        for (int r = 0; r < 4; ++r) {
+          const size_t idx = (size_t)row * vb + (size_t)(a0 + r) * J + j0;
+          const float4 y = make_float4(o[r][0], o[r][1], o[r][2], o[r][3]);
+          stv4(P.Y0, idx, y);
+          if (m == 1) stv4(P.Z, idx, y);
+        }
       });
       Sv.barrier();
       for (int jp = 1; jp < m && !Sv.fail; ++jp) {
@@ -447,26 +456,32 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
         float* yout = (jp % 2 == 1) ? P.Ya : P.Yb;
         const float aj = P.alpha[jp];
         msweep<float>(Sv, MP_B2, yin, [&](int row, int a0, int j0, float (&o)[4][4], const float*) {
-          for (int r = 0; r < 4; ++r)
-            for (int c = 0; c < 4; ++c) {
-              const size_t idx = (size_t)row * vb + (size_t)(a0 + r) * J + j0 + c;
-              yout[idx] = o[r][c];
-              const float zp = (jp == 1) ? P.Y0[idx] : P.Z[idx];
-              P.Z[idx] = fmaf(aj, o[r][c], zp);
-            }
+          for (int r = 0; r < 4; ++r) {
+            const size_t idx = (size_t)row * vb + (size_t)(a0 + r) * J + j0;
+            const float4 y = make_float4(o[r][0], o[r][1], o[r][2], o[r][3]);
+            stv4(yout, idx, y);
+            const float4 zp = ldv4((jp == 1) ? P.Y0 : P.Z, idx);
+            stv4(P.Z, idx, make_float4(fmaf(aj, y.x, zp.x), fmaf(aj, y.y, zp.y), fmaf(aj, y.z, zp.z),
+                                       fmaf(aj, y.w, zp.w)));
+          }
         });
         Sv.barrier();
       }
       // rz per column
-      double pv[4] = {0, 0, 0, 0};
+      Accum<float> pa[4];
       const int jg = tid & 15, ag = tid >> 4;
       if (ag < ngroups)
         for (int row = Sv.s; row < Sv.e; ++row)
-          for (int r = 0; r < 4; ++r)
-            for (int c = 0; c < 4; ++c) {
-              const size_t idx = (size_t)row * vb + (size_t)(4 * ag + r) * J + 4 * jg + c;
-              pv[c] += (double)P.R[idx] * (double)P.Z[idx];
-            }
+          for (int r = 0; r < 4; ++r) {
+            const size_t idx = (size_t)row * vb + (size_t)(4 * ag + r) * J + 4 * jg;
+            const float4 rv = ldv4(P.R, idx), zv = ldv4(P.Z, idx);
+            pa[0].add(rv.x * zv.x);
+            pa[1].add(rv.y * zv.y);
+            pa[2].add(rv.z * zv.z);
+            pa[3].add(rv.w * zv.w);
+          }
+      double pv[4];
+      widen(pa, pv);
       cta_col_reduce(pv, scratch, colR, ngroups);
       Sv.grid_reduce(colR);
       if (tid < J) rzout[tid] = colR[tid];
@@ -478,29 +493,32 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
       const int jg = tid & 15, ag = tid >> 4;
       if (ag < ngroups)
         for (int row = Sv.s; row < Sv.e; ++row)
-          for (int r = 0; r < 4; ++r)
-            for (int c = 0; c < 4; ++c) {
-              const size_t idx = (size_t)row * vb + (size_t)(4 * ag + r) * J + 4 * jg + c;
-              P.P[idx] = P.Z[idx];
-            }
+          for (int r = 0; r < 4; ++r) {
+            const size_t idx = (size_t)row * vb + (size_t)(4 * ag + r) * J + 4 * jg;
+            stv4(P.P, idx, ldv4(P.Z, idx));
+          }
       Sv.barrier();
     }
     // inner iterations
     for (int kit = 1; !Sv.fail; ++kit) {
-      int anyact = 0;
-      for (int j = 0; j < J; ++j) anyact |= (actv[j] > 0.0);
+      const int anyact = __syncthreads_or(tid < J && actv[tid] > 0.0);
       if (!anyact || total_it >= P.maxit) break;
       ++total_it;
       // A: q = S p, pq per column
-      double pv[4] = {0, 0, 0, 0};
+      Accum<float> pa[4];
       msweep<float>(Sv, MP_A, P.P, [&](int row, int a0, int j0, float (&o)[4][4], const float* pc) {
-        for (int r = 0; r < 4; ++r)
-          for (int c = 0; c < 4; ++c) {
-            const size_t idx = (size_t)row * vb + (size_t)(a0 + r) * J + j0 + c;
-            P.Q[idx] = o[r][c];
-            pv[c] += (double)pc[(a0 + r) * J + j0 + c] * (double)o[r][c];
-          }
+        for (int r = 0; r < 4; ++r) {
+          const size_t idx = (size_t)row * vb + (size_t)(a0 + r) * J + j0;
+          stv4(P.Q, idx, make_float4(o[r][0], o[r][1], o[r][2], o[r][3]));
+          const float4 pp = *reinterpret_cast<const float4*>(pc + (a0 + r) * J + j0);
+          pa[0].add(pp.x * o[r][0]);
+          pa[1].add(pp.y * o[r][1]);
+          pa[2].add(pp.z * o[r][2]);
+          pa[3].add(pp.w * o[r][3]);
+        }
       });
+      double pv[4];
+      widen(pa, pv);
       cta_col_reduce(pv, scratch, colR, ngroups);
       Sv.grid_reduce(colR);
       if (tid < J) {
@@ -512,25 +530,32 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
         } else {
           alp[tid] = 0.0;
         }
+        alpf[tid] = (float)alp[tid];
         if (actv[tid] > 0.0) itc[tid] += 1.0;
       }
       __syncthreads();
       // x += alpha p, r -= alpha q, rr per column
       {
-        double pr[4] = {0, 0, 0, 0};
+        Accum<float> pa[4];
         const int jg = tid & 15, ag = tid >> 4;
+        const float4 al = *reinterpret_cast<const float4*>(alpf + 4 * jg);
         if (ag < ngroups)
           for (int row = Sv.s; row < Sv.e; ++row)
-            for (int r = 0; r < 4; ++r)
-              for (int c = 0; c < 4; ++c) {
-                const int j = 4 * jg + c;
-                const size_t idx = (size_t)row * vb + (size_t)(4 * ag + r) * J + j;
-                const float a = (float)alp[j];
-                P.Xin[idx] = fmaf(a, P.P[idx], P.Xin[idx]);
-                const float rv = fmaf(-a, P.Q[idx], P.R[idx]);
-                P.R[idx] = rv;
-                pr[c] += (double)rv * (double)rv;
-              }
+            for (int r = 0; r < 4; ++r) {
+              const size_t idx = (size_t)row * vb + (size_t)(4 * ag + r) * J + 4 * jg;
+              const float4 pp = ldv4(P.P, idx), qq = ldv4(P.Q, idx), xx = ldv4(P.Xin, idx), rr = ldv4(P.R, idx);
+              stv4(P.Xin, idx, make_float4(fmaf(al.x, pp.x, xx.x), fmaf(al.y, pp.y, xx.y), fmaf(al.z, pp.z, xx.z),
+                                           fmaf(al.w, pp.w, xx.w)));
+              const float4 rv = make_float4(fmaf(-al.x, qq.x, rr.x), fmaf(-al.y, qq.y, rr.y), fmaf(-al.z, qq.z, rr.z),
+                                            fmaf(-al.w, qq.w, rr.w));
+              stv4(P.R, idx, rv);
+              pa[0].add(rv.x * rv.x);
+              pa[1].add(rv.y * rv.y);
+              pa[2].add(rv.z * rv.z);
+              pa[3].add(rv.w * rv.w);
+            }
+        double pr[4];
+        widen(pa, pr);
         cta_col_reduce(pr, scratch, colR, ngroups);
         Sv.grid_reduce(colR);
         if (tid < J) {
@@ -539,8 +564,7 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
         }
         __syncthreads();
       }
-      int still = 0;
-      for (int j = 0; j < J; ++j) still |= (actv[j] > 0.0);
+      const int still = __syncthreads_or(tid < J && actv[tid] > 0.0);
       if (!still) break;
       apply_precond(bet);   // bet temporarily holds the new r.z
       if (tid < J) {
@@ -548,6 +572,7 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
         const double b = (actv[tid] > 0.0) ? rzn / rho[tid] : 0.0;
         rho[tid] = rzn;
         bet[tid] = b;
+        betf[tid] = (float)b;
       }
       __syncthreads();
       // p = z + beta p
@@ -555,12 +580,13 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
         const int jg = tid & 15, ag = tid >> 4;
         if (ag < ngroups)
           for (int row = Sv.s; row < Sv.e; ++row)
-            for (int r = 0; r < 4; ++r)
-              for (int c = 0; c < 4; ++c) {
-                const int j = 4 * jg + c;
-                const size_t idx = (size_t)row * vb + (size_t)(4 * ag + r) * J + j;
-                P.P[idx] = fmaf((float)bet[j], P.P[idx], P.Z[idx]);
-              }
+            for (int r = 0; r < 4; ++r) {
+              const size_t idx = (size_t)row * vb + (size_t)(4 * ag + r) * J + 4 * jg;
+              const float4 be = *reinterpret_cast<const float4*>(betf + 4 * jg);
+              const float4 pp = ldv4(P.P, idx), zz = ldv4(P.Z, idx);
+              stv4(P.P, idx, make_float4(fmaf(be.x, pp.x, zz.x), fmaf(be.y, pp.y, zz.y), fmaf(be.z, pp.z, zz.z),
+                                         fmaf(be.w, pp.w, zz.w)));
+            }
         Sv.barrier();
       }
     }

@@ -288,26 +288,6 @@ __device__ __forceinline__ float4 fma4(float a, float4 x, float4 y) {
 __device__ __forceinline__ float dot4f(float4 a, float4 b) {
   return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)));
 }
-template <typename T>
-struct Accum;
-template <>
-struct Accum<float> {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(float x) {
-    const float t = s + x;
-    const float bp = t - s;
-    c += (s - (t - bp)) + (x - bp);
-    s = t;
-  }
-  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
-};
-template <>
-struct Accum<double> {
-  double s = 0.0;
-  __device__ __forceinline__ void add(double x) { s += x; }
-  __device__ __forceinline__ double value() const { return s; }
-};
-
 template <typename MT>
 struct Solver {
   const KParams& P;
