@@ -138,10 +138,10 @@ struct MSolver {
     int* flag = reinterpret_cast<int*>(sm);
     const int par = bar_count & 1;  // every thread keeps the barrier count
     ++bar_count;
+    if (threadIdx.x < kJ) P.red[((size_t)par * G + g) * kJ + threadIdx.x] = colv[threadIdx.x];
+    __syncthreads();
     if (threadIdx.x == 0) {
-      double* slot = P.red + ((size_t)par * G + g) * kJ;
-      for (int j = 0; j < kJ; ++j) slot[j] = colv[j];
-      __threadfence();
+      __threadfence();  // after the CTA barrier: publishes every thread's slot store
       atomicAdd(P.bar, 1u);
       const unsigned target = (unsigned)G * (unsigned)bar_count;
       int bad = 0;
@@ -159,10 +159,21 @@ struct MSolver {
       fail = true;
       return;
     }
-    if (threadIdx.x < kJ) {
+    // Totals: the 4 x 64 threads each sum a quarter of the G slots of one
+    // column with independent L2 loads (the barrier above acquired them),
+    // then the quarters are added in a fixed order (bitwise reproducible).
+    {
+      static_assert(kMThreads == 4 * kJ, "four threads per column");
+      double* part = colred;  // [4][kJ] doubles of the CTA's scratch
+      const int q = threadIdx.x / kJ, j = threadIdx.x % kJ;
+      const int g0 = q * G / 4, g1 = (q + 1) * G / 4;
+      const double* src = P.red + (size_t)par * G * kJ + j;
       double t = 0.0;
-      for (int gg = 0; gg < G; ++gg) t += reinterpret_cast<volatile double*>(P.red)[((size_t)par * G + gg) * kJ + threadIdx.x];
-      colv[threadIdx.x] = t;
+#pragma unroll 8
+      for (int gg = g0; gg < g1; ++gg) t += __ldcg(src + (size_t)gg * kJ);
+      part[q * kJ + j] = t;
+      __syncthreads();
+      if (threadIdx.x < kJ) colv[j] = ((part[j] + part[kJ + j]) + part[2 * kJ + j]) + part[3 * kJ + j];
     }
     __syncthreads();
   }
@@ -350,6 +361,7 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
   float* betf = alpf + kJ;
   double* scratch = reinterpret_cast<double*>(smem + kMSmScratch);
   Sv.colbuf = colR;
+  Sv.colred = scratch;
   const int n = P.n, N = P.N;
   const int tid = threadIdx.x;
   const int ngroups = n / 4;
@@ -441,45 +453,49 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
     }
     // z0 = M^-1 r0 ; rho = r.z
     auto apply_precond = [&](double* rzout) {
-      // B1: y0 = G r
-      msweep<float>(Sv, MP_B1, P.R, [&](int row, int a0, int j0, float (&o)[4][4], const float*) {
+      // r.z per column, summed in the finalize of the sweep that completes z
+      Accum<float> pa[4];
+      // B1: y0 = G r (r is the staged centre block of this sweep)
+      msweep<float>(Sv, MP_B1, P.R, [&](int row, int a0, int j0, float (&o)[4][4], const float* xc) {
         for (int r = 0; r < 4; ++r) {
           const size_t idx = (size_t)row * vb + (size_t)(a0 + r) * J + j0;
           const float4 y = make_float4(o[r][0], o[r][1], o[r][2], o[r][3]);
           stv4(P.Y0, idx, y);
-          if (m == 1) stv4(P.Z, idx, y);
+          if (m == 1) {
+            stv4(P.Z, idx, y);
+            const float4 rv = *reinterpret_cast<const float4*>(xc + (a0 + r) * J + j0);
+            pa[0].add(rv.x * y.x);
+            pa[1].add(rv.y * y.y);
+            pa[2].add(rv.z * y.z);
+            pa[3].add(rv.w * y.w);
+          }
         }
       });
-      Sv.barrier();
       for (int jp = 1; jp < m && !Sv.fail; ++jp) {
+        Sv.barrier();
         const float* yin = (jp == 1) ? P.Y0 : ((jp - 1) % 2 == 1 ? P.Ya : P.Yb);
         float* yout = (jp % 2 == 1) ? P.Ya : P.Yb;
         const float aj = P.alpha[jp];
+        const bool lastj = (jp == m - 1);
         msweep<float>(Sv, MP_B2, yin, [&](int row, int a0, int j0, float (&o)[4][4], const float*) {
           for (int r = 0; r < 4; ++r) {
             const size_t idx = (size_t)row * vb + (size_t)(a0 + r) * J + j0;
             const float4 y = make_float4(o[r][0], o[r][1], o[r][2], o[r][3]);
-            stv4(yout, idx, y);
+            if (!lastj) stv4(yout, idx, y);
             const float4 zp = ldv4((jp == 1) ? P.Y0 : P.Z, idx);
-            stv4(P.Z, idx, make_float4(fmaf(aj, y.x, zp.x), fmaf(aj, y.y, zp.y), fmaf(aj, y.z, zp.z),
-                                       fmaf(aj, y.w, zp.w)));
+            const float4 z = make_float4(fmaf(aj, y.x, zp.x), fmaf(aj, y.y, zp.y), fmaf(aj, y.z, zp.z),
+                                         fmaf(aj, y.w, zp.w));
+            stv4(P.Z, idx, z);
+            if (lastj) {
+              const float4 rv = ldv4(P.R, idx);
+              pa[0].add(rv.x * z.x);
+              pa[1].add(rv.y * z.y);
+              pa[2].add(rv.z * z.z);
+              pa[3].add(rv.w * z.w);
+            }
           }
         });
-        Sv.barrier();
       }
-      // rz per column
-      Accum<float> pa[4];
-      const int jg = tid & 15, ag = tid >> 4;
-      if (ag < ngroups)
-        for (int row = Sv.s; row < Sv.e; ++row)
-          for (int r = 0; r < 4; ++r) {
-            const size_t idx = (size_t)row * vb + (size_t)(4 * ag + r) * J + 4 * jg;
-            const float4 rv = ldv4(P.R, idx), zv = ldv4(P.Z, idx);
-            pa[0].add(rv.x * zv.x);
-            pa[1].add(rv.y * zv.y);
-            pa[2].add(rv.z * zv.z);
-            pa[3].add(rv.w * zv.w);
-          }
       double pv[4];
       widen(pa, pv);
       cta_col_reduce(pv, scratch, colR, ngroups);

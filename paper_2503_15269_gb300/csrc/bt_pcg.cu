@@ -500,20 +500,34 @@ struct Solver {
         while (ld_acquire_u32(P.bar) < target) {
           if (ld_volatile_i32(P.abort_flag) || clock64() > lim) { bad = 1; break; }
         }
-        if (!bad) {
-          for (int i = 0; i < 4; ++i) t[i] = 0.0;
-          for (int gg = 0; gg < G; ++gg) {
-            const volatile double* o = P.red + ((size_t)par * G + gg) * 4;
-            for (int i = 0; i < 4; ++i) t[i] += o[i];
-          }
-        } else {
-          atomicExch(P.abort_flag, 1);
-        }
+        if (bad) atomicExch(P.abort_flag, 1);
+        ctl[2] = par;
       }
       for (int i = 0; i < 4; ++i) bc[i] = t[i];
       ctl[0] = bad;
     }
     __syncthreads();
+    if (G > 1 && !ctl[0]) {
+      // Group totals: thread (i, k) sums the slots k, k + L, ... of quantity
+      // i with independent L2 loads (the barrier above acquired them), then L
+      // partials per quantity are added in a fixed order.  The vector staging
+      // buffers are free between sweeps.
+      static_assert(kThreads % 4 == 0, "four quantities");
+      constexpr int L = kThreads / 4;
+      double* part = reinterpret_cast<double*>(sm + kSmVs);
+      const int par = ctl[2];
+      const int i = tid / L, k = tid % L;
+      double acc = 0.0;
+      for (int gg = k; gg < G; gg += L) acc += __ldcg(P.red + ((size_t)par * G + gg) * 4 + i);
+      part[tid] = acc;
+      __syncthreads();
+      if (tid < 4) {
+        double sum = 0.0;
+        for (int kk = 0; kk < L; ++kk) sum += part[tid * L + kk];
+        bc[tid] = sum;
+      }
+      __syncthreads();
+    }
     for (int i = 0; i < 4; ++i) v[i] = bc[i];
     if (ctl[0]) fail = true;
     __syncthreads();
