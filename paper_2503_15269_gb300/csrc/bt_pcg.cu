@@ -477,8 +477,12 @@ struct Solver {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {  // v[3] is set below (timeout flag)
       double x = v[i];
+      // a sweep leaves the partials it does not produce at exactly zero: skip
+      // their float64 shuffle sums (the test is an integer one: |bits| != 0)
+      if (__any_sync(0xffffffffu, (__double_as_longlong(x) << 1) != 0)) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      }
       if (lane == 0) red[w * 4 + i] = x;
     }
     __syncthreads();

@@ -284,6 +284,41 @@ def test_float32_copies_round_to_nearest_even():
     assert np.array_equal(y.reshape(-1), d.astype(np.float32).astype(np.float64))
 
 
+@pytest.mark.parametrize("bad", [1, 3])
+def test_batched_mixed_not_spd_reports_instance_and_block(bad):
+    # in a mixed batch, a non-SPD block of a later instance is refused by the
+    # float32 factor, confirmed by the float64 refactor and reported with its
+    # instance and block
+    insts = [wl.small_ocp(90 + k, 10 + k, 4) for k in range(4)]
+    D = insts[bad].D.copy()
+    D[6] = -np.eye(4)
+    insts[bad] = wl.Instance(D=D, O=insts[bad].O, b=insts[bad].b)
+    Ns, ns, d_off, o_off, v_off, Dp, Op, b = wl.pack_batch(insts)
+    p, keep = bb.make_params(m=2, alpha=[1.0, 7.0], precision=bb.BT_MIXED)
+    st, h = bb.bt_setup_batched(Ns, ns, d_off, o_off, dev(Dp), dev(Op), p)
+    try:
+        assert st == bb.BT_ERR_NOT_SPD
+        st2, i, blk, val = bb.bt_last_error(h)
+        assert (i, blk) == (bad, 6) and val < 0
+    finally:
+        if h:
+            bb.bt_destroy(h)
+
+
+def test_batched_mixed_matches_single_setups():
+    # the same instances solved from one batched setup and from one
+    # single-instance setup each: identical blocks and sweeps, identical iterates
+    insts = wl.config2(indices=[3, 40, 41, 700, 701])
+    st, its, sts, xs, _ = _batched(insts, 2, [1.0, 7.0], bb.BT_MIXED, 1e-10, 5000)
+    assert st == bb.BT_OK and (sts == 0).all()
+    for k, inst in enumerate(insts):
+        with Single(inst, m=2, alpha=[1.0, 7.0], precision=bb.BT_MIXED, group_ctas=1) as s1:
+            s1.ok()
+            st1, it1, x1 = s1.solve(inst.b, 1e-10, 5000)
+        assert st1 == bb.BT_OK and it1 == its[k]
+        assert np.array_equal(x1, xs[k])
+
+
 def test_maxit_gives_no_convergence_and_last_iterate():
     inst = wl.config1()
     with Single(inst, m=2, alpha=[1.0, 7.0]) as s:
