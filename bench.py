@@ -58,9 +58,10 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 one-at-a-time comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-sample", type=int, default=48, help="instances in the oracle CPU sample")
-    ap.add_argument("--workload", choices=["ocp_batch", "many_rhs", "adjoint"], default="ocp_batch",
+    ap.add_argument("--workload", choices=["ocp_batch", "many_rhs", "adjoint", "small"], default="ocp_batch",
                     help="ocp_batch: the headline workload (default); many_rhs: one LL^T system, N=2048, "
-                         "n=48, 64 right-hand sides; adjoint: 256 LQR instances, N=256, n=24, forward + adjoint")
+                         "n=48, 64 right-hand sides; adjoint: 256 LQR instances, N=256, n=24, forward + adjoint; "
+                         "small: single instances LL^T N=16 n=6 (float64, tol 1e-10) and LQR N=128 n=12")
     return ap.parse_args()
 
 
@@ -515,6 +516,38 @@ def other_workload(a):
                            "frac": achieved / peak, "traffic": None, "peak_source": kind,
                            "kernel": "bt_mrhs_kernel", "alg_bytes_per_launch": abytes},
               "detail": {"iters_max": it_max, "iters_mean": float(np.mean(its)), "outer_max": o_max}})
+        return
+    if a.workload == "small":
+        # latency-bound single instances: microseconds per solve and per PCG
+        # iteration (one persistent launch per solve, setup excluded)
+        rows = []
+        for name, inst, prec, tol in (("LL^T N=16 n=6", wl.config0(), bb.BT_FP64, 1e-10),
+                                      ("LQR N=128 n=12", wl.config1(), bb.BT_FP64, 1e-8),
+                                      ("LQR N=128 n=12", wl.config1(), bb.BT_MIXED, 1e-8)):
+            dD = torch.tensor(inst.D, device=dev)
+            dO = torch.tensor(inst.O, device=dev)
+            db = torch.tensor(inst.b.reshape(-1), device=dev)
+            dx = torch.zeros_like(db)
+            p, keep = bb.make_params(m=M, alpha=ALPHA, precision=prec)
+            st, h = bb.bt_setup(inst.N, inst.n, dD, dO, p)
+            assert st == bb.BT_OK, bb.status_string(st)
+            for _ in range(a.warmup):
+                st, it = bb.bt_pcg_solve(h, db, dx, tol, 5000)
+                assert st == bb.BT_OK
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(a.steps):
+                bb.bt_pcg_solve_async(h, db, dx, tol, 5000)
+            e1.record()
+            torch.cuda.synchronize()
+            us = 1e3 * e0.elapsed_time(e1) / a.steps
+            bb.bt_destroy(h)
+            rows.append({"instance": name, "precision": "f64" if prec == bb.BT_FP64 else "f32+f64", "tol": tol,
+                         "us_per_solve": us, "iters": it, "us_per_iter": us / max(it, 1)})
+        emit({"metric": "microseconds per single-instance solve (latency-bound rows)", "value": rows[-1]["us_per_solve"],
+              "unit": "us", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "higher_is_better": False,
+              "data": "synthetic (seeded)", "config": {"workload": "single instances, one persistent launch each"},
+              "rows": rows})
         return
     from paper_2503_15269_gb300.autograd import bt_solve
     insts = wl.config4()

@@ -75,7 +75,9 @@ typedef struct bt_params {
                           NULL = all ones (the "Optimal" preconditioner).           */
   int precision;       /* bt_precision                                             */
   double tol_inner;    /* BT_MIXED: relative tolerance of each float32 inner solve;
-                          0 = 1e-5.                                                 */
+                          0 = sqrt(tol) clamped to [1e-6, 1e-4] (two refinement
+                          steps reach tol; 1e-4 at tol = 1e-8); 1e-5 for
+                          bt_pcg_solve_multi.                                       */
   int max_outer;       /* BT_MIXED: refinement steps; 0 = 30.                      */
   int use_x0;          /* 1: x holds the initial guess on entry; 0: start from 0.  */
   long long cycle_budget; /* device clock cycles one solve may take before it stops

@@ -228,7 +228,7 @@ extern "C" bt_status bt_pcg_solve_noalloc(int N, int n, const double* D, const d
   P.m = m;
   for (int j = 0; j < BT_MAX_M; ++j) P.alpha[j] = alpha[j];
   P.tol = tol;
-  P.tol_inner = p->tol_inner > 0 ? p->tol_inner : 1e-5;
+  P.tol_inner = p->tol_inner;  // 0: the kernel derives it from tol
   P.maxit = maxit;
   P.max_outer = p->max_outer > 0 ? p->max_outer : 30;
   P.use_x0 = p->use_x0;

@@ -1213,7 +1213,10 @@ __device__ void solve_instance(Solver<MT>& Sv, int inst_id) {
           resid = nr / nb;
           if (nr <= tol * nb) { st = kOK; break; }
           if (outer >= P.max_outer || iters_total >= P.maxit) { st = kErrNoConv; break; }
-          double t_in = P.tol_inner;
+          // inner tolerance: the caller's, else sqrt(tol) in [1e-6, 1e-4] --
+          // two refinement steps of sqrt(tol) each reach tol, and the float32
+          // inner iteration resolves ~1e-6 at best
+          double t_in = P.tol_inner > 0.0 ? P.tol_inner : fmin(1e-4, fmax(1e-6, sqrt(tol)));
           const double need = 0.5 * tol * nb / nr;
           if (need > t_in) t_in = need;
           if (t_in > 0.5) t_in = 0.5;
