@@ -318,8 +318,11 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
   } else {
     int G = h->prm.group_ctas;
     if (G <= 0) {
+      // 4 block rows per CTA; one CTA up to N = 32, where the cross-CTA
+      // reductions (3 per iteration) cost more than the rows they split
+      // (LL^T N = 16, n = 6: 21.6 us per iteration on 1 CTA, 37.7 on 4)
       const int rows_per = 4;
-      G = std::max(1, std::min(h->sms * cps, h->N[0] / rows_per));
+      G = h->N[0] <= 32 ? 1 : std::max(1, std::min(h->sms * cps, h->N[0] / rows_per));
     }
     G = std::min(G, h->sms * occ);
     G = std::min(G, h->N[0]);

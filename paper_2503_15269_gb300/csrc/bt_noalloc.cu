@@ -135,7 +135,7 @@ extern "C" bt_status bt_pcg_solve_noalloc(int N, int n, const double* D, const d
   const int smem = fixed + 3 * vslot + S * (int)sb;
   int occ = 0;
   if (bt_persistent_occupancy(mixed ? 1 : 0, smem, &occ) != cudaSuccess || occ < 1) return BT_ERR_CUDA;
-  int G = p->group_ctas > 0 ? p->group_ctas : std::max(1, N / 4);
+  int G = p->group_ctas > 0 ? p->group_ctas : (N <= 32 ? 1 : std::max(1, N / 4));
   G = std::max(1, std::min({G, sms * occ, N}));
 
   // carve the scratch array
