@@ -271,13 +271,13 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     return (long long)h->N[a] * h->n[a] * h->n[a] > (long long)h->N[b] * h->n[b] * h->n[b];
   });
-  cudaError_t e;
-  if ((e = cudaMemcpyAsync(h->d_inst, inst.data(), B * sizeof(bt::InstDesc), cudaMemcpyHostToDevice, st)) ||
-      (e = cudaMemcpyAsync(h->d_rows, rr.data(), rows * sizeof(bt::RowRef), cudaMemcpyHostToDevice, st)) ||
-      (e = cudaMemcpyAsync(h->d_order, order.data(), B * sizeof(int), cudaMemcpyHostToDevice, st)) ||
-      (e = cudaMemcpyAsync(h->d_doff, h->d_off.data(), B * sizeof(long long), cudaMemcpyHostToDevice, st)) ||
-      (e = cudaMemcpyAsync(h->d_ooff, h->o_off.data(), B * sizeof(long long), cudaMemcpyHostToDevice, st)) ||
-      (mixed && (e = cudaMemcpyAsync(h->d_segs, segs.data(), segs.size() * sizeof(bt::SegRef),
+  const auto ok = [](cudaError_t x) { return x == cudaSuccess; };
+  if (!ok(cudaMemcpyAsync(h->d_inst, inst.data(), B * sizeof(bt::InstDesc), cudaMemcpyHostToDevice, st)) ||
+      !ok(cudaMemcpyAsync(h->d_rows, rr.data(), rows * sizeof(bt::RowRef), cudaMemcpyHostToDevice, st)) ||
+      !ok(cudaMemcpyAsync(h->d_order, order.data(), B * sizeof(int), cudaMemcpyHostToDevice, st)) ||
+      !ok(cudaMemcpyAsync(h->d_doff, h->d_off.data(), B * sizeof(long long), cudaMemcpyHostToDevice, st)) ||
+      !ok(cudaMemcpyAsync(h->d_ooff, h->o_off.data(), B * sizeof(long long), cudaMemcpyHostToDevice, st)) ||
+      (mixed && !ok(cudaMemcpyAsync(h->d_segs, segs.data(), segs.size() * sizeof(bt::SegRef),
                                      cudaMemcpyHostToDevice, st))))
     return BT_ERR_CUDA;
   if (launch_setup_kernels(h, D, O) != BT_OK) return BT_ERR_CUDA;
@@ -408,13 +408,13 @@ bt_status run_op(bt_ctx* h, int op, const double* in, double* out) {
 bt_status collect(bt_ctx* h, int* iters, int* status_out, bool all) {
   const int B = h->B;
   std::vector<int> st(B), it(B);
-  cudaError_t e;
-  if ((e = cudaMemcpyAsync(it.data(), h->d_iters, B * sizeof(int), cudaMemcpyDeviceToHost, h->stream)) ||
-      (e = cudaMemcpyAsync(st.data(), h->d_status, B * sizeof(int), cudaMemcpyDeviceToHost, h->stream)) ||
-      (e = cudaMemcpyAsync(h->h_outer.data(), h->d_outer, B * sizeof(int), cudaMemcpyDeviceToHost, h->stream)) ||
-      (e = cudaMemcpyAsync(h->h_resid.data(), h->d_resid, B * sizeof(double), cudaMemcpyDeviceToHost,
+  const auto ok = [](cudaError_t x) { return x == cudaSuccess; };
+  if (!ok(cudaMemcpyAsync(it.data(), h->d_iters, B * sizeof(int), cudaMemcpyDeviceToHost, h->stream)) ||
+      !ok(cudaMemcpyAsync(st.data(), h->d_status, B * sizeof(int), cudaMemcpyDeviceToHost, h->stream)) ||
+      !ok(cudaMemcpyAsync(h->h_outer.data(), h->d_outer, B * sizeof(int), cudaMemcpyDeviceToHost, h->stream)) ||
+      !ok(cudaMemcpyAsync(h->h_resid.data(), h->d_resid, B * sizeof(double), cudaMemcpyDeviceToHost,
                            h->stream)) ||
-      (e = cudaStreamSynchronize(h->stream)))
+      !ok(cudaStreamSynchronize(h->stream)))
     return BT_ERR_CUDA;
   bt_status first = BT_OK;
   for (int k = 0; k < B; ++k) {

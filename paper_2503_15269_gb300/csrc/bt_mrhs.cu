@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
   double* scratch = reinterpret_cast<double*>(smem + kMSmScratch);
   Sv.colbuf = colR;
   Sv.colred = scratch;
-  const int n = P.n, N = P.N;
+  const int n = P.n;
   const int tid = threadIdx.x;
   const int ngroups = n / 4;
   const size_t vb = (size_t)n * kJ;
@@ -430,12 +430,10 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
       actv[tid] = a ? 1.0 : 0.0;
     }
     __syncthreads();
-    int any = 0;
-    for (int j = 0; j < J; ++j) any |= (actv[j] > 0.0);
+    const int any = __syncthreads_or(tid < J && actv[tid] > 0.0);
     if (!any || outer == P.max_outer || total_it >= P.maxit) break;
     // ---- inner float32 PCG: r = rhs, x_in = 0
     {
-      double pv[4] = {0, 0, 0, 0};
       const int jg = tid & 15, ag = tid >> 4;
       if (ag < ngroups)
         for (int row = Sv.s; row < Sv.e; ++row)
@@ -448,7 +446,6 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
               P.R[idx] = rv;
               P.Xin[idx] = 0.0f;
             }
-      (void)pv;
       Sv.barrier();
     }
     // z0 = M^-1 r0 ; rho = r.z
