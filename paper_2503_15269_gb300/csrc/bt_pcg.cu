@@ -638,6 +638,11 @@ struct Solver {
     unsigned consumed = this->consumed, vissued = this->vissued, vcons = this->vcons;
     const bool leader = (threadIdx.x == kLeaderTid);
     const int tid = threadIdx.x;
+    // The staging of chunk c+1 starts from the upper half of the CTA while the
+    // lower half still finalizes chunk c (at most kMaxChunkElems / 4 = 128
+    // vectorised finalize tasks): the two touch different buffers and rows,
+    // so they overlap instead of queuing on the same threads.
+    const int ts = (tid + kThreads / 2) % kThreads;
     const int R = q.rows(KIND);
     const int bse = (KIND == kKA64) ? bs64 : bs;
     const float inv_n = 1.0f / (float)n;
@@ -718,7 +723,7 @@ struct Solver {
       if constexpr (sizeof(T) == 4 && (STG == SV_P || STG == SV_R_UPD || STG == SV_Y)) {
         if (vec4) {  // 4 consecutive elements of one row per iteration
           staged4 = true;
-          for (int t = 4 * tid; t < nv; t += 4 * kThreads) {
+          for (int t = 4 * ts; t < nv; t += 4 * kThreads) {
             const int rr = qdiv(t, inv_n);
             const int a = t - rr * n;
             const int row = base + rr;
@@ -745,7 +750,7 @@ struct Solver {
         }
       }
       if (!staged4)
-      for (int t = tid; t < nv; t += kThreads) {
+      for (int t = ts; t < nv; t += kThreads) {
         const int rr = qdiv(t, inv_n);
         const int a = t - rr * n;
         const int row = base + rr;
@@ -893,7 +898,7 @@ struct Solver {
       }
       // 6. carry the pushes of the last k source rows into the other ring
       //    buffer (read by the next chunk after its barriers)
-      for (int t = tid; t < k * n; t += kThreads) {
+      for (int t = (tid + kThreads - 64) % kThreads; t < k * n; t += kThreads) {  // threads 64.. (idle in finalize)
         const int w = qdiv(t, inv_n), a = t - w * n;
         const int src = r1 - k + w;
         if (src < 0) continue;
