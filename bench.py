@@ -31,7 +31,7 @@ UNIT = "solves/s"
 TOL = 1e-8
 ALPHA = (1.0, 7.0)
 M = 2
-KERNEL_SRC = os.path.join(ROOT, "paper_2503_15269_gb300", "csrc", "bt_pcg.cu")
+KERNEL_SRC = os.path.join(ROOT, "paper_2503_15269_gb300", "csrc", "bt_pcg_kernel.cuh")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pcg_batched_ocp1024_traffic.json")
 
 
@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 one-at-a-time comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-sample", type=int, default=48, help="instances in the oracle CPU sample")
-    ap.add_argument("--workload", choices=["ocp_batch", "many_rhs", "adjoint", "small"], default="ocp_batch",
+    ap.add_argument("--workload", choices=["ocp_batch", "many_rhs", "adjoint", "small", "family"],
+                    default="ocp_batch",
                     help="ocp_batch: the headline workload (default); many_rhs: one LL^T system, N=2048, "
                          "n=48, 64 right-hand sides; adjoint: 256 LQR instances, N=256, n=24, forward + adjoint; "
                          "small: single instances LL^T N=16 n=6 (float64, tol 1e-10) and LQR N=128 n=12")
@@ -517,6 +518,9 @@ def other_workload(a):
                            "kernel": "bt_mrhs_kernel", "alg_bytes_per_launch": abytes},
               "detail": {"iters_max": it_max, "iters_mean": float(np.mean(its)), "outer_max": o_max}})
         return
+    if a.workload == "family":
+        family_protocol(a, bb, wl, torch, dev)
+        return
     if a.workload == "small":
         # latency-bound single instances: microseconds per solve and per PCG
         # iteration (one persistent launch per solve, setup excluded)
@@ -576,6 +580,71 @@ def other_workload(a):
           "value": B / (ms / 1e3), "unit": "instances/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
           "ms_per_step": ms, "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic (seeded LQR)",
           "config": {"workload": "256 LQR instances N=256 n=24 (input size 8), setup + forward + adjoint per step"}})
+
+
+def family_protocol(a, bb, wl, torch, dev):
+    """The experiment protocol of the numerical-results section on the GPU:
+    five settings of the family (block Jacobi a = 0, equal a = 1/3, stairs
+    only a = 1/2, optimal a = 1, PolyCoeff a = 1 with alpha_{m-1} = 7) at
+    m = 1..4; per (setting, m) 100 LQR matrices N = 30, n = 20, each with 100
+    unit-norm right-hand sides, solved by float64 PCG to ||S x - b|| < 1e-6 in
+    one batched launch of 10^4 instances (setup untimed).  Per row: mean
+    iterations, block gemvs n_itr * g_a(m) and solves/s; the roofline is the
+    float64 arithmetic of the block products (0.25 flop per streamed byte
+    exceeds the float64 rate / HBM bandwidth ratio of GB300)."""
+    import numpy as np
+    Ns, ns, d_off, o_off, v_off, D, O, b = wl.protocol_batch()
+    B, N, n = len(Ns), int(Ns[0]), int(ns[0])
+    dD, dO, db = (torch.tensor(v, device=dev) for v in (D, O, b))
+    dx = torch.zeros_like(db)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rows, tot_ms, tot_solves, tot_flop, tot_bytes = [], 0.0, 0, 0.0, 0.0
+    n2 = n * n
+    for name, aa, pc in wl.PROTOCOL_SETTINGS:
+        for m in (1, 2, 3, 4):
+            alpha = wl.protocol_alpha(m, pc)
+            p, keep = bb.make_params(m=m, alpha=alpha, a=aa)
+            st, h = bb.bt_setup_batched(Ns, ns, d_off, o_off, dD, dO, p)
+            assert st == bb.BT_OK, bb.status_string(st)
+            for _ in range(a.warmup):
+                st, its, sts = bb.bt_pcg_solve_batched(h, db, dx, B, 1e-6, 5000)
+                assert st == bb.BT_OK and (sts == 0).all(), (name, m, st)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(a.steps):
+                bb.bt_pcg_solve_batched_async(h, db, dx, 1e-6, 5000)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / a.steps
+            bb.bt_destroy(h)
+            # blocks each iteration streams: S, G, and m-1 H applications
+            # (3 arrays for H_opt, 5 for H_ab; a = 0 streams the zero a H_opt too)
+            h_blocks = (3 * N - 4) if aa == 1.0 else (5 * N - 6)
+            blocks = (2 * N - 1) + (2 * N - 1) + h_blocks * (m - 1)
+            it_mean = float(np.mean(its))
+            g = (2 * m + 2) if aa == 0.0 else ((3 * m + 3) if aa == 1.0 else (5 * m + 1))
+            flop = 2.0 * n2 * blocks * float(np.sum(its))
+            byts = 8.0 * n2 * blocks * float(np.sum(its))
+            rows.append({"setting": name, "a": aa, "m": m, "alpha": alpha, "iters_mean": it_mean,
+                         "gemv_mean": it_mean * g, "ms": ms, "solves_per_s": B / (ms / 1e3),
+                         "fp64_tflops": flop / (ms / 1e3) / 1e12, "hbm_gbs": byts / (ms / 1e3) / 1e9})
+            tot_ms += ms
+            tot_solves += B
+            tot_flop += flop
+            tot_bytes += byts
+    peak_tf = 1.25  # GB300 nominal float64 (non-tensor) rate, TFLOP/s
+    hbm, kind = measured_peak()
+    achieved = tot_flop / (tot_ms / 1e3) / 1e12
+    emit({"metric": "protocol solves per second (float64 PCG to ||Sx-b|| < 1e-6, 5 settings x m=1..4)",
+          "value": tot_solves / (tot_ms / 1e3), "unit": "solves/s", "n_gpus": 1, "steps": a.steps,
+          "warmup": a.warmup, "ms_per_step": tot_ms, "higher_is_better": True, "dtype": "f64",
+          "data": "synthetic (seeded LQR, unit-norm b)",
+          "config": {"workload": f"{B} solves per (setting, m): 100 LQR matrices N={N} n={n} x 100 b"},
+          "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+                       "frac": achieved / peak_tf, "traffic": None, "peak_source": "nominal float64 rate",
+                       "kernel": "bt_persistent_kernel (float64)",
+                       "hbm_gbs": tot_bytes / (tot_ms / 1e3) / 1e9, "hbm_peak": hbm, "hbm_peak_source": kind},
+          "rows": rows})
 
 
 def fp64_one_at_a_time(bb, torch, dev, stream, Ns, ns, d_off, o_off, v_off, dD, dO, db):

@@ -17,6 +17,12 @@
  *     H[i,i] = E_{i-1}^T O_{i-1} + E_i O_i^T,  H[i,i+2] = E_i O_{i+1},
  *     H[i+2,i] = E_{i+1}^T O_i^T.
  * It is applied as in Sec. 4.2: y_0 = G r, y_j = H y_{j-1}, z = sum alpha_j y_j.
+ * Other members of the family (bt_params.a in [0, 1), b = 1 - 2a) use, with
+ * the block Jacobi matrix H_J = B_d^-1 C_d,
+ *     G_ab = B_d^-1 + a B_d^-1 C_d B_d^-1   (E_i above scaled by a)
+ *     H_ab = a H_J^2 + (1 - a) H_J          (a H_opt plus the +-1 blocks
+ *            -(1-a) D_i^-1 O_i and -(1-a) D_{i+1}^-1 O_i^T),
+ * the block form of the multi-splitting of Sec. 3.1.
  *
  * Conventions for every call below:
  *   - Array arguments named D, O, b, x, r, z, y are DEVICE pointers to
@@ -65,9 +71,17 @@ typedef enum {
                            shared-memory pipeline needs two stages of five blocks) */
 
 typedef struct bt_params {
-  double a;            /* multi-splitting weight, b = 1 - 2a.  Admissible set C_g
-                          (Sec. 3.3) is a in [0,1]; this build implements the optimum
-                          a = 1 (Thm. 3.2) and rejects other values with BT_ERR_PARAM. */
+  double a;            /* multi-splitting weight, b = 1 - 2a (Sec. 3.1).  Admissible
+                          set C_g (Sec. 3.3): a in [0,1], else BT_ERR_PARAM.  a = 1 is
+                          the optimum (Thm. 3.2); a = 0 is block Jacobi, a = 1/2 the
+                          stair splittings alone, a = 1/3 equal weights.  a < 1 takes
+                          alpha = all ones only (H_ab has negative eigenvalues, where
+                          other coefficients can make M^-1 indefinite).  For a < 1
+                          and m >= 2 the handle also keeps the +-1 blocks of H_ab
+                          (two more block arrays) and H sweeps stream five arrays
+                          instead of three; n <= 36 (float64) or 48 (mixed) then,
+                          else BT_ERR_ARG from setup.  bt_pcg_solve_multi and
+                          bt_pcg_solve_noalloc implement a = 1 only (BT_ERR_PARAM). */
   int m;               /* polynomial order, 1..BT_MAX_M.                           */
   const double* alpha; /* HOST array of m coefficients (Eq. with polynomial
                           coefficients, Sec. 3.5); alpha[0] must be 1 and every

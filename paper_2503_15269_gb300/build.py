@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libbt.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["bt_api.cu", "bt_pcg.cu", "bt_setup.cu", "bt_noalloc.cu", "bt_mrhs.cu"]
+SOURCES = ["bt_api.cu", "bt_pcg.cu", "bt_pcg_gen.cu", "bt_setup.cu", "bt_noalloc.cu", "bt_mrhs.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]
@@ -43,7 +43,8 @@ def _compile(src: str, verbose: bool) -> str:
 def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    deps = srcs + [os.path.join(CSRC, "bt_common.cuh"), os.path.join(HERE, "..", "include", "bt.h")]
+    deps = srcs + [os.path.join(CSRC, "bt_common.cuh"), os.path.join(CSRC, "bt_pcg_kernel.cuh"),
+                   os.path.join(HERE, "..", "include", "bt.h")]
     if not force and os.path.exists(OUT):
         t = os.path.getmtime(OUT)
         if all(os.path.getmtime(d) <= t for d in deps):

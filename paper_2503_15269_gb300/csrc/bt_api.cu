@@ -13,8 +13,8 @@
 
 extern "C" cudaError_t bt_launch_persistent(const bt::KParams* P, int grid, int smem_bytes, int mt_is_float,
                                             int cooperative, cudaStream_t stream);
-extern "C" int bt_persistent_smem_fixed();
-extern "C" cudaError_t bt_persistent_occupancy(int mt_is_float, int smem_bytes, int* blocks_per_sm);
+extern "C" int bt_persistent_smem_fixed(int general);
+extern "C" cudaError_t bt_persistent_occupancy(int mt_is_float, int general, int smem_bytes, int* blocks_per_sm);
 extern "C" cudaError_t bt_launch_setup(const bt::SetupParams* P, int mixed, int m, int maxn, cudaStream_t st);
 extern "C" cudaError_t bt_launch_adjoint(const bt::AdjParams* P, cudaStream_t st);
 namespace bt { struct MParams; }
@@ -54,6 +54,9 @@ struct bt_ctx {
          *Hl64 = nullptr;
   float *D32 = nullptr, *O32 = nullptr, *Dinv32 = nullptr, *E32 = nullptr, *Hd32 = nullptr, *Hu32 = nullptr,
         *Hl32 = nullptr;
+  // general member of the family (a < 1, m >= 2): the +-1 blocks of H_ab
+  double *F64 = nullptr, *K64 = nullptr;
+  float *F32 = nullptr, *K32 = nullptr;
   bt::InstDesc* d_inst = nullptr;
   bt::RowRef* d_rows = nullptr;
   int* d_order = nullptr;
@@ -114,9 +117,8 @@ void free_all(bt_ctx* h) {
 
 bt_status check_params(const bt_params* p, double* alpha_out) {
   if (!p) return BT_ERR_ARG;
-  // admissible set C_g is a in [0,1]; this build implements a = 1
+  // admissible set C_g (Sec. 3.3): a in [0, 1], b = 1 - 2a
   if (!(p->a >= 0.0 && p->a <= 1.0)) return BT_ERR_PARAM;
-  if (p->a != 1.0) return BT_ERR_PARAM;
   if (p->m < 1 || p->m > BT_MAX_M) return BT_ERR_PARAM;
   for (int j = 0; j < p->m; ++j) {
     const double a = p->alpha ? p->alpha[j] : 1.0;
@@ -124,6 +126,12 @@ bt_status check_params(const bt_params* p, double* alpha_out) {
     alpha_out[j] = a;
   }
   if (alpha_out[0] != 1.0) return BT_ERR_PARAM;
+  // polynomial coefficients belong to (G_opt, H_opt) (Sec. 3.5, Thm. 3.3): H_opt
+  // has eigenvalues in [0, 1), so alpha_j >= 0 keeps M^-1 SPD; H_ab of a < 1 has
+  // negative eigenvalues too, where such a polynomial can turn M^-1 indefinite
+  if (p->a != 1.0)
+    for (int j = 0; j < p->m; ++j)
+      if (alpha_out[j] != 1.0) return BT_ERR_PARAM;
   if (p->precision != BT_FP64 && p->precision != BT_MIXED) return BT_ERR_PARAM;
   if (p->tol_inner < 0.0 || p->tol_inner >= 1.0) return BT_ERR_PARAM;
   if (p->max_outer < 0 || p->cycle_budget < 0 || p->ctas_per_sm < 0 || p->group_ctas < 0 || p->stage_kb < 0)
@@ -149,6 +157,8 @@ bt_status launch_setup_kernels(bt_ctx* h, const double* D, const double* O) {
   sp.Hd64 = h->Hd64; sp.Hu64 = h->Hu64; sp.Hl64 = h->Hl64;
   sp.D32 = h->D32; sp.O32 = h->O32; sp.Dinv32 = h->Dinv32; sp.E32 = h->E32;
   sp.Hd32 = h->Hd32; sp.Hu32 = h->Hu32; sp.Hl32 = h->Hl32;
+  sp.F64 = h->F64; sp.K64 = h->K64; sp.F32 = h->F32; sp.K32 = h->K32;
+  sp.fam_a = h->prm.a;
   sp.want32 = h->mixed ? 1 : 0;
   sp.want64 = 1;
   sp.fail_key = h->d_fail_key;
@@ -204,6 +214,7 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
   h->total_vec = vec;
   const bool mixed = h->mixed != 0;
   const bool wantH = h->prm.m >= 2;
+  const bool general = wantH && h->prm.a != 1.0;  // H_ab has +-1 blocks
   bt_status s;
 #define ALLOC(ptr, cnt) \
   if ((s = dalloc(h, &(ptr), (cnt))) != BT_OK) return s
@@ -219,6 +230,10 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
       ALLOC(h->Hu32, off32);
       ALLOC(h->Hl32, off32);
     }
+    if (general) {
+      ALLOC(h->F32, off32);
+      ALLOC(h->K32, off32);
+    }
   } else {
     ALLOC(h->Dinv64, off64);
     ALLOC(h->E64, off64);
@@ -226,6 +241,10 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
       ALLOC(h->Hd64, off64);
       ALLOC(h->Hu64, off64);
       ALLOC(h->Hl64, off64);
+    }
+    if (general) {
+      ALLOC(h->F64, off64);
+      ALLOC(h->K64, off64);
     }
   }
   ALLOC(h->d_inst, B);
@@ -253,6 +272,7 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
   auto z32 = [&](float* p) { if (p) cudaMemsetAsync(p, 0, off32 * sizeof(float), st); };
   z64(h->D64); z64(h->O64); z64(h->Dinv64); z64(h->E64); z64(h->Hd64); z64(h->Hu64); z64(h->Hl64);
   z32(h->D32); z32(h->O32); z32(h->Dinv32); z32(h->E32); z32(h->Hd32); z32(h->Hu32); z32(h->Hl32);
+  z64(h->F64); z64(h->K64); z32(h->F32); z32(h->K32);
   // row table and LPT order (largest N n^2 first)
   std::vector<bt::RowRef> rr(rows);
   {
@@ -288,12 +308,13 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
   if (mixed)
     for (int q = 1; q <= h->maxn; ++q) bsb_max = std::max<long long>(bsb_max, (long long)bt::slot32(q) * wbytes);
   const long long bsb64_max = rup((long long)h->maxn * h->maxn, 2) * 8;
-  long long need = std::max(5 * bsb_max, 3 * bsb64_max);
+  // one chunk of one row: 3 + 2 halo blocks for H, 5 + 4 for H_ab, 3 float64
+  long long need = std::max((general ? 9 : 5) * bsb_max, 3 * bsb64_max);
   long long sb = h->prm.stage_kb > 0 ? (long long)h->prm.stage_kb * 1024 : 80 * 1024;
   sb = std::max(sb, rup(need, 128));
   int smem_optin = 0;
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
-  const int fixed = bt_persistent_smem_fixed();
+  const int fixed = bt_persistent_smem_fixed(general ? 1 : 0);
   int vslot = mixed ? 9 * 1024 : 18 * 1024;  // one vector-ring slot (largest chunk plan)
   int cps = h->prm.ctas_per_sm > 0 ? h->prm.ctas_per_sm : 1;
   const int per_cta = (int)std::min<long long>(smem_optin, (228 * 1024) / cps - 1024);
@@ -309,7 +330,8 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
   h->stage_bytes = (int)sb;
   h->smem = fixed + 3 * vslot + S * (int)sb;
   int occ = 0;
-  if (cuda_st(bt_persistent_occupancy(mixed ? 1 : 0, h->smem, &occ)) != BT_OK || occ < 1) return BT_ERR_CUDA;
+  if (cuda_st(bt_persistent_occupancy(mixed ? 1 : 0, general ? 1 : 0, h->smem, &occ)) != BT_OK || occ < 1)
+    return BT_ERR_CUDA;
   cps = std::min(cps, occ);
   if (h->batched) {
     h->G = 1;
@@ -357,6 +379,8 @@ bt::KParams base_kparams(bt_ctx* h) {
   P.Hd64 = h->Hd64; P.Hu64 = h->Hu64; P.Hl64 = h->Hl64;
   P.D32 = h->D32; P.O32 = h->O32; P.Dinv32 = h->Dinv32; P.E32 = h->E32;
   P.Hd32 = h->Hd32; P.Hu32 = h->Hu32; P.Hl32 = h->Hl32;
+  P.F64 = h->F64; P.K64 = h->K64; P.F32 = h->F32; P.K32 = h->K32;
+  P.general = (h->F64 || h->F32) ? 1 : 0;
   P.inst = h->d_inst;
   P.order = h->d_order;
   P.B = h->B;
@@ -638,7 +662,7 @@ bt_status bt_graph_capture_batched(bt_handle h, const double* b, double* x, doub
   h->graph_src = nullptr;
   // make sure the kernel attributes are set before capture
   int occ = 0;
-  bt_persistent_occupancy(h->mixed, h->smem, &occ);
+  bt_persistent_occupancy(h->mixed, (h->F64 || h->F32) ? 1 : 0, h->smem, &occ);
   if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal)) return BT_ERR_CUDA;
   bt_status s = bt_pcg_solve_batched_async(h, b, x, tol, maxit, d_iters, d_status);
   cudaGraph_t g = nullptr;
@@ -687,6 +711,7 @@ bt_status bt_pcg_solve_multi(bt_handle h, const double* B, double* X, int nrhs, 
   if (!h || !B || !X) return BT_ERR_ARG;
   if (h->batched) return BT_ERR_STATE;
   if (!h->mixed) return BT_ERR_STATE;
+  if (h->prm.a != 1.0) return BT_ERR_PARAM;  // the many-RHS engine implements the optimum only
   if (nrhs < 1 || nrhs > 64 || !(tol >= 0.0) || maxit < 0) return BT_ERR_ARG;
   const int N = h->N[0], n = h->n[0];
   if (n % 4 != 0) return BT_ERR_ARG;

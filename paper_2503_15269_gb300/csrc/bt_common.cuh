@@ -46,6 +46,11 @@ enum Op : int { kOpSolve = 0, kOpSpmv64 = 1, kOpSpmv32 = 2, kOpApply = 3 };
 struct KParams {
   const double *D64, *O64, *Dinv64, *E64, *Hd64, *Hu64, *Hl64;
   const float *D32, *O32, *Dinv32, *E32, *Hd32, *Hu32, *Hl32;
+  // general member of the family (a < 1): the +-1 blocks of H_ab,
+  // F_i = -(1-a) D_i^-1 O_i and K_i = -(1-a) D_{i+1}^-1 O_i^T (slot i, i < N-1)
+  const double *F64, *K64;
+  const float *F32, *K32;
+  int general;             // 1: H sweeps use the five-array pentadiagonal H_ab
   const InstDesc* inst;
   const int* order;        // instance processing order (largest first)
   int B;
@@ -123,6 +128,9 @@ struct SetupParams {
   const long long* o_off;
   double *D64, *O64, *Dinv64, *E64, *Hd64, *Hu64, *Hl64;
   float *D32, *O32, *Dinv32, *E32, *Hd32, *Hu32, *Hl32;
+  double *F64, *K64;        // general member only (fam_a < 1), else null
+  float *F32, *K32;
+  double fam_a;             // multi-splitting weight a (1 = the optimum)
   int want32, want64;       // which precisions to produce
   unsigned long long* fail_key;  // min over failing (inst << 32 | row)
   double* fail_piv;         // per global row: the failing pivot

@@ -27,8 +27,8 @@
 
 extern "C" cudaError_t bt_launch_persistent(const bt::KParams* P, int grid, int smem_bytes, int mt_is_float,
                                             int cooperative, cudaStream_t stream);
-extern "C" int bt_persistent_smem_fixed();
-extern "C" cudaError_t bt_persistent_occupancy(int mt_is_float, int smem_bytes, int* blocks_per_sm);
+extern "C" int bt_persistent_smem_fixed(int general);
+extern "C" cudaError_t bt_persistent_occupancy(int mt_is_float, int general, int smem_bytes, int* blocks_per_sm);
 extern "C" cudaError_t bt_launch_setup(const bt::SetupParams* P, int mixed, int m, int maxn, cudaStream_t st);
 
 static __device__ __align__(256) unsigned char g_bt_noalloc_scratch[BT_NOALLOC_SCRATCH_BYTES];
@@ -96,7 +96,8 @@ extern "C" bt_status bt_pcg_solve_noalloc(int N, int n, const double* D, const d
                                           double* x, double tol, int maxit, const bt_params* p, int* iters) {
   if (N < 1 || n < 1 || n > BT_MAX_BLOCK || !D || (N > 1 && !O) || !b || !x || !p) return BT_ERR_ARG;
   if (!(tol >= 0.0) || maxit < 0) return BT_ERR_ARG;
-  // parameters: same admissible set as bt_setup
+  // parameters: bt_setup's admissible set, restricted to the optimum a = 1
+  // (the static buffer has no room for the +-1 blocks of a general H_ab)
   if (p->a != 1.0 || p->m < 1 || p->m > BT_MAX_M) return BT_ERR_PARAM;
   if (p->precision != BT_FP64 && p->precision != BT_MIXED) return BT_ERR_PARAM;
   if (p->tol_inner < 0.0 || p->tol_inner >= 1.0 || p->max_outer < 0 || p->cycle_budget < 0) return BT_ERR_PARAM;
@@ -122,7 +123,7 @@ extern "C" bt_status bt_pcg_solve_noalloc(int N, int n, const double* D, const d
   const long long bsb = mixed ? (long long)bs32 * 4 : (long long)bs64 * 8;
   long long sb = p->stage_kb > 0 ? (long long)p->stage_kb * 1024 : 80 * 1024;
   sb = std::max(sb, rup(std::max(5 * bsb, 3 * (long long)bs64 * 8), 128));
-  const int fixed = bt_persistent_smem_fixed();
+  const int fixed = bt_persistent_smem_fixed(0);
   int vslot = mixed ? 9 * 1024 : 18 * 1024;
   const long long per_cta = std::min<long long>(smem_optin, 228 * 1024 - 1024);
   int S = (int)((per_cta - fixed - 3 * vslot) / sb);
@@ -134,7 +135,7 @@ extern "C" bt_status bt_pcg_solve_noalloc(int N, int n, const double* D, const d
   if (S < 2) return BT_ERR_ARG;
   const int smem = fixed + 3 * vslot + S * (int)sb;
   int occ = 0;
-  if (bt_persistent_occupancy(mixed ? 1 : 0, smem, &occ) != cudaSuccess || occ < 1) return BT_ERR_CUDA;
+  if (bt_persistent_occupancy(mixed ? 1 : 0, 0, smem, &occ) != cudaSuccess || occ < 1) return BT_ERR_CUDA;
   int G = p->group_ctas > 0 ? p->group_ctas : (N <= 32 ? 1 : std::max(1, N / 4));
   G = std::max(1, std::min({G, sms * occ, N}));
 
@@ -195,6 +196,7 @@ extern "C" bt_status bt_pcg_solve_noalloc(int N, int n, const double* D, const d
                                                               64, fail_key);
   if (cudaGetLastError() != cudaSuccess) return BT_ERR_CUDA;
   bt::SetupParams sp{};
+  sp.fam_a = 1.0;  // the optimum: no F/K blocks, no scaling
   sp.inst = inst;
   sp.rows = rows;
   sp.nrows = N;

@@ -532,6 +532,64 @@ __global__ void k_H(const __grid_constant__ SetupParams P) {
   }
 }
 
+// ---------------------------------------------------------------- K4
+// The general member (a, b = 1 - 2a) of the family, a < 1.  With the block
+// Jacobi iteration matrix H_J = B_d^-1 C_d, the multi-splitting of Sec. 3.1
+// gives G_ab = B_d^-1 + a B_d^-1 C_d B_d^-1 and H_ab = (1 - a) H_J + a H_J^2;
+// C_d is minus the off-diagonal part of S, so B_d^-1 C_d B_d^-1 has the
+// blocks -E_i, -E_i^T and H_J^2 has the pentadiagonal blocks of H_opt
+// (Sec. 4.1).  This kernel therefore scales the stored E, Hd, Hu, Hl of row
+// i by a, and forms the +-1 blocks of H_ab that H_opt lacks:
+//     F_i = -(1 - a) D_i^-1 O_i          (block (i, i+1))
+//     K_i = -(1 - a) D_{i+1}^-1 O_i^T    (block (i+1, i), kept in slot i)
+template <typename MT>
+__global__ void k_FK(const __grid_constant__ SetupParams P) {
+  extern __shared__ __align__(16) char smraw[];
+  const long long gr = blockIdx.x;
+  if (gr >= P.nrows) return;
+  const RowRef rr = P.rows[gr];
+  const InstDesc d = P.inst[rr.inst];
+  const int n = d.n, i = rr.row, N = d.N;
+  MatSet<MT> M = matset<MT>(P, d);
+  MT* F = (sizeof(MT) == 8) ? (MT*)P.F64 : (MT*)P.F32;
+  MT* K = (sizeof(MT) == 8) ? (MT*)P.K64 : (MT*)P.K32;
+  const MT wa = (MT)P.fam_a, wc = (MT)(-(1.0 - P.fam_a));
+  const long long o = M.off + (long long)i * M.bs;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    if (i < N - 1) M.E[o + t] *= wa;
+    if (M.Hd) {
+      M.Hd[o + t] *= wa;
+      if (i < N - 2) {
+        M.Hu[o + t] *= wa;
+        M.Hl[o + t] *= wa;
+      }
+    }
+  }
+  if (i >= N - 1 || !F) return;  // padding slots stay zero
+  MT* s0 = reinterpret_cast<MT*>(smraw);
+  MT* s1 = s0 + n * n;
+  MT* s2 = s1 + n * n;
+  const auto blk = [&](const MT* base, int row) { return base + M.off + (long long)row * M.bs; };
+  const float inv_n = 1.0f / (float)n;
+  const auto store_scaled = [&](MT* dst) {  // row-major smem -> column-major slot, times wc
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+      const int c = qdiv(t, inv_n), a = t - c * n;
+      dst[t] = wc * s2[a * n + c];
+    }
+  };
+  sm_load(s0, blk(M.Dinv, i), n);
+  sm_load(s1, blk(M.O, i), n);
+  __syncthreads();
+  sm_gemm4(s2, s0, false, s1, false, n, false);  // D_i^-1 O_i
+  __syncthreads();
+  store_scaled(F + o);
+  sm_load(s0, blk(M.Dinv, i + 1), n);
+  __syncthreads();
+  sm_gemm4(s2, s0, false, s1, true, n, false);   // D_{i+1}^-1 O_i^T
+  __syncthreads();
+  store_scaled(K + o);
+}
+
 // ---------------------------------------------------------------- K2+K3 (mixed)
 // E and H fused over a segment of consecutive block rows [a, b) of one
 // instance, all blocks column-major float32 in shared-memory rings.  Step j
@@ -736,7 +794,7 @@ __global__ void k_adjoint(const __grid_constant__ AdjParams P) {
 }  // namespace bt
 
 // ---------------------------------------------------------------- host launchers
-extern "C" cudaError_t bt_launch_setup(const bt::SetupParams* P, int mixed, int m, int maxn, cudaStream_t st) {
+static cudaError_t launch_setup_opt(const bt::SetupParams* P, int mixed, int m, int maxn, cudaStream_t st) {
   const long long nb = P->nrows;
   if (nb == 0) return cudaSuccess;
   const dim3 grid((unsigned)nb);
@@ -792,6 +850,22 @@ extern "C" cudaError_t bt_launch_setup(const bt::SetupParams* P, int mixed, int 
     bt::k_E<double><<<grid, 128, sm_prod, st>>>(*P);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     if (m >= 2) bt::k_H<double><<<grid, 128, sm_prod, st>>>(*P);
+  }
+  return cudaGetLastError();
+}
+
+// Setup of the optimum (a = 1) blocks, then, for a general member of the
+// family, the scaling by a and the +-1 blocks of H_ab (k_FK).
+extern "C" cudaError_t bt_launch_setup(const bt::SetupParams* P, int mixed, int m, int maxn, cudaStream_t st) {
+  cudaError_t err = launch_setup_opt(P, mixed, m, maxn, st);
+  if (err != cudaSuccess || P->nrows == 0 || P->fam_a == 1.0) return err;
+  const int sm_prod = 3 * maxn * maxn * (mixed ? 4 : 8);
+  if (mixed) {
+    cudaFuncSetAttribute(bt::k_FK<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_prod);
+    bt::k_FK<float><<<(unsigned)P->nrows, 128, sm_prod, st>>>(*P);
+  } else {
+    cudaFuncSetAttribute(bt::k_FK<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_prod);
+    bt::k_FK<double><<<(unsigned)P->nrows, 128, sm_prod, st>>>(*P);
   }
   return cudaGetLastError();
 }

@@ -155,6 +155,42 @@ def small_ocp(seed: int, N: int, n: int, m: Optional[int] = None) -> Instance:
     return ocp_instance(_rng(200 + seed, N * 1000 + n), N, n, m if m is not None else max(1, n // 3))
 
 
+# The experiment protocol of the numerical-results section (Sec. 5): five
+# settings of the family, m = 1..4, 100 LQR matrices N = 30, n = 20 with 100
+# right-hand sides each, PCG to ||S x - b||_2 < 1e-6.
+PROTOCOL_SETTINGS = [("block Jacobi", 0.0, False), ("equal", 1.0 / 3.0, False), ("stairs only", 0.5, False),
+                     ("optimal", 1.0, False), ("PolyCoeff", 1.0, True)]
+
+
+def protocol_alpha(m: int, polycoeff: bool) -> List[float]:
+    """Polynomial coefficients of a protocol setting: all ones, or for
+    PolyCoeff alpha_{m-1} = 7 (the footnote's grid-search value)."""
+    alpha = [1.0] * m
+    if polycoeff and m > 1:
+        alpha[-1] = 7.0
+    return alpha
+
+
+def protocol_batch(nmat: int = 100, nrhs: int = 100, N: int = 30, n: int = 20):
+    """nmat LQR matrices, each repeated for nrhs right-hand sides drawn
+    standard normal and scaled to unit norm (so the relative tolerance 1e-6 is
+    the absolute exit rule); packed like pack_batch, instance k = (matrix
+    k // nrhs, right-hand side k % nrhs)."""
+    mats = [ocp_instance(_rng(5, k), N, n, max(1, n // 3)) for k in range(nmat)]
+    B = nmat * nrhs
+    D = np.repeat(np.stack([m.D for m in mats]), nrhs, axis=0).reshape(-1)
+    O = np.repeat(np.stack([m.O for m in mats]), nrhs, axis=0).reshape(-1)
+    g = np.random.Generator(np.random.PCG64([SEED_STRIDE * 5, 1]))
+    b = g.standard_normal((B, N * n))
+    b /= np.linalg.norm(b, axis=1, keepdims=True)
+    Ns = np.full(B, N, dtype=np.int32)
+    ns = np.full(B, n, dtype=np.int32)
+    d_off = np.arange(B, dtype=np.int64) * N * n * n
+    o_off = np.arange(B, dtype=np.int64) * (N - 1) * n * n
+    v_off = np.arange(B, dtype=np.int64) * N * n
+    return Ns, ns, d_off, o_off, v_off, D, O, b.reshape(-1)
+
+
 def pack_batch(instances: List[Instance]):
     """Pack a batch back to back: returns (N[], n[], d_off[], o_off[], vec_off[], D, O, b).
 

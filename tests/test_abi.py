@@ -48,8 +48,18 @@ def test_bad_arguments_rejected_without_a_gpu(built):
     h = ctypes.c_void_p()
     assert lib.bt_setup(0, 4, ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.byref(p), ctypes.byref(h)) == bb.BT_ERR_ARG
     assert lib.bt_setup(4, 65, ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.byref(p), ctypes.byref(h)) == bb.BT_ERR_ARG
-    p.a = 0.5
+    p.a = -0.25  # outside the admissible set C_g = [0, 1] (Sec. 3.3)
     assert lib.bt_setup(4, 4, ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.byref(p), ctypes.byref(h)) == bb.BT_ERR_PARAM
+    p.a = 0.5  # admissible, but the no-allocation entry implements a = 1 only
+    it = ctypes.c_int()
+    assert lib.bt_pcg_solve_noalloc(4, 4, ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16),
+                                    ctypes.c_void_p(16), ctypes.c_double(1e-8), 10, ctypes.byref(p),
+                                    ctypes.byref(it)) == bb.BT_ERR_PARAM
+    p.a = 0.5  # polynomial coefficients other than ones only with (G_opt, H_opt)
+    pc = (ctypes.c_double * 2)(1.0, 7.0)
+    p.alpha = ctypes.cast(pc, ctypes.POINTER(ctypes.c_double))
+    assert lib.bt_setup(4, 4, ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.byref(p), ctypes.byref(h)) == bb.BT_ERR_PARAM
+    p.alpha = None
     p.a = 1.5
     assert lib.bt_setup(4, 4, ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.byref(p), ctypes.byref(h)) == bb.BT_ERR_PARAM
     p.a = 1.0
