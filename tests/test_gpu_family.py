@@ -159,3 +159,27 @@ def test_general_a_limits():
         st = bb.bt_pcg_solve_multi(s.h, B, X, 2, 1e-8, 100)
         st = st[0] if isinstance(st, tuple) else st
         assert st == bb.BT_ERR_PARAM
+
+
+def test_protocol_table_matches_oracle():
+    """The numerical-results protocol on one matrix (N = 30, n = 20, unit-norm
+    b, ||S x - b|| < 1e-6): float64 PCG iterations of every (setting, m) as
+    the oracle's, and the orderings the section states hold on the GPU counts."""
+    inst = wl.small_ocp(300, 30, 20)
+    b = inst.b / np.linalg.norm(inst.b)
+    gem = {}
+    for name, a, pc in wl.PROTOCOL_SETTINGS:
+        gem[name] = []
+        for m in (1, 2, 3, 4):
+            alpha = wl.protocol_alpha(m, pc)
+            ref = orc.pcg(inst.D, inst.O, b, lambda v: orc.apply_family(inst.D, inst.O, v, a, alpha), 1e-6, 5000)
+            with Single(inst, m=m, alpha=alpha, a=a) as s:
+                s.ok()
+                st, it, x = s.solve(b, 1e-6, 5000)
+            assert st == bb.BT_OK and abs(it - ref.iters) <= 1, (name, m, it, ref.iters)
+            assert np.linalg.norm(orc.spmv(inst.D, inst.O, x) - b) < 1e-6
+            gem[name].append(it * orc.g_a(m, a))
+    for k in range(4):
+        assert gem["PolyCoeff"][k] <= min(g[k] for g in gem.values())
+        assert (gem["optimal"][k] < gem["block Jacobi"][k]) == (k % 2 == 0)
+    assert int(np.argmin(gem["PolyCoeff"])) == 1
