@@ -381,3 +381,66 @@ def adjoint(D: np.ndarray, O: np.ndarray, x: np.ndarray, gx: np.ndarray):
     for i in range(N - 1):
         gO[i] = -(np.outer(g[i], x[i + 1]) + np.outer(x[i], g[i + 1]))
     return g, gD, gO
+
+
+# ---------------------------------------------------------------------------
+# Sec. 5: the test matrices are Schur complements of LQR KKT systems (the
+# construction is deferred to the cited GPU QP solver and not printed).  The
+# reading: the equality-constrained QP over z = (x_0, u_0, x_1, ..., u_{N-2},
+# x_{N-1}),
+#     min 1/2 z^T G z + g^T z   s.t.  C z = c,
+#     G = blkdiag(Q_0, R_0, Q_1, ..., R_{N-2}, Q_{N-1}),  g = (q_0, r_0, ..., q_{N-1}),
+# with block rows of C: x_0 = c_0 (initial state) and
+# x_{k+1} - A_k x_k - B_k u_k = c_{k+1} (dynamics with an affine term).
+# Eliminating z from the KKT system [G C^T; C 0][z; lam] = [-g; c]:
+#     S lam = gamma,  S = C G^-1 C^T,  gamma = -(c + C G^-1 g),
+#     z = -G^-1 (g + C^T lam).
+# Shapes: A [N-1, n, n], Bm [N-1, n, m], Q [N, n, n], R [N-1, m, m],
+# q [N, n], r [N-1, m], c [N, n]; lam [N, n]; x [N, n], u [N-1, m].
+# ---------------------------------------------------------------------------
+def lqr_dense(A, Bm, Q, R, q, r, c):
+    """Dense (G, g, C, c) of the QP, z ordered as above."""
+    N, n = Q.shape[0], Q.shape[1]
+    m = R.shape[1] if N > 1 else 0
+    nz = N * n + (N - 1) * m
+    xc = lambda k: k * (n + m)          # column of x_k in z
+    uc = lambda k: k * (n + m) + n      # column of u_k in z
+    G = np.zeros((nz, nz))
+    g = np.zeros(nz)
+    C = np.zeros((N * n, nz))
+    for k in range(N):
+        G[xc(k):xc(k) + n, xc(k):xc(k) + n] = Q[k]
+        g[xc(k):xc(k) + n] = q[k]
+        C[k * n:(k + 1) * n, xc(k):xc(k) + n] = np.eye(n)
+        if k < N - 1:
+            G[uc(k):uc(k) + m, uc(k):uc(k) + m] = R[k]
+            g[uc(k):uc(k) + m] = r[k]
+            C[(k + 1) * n:(k + 2) * n, xc(k):xc(k) + n] = -A[k]
+            C[(k + 1) * n:(k + 2) * n, uc(k):uc(k) + m] = -Bm[k]
+    return G, g, C, np.asarray(c, dtype=np.float64).reshape(-1)
+
+
+def lqr_schur(A, Bm, Q, R, q, r, c):
+    """(D, O, gamma): the blocks of S = C G^-1 C^T and gamma = -(c + C G^-1 g),
+    formed densely and cut into block rows."""
+    N, n = Q.shape[0], Q.shape[1]
+    G, g, C, cv = lqr_dense(A, Bm, Q, R, q, r, c)
+    Gi_Ct = np.linalg.solve(G, C.T)
+    S = C @ Gi_Ct
+    gamma = -(cv + C @ np.linalg.solve(G, g))
+    D = np.stack([S[i * n:(i + 1) * n, i * n:(i + 1) * n] for i in range(N)])
+    O = (np.stack([S[i * n:(i + 1) * n, (i + 1) * n:(i + 2) * n] for i in range(N - 1)])
+         if N > 1 else np.zeros((0, n, n)))
+    return D, O, gamma.reshape(N, n)
+
+
+def lqr_recover(A, Bm, Q, R, q, r, lam):
+    """z = -G^-1 (g + C^T lam), returned as (x [N, n], u [N-1, m])."""
+    N, n = Q.shape[0], Q.shape[1]
+    m = R.shape[1] if N > 1 else 0
+    G, g, C, _ = lqr_dense(A, Bm, Q, R, q, r, np.zeros((N, n)))
+    z = -np.linalg.solve(G, g + C.T @ np.asarray(lam, dtype=np.float64).reshape(-1))
+    x = np.stack([z[k * (n + m):k * (n + m) + n] for k in range(N)])
+    u = (np.stack([z[k * (n + m) + n:(k + 1) * (n + m)] for k in range(N - 1)])
+         if N > 1 else np.zeros((0, m)))
+    return x, u

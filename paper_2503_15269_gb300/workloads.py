@@ -155,6 +155,54 @@ def small_ocp(seed: int, N: int, n: int, m: Optional[int] = None) -> Instance:
     return ocp_instance(_rng(200 + seed, N * 1000 + n), N, n, m if m is not None else max(1, n // 3))
 
 
+@dataclasses.dataclass
+class LQRData:
+    """An LQR problem (Sec. 5 builds its matrices from such problems):
+    A [N-1, n, n], Bm [N-1, n, m], Q [N, n, n], R [N-1, m, m] (dense SPD),
+    q [N, n], r [N-1, m], c [N, n] (c_0 the initial state, c_{k+1} the
+    affine term of the dynamics x_{k+1} = A_k x_k + B_k u_k + c_{k+1})."""
+    A: np.ndarray
+    Bm: np.ndarray
+    Q: np.ndarray
+    R: np.ndarray
+    q: np.ndarray
+    r: np.ndarray
+    c: np.ndarray
+
+    @property
+    def N(self) -> int:
+        return self.Q.shape[0]
+
+    @property
+    def n(self) -> int:
+        return self.Q.shape[1]
+
+    @property
+    def m(self) -> int:
+        return self.R.shape[1]
+
+
+def lqr_data(rng: np.random.Generator, N: int, n: int, m: int) -> LQRData:
+    """A_k = I + 0.05 N(0,1), B_k = 0.05 N(0,1) as in ocp_instance; dense SPD
+    Q_k = diag U[1,10] + M M^T / n and R_k = diag U[0.1,1] + P P^T / m with
+    M, P entries 0.3 N(0,1); q, r, c_0 ~ N(0,1), c_{k+1} ~ 0.1 N(0,1)."""
+    A = np.eye(n) + 0.05 * rng.standard_normal((max(N - 1, 0), n, n))
+    Bm = 0.05 * rng.standard_normal((max(N - 1, 0), n, m))
+    Mq = 0.3 * rng.standard_normal((N, n, n))
+    Q = np.stack([np.diag(rng.uniform(1.0, 10.0, n)) + Mq[k] @ Mq[k].T / n for k in range(N)])
+    Pr = 0.3 * rng.standard_normal((max(N - 1, 0), m, m))
+    R = (np.stack([np.diag(rng.uniform(0.1, 1.0, m)) + Pr[k] @ Pr[k].T / m for k in range(N - 1)])
+         if N > 1 else np.zeros((0, m, m)))
+    q = rng.standard_normal((N, n))
+    r = rng.standard_normal((max(N - 1, 0), m))
+    c = np.concatenate([rng.standard_normal((1, n)), 0.1 * rng.standard_normal((max(N - 1, 0), n))])
+    return LQRData(A, Bm, Q, R, q, r, c)
+
+
+def small_lqr(seed: int, N: int, n: int, m: int) -> LQRData:
+    return lqr_data(_rng(300 + seed, N * 1000 + n), N, n, m)
+
+
 # The experiment protocol of the numerical-results section (Sec. 5): five
 # settings of the family, m = 1..4, 100 LQR matrices N = 30, n = 20 with 100
 # right-hand sides each, PCG to ||S x - b||_2 < 1e-6.
