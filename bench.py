@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 one-at-a-time comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-sample", type=int, default=48, help="instances in the oracle CPU sample")
-    ap.add_argument("--workload", choices=["ocp_batch", "many_rhs", "adjoint", "small", "family"],
+    ap.add_argument("--workload", choices=["ocp_batch", "many_rhs", "adjoint", "small", "family", "lqr"],
                     default="ocp_batch",
                     help="ocp_batch: the headline workload (default); many_rhs: one LL^T system, N=2048, "
                          "n=48, 64 right-hand sides; adjoint: 256 LQR instances, N=256, n=24, forward + adjoint; "
@@ -521,6 +521,9 @@ def other_workload(a):
     if a.workload == "family":
         family_protocol(a, bb, wl, torch, dev)
         return
+    if a.workload == "lqr":
+        lqr_pipeline(a, bb, wl, torch, dev)
+        return
     if a.workload == "small":
         # latency-bound single instances: microseconds per solve and per PCG
         # iteration (one persistent launch per solve, setup excluded)
@@ -645,6 +648,76 @@ def family_protocol(a, bb, wl, torch, dev):
                        "kernel": "bt_persistent_kernel (float64)",
                        "hbm_gbs": tot_bytes / (tot_ms / 1e3) / 1e9, "hbm_peak": hbm, "hbm_peak_source": kind},
           "rows": rows})
+
+
+def lqr_pipeline(a, bb, wl, torch, dev):
+    """LQR problems end to end on the device: Schur-complement formation
+    (bt_lqr_schur, float64), refactor of a mixed handle, batched PCG to 1e-8
+    (a = 1, m = 2, alpha = (1, 7)) and dual-to-primal recovery
+    (bt_lqr_recover), for 1024 LQR problems with the shapes of the bench
+    batch (N ~ U{32..512}, n in {12, 24, 36}, m = n/3; dense SPD Q, R).
+    Each stage timed with CUDA events; the formation kernel's roofline is the
+    float64 rate (its FMA count per block row: 2n^3 + m^3/2 + n m^2 + n^2 m/2)."""
+    import numpy as np
+    shapes = wl.config2_shapes(1024)
+    probs = [wl.lqr_data(wl._rng(6, k), N, n, max(1, n // 3)) for k, (N, n) in enumerate(shapes)]
+    cat = lambda f: np.concatenate([getattr(p, f).reshape(-1) for p in probs])
+    dA, dB, dQ, dR, dq, dr, dc = (torch.tensor(cat(f), device=dev) for f in ("A", "Bm", "Q", "R", "q", "r", "c"))
+    Ns = np.array([p.N for p in probs], np.int32)
+    ns = np.array([p.n for p in probs], np.int32)
+    ms = np.array([p.m for p in probs], np.int32)
+    dD = torch.zeros(dQ.numel(), dtype=torch.float64, device=dev)
+    dO = torch.zeros(dA.numel(), dtype=torch.float64, device=dev)
+    dg = torch.zeros(dq.numel(), dtype=torch.float64, device=dev)
+    dl, dx = torch.zeros_like(dg), torch.zeros_like(dg)
+    du = torch.zeros(dr.numel(), dtype=torch.float64, device=dev)
+    d_off = np.concatenate([[0], np.cumsum(Ns.astype(np.int64) * ns * ns)[:-1]]).astype(np.int64)
+    o_off = np.concatenate([[0], np.cumsum((Ns.astype(np.int64) - 1) * ns * ns)[:-1]]).astype(np.int64)
+    st, _, _ = bb.bt_lqr_schur(Ns, ns, ms, dA, dB, dQ, dR, dq, dr, dc, dD, dO, dg)
+    assert st == bb.BT_OK, bb.status_string(st)
+    p, keep = bb.make_params(m=M, alpha=ALPHA, precision=bb.BT_MIXED)
+    st, h = bb.bt_setup_batched(Ns, ns, d_off, o_off, dD, dO, p)
+    assert st == bb.BT_OK, bb.status_string(st)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    t = {"schur": 0.0, "refactor": 0.0, "solve": 0.0, "recover": 0.0}
+
+    def step(timed):
+        ev[0].record()
+        st, _, _ = bb.bt_lqr_schur(Ns, ns, ms, dA, dB, dQ, dR, dq, dr, dc, dD, dO, dg)
+        assert st == bb.BT_OK
+        ev[1].record()
+        assert bb.bt_refactor(h, dD, dO) == bb.BT_OK
+        ev[2].record()
+        assert bb.bt_pcg_solve_batched_async(h, dg, dl, TOL, 5000) == bb.BT_OK
+        ev[3].record()
+        assert bb.bt_lqr_recover(Ns, ns, ms, dA, dB, dQ, dR, dq, dr, dl, dx, du) == bb.BT_OK
+        ev[4].record()
+        torch.cuda.synchronize()
+        if timed:
+            for i, k in enumerate(t):
+                t[k] += ev[i].elapsed_time(ev[i + 1])
+
+    for _ in range(a.warmup):
+        step(False)
+    for _ in range(a.steps):
+        step(True)
+    st, its, sts = bb.bt_pcg_solve_batched(h, dg, dl, len(probs), TOL, 5000)
+    assert st == bb.BT_OK and (sts == 0).all()
+    bb.bt_destroy(h)
+    ms_step = {k: v / a.steps for k, v in t.items()}
+    tot = sum(ms_step.values())
+    fma = sum(int(N) * (2 * n ** 3 + m ** 3 / 2 + n * m * m + n * n * m / 2) for N, n, m in zip(Ns, ns, ms))
+    achieved = 2 * fma / (ms_step["schur"] / 1e3) / 1e12
+    peak_tf = 1.25  # GB300 nominal float64 (non-tensor) rate, TFLOP/s
+    emit({"metric": "LQR problems per second end to end on the device (formation, refactor, PCG to 1e-8, recovery)",
+          "value": len(probs) / (tot / 1e3), "unit": "problems/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+          "ms_per_step": tot, "higher_is_better": True, "dtype": "f64 formation + f32/f64 solve",
+          "data": "synthetic (seeded LQR, dense SPD Q and R)",
+          "config": {"workload": "1024 LQR problems, N~U{32..512}, n in {12,24,36}, m=n/3"},
+          "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+                       "frac": achieved / peak_tf, "traffic": None, "peak_source": "nominal float64 rate",
+                       "kernel": "k_lqr_schur", "flop_per_launch": 2 * fma},
+          "detail": {"ms": ms_step, "iters_mean": float(np.mean(its))}})
 
 
 def fp64_one_at_a_time(bb, torch, dev, stream, Ns, ns, d_off, o_off, v_off, dD, dO, db):

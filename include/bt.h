@@ -244,6 +244,43 @@ bt_status bt_pcg_solve_noalloc(int N, int n, const double* D, const double* O, c
                                double* x, double tol, int maxit, const bt_params* params,
                                int* iters);
 
+/* bt_lqr_schur -- form the systems S lam = gamma of B LQR problems on the
+ * device: the construction of the test matrices of Sec. 5 (an LQR problem as
+ * an equality-constrained QP, its KKT system, the Schur complement with
+ * respect to the Hessian).  Problem k has N[k] knots, state size n[k] and
+ * input size m[k] (HOST arrays; 1 <= n[k], m[k] <= 48).  The QP over
+ * z = (x_0, u_0, x_1, ..., u_{N-2}, x_{N-1}) is
+ *     min 1/2 z^T G z + g^T z  s.t.  x_0 = c_0,  x_{k+1} - A_k x_k - B_k u_k = c_{k+1},
+ * G = blkdiag(Q_0, R_0, ..., R_{N-2}, Q_{N-1}), g = (q_0, r_0, ..., q_{N-1}),
+ * and with S = C G^-1 C^T, gamma = -(c + C G^-1 g) in blocks:
+ *     D_0 = Q_0^-1,  D_k = Q_k^-1 + A_{k-1} Q_{k-1}^-1 A_{k-1}^T + B_{k-1} R_{k-1}^-1 B_{k-1}^T,
+ *     O_k = -Q_k^-1 A_k^T.
+ * DEVICE inputs, float64, row-major blocks, problems packed back to back:
+ *     A [sum (N-1)][n][n], Bm [sum (N-1)][n][m], Q [sum N][n][n] (SPD),
+ *     R [sum (N-1)][m][m] (SPD), q [sum N][n], r [sum (N-1)][m], c [sum N][n]
+ * (A, Bm, R, r may be NULL when every N[k] = 1).  DEVICE outputs in exactly
+ * the layout bt_setup_batched takes: D [sum N][n][n], O [sum (N-1)][n][n]
+ * (d_off[k] = sum_{j<k} N_j n_j^2, o_off[k] = sum_{j<k} (N_j-1) n_j^2) and
+ * gamma [sum N][n] (vec_off[k] = sum_{j<k} N_j n_j).  Float64 arithmetic;
+ * one CTA per 16 knots of a problem.  Queued on `stream` (a cudaStream_t),
+ * then synchronised: returns BT_ERR_NOT_SPD if some Q_k or R_k has a
+ * non-positive Cholesky pivot (*bad_inst, *bad_row name the first one if
+ * non-NULL; for R_k the row is k), BT_ERR_ARG on bad sizes or pointers. */
+bt_status bt_lqr_schur(int B, const int* N, const int* n, const int* m, const double* A, const double* Bm,
+                       const double* Q, const double* R, const double* q, const double* r, const double* c,
+                       double* D, double* O, double* gamma, void* stream, int* bad_inst, int* bad_row);
+
+/* bt_lqr_recover -- the primal solution of the QP above from the solution
+ * lam of S lam = gamma: z = -G^-1 (g + C^T lam), i.e.
+ *     x_k = -Q_k^-1 (q_k + lam_k - A_k^T lam_{k+1})  (no A term at k = N-1),
+ *     u_k = -R_k^-1 (r_k - B_k^T lam_{k+1}),
+ * by a float64 Cholesky solve per block.  Inputs as for bt_lqr_schur plus
+ * lambda [sum N][n] (DEVICE); outputs x [sum N][n], u [sum (N-1)][m]
+ * (DEVICE).  Synchronises `stream`; BT_ERR_NOT_SPD as above. */
+bt_status bt_lqr_recover(int B, const int* N, const int* n, const int* m, const double* A, const double* Bm,
+                         const double* Q, const double* R, const double* q, const double* r,
+                         const double* lambda, double* x, double* u, void* stream);
+
 /* Detail of the last failure on h: instance, block row and a value (the
  * failing Cholesky pivot, or the offending p.q).  Any pointer may be NULL. */
 bt_status bt_last_error(bt_handle h, int* instance, int* block, double* value);

@@ -81,6 +81,8 @@ def lib() -> C.CDLL:
         "bt_pcg_solve_multi": (C.c_int, [H, dp, dp, C.c_int, C.c_double, C.c_int, ip, ip]),
         "bt_multi_info": (C.c_int, [H, C.c_int, ip, C.POINTER(C.c_double)]),
         "bt_last_error": (C.c_int, [H, ip, ip, C.POINTER(C.c_double)]),
+        "bt_lqr_schur": (C.c_int, [C.c_int, ip, ip, ip, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, vp, ip, ip]),
+        "bt_lqr_recover": (C.c_int, [C.c_int, ip, ip, ip, dp, dp, dp, dp, dp, dp, dp, dp, dp, vp]),
         "bt_device_bytes": (C.c_longlong, [H]),
         "bt_destroy": (None, [H]),
         "bt_status_string": (C.c_char_p, [C.c_int]),
@@ -253,6 +255,30 @@ def bt_pcg_solve_multi(h, B, X, nrhs: int, tol: float, maxit: int):
     ss = (C.c_int * nrhs)()
     st = lib().bt_pcg_solve_multi(h, _ptr(B), _ptr(X), int(nrhs), float(tol), int(maxit), it, ss)
     return st, np.array(it[:], dtype=np.int64), np.array(ss[:], dtype=np.int64)
+
+
+def _iarr(v):
+    a = np.ascontiguousarray(np.asarray(v, dtype=np.int32))
+    return a, a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def _optr(t):
+    return _ptr(t) if t is not None and t.numel() else C.c_void_p(0)
+
+
+def bt_lqr_schur(N, n, m, A, Bm, Q, R, q, r, c, D, O, gamma, stream=None):
+    """Returns (status, bad_instance, bad_row)."""
+    (Na, Np), (na, nP), (ma, mP) = _iarr(N), _iarr(n), _iarr(m)
+    bi, br = C.c_int(-1), C.c_int(-1)
+    st = lib().bt_lqr_schur(len(Na), Np, nP, mP, _optr(A), _optr(Bm), _ptr(Q), _optr(R), _ptr(q), _optr(r),
+                            _ptr(c), _ptr(D), _optr(O), _ptr(gamma), _stream_ptr(stream), C.byref(bi), C.byref(br))
+    return st, bi.value, br.value
+
+
+def bt_lqr_recover(N, n, m, A, Bm, Q, R, q, r, lam, x, u, stream=None) -> int:
+    (Na, Np), (na, nP), (ma, mP) = _iarr(N), _iarr(n), _iarr(m)
+    return lib().bt_lqr_recover(len(Na), Np, nP, mP, _optr(A), _optr(Bm), _ptr(Q), _optr(R), _ptr(q), _optr(r),
+                                _ptr(lam), _ptr(x), _optr(u), _stream_ptr(stream))
 
 
 def bt_multi_info(h, j: int):
