@@ -444,3 +444,34 @@ def lqr_recover(A, Bm, Q, R, q, r, lam):
     u = (np.stack([z[k * (n + m) + n:(k + 1) * (n + m)] for k in range(N - 1)])
          if N > 1 else np.zeros((0, m)))
     return x, u
+
+
+# ---------------------------------------------------------------------------
+# Polynomial coefficients beyond grid search (the paper's stated future work,
+# Sec. 6).  At a = 1 the preconditioned matrix M^-1 S has the eigenvalues
+# phi(h) = q(h) (1 - h), q(h) = sum_j alpha_j h^j, over the eigenvalues h of
+# H_opt in [0, rho] (Sec. 3.5).  The q of degree m-1 that makes phi closest to
+# a constant on [0, rho] -- the smallest max |1 - c phi(h)| -- comes from the
+# shifted Chebyshev polynomial T_m (the classic minimax property):
+#     p(h) = T_m((2h - rho)/rho) / T_m((2 - rho)/rho),   p(1) = 1,
+#     q(h) = (1 - p(h)) / (1 - h)   (exact division, 1 - p vanishes at 1),
+# normalised to alpha_0 = 1 (scaling M^-1 does not change PCG's iterates).
+# ---------------------------------------------------------------------------
+def chebyshev_alpha(m: int, rho: float) -> np.ndarray:
+    """alpha (length m, alpha_0 = 1) of the Chebyshev choice for rho(H_opt) <= rho."""
+    P = np.polynomial.polynomial
+    # T_0 = 1, T_1 = x, T_{k+1} = 2 x T_k - T_{k-1}, in the variable
+    # x = (2h - rho)/rho, as power-basis coefficient arrays in h
+    x = np.array([-1.0, 2.0 / rho])
+    t_prev, t = np.array([1.0]), x.copy()
+    if m == 0:
+        t = t_prev
+    for _ in range(m - 1):
+        t_prev, t = t, P.polysub(2.0 * P.polymul(x, t), t_prev)
+    p = t / P.polyval(1.0, t)                       # p(1) = 1
+    one_minus_p = P.polysub(np.array([1.0]), p)
+    q, rem = P.polydiv(one_minus_p, np.array([1.0, -1.0]))
+    assert np.allclose(rem, 0.0, atol=1e-9 * np.abs(one_minus_p).max())
+    q = np.asarray(q, dtype=np.float64)
+    q = np.concatenate([q, np.zeros(max(0, m - q.size))])[:m]
+    return q / q[0]
