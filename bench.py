@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 one-at-a-time comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-sample", type=int, default=48, help="instances in the oracle CPU sample")
-    ap.add_argument("--workload", choices=["ocp_batch", "many_rhs", "adjoint", "small", "family", "lqr"],
+    ap.add_argument("--workload", choices=["ocp_batch", "many_rhs", "adjoint", "small", "family", "lqr", "alpha"],
                     default="ocp_batch",
                     help="ocp_batch: the headline workload (default); many_rhs: one LL^T system, N=2048, "
                          "n=48, 64 right-hand sides; adjoint: 256 LQR instances, N=256, n=24, forward + adjoint; "
@@ -524,6 +524,9 @@ def other_workload(a):
     if a.workload == "lqr":
         lqr_pipeline(a, bb, wl, torch, dev)
         return
+    if a.workload == "alpha":
+        alpha_choices(a, bb, wl, torch, dev)
+        return
     if a.workload == "small":
         # latency-bound single instances: microseconds per solve and per PCG
         # iteration (one persistent launch per solve, setup excluded)
@@ -647,6 +650,57 @@ def family_protocol(a, bb, wl, torch, dev):
                        "frac": achieved / peak_tf, "traffic": None, "peak_source": "nominal float64 rate",
                        "kernel": "bt_persistent_kernel (float64)",
                        "hbm_gbs": tot_bytes / (tot_ms / 1e3) / 1e9, "hbm_peak": hbm, "hbm_peak_source": kind},
+          "rows": rows})
+
+
+def alpha_choices(a, bb, wl, torch, dev):
+    """The bench batch (1024 LQR instances, mixed, tol 1e-8, one persistent
+    launch per step, refactor untimed) with the polynomial coefficients of the
+    paper's PolyCoeff (m = 2, alpha = (1, 7)) and the Chebyshev choice
+    (bt_alpha_chebyshev) for rho(H_opt) <= 0.985 at m = 2..5; per row the
+    solve time, solves/s, mean iterations and the solve kernel's algorithmic
+    HBM bandwidth."""
+    import numpy as np
+    insts = wl.config2()
+    Ns, ns, d_off, o_off, v_off, D, O, b = wl.pack_batch(insts)
+    dD, dO, db = (torch.tensor(v, device=dev) for v in (D, O, b))
+    dx = torch.zeros_like(db)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    peak, kind = measured_peak()
+    rows = []
+    choices = [("PolyCoeff", 2, [1.0, 7.0])] + [(f"Chebyshev rho<=0.985", m, bb.bt_alpha_chebyshev(m, 0.985)[1])
+                                                for m in (2, 3, 4, 5)]
+    for name, m, alpha in choices:
+        p, keep = bb.make_params(m=m, alpha=alpha, precision=bb.BT_MIXED)
+        st, h = bb.bt_setup_batched(Ns, ns, d_off, o_off, dD, dO, p)
+        assert st == bb.BT_OK, bb.status_string(st)
+        for _ in range(a.warmup):
+            st, its, sts = bb.bt_pcg_solve_batched(h, db, dx, len(insts), TOL, 5000)
+            assert st == bb.BT_OK and (sts == 0).all()
+        outers = [bb.bt_solve_info(h, k)[1] for k in range(len(insts))]
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(a.steps):
+            bb.bt_pcg_solve_batched_async(h, db, dx, TOL, 5000)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.steps
+        bb.bt_destroy(h)
+        ab = alg_bytes(Ns, ns, its, outers, m=m)
+        gbs = ab / (ms / 1e3) / 1e9
+        rows.append({"alpha": name, "m": m, "coefficients": [round(v, 4) for v in alpha], "ms_solve": ms,
+                     "solves_per_s": len(insts) / (ms / 1e3), "iters_mean": float(np.mean(its)),
+                     "hbm_gbs": gbs, "frac": gbs / peak})
+    best = max(rows, key=lambda r: r["solves_per_s"])
+    emit({"metric": "batched mixed solves/s at rel. residual 1e-8 by choice of polynomial coefficients",
+          "value": best["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+          "ms_per_step": best["ms_solve"], "higher_is_better": True, "dtype": "f32+f64",
+          "data": "synthetic (seeded LQR Schur complements)",
+          "config": {"workload": "ocp batch of 1024 (solve only, refactor untimed)", "best": best["alpha"],
+                     "best_m": best["m"]},
+          "roofline": {"bound": "hbm", "achieved": best["hbm_gbs"], "peak": peak, "unit": "GB/s",
+                       "frac": best["frac"], "traffic": None, "peak_source": kind,
+                       "kernel": "bt_persistent_kernel<float, false>"},
           "rows": rows})
 
 

@@ -84,8 +84,13 @@ typedef struct bt_params {
                           bt_pcg_solve_noalloc implement a = 1 only (BT_ERR_PARAM). */
   int m;               /* polynomial order, 1..BT_MAX_M.                           */
   const double* alpha; /* HOST array of m coefficients (Eq. with polynomial
-                          coefficients, Sec. 3.5); alpha[0] must be 1 and every
-                          alpha_j >= 0 (keeps M^-1 SPD, Thm. 3.3's setting).
+                          coefficients, Sec. 3.5); alpha[0] must be 1 and
+                          q(h) = sum_j alpha_j h^j positive on [0, 1] (then M^-1
+                          is SPD for every S: the eigenvalues of M^-1 S are
+                          q(h)(1-h) over the eigenvalues h in [0, 1) of H_opt);
+                          every alpha_j >= 0 qualifies (Thm. 3.3's setting), so
+                          do the coefficients of bt_alpha_chebyshev.  Checked
+                          exactly (Sturm sequence), else BT_ERR_PARAM.
                           NULL = all ones (the "Optimal" preconditioner).           */
   int precision;       /* bt_precision                                             */
   double tol_inner;    /* BT_MIXED: relative tolerance of each float32 inner solve;
@@ -108,6 +113,12 @@ typedef struct bt_ctx* bt_handle;
 /* Fill *p with the defaults: a = 1, m = 2, alpha = NULL, BT_FP64, everything
  * else 0 (= automatic). */
 void bt_params_init(bt_params* p);
+
+/* Check *params against the admissible sets (a, m, alpha, precision and the
+ * other fields as documented above) on the host, without touching the GPU:
+ * BT_OK, BT_ERR_PARAM, or BT_ERR_ARG for params == NULL.  bt_setup* run the
+ * same check. */
+bt_status bt_params_check(const bt_params* params);
 
 /* Single instance setup (Sec. 4.1).  Copies D and O into the library's
  * layout, factors every D_i by Cholesky in float64, forms D_i^-1, E_i and
@@ -243,6 +254,18 @@ bt_status bt_adjoint_blocks(bt_handle h, const double* x, const double* g, doubl
 bt_status bt_pcg_solve_noalloc(int N, int n, const double* D, const double* O, const double* b,
                                double* x, double tol, int maxit, const bt_params* params,
                                int* iters);
+
+/* bt_alpha_chebyshev -- polynomial coefficients beyond grid search (the
+ * paper's stated future work, Sec. 6), host only: for a bound rho on the
+ * spectral radius of H_opt (0 < rho < 1), the alpha[0..m-1] (alpha_0 = 1)
+ * that make the eigenvalues q(h)(1-h) of M^-1 S closest to constant over
+ * [0, rho] in the minimax sense: p(h) = T_m((2h - rho)/rho) / T_m((2 - rho)/rho)
+ * (Chebyshev, p(1) = 1), q(h) = (1 - p(h)) / (1 - h).  The spread of the
+ * preconditioned spectrum is then (1 + e)/(1 - e), e = 1/T_m((2 - rho)/rho).
+ * m = 2 gives alpha = (1, 1/(1 - rho)).  The coefficients alternate in sign
+ * for m >= 3; q stays positive on [0, 1].  A rho below the true spectral
+ * radius leaves M^-1 SPD but loses the bound.  BT_ERR_ARG on bad arguments. */
+bt_status bt_alpha_chebyshev(int m, double rho, double* alpha);
 
 /* bt_lqr_schur -- form the systems S lam = gamma of B LQR problems on the
  * device: the construction of the test matrices of Sec. 5 (an LQR problem as

@@ -81,6 +81,8 @@ def lib() -> C.CDLL:
         "bt_pcg_solve_multi": (C.c_int, [H, dp, dp, C.c_int, C.c_double, C.c_int, ip, ip]),
         "bt_multi_info": (C.c_int, [H, C.c_int, ip, C.POINTER(C.c_double)]),
         "bt_last_error": (C.c_int, [H, ip, ip, C.POINTER(C.c_double)]),
+        "bt_params_check": (C.c_int, [C.POINTER(bt_params)]),
+        "bt_alpha_chebyshev": (C.c_int, [C.c_int, C.c_double, C.POINTER(C.c_double)]),
         "bt_lqr_schur": (C.c_int, [C.c_int, ip, ip, ip, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, vp, ip, ip]),
         "bt_lqr_recover": (C.c_int, [C.c_int, ip, ip, ip, dp, dp, dp, dp, dp, dp, dp, dp, dp, vp]),
         "bt_device_bytes": (C.c_longlong, [H]),
@@ -255,6 +257,13 @@ def bt_pcg_solve_multi(h, B, X, nrhs: int, tol: float, maxit: int):
     ss = (C.c_int * nrhs)()
     st = lib().bt_pcg_solve_multi(h, _ptr(B), _ptr(X), int(nrhs), float(tol), int(maxit), it, ss)
     return st, np.array(it[:], dtype=np.int64), np.array(ss[:], dtype=np.int64)
+
+
+def bt_alpha_chebyshev(m: int, rho: float):
+    """Returns (status, alpha list)."""
+    a = (C.c_double * max(1, m))()
+    st = lib().bt_alpha_chebyshev(int(m), float(rho), a)
+    return st, list(a[:m])
 
 
 def _iarr(v):

@@ -43,7 +43,7 @@ def _compile(src: str, verbose: bool) -> str:
 def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    deps = srcs + [os.path.join(CSRC, "bt_common.cuh"), os.path.join(CSRC, "bt_pcg_kernel.cuh"),
+    deps = srcs + [os.path.join(CSRC, "bt_common.cuh"), os.path.join(CSRC, "bt_pcg_kernel.cuh"), os.path.join(CSRC, "bt_alpha.h"),
                    os.path.join(HERE, "..", "include", "bt.h")]
     if not force and os.path.exists(OUT):
         t = os.path.getmtime(OUT)

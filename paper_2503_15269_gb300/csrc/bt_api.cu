@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/bt.h"
+#include "bt_alpha.h"
 #include "bt_common.cuh"
 
 extern "C" cudaError_t bt_launch_persistent(const bt::KParams* P, int grid, int smem_bytes, int mt_is_float,
@@ -122,10 +123,12 @@ bt_status check_params(const bt_params* p, double* alpha_out) {
   if (p->m < 1 || p->m > BT_MAX_M) return BT_ERR_PARAM;
   for (int j = 0; j < p->m; ++j) {
     const double a = p->alpha ? p->alpha[j] : 1.0;
-    if (!std::isfinite(a) || a < 0.0) return BT_ERR_PARAM;
+    if (!std::isfinite(a)) return BT_ERR_PARAM;
     alpha_out[j] = a;
   }
   if (alpha_out[0] != 1.0) return BT_ERR_PARAM;
+  // M^-1 SPD for every admissible S: q(h) = sum alpha_j h^j > 0 on [0, 1]
+  if (!bt::alpha_positive_on_unit_interval(alpha_out, p->m)) return BT_ERR_PARAM;
   // polynomial coefficients belong to (G_opt, H_opt) (Sec. 3.5, Thm. 3.3): H_opt
   // has eigenvalues in [0, 1), so alpha_j >= 0 keeps M^-1 SPD; H_ab of a < 1 has
   // negative eigenvalues too, where such a polynomial can turn M^-1 indefinite
@@ -460,6 +463,16 @@ bt_status collect(bt_ctx* h, int* iters, int* status_out, bool all) {
 }  // namespace
 
 extern "C" {
+
+bt_status bt_params_check(const bt_params* params) {
+  double alpha[BT_MAX_M];
+  return check_params(params, alpha);
+}
+
+bt_status bt_alpha_chebyshev(int m, double rho, double* alpha) {
+  if (!alpha || m < 1 || m > BT_MAX_M || !(rho > 0.0 && rho < 1.0)) return BT_ERR_ARG;
+  return bt::alpha_chebyshev(m, rho, alpha) ? BT_OK : BT_ERR_ARG;
+}
 
 void bt_params_init(bt_params* p) {
   if (!p) return;

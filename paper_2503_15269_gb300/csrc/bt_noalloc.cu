@@ -23,6 +23,7 @@
 #include <mutex>
 
 #include "../../include/bt.h"
+#include "bt_alpha.h"
 #include "bt_common.cuh"
 
 extern "C" cudaError_t bt_launch_persistent(const bt::KParams* P, int grid, int smem_bytes, int mt_is_float,
@@ -104,10 +105,11 @@ extern "C" bt_status bt_pcg_solve_noalloc(int N, int n, const double* D, const d
   double alpha[BT_MAX_M] = {0};
   for (int j = 0; j < p->m; ++j) {
     const double a = p->alpha ? p->alpha[j] : 1.0;
-    if (!(a >= 0.0) || !(a < 1e300)) return BT_ERR_PARAM;
+    if (!std::isfinite(a)) return BT_ERR_PARAM;
     alpha[j] = a;
   }
   if (alpha[0] != 1.0) return BT_ERR_PARAM;
+  if (!bt::alpha_positive_on_unit_interval(alpha, p->m)) return BT_ERR_PARAM;
   const bool mixed = p->precision == BT_MIXED;
   const int m = p->m;
   cudaStream_t st = static_cast<cudaStream_t>(p->stream);

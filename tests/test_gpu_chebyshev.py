@@ -1,0 +1,69 @@
+"""GPU solves with the Chebyshev polynomial coefficients (bt_alpha_chebyshev,
+alternating in sign for m >= 3) against the oracle's PCG with the same
+coefficients, through the C ABI.  Tolerances as in test_gpu_parity.py."""
+import numpy as np
+import pytest
+
+from oracle import bt_oracle as orc
+from paper_2503_15269_gb300 import binding as bb
+from paper_2503_15269_gb300 import workloads as wl
+
+from _util import Single, dev, host, maxrel, rel
+
+pytestmark = pytest.mark.gpu
+RHO = 0.985  # bounds rho(H_opt) on the LQR family (0.977-0.982 measured)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2503_15269_gb300 import build
+    build.build()
+    bb.lib()
+
+
+@pytest.mark.parametrize("m", [2, 3, 4])
+def test_fp64_solve_matches_oracle(m):
+    inst = wl.small_ocp(400, 128, 12)
+    st, a = bb.bt_alpha_chebyshev(m, RHO)
+    assert st == bb.BT_OK
+    ref = orc.pcg_opt(inst.D, inst.O, inst.b, a, 1e-10, 3000)
+    with Single(inst, m=m, alpha=a) as s:
+        s.ok()
+        st, it, x = s.solve(inst.b, 1e-10, 3000)
+    assert st == bb.BT_OK and abs(it - ref.iters) <= 1
+    assert rel(x, ref.x) <= 1e-10
+
+
+@pytest.mark.parametrize("m", [3, 4])
+@pytest.mark.parametrize("precision,tol", [(bb.BT_FP64, 1e-12), (bb.BT_MIXED, 2e-4)])
+def test_apply_matches_oracle(m, precision, tol):
+    inst = wl.small_ocp(401, 40, 36)
+    st, a = bb.bt_alpha_chebyshev(m, RHO)
+    r = np.random.default_rng(m).standard_normal((40, 36))
+    with Single(inst, m=m, alpha=a, precision=precision) as s:
+        s.ok()
+        z = s.apply(r)
+    assert maxrel(z, orc.apply_opt(orc.opt_blocks(inst.D, inst.O), r, a)) <= tol
+
+
+def test_batched_mixed_fewer_iterations_than_polycoeff():
+    insts = wl.config2(indices=[0, 1, 2, 3, 100, 511, 777, 1023])
+    Ns, ns, d_off, o_off, v_off, D, O, b = wl.pack_batch(insts)
+    out = {}
+    for name, m, alpha in (("polycoeff", 2, [1.0, 7.0]), ("cheb3", 3, bb.bt_alpha_chebyshev(3, RHO)[1]),
+                           ("cheb4", 4, bb.bt_alpha_chebyshev(4, RHO)[1])):
+        p, keep = bb.make_params(m=m, alpha=alpha, precision=bb.BT_MIXED)
+        st, h = bb.bt_setup_batched(Ns, ns, d_off, o_off, dev(D), dev(O), p)
+        assert st == bb.BT_OK
+        x = dev(np.zeros(b.size))
+        try:
+            st, its, sts = bb.bt_pcg_solve_batched(h, dev(b), x, len(insts), 1e-8, 5000)
+        finally:
+            bb.bt_destroy(h)
+        assert st == bb.BT_OK and (sts == 0).all()
+        xs = host(x)
+        for k, inst in enumerate(insts):
+            xk = xs[v_off[k]:v_off[k] + inst.N * inst.n].reshape(inst.N, inst.n)
+            assert np.linalg.norm(orc.spmv(inst.D, inst.O, xk) - inst.b) <= 1e-8 * np.linalg.norm(inst.b)
+        out[name] = float(np.mean(its))
+    assert out["cheb3"] < out["polycoeff"] and out["cheb4"] < out["cheb3"], out
