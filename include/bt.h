@@ -106,6 +106,13 @@ typedef struct bt_params {
   int group_ctas;      /* single-instance solves: CTAs that split the block rows;
                           0 = chosen from N and n.                                  */
   int stage_kb;        /* shared-memory pipeline stage size in KiB; 0 = default.   */
+  int h_matrix_free;   /* 1: apply H_opt = H_J^2 matrix-free, H_J v = -D^-1 (O_{i-1}^T
+                          v_{i-1} + O_i v_{i+1}) from the D^-1 and O blocks the handle
+                          keeps anyway, two sweeps per application: no Hd, Hu, Hl
+                          blocks are formed or stored (3 of 7 block arrays; for
+                          problems bound by memory capacity), 4 instead of 3 block
+                          reads per application.  a = 1 only; not for
+                          bt_pcg_solve_multi or bt_pcg_solve_noalloc (BT_ERR_PARAM). */
 } bt_params;
 
 typedef struct bt_ctx* bt_handle;

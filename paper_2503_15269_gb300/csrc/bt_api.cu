@@ -14,8 +14,8 @@
 
 extern "C" cudaError_t bt_launch_persistent(const bt::KParams* P, int grid, int smem_bytes, int mt_is_float,
                                             int cooperative, cudaStream_t stream);
-extern "C" int bt_persistent_smem_fixed(int general);
-extern "C" cudaError_t bt_persistent_occupancy(int mt_is_float, int general, int smem_bytes, int* blocks_per_sm);
+extern "C" int bt_persistent_smem_fixed(int variant);
+extern "C" cudaError_t bt_persistent_occupancy(int mt_is_float, int variant, int smem_bytes, int* blocks_per_sm);
 extern "C" cudaError_t bt_launch_setup(const bt::SetupParams* P, int mixed, int m, int maxn, cudaStream_t st);
 extern "C" cudaError_t bt_launch_adjoint(const bt::AdjParams* P, cudaStream_t st);
 namespace bt { struct MParams; }
@@ -58,6 +58,7 @@ struct bt_ctx {
   // general member of the family (a < 1, m >= 2): the +-1 blocks of H_ab
   double *F64 = nullptr, *K64 = nullptr;
   float *F32 = nullptr, *K32 = nullptr;
+  int variant = 0;  // persistent kernel: 0 stored H_opt, 1 general member, 2 matrix-free H_opt
   bt::InstDesc* d_inst = nullptr;
   bt::RowRef* d_rows = nullptr;
   int* d_order = nullptr;
@@ -139,6 +140,8 @@ bt_status check_params(const bt_params* p, double* alpha_out) {
   if (p->tol_inner < 0.0 || p->tol_inner >= 1.0) return BT_ERR_PARAM;
   if (p->max_outer < 0 || p->cycle_budget < 0 || p->ctas_per_sm < 0 || p->group_ctas < 0 || p->stage_kb < 0)
     return BT_ERR_PARAM;
+  // the matrix-free H applies H_opt = H_J^2: the optimum only
+  if (p->h_matrix_free != 0 && (p->h_matrix_free != 1 || p->a != 1.0)) return BT_ERR_PARAM;
   return BT_OK;
 }
 
@@ -169,7 +172,8 @@ bt_status launch_setup_kernels(bt_ctx* h, const double* D, const double* O) {
   sp.retry = h->d_retry;
   sp.segs = h->d_segs;
   sp.nsegs = h->nsegs;
-  return cuda_st(bt_launch_setup(&sp, h->mixed ? 1 : 0, h->prm.m, h->maxn, st));
+  // the matrix-free variant forms no H blocks
+  return cuda_st(bt_launch_setup(&sp, h->mixed ? 1 : 0, h->variant == 2 ? 1 : h->prm.m, h->maxn, st));
 }
 
 // Read the setup failure key (synchronises); fills the error detail.
@@ -216,8 +220,10 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
   h->total_rows = rows;
   h->total_vec = vec;
   const bool mixed = h->mixed != 0;
-  const bool wantH = h->prm.m >= 2;
+  const bool mf = h->prm.m >= 2 && h->prm.h_matrix_free == 1;  // H_opt = H_J^2 from D^-1, O
+  const bool wantH = h->prm.m >= 2 && !mf;
   const bool general = wantH && h->prm.a != 1.0;  // H_ab has +-1 blocks
+  h->variant = general ? 1 : (mf ? 2 : 0);
   bt_status s;
 #define ALLOC(ptr, cnt) \
   if ((s = dalloc(h, &(ptr), (cnt))) != BT_OK) return s
@@ -312,12 +318,12 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
     for (int q = 1; q <= h->maxn; ++q) bsb_max = std::max<long long>(bsb_max, (long long)bt::slot32(q) * wbytes);
   const long long bsb64_max = rup((long long)h->maxn * h->maxn, 2) * 8;
   // one chunk of one row: 3 + 2 halo blocks for H, 5 + 4 for H_ab, 3 float64
-  long long need = std::max((general ? 9 : 5) * bsb_max, 3 * bsb64_max);
+  long long need = std::max((general ? 9 : (mf ? 3 : 5)) * bsb_max, 3 * bsb64_max);
   long long sb = h->prm.stage_kb > 0 ? (long long)h->prm.stage_kb * 1024 : 80 * 1024;
   sb = std::max(sb, rup(need, 128));
   int smem_optin = 0;
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
-  const int fixed = bt_persistent_smem_fixed(general ? 1 : 0);
+  const int fixed = bt_persistent_smem_fixed(h->variant);
   int vslot = mixed ? 9 * 1024 : 18 * 1024;  // one vector-ring slot (largest chunk plan)
   int cps = h->prm.ctas_per_sm > 0 ? h->prm.ctas_per_sm : 1;
   const int per_cta = (int)std::min<long long>(smem_optin, (228 * 1024) / cps - 1024);
@@ -333,7 +339,7 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
   h->stage_bytes = (int)sb;
   h->smem = fixed + 3 * vslot + S * (int)sb;
   int occ = 0;
-  if (cuda_st(bt_persistent_occupancy(mixed ? 1 : 0, general ? 1 : 0, h->smem, &occ)) != BT_OK || occ < 1)
+  if (cuda_st(bt_persistent_occupancy(mixed ? 1 : 0, h->variant, h->smem, &occ)) != BT_OK || occ < 1)
     return BT_ERR_CUDA;
   cps = std::min(cps, occ);
   if (h->batched) {
@@ -383,7 +389,7 @@ bt::KParams base_kparams(bt_ctx* h) {
   P.D32 = h->D32; P.O32 = h->O32; P.Dinv32 = h->Dinv32; P.E32 = h->E32;
   P.Hd32 = h->Hd32; P.Hu32 = h->Hu32; P.Hl32 = h->Hl32;
   P.F64 = h->F64; P.K64 = h->K64; P.F32 = h->F32; P.K32 = h->K32;
-  P.general = (h->F64 || h->F32) ? 1 : 0;
+  P.variant = h->variant;
   P.inst = h->d_inst;
   P.order = h->d_order;
   P.B = h->B;
@@ -675,7 +681,7 @@ bt_status bt_graph_capture_batched(bt_handle h, const double* b, double* x, doub
   h->graph_src = nullptr;
   // make sure the kernel attributes are set before capture
   int occ = 0;
-  bt_persistent_occupancy(h->mixed, (h->F64 || h->F32) ? 1 : 0, h->smem, &occ);
+  bt_persistent_occupancy(h->mixed, h->variant, h->smem, &occ);
   if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal)) return BT_ERR_CUDA;
   bt_status s = bt_pcg_solve_batched_async(h, b, x, tol, maxit, d_iters, d_status);
   cudaGraph_t g = nullptr;
@@ -724,7 +730,7 @@ bt_status bt_pcg_solve_multi(bt_handle h, const double* B, double* X, int nrhs, 
   if (!h || !B || !X) return BT_ERR_ARG;
   if (h->batched) return BT_ERR_STATE;
   if (!h->mixed) return BT_ERR_STATE;
-  if (h->prm.a != 1.0) return BT_ERR_PARAM;  // the many-RHS engine implements the optimum only
+  if (h->variant != 0) return BT_ERR_PARAM;  // the many-RHS engine: the optimum with stored H only
   if (nrhs < 1 || nrhs > 64 || !(tol >= 0.0) || maxit < 0) return BT_ERR_ARG;
   const int N = h->N[0], n = h->n[0];
   if (n % 4 != 0) return BT_ERR_ARG;

@@ -50,7 +50,8 @@ struct KParams {
   // F_i = -(1-a) D_i^-1 O_i and K_i = -(1-a) D_{i+1}^-1 O_i^T (slot i, i < N-1)
   const double *F64, *K64;
   const float *F32, *K32;
-  int general;             // 1: H sweeps use the five-array pentadiagonal H_ab
+  int variant;             // kernel: 0 optimum (stored H_opt), 1 general member
+                           // (five-array H_ab), 2 optimum with the matrix-free H_opt
   const InstDesc* inst;
   const int* order;        // instance processing order (largest first)
   int B;

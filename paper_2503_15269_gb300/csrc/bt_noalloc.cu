@@ -28,8 +28,8 @@
 
 extern "C" cudaError_t bt_launch_persistent(const bt::KParams* P, int grid, int smem_bytes, int mt_is_float,
                                             int cooperative, cudaStream_t stream);
-extern "C" int bt_persistent_smem_fixed(int general);
-extern "C" cudaError_t bt_persistent_occupancy(int mt_is_float, int general, int smem_bytes, int* blocks_per_sm);
+extern "C" int bt_persistent_smem_fixed(int variant);
+extern "C" cudaError_t bt_persistent_occupancy(int mt_is_float, int variant, int smem_bytes, int* blocks_per_sm);
 extern "C" cudaError_t bt_launch_setup(const bt::SetupParams* P, int mixed, int m, int maxn, cudaStream_t st);
 
 static __device__ __align__(256) unsigned char g_bt_noalloc_scratch[BT_NOALLOC_SCRATCH_BYTES];
@@ -99,7 +99,7 @@ extern "C" bt_status bt_pcg_solve_noalloc(int N, int n, const double* D, const d
   if (!(tol >= 0.0) || maxit < 0) return BT_ERR_ARG;
   // parameters: bt_setup's admissible set, restricted to the optimum a = 1
   // (the static buffer has no room for the +-1 blocks of a general H_ab)
-  if (p->a != 1.0 || p->m < 1 || p->m > BT_MAX_M) return BT_ERR_PARAM;
+  if (p->a != 1.0 || p->h_matrix_free != 0 || p->m < 1 || p->m > BT_MAX_M) return BT_ERR_PARAM;
   if (p->precision != BT_FP64 && p->precision != BT_MIXED) return BT_ERR_PARAM;
   if (p->tol_inner < 0.0 || p->tol_inner >= 1.0 || p->max_outer < 0 || p->cycle_budget < 0) return BT_ERR_PARAM;
   double alpha[BT_MAX_M] = {0};

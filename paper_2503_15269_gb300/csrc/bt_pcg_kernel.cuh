@@ -32,10 +32,12 @@
 
 namespace bt {
 
-// kKB2G: H_ab of a general member of the family (a < 1), five block arrays
-enum Kind : int { kKA = 0, kKB1 = 1, kKB2 = 2, kKA64 = 3, kKB2G = 4 };
+// kKB2G: H_ab of a general member of the family (a < 1), five block arrays;
+// kKJ: one application of H_J = -D^-1 (off-diagonal part of S), from D^-1 and O
+// (the matrix-free H_opt = H_J^2 is two of them)
+enum Kind : int { kKA = 0, kKB1 = 1, kKB2 = 2, kKA64 = 3, kKB2G = 4, kKJ = 5 };
 enum StageMode : int { SV_P = 0, SV_VEC = 1, SV_R_UPD = 2, SV_R_FIRST = 3, SV_R_X0 = 4, SV_Y = 5 };
-enum FinMode : int { FN_Q = 0, FN_OUT64 = 1, FN_R64 = 2, FN_Y0 = 3, FN_YJ = 4 };
+enum FinMode : int { FN_Q = 0, FN_OUT64 = 1, FN_R64 = 2, FN_Y0 = 3, FN_YJ = 4, FN_T = 5 };
 
 // Per-kind chunk geometry.
 struct Geo {
@@ -230,6 +232,48 @@ __device__ __forceinline__ void chunk_products(const T* __restrict__ stg, int R,
   const T* a0 = stg;
   const T* a1 = stg + (size_t)R * bse;
   const T* a2 = stg + (size_t)2 * R * bse;
+  if constexpr (KIND == kKJ) {
+    // stage: D^-1 [R] | O [R+1]; first phase of H_J v: part2 = O_i v_{i+1},
+    // push = O_i^T v_i (to row i+1); D^-1 is applied in a second phase
+    if constexpr (NB > 0) {
+      constexpr int n = NB;
+      constexpr int hp = NB / 2;
+      const int nd2 = nr * hp;
+      const int np = (nr + h) * n;
+      for (int t = tid; t < nd2 + np; t += kThreads) {
+        if (t < nd2) {
+          const int jj = t / hp, a = 2 * (t - jj * hp);
+          if (r0 + jj + 1 < N) {
+            dcol2<NB>(a1 + (size_t)(jj + h) * bse, a, vs + (r0 + jj + 1 - base) * n, part2[jj * n + a],
+                      part2[jj * n + a + 1]);
+          } else {
+            part2[jj * n + a] = T(0);
+            part2[jj * n + a + 1] = T(0);
+          }
+        } else {
+          const int t3 = t - nd2;
+          const int jj = t3 / n, a = t3 - jj * n;
+          push[jj * n + a] = dtr1<NB>(a1 + (size_t)jj * bse, a, vs + jj * n, 0);
+        }
+      }
+    } else {
+      const int n = n_rt;
+      const int nd = nr * n, np = (nr + h) * n;
+      for (int t = tid; t < nd + np; t += kThreads) {
+        if (t < nd) {
+          const int jj = t / n, a = t - jj * n;
+          T val = T(0);
+          if (r0 + jj + 1 < N) val = dot_col(a1 + (size_t)(jj + h) * bse, n, a, vs + (r0 + jj + 1 - base) * n);
+          part2[t] = val;
+        } else {
+          const int t3 = t - nd;
+          const int jj = t3 / n, a = t3 - jj * n;
+          push[t3] = dot_tr(a1 + (size_t)jj * bse, n, a, vs + jj * n);
+        }
+      }
+    }
+    return;
+  }
   if constexpr (KIND == kKB2G) {
     // stage: Hd [R] | Hu [R] | Hl [R+2] | F [R] | K [R+2]; every product is a
     // direct (column-major) one, the two lower bands are pushed forward
@@ -349,6 +393,27 @@ __device__ __forceinline__ void chunk_products(const T* __restrict__ stg, int R,
   }
 }
 
+// Second phase of a kKJ chunk: out_i = D^-1_i s_i over the owned rows
+// (D^-1 in the first R slots of the stage, s in shared memory).
+template <int NB, typename T>
+__device__ __forceinline__ void chunk_dinv(const T* __restrict__ a0, int bse, int n_rt, int nr,
+                                           const T* __restrict__ s, T* out) {
+  const int tid = threadIdx.x;
+  if constexpr (NB > 0) {
+    constexpr int hp = NB / 2;
+    for (int t = tid; t < nr * hp; t += kThreads) {
+      const int jj = t / hp, a = 2 * (t - jj * hp);
+      dcol2<NB>(a0 + (size_t)jj * bse, a, s + jj * NB, out[jj * NB + a], out[jj * NB + a + 1]);
+    }
+  } else {
+    const int n = n_rt;
+    for (int t = tid; t < nr * n; t += kThreads) {
+      const int jj = t / n, a = t - jj * n;
+      out[t] = dot_col(a0 + (size_t)jj * bse, n, a, s + jj * n);
+    }
+  }
+}
+
 __device__ __forceinline__ float4 ld4f(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4f(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 __device__ __forceinline__ float4 fma4(float a, float4 x, float4 y) {
@@ -363,11 +428,17 @@ __device__ __forceinline__ float4 fma4(float a, float4 x, float4 y) {
 __device__ __forceinline__ float dot4f(float4 a, float4 b) {
   return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)));
 }
-// GEN: kernels of a general member of the family (a < 1, H sweeps of kind
-// kKB2G); the optimum's kernels carry none of its code or shared memory.
-template <typename MT, bool GEN>
+// VAR: 0 = the optimum with stored H_opt; 1 = a general member of the family
+// (a < 1, H sweeps of kind kKB2G); 2 = the optimum with the matrix-free
+// H_opt = H_J^2 (two kKJ sweeps per application, no H blocks stored).  Each
+// variant is its own kernel: the optimum's carries none of the others' code
+// or shared memory.
+template <typename MT, int VAR>
 struct Solver {
-  static constexpr int kHK = GEN ? kKB2G : kKB2;  // kind of the H sweeps
+  static constexpr bool GEN = (VAR == 1);
+  static constexpr bool MF = (VAR == 2);
+  static constexpr int kHK = GEN ? kKB2G : (MF ? kKJ : kKB2);  // kind of the H sweeps
+  static constexpr int kHPS = MF ? 2 : 1;                      // sweeps per H application
   const KParams& P;
   char* sm;
   int tid;
@@ -467,8 +538,9 @@ struct Solver {
             (unsigned)((GEN && kind == kKB2G) ? 5 * nr + 2 * h : ((kind == kKB2 ? 3 * nr : 2 * nr) + h)) * bsb;
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(bar, total);
-        const char* A0 = kind == kKA ? m0 : (kind == kKB1 ? m2 : (hkind ? m4 : d64));
-        const char* A1 = kind == kKA ? m1 : (kind == kKB1 ? m3 : (hkind ? m5 : o64));
+        const bool kj = MF && kind == kKJ;
+        const char* A0 = kind == kKA ? m0 : ((kind == kKB1 || kj) ? m2 : (hkind ? m4 : d64));
+        const char* A1 = kind == kKA ? m1 : (kind == kKB1 ? m3 : (hkind ? m5 : (kj ? m1 : o64)));
         bulk_g2s(dst, A0 + (size_t)r0 * bsb, nr * bsb, bar);
         if (hkind) {
           bulk_g2s(dst + (size_t)R * bsb, A1 + (size_t)r0 * bsb, nr * bsb, bar);
@@ -909,6 +981,27 @@ struct Solver {
         default: chunk_products<KIND, 0, T>(stg, R, bse, n, N, nr, h, r0, base, vs, part1, part2, push, part3, push1); break;
       }
       __syncthreads();
+      if constexpr (KIND == kKJ) {
+        // s_i = O_i v_{i+1} + O_{i-1}^T v_{i-1} (the push) into part1; the push
+        // of the last row goes to the next chunk; then part2 = D^-1_i s_i
+        for (int t = tid; t < nr * n; t += kThreads) {
+          const int jj = qdiv(t, inv_n), a = t - jj * n;
+          const int src = r0 + jj - 1;
+          T carry = T(0);
+          if (src >= 0) carry = (src >= base) ? push[(src - base) * n + a] : ring_in[a];
+          part1[t] = part2[t] + carry;
+        }
+        for (int t = (tid + kThreads - 64) % kThreads; t < n; t += kThreads) ring_out[t] = push[(r1 - 1 - base) * n + t];
+        __syncthreads();
+        switch (n) {
+          case 12: chunk_dinv<12, T>(stg, bse, n, nr, part1, part2); break;
+          case 24: chunk_dinv<24, T>(stg, bse, n, nr, part1, part2); break;
+          case 36: chunk_dinv<36, T>(stg, bse, n, nr, part1, part2); break;
+          case 48: chunk_dinv<48, T>(stg, bse, n, nr, part1, part2); break;
+          default: chunk_dinv<0, T>(stg, bse, n, nr, part1, part2); break;
+        }
+        __syncthreads();
+      }
       // 4. the stage is free: refill it with the next predicted chunk
       q.step(leader);
       // 5. finalize owned rows
@@ -920,7 +1013,7 @@ struct Solver {
       const T* fr = (ir == 1) ? sv1 : ((ir == 2) ? sv2 : sv3);
       const double* fb = reinterpret_cast<const double*>((const char*)fz);
       bool fin4 = false;
-      if constexpr (sizeof(T) == 4 && (FIN == FN_Q || FIN == FN_Y0 || FIN == FN_YJ)) {
+      if constexpr (sizeof(T) == 4 && (FIN == FN_Q || FIN == FN_Y0 || FIN == FN_YJ || FIN == FN_T)) {
         if (vec4 && !out_to_user) {
           fin4 = true;
           for (int t = 4 * tid; t < nd; t += 4 * kThreads) {
@@ -940,6 +1033,7 @@ struct Solver {
               out = make_float4(out.x + (p3.x + c1.x), out.y + (p3.y + c1.y), out.z + (p3.z + c1.z),
                                 out.w + (p3.w + c1.w));
             }
+            if constexpr (KIND == kKJ) out = make_float4(-p2.x, -p2.y, -p2.z, -p2.w);  // H_J v = -D^-1 s
             const long long idx = (long long)row * n + a;
             const float4 vi = ld4f(vs + (row - base) * n + a);
             if constexpr (FIN == FN_Q) {
@@ -951,7 +1045,10 @@ struct Solver {
                 acc1.add(dot4f(vi, out));
               } else {
                 st4f(sw.y0 + idx, out);
+                if constexpr (MF) st4f(sw.zv + idx, out);  // z starts at y0
               }
+            } else if constexpr (FIN == FN_T) {
+              st4f(sw.ynext + idx, out);
             } else {
               const float4 zprev = (jpow == 1) ? vi : ld4f(fz + t);
               const float4 zz = fma4(alpha_j, out, zprev);
@@ -976,6 +1073,7 @@ struct Solver {
           if (src1 >= 0) c1 = (src1 >= base) ? push1[(src1 - base) * n + a] : ring1_in[a];
           out += part3[t] + c1;
         }
+        if constexpr (KIND == kKJ) out = -part2[t];  // H_J v = -D^-1 s
         const long long idx = (long long)row * n + a;
         const T vi = vs[(row - base) * n + a];
         if constexpr (FIN == FN_Q) {
@@ -994,7 +1092,10 @@ struct Solver {
             acc1.add(vi * out);
           } else {
             sw.y0[idx] = out;
+            if constexpr (MF) sw.zv[idx] = out;  // z starts at y0
           }
+        } else if constexpr (FIN == FN_T) {
+          sw.ynext[idx] = out;
         } else {  // FN_YJ
           const T zprev = (jpow == 1) ? vi : (va ? fz[t] : sw.zv[idx]);
           const T zz = fma(alpha_j, out, zprev);
@@ -1007,7 +1108,7 @@ struct Solver {
       // 6. carry the pushes of the last k source rows into the other ring
       //    buffer (read by the next chunk after its barriers); kKB2G also
       //    carries push1 of its last row
-      constexpr int kc = (KIND == kKB2G) ? k + 1 : k;
+      constexpr int kc = (KIND == kKB2G) ? k + 1 : ((KIND == kKJ) ? 0 : k);  // kKJ carried before its D^-1 phase
       for (int t = (tid + kThreads - 64) % kThreads; t < kc * n; t += kThreads) {  // threads 64.. (idle in finalize)
         const int w = qdiv(t, inv_n), a = t - w * n;
         if (KIND == kKB2G && w == k) {
@@ -1040,13 +1141,13 @@ struct Solver {
 // ---------------------------------------------------------------------------
 // The kernel.
 // ---------------------------------------------------------------------------
-template <typename MT, bool GEN>
-__device__ void solve_instance(Solver<MT, GEN>& Sv, int inst_id);
+template <typename MT, int VAR>
+__device__ void solve_instance(Solver<MT, VAR>& Sv, int inst_id);
 
-template <typename MT, bool GEN>
+template <typename MT, int VAR>
 __global__ void __launch_bounds__(kThreads, 1) bt_persistent_kernel(const __grid_constant__ KParams P) {
   extern __shared__ __align__(128) char smem[];
-  Solver<MT, GEN> Sv(P, smem);
+  Solver<MT, VAR> Sv(P, smem);
   if (threadIdx.x == kLeaderTid) {
     for (int i = 0; i < P.stages; ++i) mbar_init(&Sv.full[i], 1);
     for (int i = 0; i < kVecSlots; ++i) mbar_init(&Sv.vbar[i], 1);
@@ -1068,13 +1169,15 @@ __global__ void __launch_bounds__(kThreads, 1) bt_persistent_kernel(const __grid
       if (idx >= P.B) break;
       inst = P.order[idx];
     }
-    solve_instance<MT, GEN>(Sv, inst);
+    solve_instance<MT, VAR>(Sv, inst);
     if (P.G > 1) break;
   }
 }
 
-template <typename MT, bool GEN>
-__device__ void solve_instance(Solver<MT, GEN>& Sv, int inst_id) {
+template <typename MT, int VAR>
+__device__ void solve_instance(Solver<MT, VAR>& Sv, int inst_id) {
+  constexpr bool GEN = Solver<MT, VAR>::GEN;
+  constexpr bool MF = Solver<MT, VAR>::MF;
   const KParams& P = Sv.P;
   const InstDesc d = P.inst[inst_id];
   const int tid = threadIdx.x;
@@ -1154,16 +1257,30 @@ __device__ void solve_instance(Solver<MT, GEN>& Sv, int inst_id) {
   // Runs B1 then B2 x (m-1); rz accumulates in acc[1] of the last sweep.
   // rhs given by (src64, scale) when first_from_user, else r already staged
   // through SV_R_UPD by the caller.
+  // Matrix-free variant: H_opt y = H_J (H_J y); the first H_J goes to q
+  // (free between B1 and the next A), the second finalizes y_j.  B1 has
+  // written z = y0 already, so every y_j step adds to z (j > 1 form).
   auto precond_sweeps_after_b1 = [&](MT* rcur, bool to_user) {
     for (int j = 1; j < m; ++j) {
+      const MT* yp = (j == 1) ? y0 : ((j - 1) % 2 == 1 ? ya : yb);
+      if constexpr (MF) {
+        Sweep<MT> st = {};
+        st.kind = kKJ; st.stg = SV_Y; st.fin = FN_T; st.sgn = MT(1);
+        st.yprev = yp; st.ynext = q;
+        zero_acc();
+        Sv.template sweep<kKJ, SV_Y, FN_T>(st, acc);
+        Sv.group_reduce(acc);
+        if (Sv.fail) return;
+        yp = q;
+      }
       Sweep<MT> sw = {};
-      sw.kind = Solver<MT, GEN>::kHK; sw.stg = SV_Y; sw.fin = FN_YJ; sw.sgn = MT(1);
-      sw.yprev = (j == 1) ? y0 : ((j - 1) % 2 == 1 ? ya : yb);
+      sw.kind = Solver<MT, VAR>::kHK; sw.stg = SV_Y; sw.fin = FN_YJ; sw.sgn = MT(1);
+      sw.yprev = yp;
       sw.ynext = (j % 2 == 1) ? ya : yb;
-      sw.zv = z; sw.j = j; sw.m = m; sw.alpha_j = (MT)P.alpha[j]; sw.last = (j == m - 1);
+      sw.zv = z; sw.j = MF ? j + 1 : j; sw.m = m; sw.alpha_j = (MT)P.alpha[j]; sw.last = (j == m - 1);
       sw.rcur_for_dot = rcur; sw.out_to_user = to_user; sw.out64 = xu;
       zero_acc();
-      Sv.template sweep<Solver<MT, GEN>::kHK, SV_Y, FN_YJ>(sw, acc);
+      Sv.template sweep<Solver<MT, VAR>::kHK, SV_Y, FN_YJ>(sw, acc);
       Sv.group_reduce(acc);
       if (Sv.fail) return;
     }
@@ -1189,7 +1306,7 @@ __device__ void solve_instance(Solver<MT, GEN>& Sv, int inst_id) {
     Sv.template sweep<kKA, SV_VEC, FN_OUT64>(sw, acc);
     Sv.group_reduce(acc);
   } else if (P.op == kOpApply) {
-    Sv.restart(kKA, m + 1, 1);
+    Sv.restart(kKA, 2 + Solver<MT, VAR>::kHPS * (m - 1), 1);
     Sweep<MT> sw = {};
     sw.kind = kKB1; sw.stg = SV_R_FIRST; sw.fin = FN_Y0; sw.sgn = MT(-1);
     sw.src64 = bu; sw.scale = 1.0; sw.r_cur = rb[0]; sw.write_r = true; sw.zero_x = false;
@@ -1207,7 +1324,7 @@ __device__ void solve_instance(Solver<MT, GEN>& Sv, int inst_id) {
       it_out = 0;
       st_out = kOK;
       // initial residual and z0 = M^-1 r0
-      Sv.restart(kKA, m + 1, from_x0 ? 0 : 1);
+      Sv.restart(kKA, 2 + Solver<MT, VAR>::kHPS * (m - 1), from_x0 ? 0 : 1);
       if (from_x0) {
         Sweep<MT> sa = {};
         sa.kind = kKA; sa.stg = SV_VEC; sa.fin = FN_Q; sa.sgn = MT(1);
