@@ -420,7 +420,7 @@ def main():
     peak, peak_kind = measured_peak()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": stored_traffic(abytes), "peak_source": peak_kind,
-            "kernel": "bt_persistent_kernel<float, false> (batched mixed solve)",
+            "kernel": "bt_persistent_kernel<float, 0> (batched mixed solve)",
             "alg_bytes_per_launch": abytes, "ms_per_launch": ms_solve}
 
     # ---- plain FP64 single-instance PCG, one instance at a time ----

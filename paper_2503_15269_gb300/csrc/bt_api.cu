@@ -327,7 +327,8 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
   int vslot = mixed ? 9 * 1024 : 18 * 1024;  // one vector-ring slot (largest chunk plan)
   int cps = h->prm.ctas_per_sm > 0 ? h->prm.ctas_per_sm : 1;
   const int per_cta = (int)std::min<long long>(smem_optin, (228 * 1024) / cps - 1024);
-  int S = (int)((per_cta - fixed - 3 * vslot) / sb);
+  const int vslots = (h->variant) == 1 ? 3 : 4;  // vector ring slots of the kernel variant
+  int S = (int)((per_cta - fixed - vslots * vslot) / sb);
   if (S < 2) {  // large blocks: keep two block stages, stage vectors directly
     vslot = 0;
     S = (int)((per_cta - fixed) / sb);
@@ -337,7 +338,7 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
   if (S < 2) return BT_ERR_ARG;  // block too large for the shared-memory pipeline
   h->stages = S;
   h->stage_bytes = (int)sb;
-  h->smem = fixed + 3 * vslot + S * (int)sb;
+  h->smem = fixed + vslots * vslot + S * (int)sb;
   int occ = 0;
   if (cuda_st(bt_persistent_occupancy(mixed ? 1 : 0, h->variant, h->smem, &occ)) != BT_OK || occ < 1)
     return BT_ERR_CUDA;

@@ -128,14 +128,15 @@ extern "C" bt_status bt_pcg_solve_noalloc(int N, int n, const double* D, const d
   const int fixed = bt_persistent_smem_fixed(0);
   int vslot = mixed ? 9 * 1024 : 18 * 1024;
   const long long per_cta = std::min<long long>(smem_optin, 228 * 1024 - 1024);
-  int S = (int)((per_cta - fixed - 3 * vslot) / sb);
+  const int vslots = (0) == 1 ? 3 : 4;  // vector ring slots of the kernel variant
+  int S = (int)((per_cta - fixed - vslots * vslot) / sb);
   if (S < 2) {
     vslot = 0;
     S = (int)((per_cta - fixed) / sb);
   }
   S = std::min(S, bt::kMaxStages);
   if (S < 2) return BT_ERR_ARG;
-  const int smem = fixed + 3 * vslot + S * (int)sb;
+  const int smem = fixed + vslots * vslot + S * (int)sb;
   int occ = 0;
   if (bt_persistent_occupancy(mixed ? 1 : 0, 0, smem, &occ) != cudaSuccess || occ < 1) return BT_ERR_CUDA;
   int G = p->group_ctas > 0 ? p->group_ctas : (N <= 32 ? 1 : std::max(1, N / 4));

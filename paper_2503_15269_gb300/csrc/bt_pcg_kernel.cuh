@@ -75,13 +75,14 @@ constexpr int kSmFam = kSmParts + (3 * kMaxChunkElems + 2 * kMaxBlock) * 8;   //
 // the family region exists in the kernels of the general member only (GEN)
 template <bool GEN>
 constexpr int kSmFull = GEN ? kSmFam + (2 * kMaxChunkElems + 4 * kMaxBlock) * 8 : kSmFam;  // uint64 full[kMaxStages]
-constexpr int kVecSlots = 3;                                   // vector ring depth
+constexpr int kVecSlots = 4;  // vector ring slots at most (the general member's kernels use 3)
 template <bool GEN>
 constexpr int kSmVbar = kSmFull<GEN> + kMaxStages * 8;         // uint64 vbar[kVecSlots]
 template <bool GEN>
 constexpr int kSmVring = ((kSmVbar<GEN> + kVecSlots * 8 + 127) / 128) * 128;  // vector ring, then the stages
 
-// fixed part; the host adds kVecSlots * vec_slot_bytes + stages * stage_bytes
+// fixed part; the host adds (4, or 3 for the general member) * vec_slot_bytes
+// + stages * stage_bytes
 template <bool GEN>
 __host__ __device__ constexpr int smem_fixed_bytes() { return kSmVring<GEN>; }
 
@@ -439,6 +440,10 @@ struct Solver {
   static constexpr bool MF = (VAR == 2);
   static constexpr int kHK = GEN ? kKB2G : (MF ? kKJ : kKB2);  // kind of the H sweeps
   static constexpr int kHPS = MF ? 2 : 1;                      // sweeps per H application
+  // vector ring slots: 4 (the pipelined sweeps keep a chunk's slot one phase
+  // longer); 3 for the general member, whose extra shared memory leaves no
+  // room for a fourth
+  static constexpr int kVS = GEN ? 3 : kVecSlots;
   const KParams& P;
   char* sm;
   int tid;
@@ -474,7 +479,7 @@ struct Solver {
     vbar = reinterpret_cast<uint64_t*>(sm + kSmVbar<GEN>);
     vring = sm + kSmVring<GEN>;
     VSB = P.vec_slot_bytes;
-    stages = vring + (size_t)kVecSlots * VSB;
+    stages = vring + (size_t)kVS * VSB;
     issued = consumed = 0;
     vissued = vcons = 0;
     bar_count = 0;
@@ -596,8 +601,8 @@ struct Solver {
   __device__ void flush() {
     bool ok = true;
     while (vcons < vissued) {
-      const int st = vcons % kVecSlots;
-      const unsigned par = (vcons / kVecSlots) & 1u;
+      const int st = vcons % kVS;
+      const unsigned par = (vcons / kVS) & 1u;
       if (ok && !mbar_wait(&vbar[st], par, deadline + (1ll << 31))) ok = false;
       ++vcons;
     }
@@ -777,17 +782,259 @@ struct Solver {
     }
   }
 
+  // ---- one sweep, software-pipelined ---------------------------------------
+  // The float32 sweeps of the inner iteration (A, B1, B2 with their vector
+  // rows staged by bulk copies, n % 4 == 0).  Phase c computes the block
+  // products of chunk c, finalizes chunk c-1 (and carries its pushes) and
+  // stages the vector rows of chunk c+1: three disjoint sets of buffers
+  // (partials double-, vector rows triple-buffered, in the room the layout
+  // reserves for float64), so one CTA barrier per chunk separates the phases
+  // instead of two, and the three kinds of work overlap across warps.  A
+  // chunk's vector slot lives until its finalize, one phase after its
+  // staging: the ring runs four slots, three chunks ahead.
+  template <int KIND, int STG, int FIN>
+  __device__ __noinline__ void sweep_pipe(const Sweep<float> sw, double acc[4]) {
+    static_assert(KIND == kKA || KIND == kKB1 || KIND == kKB2, "stored-block sweeps only");
+    static_assert(STG == SV_P || STG == SV_R_UPD || STG == SV_Y, "vectorised staging only");
+    static_assert(FIN == FN_Q || FIN == FN_Y0 || FIN == FN_YJ, "vectorised finalize only");
+    constexpr int kHalo = (KIND == kKB2) ? 2 : 1;
+    constexpr int k = kHalo;
+    constexpr int kPB = 3 * kMaxChunkElems + 2 * kMaxBlock;  // part1 | part2 | push of one buffer
+    static_assert(2 * kPB * 4 <= (3 * kMaxChunkElems + 2 * kMaxBlock) * 8, "partials fit the float64 layout");
+    static_assert(3 * kVsElems * 4 <= 2 * kVsElems * 8, "vector rows fit the float64 layout");
+    static_assert(kVS == 4, "a chunk's vector slot lives one phase past its staging");
+    Producer q = producer();
+    const int n = this->n, N = this->N, s = this->s, e = this->e;
+    const int S = this->S, SB = this->SB, VSB = this->VSB;
+    const long long dl = deadline + (1ll << 31);
+    uint64_t* const full = this->full;
+    uint64_t* const vbar = this->vbar;
+    char* const stages = this->stages;
+    char* const vring = this->vring;
+    unsigned consumed = this->consumed, vissued = this->vissued, vcons = this->vcons;
+    const unsigned vbase = vcons;  // every slot issued so far has been consumed
+    const bool leader = (threadIdx.x == kLeaderTid);
+    const int tid = threadIdx.x;
+    const int ts = (tid + kThreads / 2) % kThreads;  // staging from the upper half of the CTA
+    const int R = q.rows(KIND);
+    const int bse = bs;
+    const float inv_n = 1.0f / (float)n;
+    float* ringb = reinterpret_cast<float*>(sm + kSmRing);  // [2][k][n] by chunk parity
+    float* vs3 = reinterpret_cast<float*>(sm + kSmVs);      // [3][kVsElems]
+    float* pbuf = reinterpret_cast<float*>(sm + kSmParts);  // [2][kPB]
+    const float sgn = (KIND == kKB1) ? -1.f : 1.f;
+    const int nc = (e - s + R - 1) / R;
+    const VecPlan vp = vec_plan<STG, FIN, float>(sw);
+    const float alpha = sw.alpha, beta = sw.beta, alpha_j = sw.alpha_j;
+    const bool first = sw.first, m1 = sw.m1, last = sw.last;
+    const int jpow = sw.j;
+    Accum<float> acc0, acc1, acc2;
+    auto chunk_rows = [&](int c, int& r0, int& r1, int& base, int& vend) {
+      r0 = s + c * R;
+      r1 = min(e, r0 + R);
+      base = r0 - ((c == 0) ? min(kHalo, s) : 0);
+      vend = min(N, r1 + k);
+    };
+    auto issue = [&](int c) {
+      if (leader) {
+        int r0, r1, base, vend;
+        chunk_rows(c, r0, r1, base, vend);
+        const int slot = (int)((vbase + (unsigned)c) % kVS);
+        issue_vec(vp, n, r0, r1, base, vend, vring + (size_t)slot * VSB, &vbar[slot]);
+      }
+      ++vissued;
+    };
+    // the vector arrays of chunk c inside its slot (staging arrays first)
+    auto slot_arrays = [&](int c, int nr, int rows, const float*& a0, const float*& a1, const float*& a2,
+                           const float*& a3) {
+      const char* vslot = vring + (size_t)((vbase + (unsigned)c) % kVS) * VSB;
+      const int rng = rows * n, ow = nr * n;
+      const int b0 = (vp.cnt > 0) ? (vp.own0 ? ow : rng) * vp.esz0 : 0;
+      const int b1 = (vp.cnt > 1) ? (vp.own1 ? ow : rng) * vp.esz1 : 0;
+      const int b2 = (vp.cnt > 2) ? (vp.own2 ? ow : rng) * vp.esz2 : 0;
+      a0 = reinterpret_cast<const float*>(vslot);
+      a1 = reinterpret_cast<const float*>(vslot + b0);
+      a2 = reinterpret_cast<const float*>(vslot + b0 + b1);
+      a3 = reinterpret_cast<const float*>(vslot + b0 + b1 + b2);
+    };
+    // stage the vector rows [base, vend) of chunk c with the fused PCG updates
+    auto stage = [&](int c, bool& ok) {
+      int r0, r1, base, vend;
+      chunk_rows(c, r0, r1, base, vend);
+      const int nr = r1 - r0, h = r0 - base;
+      const unsigned vi = vbase + (unsigned)c;
+      ok = ok && mbar_wait(&vbar[vi % kVS], (vi / kVS) & 1u, dl);
+      ++vcons;
+      const float *sv0, *sv1, *sv2, *sv3;
+      slot_arrays(c, nr, vend - base, sv0, sv1, sv2, sv3);
+      float* vs = vs3 + (c % 3) * kVsElems;
+      const int nv = (vend - base) * n;
+      for (int t = 4 * ts; t < nv; t += 4 * kThreads) {
+        const int rr = qdiv(t, inv_n);
+        const int a = t - rr * n;
+        const int row = base + rr;
+        const long long idx = (long long)row * n + a;
+        const bool own = row >= r0 && row < r1;
+        const int lo = t - h * n;
+        float4 v;
+        if constexpr (STG == SV_P) {
+          const float4 zz = ld4f(sv0 + t);
+          v = first ? zz : fma4(beta, ld4f(sv1 + t), zz);
+          if (own) st4f(sw.p_cur + idx, v);
+        } else if constexpr (STG == SV_R_UPD) {
+          v = fma4(-alpha, ld4f(sv1 + t), ld4f(sv0 + t));
+          if (own) {
+            st4f(sw.r_cur + idx, v);
+            st4f(sw.x + idx, fma4(alpha, ld4f(sv3 + lo), ld4f(sv2 + lo)));
+            acc2.add(dot4f(v, v));
+          }
+        } else {
+          v = ld4f(sv0 + t);
+        }
+        st4f(vs + t, v);
+      }
+    };
+    // finalize the owned rows of chunk c (partials of phase c, pushes of the
+    // row above from this chunk or the ring filled by chunk c-1)
+    auto finalize = [&](int c) {
+      int r0, r1, base, vend;
+      chunk_rows(c, r0, r1, base, vend);
+      const int nr = r1 - r0;
+      const float *sv0, *sv1, *sv2, *sv3;
+      slot_arrays(c, nr, vend - base, sv0, sv1, sv2, sv3);
+      const float* vs = vs3 + (c % 3) * kVsElems;
+      const float* part1 = pbuf + (c & 1) * kPB;
+      const float* part2 = part1 + kMaxChunkElems;
+      const float* push = part2 + kMaxChunkElems;
+      const float* ring_in = ringb + ((c - 1) & 1) * (2 * kMaxBlock);
+      const int ns = (STG == SV_P) ? (first ? 1 : 2) : ((STG == SV_R_UPD) ? 4 : 1);
+      const int iz = ns, ir = ns + ((FIN == FN_YJ && jpow > 1) ? 1 : 0);
+      const float* fz = (iz == 1) ? sv1 : ((iz == 2) ? sv2 : sv3);
+      const float* fr = (ir == 1) ? sv1 : ((ir == 2) ? sv2 : sv3);
+      const int nd = nr * n;
+      for (int t = 4 * tid; t < nd; t += 4 * kThreads) {
+        const int jj = qdiv(t, inv_n), a = t - jj * n;
+        const int row = r0 + jj;
+        const int src = row - k;
+        float4 carry = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (src >= 0) carry = (src >= base) ? ld4f(push + (src - base) * n + a) : ld4f(ring_in + (src % k) * n + a);
+        const float4 p1 = ld4f(part1 + t), p2 = ld4f(part2 + t);
+        const float4 out = make_float4(p1.x + sgn * (p2.x + carry.x), p1.y + sgn * (p2.y + carry.y),
+                                       p1.z + sgn * (p2.z + carry.z), p1.w + sgn * (p2.w + carry.w));
+        const long long idx = (long long)row * n + a;
+        const float4 vi = ld4f(vs + (row - base) * n + a);
+        if constexpr (FIN == FN_Q) {
+          st4f(sw.qout + idx, out);
+          acc0.add(dot4f(vi, out));
+        } else if constexpr (FIN == FN_Y0) {
+          if (m1) {
+            st4f(sw.zv + idx, out);
+            acc1.add(dot4f(vi, out));
+          } else {
+            st4f(sw.y0 + idx, out);
+            if constexpr (MF) st4f(sw.zv + idx, out);  // z starts at y0
+          }
+        } else {
+          const float4 zprev = (jpow == 1) ? vi : ld4f(fz + t);
+          const float4 zz = fma4(alpha_j, out, zprev);
+          if (!last) st4f(sw.ynext + idx, out);
+          st4f(sw.zv + idx, zz);
+          if (last) acc1.add(dot4f(ld4f(fr + t), zz));
+        }
+      }
+    };
+    // the pushes of the last k source rows of chunk c, for chunk c+1
+    auto carry = [&](int c) {
+      int r0, r1, base, vend;
+      chunk_rows(c, r0, r1, base, vend);
+      const float* push = pbuf + (c & 1) * kPB + 2 * kMaxChunkElems;
+      const float* ring_in = ringb + ((c - 1) & 1) * (2 * kMaxBlock);
+      float* ring_out = ringb + (c & 1) * (2 * kMaxBlock);
+      for (int t = (tid + kThreads - 64) % kThreads; t < k * n; t += kThreads) {
+        const int w = qdiv(t, inv_n), a = t - w * n;
+        const int src = r1 - k + w;
+        if (src < 0) continue;
+        ring_out[(src % k) * n + a] = (src >= base) ? push[(src - base) * n + a] : ring_in[(src % k) * n + a];
+      }
+    };
+
+    for (int c = 0; c < min(kVS - 1, nc); ++c) issue(c);
+    bool failed = false;
+    {
+      bool ok = true;
+      if (nc > 0) stage(0, ok);
+      if (__syncthreads_or(!ok)) {
+        if (G > 1 && leader) atomicExch(P.abort_flag, 1);
+        failed = true;
+      }
+    }
+    for (int c = 0; c < nc && !failed; ++c) {
+      int r0, r1, base, vend;
+      chunk_rows(c, r0, r1, base, vend);
+      const int nr = r1 - r0, h = r0 - base;
+      const int st = consumed % S;
+      const unsigned par = (consumed / S) & 1u;
+      bool ok = mbar_wait(&full[st], par, dl);
+      ++consumed;
+      // products of chunk c (its vector rows were staged in the previous phase)
+      const float* stg = reinterpret_cast<const float*>(stages + (size_t)st * SB);
+      float* part1 = pbuf + (c & 1) * kPB;
+      float* part2 = part1 + kMaxChunkElems;
+      float* push = part2 + kMaxChunkElems;
+      const float* vs = vs3 + (c % 3) * kVsElems;
+      if (ok) {
+        switch (n) {
+          case 12: chunk_products<KIND, 12, float>(stg, R, bse, n, N, nr, h, r0, base, vs, part1, part2, push, nullptr, nullptr); break;
+          case 24: chunk_products<KIND, 24, float>(stg, R, bse, n, N, nr, h, r0, base, vs, part1, part2, push, nullptr, nullptr); break;
+          case 36: chunk_products<KIND, 36, float>(stg, R, bse, n, N, nr, h, r0, base, vs, part1, part2, push, nullptr, nullptr); break;
+          case 48: chunk_products<KIND, 48, float>(stg, R, bse, n, N, nr, h, r0, base, vs, part1, part2, push, nullptr, nullptr); break;
+          default: chunk_products<KIND, 0, float>(stg, R, bse, n, N, nr, h, r0, base, vs, part1, part2, push, nullptr, nullptr); break;
+        }
+      }
+      if (c > 0) {
+        finalize(c - 1);
+        carry(c - 1);
+      }
+      if (c + 1 < nc) stage(c + 1, ok);
+      if (__syncthreads_or(!ok)) {
+        if (G > 1 && leader) atomicExch(P.abort_flag, 1);
+        failed = true;
+        break;
+      }
+      q.step(leader);                          // the stage of chunk c is free
+      if (c + kVS - 1 < nc) issue(c + kVS - 1);  // into the slot of chunk c-1
+    }
+    if (!failed && nc > 0) finalize(nc - 1);
+    __syncthreads();
+    this->consumed = consumed;
+    this->vissued = vissued;
+    this->vcons = vcons;
+    store_producer(q);
+    acc[0] += acc0.value();
+    acc[1] += acc1.value();
+    acc[2] += acc2.value();
+    if (failed) fail = true;
+  }
+
   // ---- one sweep -----------------------------------------------------------
   // KIND / STG / FIN are compile-time: each instantiation carries only the
   // staging and finalize code it uses.  The block products dispatch once per
   // chunk on n to compile-time block sizes (unrolled, vector loads).  The
-  // vector rows each chunk reads arrive by bulk copies issued kVecSlots-1
+  // vector rows each chunk reads arrive by bulk copies issued kVS-1
   // chunks ahead inside the sweep (they are final once the sweep starts).
   // All pipeline state is held in registers for the duration of the sweep.
   template <int KIND, int STG, int FIN, typename T>
   __device__ __noinline__ void sweep(const Sweep<T> sw, double acc[4]) {
     constexpr int kHalo = (KIND == kKB2 || KIND == kKB2G) ? 2 : 1;
     constexpr int k = (KIND == kKB2 || KIND == kKB2G) ? 2 : 1;
+    if constexpr (sizeof(T) == 4 && kVS == 4 && (KIND == kKA || KIND == kKB1 || KIND == kKB2) &&
+                  (STG == SV_P || STG == SV_R_UPD || STG == SV_Y) && (FIN == FN_Q || FIN == FN_Y0 || FIN == FN_YJ)) {
+      if ((n & 3) == 0 && !sw.out_to_user &&
+          vec_plan_ok(vec_plan<STG, FIN, T>(sw), n, geo(KIND).R, k, kHalo, VSB)) {
+        sweep_pipe<KIND, STG, FIN>(sw, acc);
+        return;
+      }
+    }
     Producer q = producer();
     const int n = this->n, N = this->N, s = this->s, e = this->e;
     const int S = this->S, SB = this->SB, VSB = this->VSB;
@@ -834,12 +1081,12 @@ struct Solver {
       vend = min(N, r1 + k);
     };
     if (va) {
-      const int pre = min(kVecSlots - 1, nc);
+      const int pre = min(kVS - 1, nc);
       for (int c = 0; c < pre; ++c) {
         if (leader) {
           int r0, r1, base, vend;
           chunk_rows(c, r0, r1, base, vend);
-          const int slot = vissued % kVecSlots;
+          const int slot = vissued % kVS;
           issue_vec(vp, n, r0, r1, base, vend, vring + (size_t)slot * VSB, &vbar[slot]);
         }
         ++vissued;
@@ -862,9 +1109,9 @@ struct Solver {
       // 1. wait for the chunk's blocks and vector rows
       bool ok = mbar_wait(&full[st], par, dl);
       ++consumed;
-      const char* vslot = vring + (size_t)(vcons % kVecSlots) * VSB;
+      const char* vslot = vring + (size_t)(vcons % kVS) * VSB;
       if (va) {
-        ok = ok && mbar_wait(&vbar[vcons % kVecSlots], (vcons / kVecSlots) & 1u, dl);
+        ok = ok && mbar_wait(&vbar[vcons % kVS], (vcons / kVS) & 1u, dl);
         ++vcons;
       }
       // byte offsets of the vector arrays inside the slot
@@ -961,12 +1208,12 @@ struct Solver {
         failed = true;
         break;
       }
-      // the vector slot of chunk c-1 is free now: prefetch chunk c + kVecSlots - 1
-      if (va && c + kVecSlots - 1 < nc) {
+      // the vector slot of chunk c-1 is free now: prefetch chunk c + kVS - 1
+      if (va && c + kVS - 1 < nc) {
         if (leader) {
           int pr0, pr1, pbase, pvend;
-          chunk_rows(c + kVecSlots - 1, pr0, pr1, pbase, pvend);
-          const int slot = vissued % kVecSlots;
+          chunk_rows(c + kVS - 1, pr0, pr1, pbase, pvend);
+          const int slot = vissued % kVS;
           issue_vec(vp, n, pr0, pr1, pbase, pvend, vring + (size_t)slot * VSB, &vbar[slot]);
         }
         ++vissued;
