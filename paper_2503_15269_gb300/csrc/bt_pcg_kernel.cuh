@@ -47,15 +47,18 @@ struct Geo {
   int narr;   // block arrays in the chunk
 };
 
-__device__ __forceinline__ Geo geo_of(int kind, int stage_bytes, int bs_bytes, int n) {
+// `group`: the instance's rows are split over several CTAs, so the first chunk
+// of a range may carry halo rows; a whole instance (batched mode) starts at
+// row 0 and never does, and its stages need no slots for them.
+__device__ __forceinline__ Geo geo_of(int kind, int stage_bytes, int bs_bytes, int n, bool group) {
   Geo g;
   const int slots = stage_bytes / bs_bytes;
   if (kind == kKB2) {
-    g.R = (slots - 2) / 3; g.halo = 2; g.k = 2; g.narr = 3;
+    g.R = (slots - (group ? 2 : 0)) / 3; g.halo = 2; g.k = 2; g.narr = 3;
   } else if (kind == kKB2G) {
-    g.R = (slots - 4) / 5; g.halo = 2; g.k = 2; g.narr = 5;
+    g.R = (slots - 4) / 5; g.halo = 2; g.k = 2; g.narr = 5;  // fixed stage layout (halo slots kept)
   } else {
-    g.R = (slots - 1) / 2; g.halo = 1; g.k = 1; g.narr = 2;
+    g.R = (slots - (group ? 1 : 0)) / 2; g.halo = 1; g.k = 1; g.narr = 2;
   }
   const int cap = kMaxChunkElems / n;
   if (g.R > cap) g.R = cap;
@@ -487,7 +490,7 @@ struct Solver {
 
   // ---- chunk geometry ----------------------------------------------------
   __device__ int bsb_of(int kind) const { return kind == kKA64 ? bs64 * 8 : bs * (int)sizeof(MT); }
-  __device__ Geo geo(int kind) const { return geo_of(kind, SB, bsb_of(kind), n); }
+  __device__ Geo geo(int kind) const { return geo_of(kind, SB, bsb_of(kind), n, G > 1); }
   __device__ int nchunks(int kind) const {
     Geo gg = geo(kind);
     return (e - s + gg.R - 1) / gg.R;
