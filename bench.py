@@ -97,6 +97,23 @@ def run_oracle(indices, procs):
     return wall, out
 
 
+def max_over_ranks(ms, dist, device):
+    """The job's time: the slowest rank's (every rank calls it; at N = 1 it
+    returns ms).  The only exchange between ranks: instances are independent,
+    each rank solves its own batch (weak scaling, no data-path collective)."""
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, units_per_rank, steps, ms):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time."""
+    return world * units_per_rank * steps / (ms / 1e3)
+
+
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -336,11 +353,8 @@ def main():
     ms = e0.elapsed_time(e1)
     ms_setup = sum(x[0].elapsed_time(x[1]) for x in ev) / a.steps
     ms_solve = sum(x[1].elapsed_time(x[2]) for x in ev) / a.steps
-    t = torch.tensor([ms], device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
-    value = world * B * a.steps / (ms / 1e3)
+    ms = max_over_ranks(ms, dist, dev)
+    value = job_value(world, B, a.steps, ms)
 
     if a.profile:
         if rank == 0:
@@ -404,11 +418,8 @@ def main():
     e2e_steps(a.steps)
     f1.record(stream)
     torch.cuda.synchronize()
-    ms_e2e = f0.elapsed_time(f1)
-    te = torch.tensor([ms_e2e], device=dev)
-    if dist:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * B * a.steps / (float(te.item()) / 1e3)
+    ms_e2e = max_over_ranks(f0.elapsed_time(f1), dist, dev)
+    e2e_value = job_value(world, B, a.steps, ms_e2e)
     for j in range(min(2, a.steps)):
         assert (hsts[j][B:].numpy() == 0).all()
     h2d = hD.numel() * 8 + hO.numel() * 8 + hb.numel() * 8
