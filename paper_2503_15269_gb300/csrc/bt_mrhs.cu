@@ -234,6 +234,72 @@ namespace bt {
 
 enum MPhase : int { MP_A = 0, MP_B1 = 1, MP_B2 = 2, MP_A64 = 3 };
 
+// Float32 sweeps: the vector rows a row job reads (i-k, i, i+k) come from a
+// ring of 2k+2 rows in shared memory, each loaded once per sweep (one row
+// ahead, with the blocks of the next job), instead of three copies per row in
+// every job; the ring occupies the room of the second job's vector rows.
+template <typename Fin, typename Blk>
+__device__ void msweep_ring(MSolver& Sv, int phase, const float* v_in, Fin fin, Blk blk) {
+  const int n = Sv.n, N = Sv.N;
+  const int tid = threadIdx.x;
+  const int ngroups = n / 4;
+  const int jg = tid & 15, ag = tid >> 4;
+  const bool active = ag < ngroups;
+  const int a0 = 4 * ag, j0 = 4 * jg;
+  const int bb = n * n, vb = n * kJ;
+  const int k = (phase == MP_B2) ? 2 : 1;
+  const int kv = 2 * k + 2;
+  float* blocks = reinterpret_cast<float*>(Sv.sm + kMSmJobs);  // [2][3 bb]
+  float* ring = blocks + 6 * bb;                               // [kv][vb]
+  const auto slot = [&](int r) { return ring + (size_t)(((r % kv) + kv) % kv) * vb; };
+  const auto issue_blocks = [&](int row, int buf) {
+    float* m = blocks + (size_t)buf * 3 * bb;
+    cp_block(m, blk(0, row), bb);
+    if (row + k < N) cp_block(m + bb, blk(1, row), bb);
+    if (row - k >= 0) cp_block(m + 2 * bb, blk(2, row - k), bb);
+  };
+  const int s = Sv.s, e = Sv.e;
+  // prologue: the first job's blocks and vector rows s-k .. s+k
+  issue_blocks(s, 0);
+  for (int r = max(0, s - k); r <= min(N - 1, s + k); ++r) cp_block(slot(r), v_in + (size_t)r * vb, vb);
+  cp_commit();
+  for (int row = s; row < e; ++row) {
+    const int it = row - s;
+    if (row + 1 < e) {  // the next job: its blocks and its one new vector row
+      issue_blocks(row + 1, (it + 1) & 1);
+      const int nr = row + 1 + k;
+      if (nr < N) cp_block(slot(nr), v_in + (size_t)nr * vb, vb);
+      cp_commit();
+      cp_wait<1>();
+    } else {
+      cp_wait<0>();
+    }
+    __syncthreads();
+    const float* m0 = blocks + (size_t)(it & 1) * 3 * bb;
+    const float* m1 = m0 + bb;
+    const float* m2 = m0 + 2 * bb;
+    const float* xc = slot(row);
+    float acc[4][4] = {};
+    float acc2[4][4] = {};
+    if (active) {
+      prod_direct(m0, xc, n, a0, j0, acc);
+      if (row + k < N) prod_direct(m1, slot(row + k), n, a0, j0, acc2);
+      if (row - k >= 0) {
+        if (phase == MP_B2) prod_direct(m2, slot(row - k), n, a0, j0, acc2);
+        else prod_trans(m2, slot(row - k), n, a0, j0, acc2);
+      }
+    }
+    const float sg = (phase == MP_B1) ? -1.f : 1.f;
+    float out[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) out[r][c] = acc[r][c] + sg * acc2[r][c];
+    if (active) fin(row, a0, j0, out, xc);
+    __syncthreads();
+  }
+}
+
 // One sweep over the owned rows of float32 (T = float) or the float64
 // refinement residual (T = double).  The finalize functor receives the 4x4
 // tile (rows a0.., columns j0..) of row i.
@@ -287,6 +353,10 @@ __device__ void msweep(MSolver& Sv, int phase, const T* v_in, Fin fin) {
   };
   const int nrows = Sv.e - Sv.s;
   if (nrows <= 0) return;
+  if constexpr (sizeof(T) == 4) {
+    msweep_ring(Sv, phase, v_in, fin, blk);
+    return;
+  }
   if (nbuf == 2) issue(Sv.s, 0);
   for (int it = 0; it < nrows; ++it) {
     const int row = Sv.s + it;
