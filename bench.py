@@ -787,7 +787,7 @@ def lqr_pipeline(a, bb, wl, torch, dev):
     Each stage timed with CUDA events; the formation kernel's roofline is the
     float64 rate (its FMA count per block row: 2n^3 + m^3/2 + n m^2 + n^2 m/2)."""
     import numpy as np
-    shapes = wl.config2_shapes(1024)
+    shapes = wl.config2_shapes(1024)[:max(1, min(a.batch, 1024))]  # --batch: the first problems only
     probs = [wl.lqr_data(wl._rng(6, k), N, n, max(1, n // 3)) for k, (N, n) in enumerate(shapes)]
     cat = lambda f: np.concatenate([getattr(p, f).reshape(-1) for p in probs])
     dA, dB, dQ, dR, dq, dr, dc = (torch.tensor(cat(f), device=dev) for f in ("A", "Bm", "Q", "R", "q", "r", "c"))
@@ -841,7 +841,7 @@ def lqr_pipeline(a, bb, wl, torch, dev):
           "value": len(probs) / (tot / 1e3), "unit": "problems/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
           "ms_per_step": tot, "higher_is_better": True, "dtype": "f64 formation + f32/f64 solve",
           "data": "synthetic (seeded LQR, dense SPD Q and R)",
-          "config": {"workload": "1024 LQR problems, N~U{32..512}, n in {12,24,36}, m=n/3"},
+          "config": {"workload": f"{len(probs)} LQR problems, N~U{{32..512}}, n in {{12,24,36}}, m=n/3"},
           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                        "frac": achieved / peak_tf, "traffic": None, "peak_source": "nominal float64 rate",
                        "kernel": "k_lqr_schur", "flop_per_launch": 2 * fma},
