@@ -391,3 +391,21 @@ def test_deterministic_bitwise():
         with Single(inst, m=2, alpha=[1.0, 7.0], group_ctas=8) as s:
             outs.append(s.solve(inst.b, 1e-10, 1000)[2])
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("m,alpha", [(2, [1.0, 7.0]), (3, None)])
+def test_batched_mixed_ragged_block_sizes(m, alpha):
+    """Batched mixed solves over block sizes that take every sweep form:
+    odd n (scalar staging, unpipelined), n % 4 == 0 at run-time sizes (8, 20:
+    pipelined with generic products) and at compiled sizes (12, 24, 36, 48),
+    horizons from 1 to 70 (one to several chunks, ragged tails).  Every
+    instance meets the float64 true residual and matches the direct solve."""
+    rng = np.random.default_rng(17)
+    sizes = [1, 3, 5, 7, 8, 12, 20, 24, 36, 48]
+    insts = [wl.small_ocp(130 + k, int(rng.integers(1, 71)), sizes[k % len(sizes)]) for k in range(30)]
+    st, its, sts, xs, infos = _batched(insts, m, alpha, bb.BT_MIXED, 1e-10, 20000)
+    assert st == bb.BT_OK and (sts == 0).all()
+    for k, inst in enumerate(insts):
+        res = np.linalg.norm(orc.spmv(inst.D, inst.O, xs[k]) - inst.b) / np.linalg.norm(inst.b)
+        assert res <= 1e-10, (k, inst.N, inst.n, res)
+        assert rel(xs[k], orc.direct_solve(inst.D, inst.O, inst.b)) <= 1e-8, k
