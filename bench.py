@@ -459,7 +459,8 @@ def main():
                        "preconditioner": "a=1, m=2, alpha=(1,7)", "tol": TOL,
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": 5 * a.steps,
+            # per step: k_factor32, k_factor_retry, k_EH (refactor) and the persistent solve kernel
+            "gpu_launches": 4 * a.steps,
             "roofline": roof,
             "cpu_baseline": cpu,
             "clocks": clocks.summary() if clocks else None,
