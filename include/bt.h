@@ -274,6 +274,20 @@ bt_status bt_pcg_solve_noalloc(int N, int n, const double* D, const double* O, c
  * radius leaves M^-1 SPD but loses the bound.  BT_ERR_ARG on bad arguments. */
 bt_status bt_alpha_chebyshev(int m, double rho, double* alpha);
 
+/* bt_estimate_rho -- the bound rho that bt_alpha_chebyshev takes, per
+ * instance of a handle with a = 1 (stored or matrix-free H): power iteration
+ * on H_opt, using that M^-1 S = I - H_opt at m = 1 (Sec. 3.5), i.e.
+ *     v <- (v - G_opt (S v)) / || . ||,   rho[k] = ||v - G_opt S v||, ||v|| = 1,
+ * `iters` steps from the fixed start vector v_i = 1 + sin(i)/10 (i the element
+ * index within the instance), S in float64 and G_opt in the handle's
+ * precision.  rho[k] (HOST array of the handle's instance count) approaches
+ * rho(H_opt), mostly from below (H_opt is not symmetric, so the norm ratio
+ * may also end a little above it); the top eigenvalues of H_opt come in pairs
+ * with close neighbours, so convergence is slow (within about 1e-3 after 400
+ * steps on the LQR family): add a margin before passing it on.  Three launches per step
+ * on the handle's stream, then synchronises.  BT_ERR_PARAM for a < 1. */
+bt_status bt_estimate_rho(bt_handle h, int iters, double* rho);
+
 /* bt_lqr_schur -- form the systems S lam = gamma of B LQR problems on the
  * device: the construction of the test matrices of Sec. 5 (an LQR problem as
  * an equality-constrained QP, its KKT system, the Schur complement with

@@ -475,3 +475,21 @@ def chebyshev_alpha(m: int, rho: float) -> np.ndarray:
     q = np.asarray(q, dtype=np.float64)
     q = np.concatenate([q, np.zeros(max(0, m - q.size))])[:m]
     return q / q[0]
+
+
+def power_rho(D: np.ndarray, O: np.ndarray, iters: int) -> float:
+    """Estimate of the spectral radius of H_opt by power iteration, using
+    M^-1 S = I - H_opt for the optimum at m = 1 (Sec. 3.5): from
+    v_i = 1 + sin(i)/10 (normalised), v <- h / ||h|| with h = v - G_opt S v;
+    returns ||h|| of the last step (H_opt is not symmetric: the ratio can
+    end slightly above rho)."""
+    B = opt_blocks(D, O)
+    N, n = D.shape[0], D.shape[1]
+    v = (1.0 + 0.1 * np.sin(np.arange(N * n, dtype=np.float64))).reshape(N, n)
+    v = v / np.linalg.norm(v)
+    nh = 0.0
+    for _ in range(iters):
+        h = v - apply_G_opt(B, spmv(D, O, v))
+        nh = float(np.linalg.norm(h))
+        v = h / nh
+    return nh

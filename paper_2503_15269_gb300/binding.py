@@ -83,6 +83,7 @@ def lib() -> C.CDLL:
         "bt_multi_info": (C.c_int, [H, C.c_int, ip, C.POINTER(C.c_double)]),
         "bt_last_error": (C.c_int, [H, ip, ip, C.POINTER(C.c_double)]),
         "bt_params_check": (C.c_int, [C.POINTER(bt_params)]),
+        "bt_estimate_rho": (C.c_int, [H, C.c_int, C.POINTER(C.c_double)]),
         "bt_alpha_chebyshev": (C.c_int, [C.c_int, C.c_double, C.POINTER(C.c_double)]),
         "bt_lqr_schur": (C.c_int, [C.c_int, ip, ip, ip, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, vp, ip, ip]),
         "bt_lqr_recover": (C.c_int, [C.c_int, ip, ip, ip, dp, dp, dp, dp, dp, dp, dp, dp, dp, vp]),
@@ -259,6 +260,13 @@ def bt_pcg_solve_multi(h, B, X, nrhs: int, tol: float, maxit: int):
     ss = (C.c_int * nrhs)()
     st = lib().bt_pcg_solve_multi(h, _ptr(B), _ptr(X), int(nrhs), float(tol), int(maxit), it, ss)
     return st, np.array(it[:], dtype=np.int64), np.array(ss[:], dtype=np.int64)
+
+
+def bt_estimate_rho(h, iters: int, count: int):
+    """Returns (status, rho per instance)."""
+    r = (C.c_double * max(1, count))()
+    st = lib().bt_estimate_rho(h, int(iters), r)
+    return st, list(r[:count])
 
 
 def bt_alpha_chebyshev(m: int, rho: float):

@@ -92,6 +92,38 @@ struct bt_ctx {
   std::vector<double> mr_resid;
 };
 
+namespace bt {
+// One power-iteration step per instance (one CTA each): hv = v - u with
+// u = G (S v), then v <- hv / ||hv|| and est = ||hv||.  first: v <- the fixed
+// start vector 1 + sin(i)/10 (i the element index in the instance), normalised.
+__global__ void k_rho_step(const InstDesc* inst, double* v, const double* u, double* est, int first) {
+  __shared__ double red[32];
+  const InstDesc d = inst[blockIdx.x];
+  const long long len = (long long)d.N * d.n;
+  double* vv = v + d.vec;
+  const double* uu = u + d.vec;
+  double s = 0.0;
+  for (long long t = threadIdx.x; t < len; t += blockDim.x) {
+    const double h = first ? 1.0 + 0.1 * sin((double)t) : vv[t] - uu[t];
+    vv[t] = h;
+    s += h * h;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    red[0] = sqrt(t);
+  }
+  __syncthreads();
+  const double nrm = red[0];
+  const double sc = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  for (long long t = threadIdx.x; t < len; t += blockDim.x) vv[t] *= sc;
+  if (threadIdx.x == 0 && !first) est[blockIdx.x] = nrm;
+}
+}  // namespace bt
+
 namespace {
 
 inline bt_status cuda_st(cudaError_t e) { return e == cudaSuccess ? BT_OK : BT_ERR_CUDA; }
@@ -470,6 +502,42 @@ bt_status collect(bt_ctx* h, int* iters, int* status_out, bool all) {
 }  // namespace
 
 extern "C" {
+
+bt_status bt_estimate_rho(bt_handle h, int iters, double* rho) {
+  if (!h || !rho || iters < 1) return BT_ERR_ARG;
+  if (h->variant == 1 || h->prm.a != 1.0) return BT_ERR_PARAM;  // H_opt = I - G_opt S holds at a = 1
+  cudaStream_t st = h->stream;
+  const size_t len = (size_t)std::max<long long>(h->total_vec, 1);
+  char* buf = nullptr;
+  const size_t bytes = (3 * len + (size_t)h->B) * sizeof(double);
+  if (cudaMallocAsync((void**)&buf, bytes, st) != cudaSuccess) return BT_ERR_ALLOC;
+  double* v = reinterpret_cast<double*>(buf);
+  double* w = v + len;
+  double* u = w + len;
+  double* est = u + len;
+  bt_status out = BT_OK;
+  bt::k_rho_step<<<h->B, 256, 0, st>>>(h->d_inst, v, u, est, 1);
+  if (cudaGetLastError() != cudaSuccess) out = BT_ERR_CUDA;
+  for (int k = 0; k < iters && out == BT_OK; ++k) {
+    if ((out = run_op(h, bt::kOpSpmv64, v, w)) != BT_OK) break;     // w = S v (float64 blocks)
+    bt::KParams P = base_kparams(h);                                 // u = G w (m = 1)
+    P.op = bt::kOpApply;
+    P.m = 1;
+    P.bvec = w;
+    P.xvec = u;
+    P.tol = 0;
+    P.maxit = 0;
+    if ((out = launch(h, P)) != BT_OK) break;
+    bt::k_rho_step<<<h->B, 256, 0, st>>>(h->d_inst, v, u, est, 0);  // v <- H v / ||H v||
+    if (cudaGetLastError() != cudaSuccess) out = BT_ERR_CUDA;
+  }
+  if (out == BT_OK &&
+      (cudaMemcpyAsync(rho, est, (size_t)h->B * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+       cudaStreamSynchronize(st) != cudaSuccess))
+    out = BT_ERR_CUDA;
+  cudaFreeAsync(buf, st);
+  return out;
+}
 
 bt_status bt_params_check(const bt_params* params) {
   double alpha[BT_MAX_M];

@@ -67,3 +67,29 @@ def test_batched_mixed_fewer_iterations_than_polycoeff():
             assert np.linalg.norm(orc.spmv(inst.D, inst.O, xk) - inst.b) <= 1e-8 * np.linalg.norm(inst.b)
         out[name] = float(np.mean(its))
     assert out["cheb3"] < out["polycoeff"] and out["cheb4"] < out["cheb3"], out
+
+
+@pytest.mark.parametrize("precision,tol", [(bb.BT_FP64, 1e-9), (bb.BT_MIXED, 1e-5)])
+def test_estimate_rho_matches_oracle(precision, tol):
+    """bt_estimate_rho per instance of a batched handle against the oracle's
+    power iteration with the same start vector and step count."""
+    insts = [wl.small_ocp(600 + k, N, n) for k, (N, n) in enumerate([(16, 6), (30, 20), (33, 12)])]
+    Ns, ns, d_off, o_off, v_off, D, O, b = wl.pack_batch(insts)
+    p, keep = bb.make_params(m=2, alpha=[1.0, 7.0], precision=precision)
+    st, h = bb.bt_setup_batched(Ns, ns, d_off, o_off, dev(D), dev(O), p)
+    assert st == bb.BT_OK
+    try:
+        st, rho = bb.bt_estimate_rho(h, 100, len(insts))
+    finally:
+        bb.bt_destroy(h)
+    assert st == bb.BT_OK
+    for k, inst in enumerate(insts):
+        ref = orc.power_rho(inst.D, inst.O, 100)
+        assert abs(rho[k] - ref) <= tol * ref, (k, rho[k], ref)
+
+
+def test_estimate_rho_refuses_general_member():
+    inst = wl.small_ocp(610, 8, 6)
+    with Single(inst, m=2, a=0.5) as s:
+        s.ok()
+        assert bb.bt_estimate_rho(s.h, 10, 1)[0] == bb.BT_ERR_PARAM

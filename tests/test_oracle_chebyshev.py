@@ -77,3 +77,19 @@ def test_fewer_iterations_than_polycoeff_at_m3_m4():
         pc = orc.pcg_opt(inst.D, inst.O, inst.b, [1.0] * (m - 1) + [7.0], 1e-8, 3000).iters
         ch = orc.pcg_opt(inst.D, inst.O, inst.b, orc.chebyshev_alpha(m, 0.985), 1e-8, 3000).iters
         assert ch < pc, (m, ch, pc)
+
+
+def test_power_rho_approaches_the_dense_spectral_radius():
+    """The power-iteration estimate against the eigenvalues of the dense
+    H_opt (from apply_H_opt on the columns of I): the error shrinks with the
+    step count.  H_opt is not symmetric, so ||H v|| / ||v|| is not bounded by
+    rho and may end slightly above it."""
+    inst = wl.small_ocp(500, 16, 6)
+    B = orc.opt_blocks(inst.D, inst.O)
+    N, n = 16, 6
+    eye = np.eye(N * n)
+    H = np.column_stack([orc.apply_H_opt(B, eye[:, k].reshape(N, n)).reshape(-1) for k in range(N * n)])
+    rho = np.abs(np.linalg.eigvals(H)).max()
+    est = [orc.power_rho(inst.D, inst.O, k) for k in (50, 400)]
+    assert abs(rho - est[1]) < abs(rho - est[0])
+    assert abs(rho - est[1]) < 1e-4
