@@ -838,8 +838,11 @@ struct Solver {
       base = r0 - ((c == 0) ? min(kHalo, s) : 0);
       vend = min(N, r1 + k);
     };
+    // the vector-ring copies come from lane 0 of the warp below the stage
+    // producer's, so the two issues after a phase barrier do not queue on one thread
+    const bool vleader = (threadIdx.x == kLeaderTid - 32);
     auto issue = [&](int c) {
-      if (leader) {
+      if (vleader) {
         int r0, r1, base, vend;
         chunk_rows(c, r0, r1, base, vend);
         const int slot = (int)((vbase + (unsigned)c) % kVS);
