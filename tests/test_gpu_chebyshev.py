@@ -93,3 +93,13 @@ def test_estimate_rho_refuses_general_member():
     with Single(inst, m=2, a=0.5) as s:
         s.ok()
         assert bb.bt_estimate_rho(s.h, 10, 1)[0] == bb.BT_ERR_PARAM
+
+
+def test_estimate_rho_matrix_free_handle():
+    """The matrix-free variant applies the same G_opt: the same estimate."""
+    inst = wl.small_ocp(620, 24, 12)
+    ref = orc.power_rho(inst.D, inst.O, 60)
+    with Single(inst, m=2, alpha=[1.0, 7.0], h_matrix_free=True) as s:
+        s.ok()
+        st, rho = bb.bt_estimate_rho(s.h, 60, 1)
+    assert st == bb.BT_OK and abs(rho[0] - ref) <= 1e-9 * ref

@@ -183,3 +183,18 @@ def test_protocol_table_matches_oracle():
         assert gem["PolyCoeff"][k] <= min(g[k] for g in gem.values())
         assert (gem["optimal"][k] < gem["block Jacobi"][k]) == (k % 2 == 0)
     assert int(np.argmin(gem["PolyCoeff"])) == 1
+
+
+@pytest.mark.parametrize("G", [2, 4])
+def test_group_ctas_family_mixed(G):
+    """Mixed precision over G CTAs: the float32 five-array H sweep across range
+    starts (halo rows of both lower bands)."""
+    inst = wl.small_ocp(89, 41, 12)
+    xref = orc.direct_solve(inst.D, inst.O, inst.b)
+    r = np.random.default_rng(G).standard_normal((41, 12))
+    with Single(inst, m=3, a=0.5, precision=bb.BT_MIXED, group_ctas=G) as s:
+        s.ok()
+        st, it, x = s.solve(inst.b, 1e-12, 20000)
+        z = s.apply(r)
+    assert st == bb.BT_OK and rel(x, xref) <= 1e-8
+    assert maxrel(z, orc.apply_family(inst.D, inst.O, r, 0.5, [1.0, 1.0, 1.0])) <= 2e-4

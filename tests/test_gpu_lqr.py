@@ -151,3 +151,15 @@ def test_non_spd_blocks_are_reported():
     probs[0].R[3] = np.diag([1.0, -2.0])
     st, bi, br, *_ = _schur_gpu(probs)
     assert st == bb.BT_ERR_NOT_SPD and (bi, br) == (0, 3)
+
+
+def test_single_knot_problems_without_dynamics():
+    """N = 1 everywhere: no A, B, R, r; D_0 = Q_0^-1, gamma_0 = -(c_0 + Q_0^-1 q_0)."""
+    probs = [wl.small_lqr(80 + k, 1, n, 2) for k, n in enumerate([1, 4, 7])]
+    st, bi, br, D, O, g = _schur_gpu(probs)
+    assert st == bb.BT_OK
+    Ds = _split(D, [p.n * p.n for p in probs], [(1, p.n, p.n) for p in probs])
+    gs = _split(g, [p.n for p in probs], [(1, p.n) for p in probs])
+    for k, p in enumerate(probs):
+        Dr, Or, gr = orc.lqr_schur(p.A, p.Bm, p.Q, p.R, p.q, p.r, p.c)
+        assert maxrel(Ds[k], Dr) <= 1e-12 and maxrel(gs[k], gr) <= 1e-12
