@@ -274,6 +274,19 @@ bt_status bt_pcg_solve_noalloc(int N, int n, const double* D, const double* O, c
  * radius leaves M^-1 SPD but loses the bound.  BT_ERR_ARG on bad arguments. */
 bt_status bt_alpha_chebyshev(int m, double rho, double* alpha);
 
+/* bt_autotune -- choose the persistent kernel's launch shape for this handle
+ * by timing its own solves of b (DEVICE, packed as for the solve calls):
+ * batched handles try stage sizes of 64, 72 and 80 KiB, single-instance
+ * handles 1, N/16, N/8, N/4 and N/2 CTAs per instance (shapes that do not
+ * fit are skipped); each candidate runs one untimed and `trials` timed
+ * solves (CUDA events on the handle's stream) and the fastest stays
+ * configured for later calls (a captured CUDA graph is dropped).  x (DEVICE)
+ * holds a solve in the chosen shape on return; *stage_kb and *group_ctas
+ * (may be NULL) report the shape.  Synchronises the stream.  Not for the
+ * many-RHS engine, which has its own shape. */
+bt_status bt_autotune(bt_handle h, const double* b, double* x, double tol, int maxit, int trials, int* stage_kb,
+                      int* group_ctas);
+
 /* bt_estimate_rho -- the bound rho that bt_alpha_chebyshev takes, per
  * instance of a handle with a = 1 (stored or matrix-free H): power iteration
  * on H_opt, using that M^-1 S = I - H_opt at m = 1 (Sec. 3.5), i.e.

@@ -84,6 +84,7 @@ def lib() -> C.CDLL:
         "bt_last_error": (C.c_int, [H, ip, ip, C.POINTER(C.c_double)]),
         "bt_params_check": (C.c_int, [C.POINTER(bt_params)]),
         "bt_estimate_rho": (C.c_int, [H, C.c_int, C.POINTER(C.c_double)]),
+        "bt_autotune": (C.c_int, [H, dp, dp, C.c_double, C.c_int, C.c_int, ip, ip]),
         "bt_alpha_chebyshev": (C.c_int, [C.c_int, C.c_double, C.POINTER(C.c_double)]),
         "bt_lqr_schur": (C.c_int, [C.c_int, ip, ip, ip, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, vp, ip, ip]),
         "bt_lqr_recover": (C.c_int, [C.c_int, ip, ip, ip, dp, dp, dp, dp, dp, dp, dp, dp, dp, vp]),
@@ -260,6 +261,13 @@ def bt_pcg_solve_multi(h, B, X, nrhs: int, tol: float, maxit: int):
     ss = (C.c_int * nrhs)()
     st = lib().bt_pcg_solve_multi(h, _ptr(B), _ptr(X), int(nrhs), float(tol), int(maxit), it, ss)
     return st, np.array(it[:], dtype=np.int64), np.array(ss[:], dtype=np.int64)
+
+
+def bt_autotune(h, b, x, tol: float, maxit: int, trials: int = 2):
+    """Returns (status, stage_kb, group_ctas)."""
+    kb, g = C.c_int(0), C.c_int(0)
+    st = lib().bt_autotune(h, _ptr(b), _ptr(x), float(tol), int(maxit), int(trials), C.byref(kb), C.byref(g))
+    return st, kb.value, g.value
 
 
 def bt_estimate_rho(h, iters: int, count: int):

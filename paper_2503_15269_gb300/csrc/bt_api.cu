@@ -76,6 +76,7 @@ struct bt_ctx {
   char* d_ws = nullptr;
   long long ws_stride = 0, ws_vec = 0;
   int ws_slots = 0;
+  int ws_cap = 0;  // workspace slots allocated (a later configure() may not exceed them)
   // launch configuration
   int stages = 0, stage_bytes = 0, smem = 0, grid = 0, G = 1, vec_slot_bytes = 0;
   // results of the last solve
@@ -223,6 +224,68 @@ bt_status read_setup_status(bt_ctx* h) {
   return BT_ERR_NOT_SPD;
 }
 
+// Launch shape of the persistent kernel for a stage size and (single
+// instance) a CTA count; 0 = the defaults.  Sets stages, stage and vector-slot
+// bytes, dynamic shared memory, grid and group size; allocates nothing.
+bt_status configure(bt_ctx* h, int stage_kb, int group_ctas) {
+  const bool mixed = h->mixed != 0;
+  const bool general = h->variant == 1;
+  const bool mf = h->variant == 2;
+  const int B = h->B;
+  const int wbytes = mixed ? 4 : 8;
+  long long bsb_max = rup((long long)h->maxn * h->maxn, 2) * wbytes;
+  if (mixed)
+    for (int q = 1; q <= h->maxn; ++q) bsb_max = std::max<long long>(bsb_max, (long long)bt::slot32(q) * wbytes);
+  const long long bsb64_max = rup((long long)h->maxn * h->maxn, 2) * 8;
+  // one chunk of one row: 3 + 2 halo blocks for H, 5 + 4 for H_ab, 3 float64
+  long long need = std::max((general ? 9 : (mf ? 3 : 5)) * bsb_max, 3 * bsb64_max);
+  long long sb = stage_kb > 0 ? (long long)stage_kb * 1024 : 80 * 1024;
+  sb = std::max(sb, rup(need, 128));
+  int smem_optin = 0;
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
+  const int fixed = bt_persistent_smem_fixed(h->variant);
+  int vslot = mixed ? 9 * 1024 : 18 * 1024;  // one vector-ring slot (largest chunk plan)
+  int cps = h->prm.ctas_per_sm > 0 ? h->prm.ctas_per_sm : 1;
+  const int per_cta = (int)std::min<long long>(smem_optin, (228 * 1024) / cps - 1024);
+  const int vslots = (h->variant) == 1 ? 3 : 4;  // vector ring slots of the kernel variant
+  int S = (int)((per_cta - fixed - vslots * vslot) / sb);
+  if (S < 2) {  // large blocks: keep two block stages, stage vectors directly
+    vslot = 0;
+    S = (int)((per_cta - fixed) / sb);
+  }
+  h->vec_slot_bytes = vslot;
+  if (S > bt::kMaxStages) S = bt::kMaxStages;
+  if (S < 2) return BT_ERR_ARG;  // block too large for the shared-memory pipeline
+  h->stages = S;
+  h->stage_bytes = (int)sb;
+  h->smem = fixed + vslots * vslot + S * (int)sb;
+  int occ = 0;
+  if (cuda_st(bt_persistent_occupancy(mixed ? 1 : 0, h->variant, h->smem, &occ)) != BT_OK || occ < 1)
+    return BT_ERR_CUDA;
+  cps = std::min(cps, occ);
+  if (h->batched) {
+    h->G = 1;
+    h->grid = std::min(h->sms * cps, std::max(1, B));
+    if (h->ws_cap > 0) h->grid = std::min(h->grid, h->ws_cap);
+    h->ws_slots = h->grid;
+  } else {
+    int G = group_ctas;
+    if (G <= 0) {
+      // 4 block rows per CTA; one CTA up to N = 32, where the cross-CTA
+      // reductions (3 per iteration) cost more than the rows they split
+      // (LL^T N = 16, n = 6: 21.6 us per iteration on 1 CTA, 37.7 on 4)
+      const int rows_per = 4;
+      G = h->N[0] <= 32 ? 1 : std::max(1, std::min(h->sms * cps, h->N[0] / rows_per));
+    }
+    G = std::min(G, h->sms * std::min(occ, 2));
+    G = std::min(G, h->N[0]);
+    h->G = std::max(1, G);
+    h->grid = h->G;
+    h->ws_slots = 1;
+  }
+  return BT_OK;
+}
+
 // Common setup for one or many instances.
 bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
   cudaStream_t st = h->stream;
@@ -344,61 +407,14 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
   if (launch_setup_kernels(h, D, O) != BT_OK) return BT_ERR_CUDA;
 
   // ---- launch configuration of the persistent kernel ----
-  const int wbytes = mixed ? 4 : 8;
-  long long bsb_max = rup((long long)h->maxn * h->maxn, 2) * wbytes;
-  if (mixed)
-    for (int q = 1; q <= h->maxn; ++q) bsb_max = std::max<long long>(bsb_max, (long long)bt::slot32(q) * wbytes);
-  const long long bsb64_max = rup((long long)h->maxn * h->maxn, 2) * 8;
-  // one chunk of one row: 3 + 2 halo blocks for H, 5 + 4 for H_ab, 3 float64
-  long long need = std::max((general ? 9 : (mf ? 3 : 5)) * bsb_max, 3 * bsb64_max);
-  long long sb = h->prm.stage_kb > 0 ? (long long)h->prm.stage_kb * 1024 : 80 * 1024;
-  sb = std::max(sb, rup(need, 128));
-  int smem_optin = 0;
-  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
-  const int fixed = bt_persistent_smem_fixed(h->variant);
-  int vslot = mixed ? 9 * 1024 : 18 * 1024;  // one vector-ring slot (largest chunk plan)
-  int cps = h->prm.ctas_per_sm > 0 ? h->prm.ctas_per_sm : 1;
-  const int per_cta = (int)std::min<long long>(smem_optin, (228 * 1024) / cps - 1024);
-  const int vslots = (h->variant) == 1 ? 3 : 4;  // vector ring slots of the kernel variant
-  int S = (int)((per_cta - fixed - vslots * vslot) / sb);
-  if (S < 2) {  // large blocks: keep two block stages, stage vectors directly
-    vslot = 0;
-    S = (int)((per_cta - fixed) / sb);
-  }
-  h->vec_slot_bytes = vslot;
-  if (S > bt::kMaxStages) S = bt::kMaxStages;
-  if (S < 2) return BT_ERR_ARG;  // block too large for the shared-memory pipeline
-  h->stages = S;
-  h->stage_bytes = (int)sb;
-  h->smem = fixed + vslots * vslot + S * (int)sb;
-  int occ = 0;
-  if (cuda_st(bt_persistent_occupancy(mixed ? 1 : 0, h->variant, h->smem, &occ)) != BT_OK || occ < 1)
-    return BT_ERR_CUDA;
-  cps = std::min(cps, occ);
-  if (h->batched) {
-    h->G = 1;
-    h->grid = std::min(h->sms * cps, std::max(1, B));
-    h->ws_slots = h->grid;
-  } else {
-    int G = h->prm.group_ctas;
-    if (G <= 0) {
-      // 4 block rows per CTA; one CTA up to N = 32, where the cross-CTA
-      // reductions (3 per iteration) cost more than the rows they split
-      // (LL^T N = 16, n = 6: 21.6 us per iteration on 1 CTA, 37.7 on 4)
-      const int rows_per = 4;
-      G = h->N[0] <= 32 ? 1 : std::max(1, std::min(h->sms * cps, h->N[0] / rows_per));
-    }
-    G = std::min(G, h->sms * occ);
-    G = std::min(G, h->N[0]);
-    h->G = std::max(1, G);
-    h->grid = h->G;
-    h->ws_slots = 1;
-  }
+  if ((s = configure(h, h->prm.stage_kb, h->prm.group_ctas)) != BT_OK) return s;
   h->ws_vec = rup(std::max<long long>(h->maxNn, 1), 64);
   const int mts = mixed ? 4 : 8;
   h->ws_stride = rup(10 * h->ws_vec * mts + h->ws_vec * 8, 256);
   if ((s = dalloc(h, &h->d_ws, (size_t)h->ws_stride * h->ws_slots)) != BT_OK) return s;
-  if ((s = dalloc(h, &h->d_red, (size_t)2 * std::max(1, h->G) * 4)) != BT_OK) return s;
+  h->ws_cap = h->ws_slots;
+  // group reduction slots for the largest group a later bt_autotune may choose
+  if ((s = dalloc(h, &h->d_red, (size_t)2 * std::max(std::max(1, h->G), h->sms * 2) * 4)) != BT_OK) return s;
   cudaMemsetAsync(h->d_ws, 0, (size_t)h->ws_stride * h->ws_slots, st);
 
   // ---- setup status ----
@@ -502,6 +518,73 @@ bt_status collect(bt_ctx* h, int* iters, int* status_out, bool all) {
 }  // namespace
 
 extern "C" {
+
+bt_status bt_autotune(bt_handle h, const double* b, double* x, double tol, int maxit, int trials, int* stage_kb,
+                      int* group_ctas) {
+  if (!h || !b || !x || trials < 1 || !(tol >= 0.0) || maxit < 0) return BT_ERR_ARG;
+  cudaStream_t st = h->stream;
+  // candidates: stage sizes for batched handles, CTAs per instance otherwise
+  std::vector<std::pair<int, int>> cand;
+  if (h->batched) {
+    for (int kb : {64, 72, 80}) cand.push_back({kb, 0});
+  } else {
+    const int N = h->N[0];
+    std::vector<int> gs = {1, N / 16, N / 8, N / 4, N / 2};
+    for (int g : gs)
+      if (g >= 1 && g <= N) {
+        bool dup = false;
+        for (auto& c : cand) dup = dup || c.second == g;
+        if (!dup) cand.push_back({h->prm.stage_kb, g});
+      }
+  }
+  if (h->graph) cudaGraphExecDestroy(h->graph);  // a captured graph holds the old shape
+  if (h->graph_src) cudaGraphDestroy(h->graph_src);
+  h->graph = nullptr;
+  h->graph_src = nullptr;
+  const int use_x0 = h->prm.use_x0;  // every timed solve starts from x = 0
+  h->prm.use_x0 = 0;
+  struct Restore {
+    bt_ctx* h;
+    int v;
+    ~Restore() { h->prm.use_x0 = v; }
+  } restore{h, use_x0};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return BT_ERR_CUDA;
+  const auto solve = [&]() -> bt_status {
+    return h->batched ? bt_pcg_solve_batched_async(h, b, x, tol, maxit, nullptr, nullptr)
+                      : bt_pcg_solve_async(h, b, x, tol, maxit, nullptr, nullptr);
+  };
+  float best_ms = 0.f;
+  int best = -1;
+  bt_status out = BT_OK;
+  for (size_t i = 0; i < cand.size() && out == BT_OK; ++i) {
+    if (configure(h, cand[i].first, cand[i].second) != BT_OK) continue;  // shape does not fit: skip
+    if ((out = solve()) != BT_OK) break;                                  // untimed
+    cudaEventRecord(e0, st);
+    for (int t = 0; t < trials && out == BT_OK; ++t) out = solve();
+    cudaEventRecord(e1, st);
+    if (out != BT_OK || cudaEventSynchronize(e1) != cudaSuccess) { out = out != BT_OK ? out : BT_ERR_CUDA; break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (best < 0 || ms < best_ms) { best_ms = ms; best = (int)i; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best < 0) {
+    configure(h, h->prm.stage_kb, h->prm.group_ctas);
+    return out != BT_OK ? out : BT_ERR_ARG;
+  }
+  const bt_status cs = configure(h, cand[best].first, cand[best].second);
+  if (cs != BT_OK) return cs;
+  h->prm.stage_kb = cand[best].first;
+  h->prm.group_ctas = h->batched ? 0 : h->G;
+  if (stage_kb) *stage_kb = h->stage_bytes / 1024;
+  if (group_ctas) *group_ctas = h->G;
+  if (out != BT_OK) return out;
+  // leave x with a solve in the chosen shape
+  if ((out = solve()) != BT_OK) return out;
+  return cudaStreamSynchronize(st) == cudaSuccess ? BT_OK : BT_ERR_CUDA;
+}
 
 bt_status bt_estimate_rho(bt_handle h, int iters, double* rho) {
   if (!h || !rho || iters < 1) return BT_ERR_ARG;

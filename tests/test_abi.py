@@ -73,6 +73,7 @@ def test_bad_arguments_rejected_without_a_gpu(built):
     p.alpha = ctypes.cast(neg, ctypes.POINTER(ctypes.c_double))
     assert lib.bt_setup(4, 4, ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.byref(p), ctypes.byref(h)) == bb.BT_ERR_PARAM
     assert lib.bt_pcg_solve(None, None, None, 1e-8, 10, None) == bb.BT_ERR_ARG
+    assert lib.bt_autotune(None, None, None, 1e-8, 10, 1, None, None) == bb.BT_ERR_ARG
     # LQR formation: sizes are checked on the host before any CUDA call
     one = (ctypes.c_int * 1)(4)
     big = (ctypes.c_int * 1)(49)
