@@ -282,7 +282,11 @@ bt_status bt_alpha_chebyshev(int m, double rho, double* alpha);
  * solves (CUDA events on the handle's stream) and the fastest stays
  * configured for later calls (a captured CUDA graph is dropped).  x (DEVICE)
  * holds a solve in the chosen shape on return; *stage_kb and *group_ctas
- * (may be NULL) report the shape.  Synchronises the stream.  Not for the
+ * (may be NULL) report the shape.  With the environment variable
+ * BT_TUNE_CACHE naming a file, a shape recorded there for the same handle
+ * layout (batched or not, variant, precision, m, instance count and sizes,
+ * SM count) is configured without timing, and a newly timed one is appended
+ * (one JSON object per line).  Synchronises the stream.  Not for the
  * many-RHS engine, which has its own shape. */
 bt_status bt_autotune(bt_handle h, const double* b, double* x, double tol, int maxit, int trials, int* stage_kb,
                       int* group_ctas);

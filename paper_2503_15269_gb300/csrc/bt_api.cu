@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <numeric>
+#include <string>
 #include <vector>
 
 #include "../../include/bt.h"
@@ -519,10 +520,53 @@ bt_status collect(bt_ctx* h, int* iters, int* status_out, bool all) {
 
 extern "C" {
 
+// Key of a handle's shape in the tuning cache (BT_TUNE_CACHE).
+static std::string tune_key(const bt_ctx* h) {
+  long long sumN = 0;
+  for (int v : h->N) sumN += v;
+  char buf[256];
+  std::snprintf(buf, sizeof(buf), "%s-v%d-p%d-m%d-B%d-N%lld-maxN%d-maxn%d-sms%d", h->batched ? "batched" : "single",
+                h->variant, h->mixed, h->prm.m, h->B, sumN, h->maxN, h->maxn, h->sms);
+  return buf;
+}
+
 bt_status bt_autotune(bt_handle h, const double* b, double* x, double tol, int maxit, int trials, int* stage_kb,
                       int* group_ctas) {
   if (!h || !b || !x || trials < 1 || !(tol >= 0.0) || maxit < 0) return BT_ERR_ARG;
   cudaStream_t st = h->stream;
+  // tuning cache: one JSON object per line, {"key": "...", "stage_kb": K, "group_ctas": G}
+  const char* cache = std::getenv("BT_TUNE_CACHE");
+  const std::string key = tune_key(h);
+  if (cache && *cache) {
+    if (FILE* f = std::fopen(cache, "r")) {
+      char line[512];
+      int hit_kb = -1, hit_g = -1;
+      while (std::fgets(line, sizeof(line), f)) {
+        char k[300];
+        int kb = 0, g = 0;
+        if (std::sscanf(line, " {\"key\": \"%299[^\"]\", \"stage_kb\": %d, \"group_ctas\": %d", k, &kb, &g) == 3 &&
+            key == k) {
+          hit_kb = kb;
+          hit_g = g;
+        }
+      }
+      std::fclose(f);
+      if (hit_kb >= 0 && configure(h, hit_kb, h->batched ? 0 : hit_g) == BT_OK) {
+        if (h->graph) cudaGraphExecDestroy(h->graph);
+        if (h->graph_src) cudaGraphDestroy(h->graph_src);
+        h->graph = nullptr;
+        h->graph_src = nullptr;
+        h->prm.stage_kb = hit_kb;
+        h->prm.group_ctas = h->batched ? 0 : h->G;
+        if (stage_kb) *stage_kb = h->stage_bytes / 1024;
+        if (group_ctas) *group_ctas = h->G;
+        const bt_status o = h->batched ? bt_pcg_solve_batched_async(h, b, x, tol, maxit, nullptr, nullptr)
+                                       : bt_pcg_solve_async(h, b, x, tol, maxit, nullptr, nullptr);
+        if (o != BT_OK) return o;
+        return cudaStreamSynchronize(st) == cudaSuccess ? BT_OK : BT_ERR_CUDA;
+      }
+    }
+  }
   // candidates: stage sizes for batched handles, CTAs per instance otherwise
   std::vector<std::pair<int, int>> cand;
   if (h->batched) {
@@ -578,6 +622,13 @@ bt_status bt_autotune(bt_handle h, const double* b, double* x, double tol, int m
   if (cs != BT_OK) return cs;
   h->prm.stage_kb = cand[best].first;
   h->prm.group_ctas = h->batched ? 0 : h->G;
+  if (cache && *cache) {
+    if (FILE* f = std::fopen(cache, "a")) {
+      std::fprintf(f, "{\"key\": \"%s\", \"stage_kb\": %d, \"group_ctas\": %d}\n", key.c_str(),
+                   h->prm.stage_kb, h->prm.group_ctas);
+      std::fclose(f);
+    }
+  }
   if (stage_kb) *stage_kb = h->stage_bytes / 1024;
   if (group_ctas) *group_ctas = h->G;
   if (out != BT_OK) return out;

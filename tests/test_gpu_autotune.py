@@ -64,3 +64,23 @@ def test_single_autotune_keeps_parity(precision):
     else:
         assert rel(xs, orc.direct_solve(inst.D, inst.O, inst.b)) <= 1e-8
     assert rel(host(x).reshape(inst.b.shape), ref.x) <= 1e-8
+
+
+def test_tune_cache_records_and_reuses_the_shape(tmp_path, monkeypatch):
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("BT_TUNE_CACHE", str(cache))
+    inst = wl.small_ocp(140, 96, 12)
+    db = dev(inst.b.reshape(-1))
+    shapes = []
+    for _ in range(2):
+        with Single(inst, m=2, alpha=[1.0, 7.0], precision=bb.BT_MIXED) as s:
+            s.ok()
+            x = dev(np.zeros(inst.b.size))
+            st, kb, g = bb.bt_autotune(s.h, db, x, 1e-8, 5000, 1)
+            assert st == bb.BT_OK
+            shapes.append((kb, g))
+            res = np.linalg.norm(orc.spmv(inst.D, inst.O, host(x).reshape(inst.b.shape)) - inst.b)
+            assert res <= 1e-8 * np.linalg.norm(inst.b)
+    lines = cache.read_text().strip().splitlines()
+    assert len(lines) == 1 and '"key": "single-' in lines[0]   # timed once, reused once
+    assert shapes[0] == shapes[1]
