@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/bt.h"
 #include "bt_alpha.h"
 #include "bt_common.cuh"
@@ -129,6 +131,14 @@ __global__ void k_rho_step(const InstDesc* inst, double* v, const double* u, dou
 namespace {
 
 inline bt_status cuda_st(cudaError_t e) { return e == cudaSuccess ? BT_OK : BT_ERR_CUDA; }
+
+// NVTX range over an entry point (host-side span of the call; the kernels it
+// queues show up inside it on a profiler's timeline).  Header-only NVTX: no
+// cost unless a tool is attached.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 template <typename T>
 bt_status dalloc(bt_ctx* h, T** p, size_t count) {
@@ -532,6 +542,7 @@ static std::string tune_key(const bt_ctx* h) {
 
 bt_status bt_autotune(bt_handle h, const double* b, double* x, double tol, int maxit, int trials, int* stage_kb,
                       int* group_ctas) {
+  Range nvtx_range("bt_autotune");
   if (!h || !b || !x || trials < 1 || !(tol >= 0.0) || maxit < 0) return BT_ERR_ARG;
   cudaStream_t st = h->stream;
   // tuning cache: one JSON object per line, {"key": "...", "stage_kb": K, "group_ctas": G}
@@ -638,6 +649,7 @@ bt_status bt_autotune(bt_handle h, const double* b, double* x, double tol, int m
 }
 
 bt_status bt_estimate_rho(bt_handle h, int iters, double* rho) {
+  Range nvtx_range("bt_estimate_rho");
   if (!h || !rho || iters < 1) return BT_ERR_ARG;
   if (h->variant == 1 || h->prm.a != 1.0) return BT_ERR_PARAM;  // H_opt = I - G_opt S holds at a = 1
   cudaStream_t st = h->stream;
@@ -710,6 +722,7 @@ const char* bt_status_string(bt_status s) {
 }
 
 bt_status bt_setup(int N, int n, const double* D, const double* O, const bt_params* params, bt_handle* out) {
+  Range nvtx_range("bt_setup");
   if (!out) return BT_ERR_ARG;
   *out = nullptr;
   if (N < 1 || n < 1 || n > BT_MAX_BLOCK || !D || (N > 1 && !O)) return BT_ERR_ARG;
@@ -736,6 +749,7 @@ bt_status bt_setup(int N, int n, const double* D, const double* O, const bt_para
 
 bt_status bt_setup_batched(int B, const int* N, const int* n, const long long* d_off, const long long* o_off,
                            const double* D, const double* O, const bt_params* params, bt_handle* out) {
+  Range nvtx_range("bt_setup_batched");
   if (!out) return BT_ERR_ARG;
   *out = nullptr;
   if (B < 1 || !N || !n || !d_off || !o_off || !D) return BT_ERR_ARG;
@@ -767,6 +781,7 @@ bt_status bt_setup_batched(int B, const int* N, const int* n, const long long* d
 }
 
 bt_status bt_refactor(bt_handle h, const double* D, const double* O) {
+  Range nvtx_range("bt_refactor");
   if (!h || !D || (h->maxN > 1 && !O)) return BT_ERR_ARG;
   return launch_setup_kernels(h, D, O);
 }
@@ -777,6 +792,7 @@ bt_status bt_setup_status(bt_handle h) {
 }
 
 bt_status bt_apply_precond(bt_handle h, const double* r, double* z) {
+  Range nvtx_range("bt_apply_precond");
   if (!h || !r || !z) return BT_ERR_ARG;
   bt_status s = run_op(h, bt::kOpApply, r, z);
   if (s != BT_OK) return s;
@@ -810,6 +826,7 @@ static bt_status solve_launch(bt_handle h, const double* b, double* x, double to
 }
 
 bt_status bt_pcg_solve(bt_handle h, const double* b, double* x, double tol, int maxit, int* iters) {
+  Range nvtx_range("bt_pcg_solve");
   if (!h || !b || !x) return BT_ERR_ARG;
   if (h->batched) return BT_ERR_STATE;
   bt_status s = solve_launch(h, b, x, tol, maxit);
@@ -822,6 +839,7 @@ bt_status bt_pcg_solve(bt_handle h, const double* b, double* x, double tol, int 
 
 bt_status bt_pcg_solve_async(bt_handle h, const double* b, double* x, double tol, int maxit, int* d_iters,
                              int* d_status) {
+  Range nvtx_range("bt_pcg_solve_async");
   if (!h || !b || !x) return BT_ERR_ARG;
   if (h->batched) return BT_ERR_STATE;
   bt_status s = solve_launch(h, b, x, tol, maxit);
@@ -835,6 +853,7 @@ bt_status bt_pcg_solve_async(bt_handle h, const double* b, double* x, double tol
 
 bt_status bt_pcg_solve_batched(bt_handle h, const double* b, double* x, const long long* vec_off, double tol,
                                int maxit, int* iters, int* status) {
+  Range nvtx_range("bt_pcg_solve_batched");
   if (!h || !b || !x) return BT_ERR_ARG;
   if (!h->batched) return BT_ERR_STATE;
   if (vec_off) {
@@ -860,6 +879,7 @@ bt_status bt_pcg_solve_batched(bt_handle h, const double* b, double* x, const lo
 
 bt_status bt_pcg_solve_batched_async(bt_handle h, const double* b, double* x, double tol, int maxit,
                                      int* d_iters, int* d_status) {
+  Range nvtx_range("bt_pcg_solve_batched_async");
   if (!h || !b || !x) return BT_ERR_ARG;
   if (!h->batched) return BT_ERR_STATE;
   bt_status s = solve_launch(h, b, x, tol, maxit);
@@ -875,6 +895,7 @@ bt_status bt_pcg_solve_batched_async(bt_handle h, const double* b, double* x, do
 
 bt_status bt_graph_capture_batched(bt_handle h, const double* b, double* x, double tol, int maxit, int* d_iters,
                                    int* d_status) {
+  Range nvtx_range("bt_graph_capture_batched");
   if (!h) return BT_ERR_ARG;
   if (!h->batched) return BT_ERR_STATE;
   if (!h->stream) return BT_ERR_ARG;  // the legacy default stream cannot be captured
@@ -913,6 +934,7 @@ bt_status bt_solve_info(bt_handle h, int k, int* outer, double* rel_residual) {
 }
 
 bt_status bt_adjoint_blocks(bt_handle h, const double* x, const double* g, double* gD, double* gO) {
+  Range nvtx_range("bt_adjoint_blocks");
   if (!h || !x || !g || !gD) return BT_ERR_ARG;
   if (!gO && h->maxN > 1) return BT_ERR_ARG;
   bt::AdjParams a{};
@@ -930,6 +952,7 @@ bt_status bt_adjoint_blocks(bt_handle h, const double* x, const double* g, doubl
 
 bt_status bt_pcg_solve_multi(bt_handle h, const double* B, double* X, int nrhs, double tol, int maxit, int* iters,
                              int* status) {
+  Range nvtx_range("bt_pcg_solve_multi");
   if (!h || !B || !X) return BT_ERR_ARG;
   if (h->batched) return BT_ERR_STATE;
   if (!h->mixed) return BT_ERR_STATE;
