@@ -305,6 +305,26 @@ bt_status bt_autotune(bt_handle h, const double* b, double* x, double tol, int m
  * on the handle's stream, then synchronises.  BT_ERR_PARAM for a < 1. */
 bt_status bt_estimate_rho(bt_handle h, int iters, double* rho);
 
+/* bt_set_history -- per-iteration history of later solves on h: hist (DEVICE,
+ * [instances][len][3] doubles, owned by the caller, which keeps it alive)
+ * receives for PCG iteration k < len of instance i: the relative residual
+ * ||r_k|| / ||rhs|| of the PCG run it belongs to (for BT_MIXED the float32
+ * inner solve of its refinement step), alpha_k and beta_k (the CG scalars;
+ * with them the Lanczos tridiagonal of M^-1 S).  Iterations of successive
+ * refinement steps follow one another.  len = 0 turns it off. */
+bt_status bt_set_history(bt_handle h, double* hist, int len);
+
+/* bt_ritz_rho -- the bound for bt_alpha_chebyshev from Ritz values (the
+ * paper's future work names a spectral estimate): `iters` iterations of PCG
+ * on S x = b with M^-1 = G_opt (m = 1, whose M^-1 S = I - H_opt, Sec. 3.5),
+ * then per instance rho[k] = 1 - lambda_min(T), T the Lanczos tridiagonal
+ * of the CG scalars, its smallest eigenvalue by Sturm bisection on the host.
+ * Converges much faster than bt_estimate_rho (extreme Ritz values); for
+ * BT_MIXED the scalars come from float32 iterations.  b (DEVICE, packed as
+ * for the solves) should excite the whole spectrum (random entries do).
+ * a = 1 handles; synchronises. */
+bt_status bt_ritz_rho(bt_handle h, const double* b, int iters, double* rho);
+
 /* bt_lqr_schur -- form the systems S lam = gamma of B LQR problems on the
  * device: the construction of the test matrices of Sec. 5 (an LQR problem as
  * an equality-constrained QP, its KKT system, the Schur complement with

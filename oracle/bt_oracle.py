@@ -493,3 +493,21 @@ def power_rho(D: np.ndarray, O: np.ndarray, iters: int) -> float:
         nh = float(np.linalg.norm(h))
         v = h / nh
     return nh
+
+
+def ritz_rho(D: np.ndarray, O: np.ndarray, b: np.ndarray, iters: int) -> float:
+    """rho(H_opt) estimated from Ritz values: `iters` iterations of textbook
+    PCG with M^-1 = G_opt (m = 1, where M^-1 S = I - H_opt, Sec. 3.5); the
+    CG scalars give the Lanczos tridiagonal T of the preconditioned operator
+    (T_00 = 1/a_0, T_jj = 1/a_j + b_{j-1}/a_{j-1}, T_j,j-1 = sqrt(b_{j-1})/a_{j-1});
+    returns 1 - lambda_min(T)."""
+    B = opt_blocks(D, O)
+    res = pcg(D, O, b, lambda r: apply_G_opt(B, r), 0.0, iters)
+    a, be = res.alphas, res.betas
+    K = min(len(a), len(be) + 1)
+    T = np.zeros((K, K))
+    for j in range(K):
+        T[j, j] = 1.0 / a[j] + (be[j - 1] / a[j - 1] if j > 0 else 0.0)
+        if j > 0:
+            T[j, j - 1] = T[j - 1, j] = np.sqrt(be[j - 1]) / a[j - 1]
+    return 1.0 - float(np.linalg.eigvalsh(T).min())

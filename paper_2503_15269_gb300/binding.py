@@ -85,6 +85,8 @@ def lib() -> C.CDLL:
         "bt_params_check": (C.c_int, [C.POINTER(bt_params)]),
         "bt_estimate_rho": (C.c_int, [H, C.c_int, C.POINTER(C.c_double)]),
         "bt_autotune": (C.c_int, [H, dp, dp, C.c_double, C.c_int, C.c_int, ip, ip]),
+        "bt_set_history": (C.c_int, [H, dp, C.c_int]),
+        "bt_ritz_rho": (C.c_int, [H, dp, C.c_int, C.POINTER(C.c_double)]),
         "bt_alpha_chebyshev": (C.c_int, [C.c_int, C.c_double, C.POINTER(C.c_double)]),
         "bt_lqr_schur": (C.c_int, [C.c_int, ip, ip, ip, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, vp, ip, ip]),
         "bt_lqr_recover": (C.c_int, [C.c_int, ip, ip, ip, dp, dp, dp, dp, dp, dp, dp, dp, dp, vp]),
@@ -268,6 +270,17 @@ def bt_autotune(h, b, x, tol: float, maxit: int, trials: int = 2):
     kb, g = C.c_int(0), C.c_int(0)
     st = lib().bt_autotune(h, _ptr(b), _ptr(x), float(tol), int(maxit), int(trials), C.byref(kb), C.byref(g))
     return st, kb.value, g.value
+
+
+def bt_set_history(h, hist, length: int) -> int:
+    return lib().bt_set_history(h, _ptr(hist) if hist is not None else C.c_void_p(0), int(length))
+
+
+def bt_ritz_rho(h, b, iters: int, count: int):
+    """Returns (status, rho per instance)."""
+    r = (C.c_double * max(1, count))()
+    st = lib().bt_ritz_rho(h, _ptr(b), int(iters), r)
+    return st, list(r[:count])
 
 
 def bt_estimate_rho(h, iters: int, count: int):

@@ -62,6 +62,8 @@ struct bt_ctx {
   double *F64 = nullptr, *K64 = nullptr;
   float *F32 = nullptr, *K32 = nullptr;
   int variant = 0;  // persistent kernel: 0 stored H_opt, 1 general member, 2 matrix-free H_opt
+  double* hist = nullptr;  // caller's per-iteration history buffer (bt_set_history), or null
+  int hist_len = 0;
   bt::InstDesc* d_inst = nullptr;
   bt::RowRef* d_rows = nullptr;
   int* d_order = nullptr;
@@ -450,6 +452,8 @@ bt::KParams base_kparams(bt_ctx* h) {
   P.Hd32 = h->Hd32; P.Hu32 = h->Hu32; P.Hl32 = h->Hl32;
   P.F64 = h->F64; P.K64 = h->K64; P.F32 = h->F32; P.K32 = h->K32;
   P.variant = h->variant;
+  P.hist = h->hist;
+  P.hist_len = h->hist_len;
   P.inst = h->d_inst;
   P.order = h->d_order;
   P.B = h->B;
@@ -646,6 +650,101 @@ bt_status bt_autotune(bt_handle h, const double* b, double* x, double tol, int m
   // leave x with a solve in the chosen shape
   if ((out = solve()) != BT_OK) return out;
   return cudaStreamSynchronize(st) == cudaSuccess ? BT_OK : BT_ERR_CUDA;
+}
+
+bt_status bt_set_history(bt_handle h, double* hist, int len) {
+  if (!h || len < 0 || (len > 0 && !hist)) return BT_ERR_ARG;
+  h->hist = len > 0 ? hist : nullptr;
+  h->hist_len = len;
+  return BT_OK;
+}
+
+// Smallest eigenvalue of the symmetric tridiagonal (d, e) by bisection on its
+// Sturm count (the number of eigenvalues below x is the number of negative
+// pivots of T - x I).
+static double tridiag_min_eig(const std::vector<double>& d, const std::vector<double>& e) {
+  const int K = (int)d.size();
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < K; ++i) {  // Gershgorin bounds
+    const double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < K ? std::fabs(e[i]) : 0.0);
+    lo = std::min(lo, d[i] - r);
+    hi = std::max(hi, d[i] + r);
+  }
+  const auto below = [&](double x) {
+    int cnt = 0;
+    double q = 1.0;
+    for (int i = 0; i < K; ++i) {
+      q = d[i] - x - (i > 0 ? e[i - 1] * e[i - 1] / q : 0.0);
+      if (q == 0.0) q = -1e-300;
+      if (q < 0.0) ++cnt;
+    }
+    return cnt;
+  };
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(1.0, std::fabs(hi)); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (below(mid) >= 1) hi = mid;
+    else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+bt_status bt_ritz_rho(bt_handle h, const double* b, int iters, double* rho) {
+  Range nvtx_range("bt_ritz_rho");
+  if (!h || !b || !rho || iters < 2) return BT_ERR_ARG;
+  if (h->variant == 1 || h->prm.a != 1.0) return BT_ERR_PARAM;  // M^-1 S = I - H_opt at m = 1 needs a = 1
+  cudaStream_t st = h->stream;
+  const size_t len = (size_t)std::max<long long>(h->total_vec, 1);
+  const size_t hl = (size_t)h->B * iters * 3;
+  char* buf = nullptr;
+  if (cudaMallocAsync((void**)&buf, (len + hl) * sizeof(double), st) != cudaSuccess) return BT_ERR_ALLOC;
+  double* x = reinterpret_cast<double*>(buf);
+  double* hist = x + len;
+  std::vector<double> hh(hl, 0.0);
+  bt_status out = BT_OK;
+  if (cudaMemsetAsync(hist, 0, hl * sizeof(double), st) != cudaSuccess) out = BT_ERR_CUDA;
+  if (out == BT_OK) {
+    // `iters` iterations of PCG with M^-1 = G_opt (m = 1) from x = 0: one inner
+    // solve for mixed handles, run to its iteration cap
+    bt::KParams P = base_kparams(h);
+    P.op = bt::kOpSolve;
+    P.m = 1;
+    P.bvec = b;
+    P.xvec = x;
+    P.tol = 0.0;
+    P.tol_inner = 1e-300;
+    P.maxit = iters;
+    P.max_outer = 1;
+    P.use_x0 = 0;
+    P.hist = hist;
+    P.hist_len = iters;
+    out = launch(h, P);
+  }
+  if (out == BT_OK && (cudaMemcpyAsync(hh.data(), hist, hl * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                       cudaStreamSynchronize(st) != cudaSuccess))
+    out = BT_ERR_CUDA;
+  cudaFreeAsync(buf, st);
+  if (out != BT_OK) return out;
+  for (int k = 0; k < h->B; ++k) {
+    // Lanczos tridiagonal of the preconditioned operator from the CG scalars:
+    // T_00 = 1/alpha_0, T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1},
+    // T_j,j-1 = sqrt(beta_{j-1})/alpha_{j-1}
+    std::vector<double> d, e;
+    const double* hk = hh.data() + (size_t)k * iters * 3;
+    for (int j = 0; j < iters; ++j) {
+      const double a = hk[3 * j + 1];
+      if (!(a > 0.0) || !std::isfinite(a)) break;
+      if (j == 0) {
+        d.push_back(1.0 / a);
+      } else {
+        const double ap = hk[3 * (j - 1) + 1], bp = hk[3 * (j - 1) + 2];
+        if (!(bp >= 0.0)) break;
+        d.push_back(1.0 / a + bp / ap);
+        e.push_back(std::sqrt(bp) / ap);
+      }
+    }
+    rho[k] = d.empty() ? 0.0 : 1.0 - tridiag_min_eig(d, e);
+  }
+  return BT_OK;
 }
 
 bt_status bt_estimate_rho(bt_handle h, int iters, double* rho) {

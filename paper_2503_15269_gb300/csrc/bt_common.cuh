@@ -50,6 +50,8 @@ struct KParams {
   // F_i = -(1-a) D_i^-1 O_i and K_i = -(1-a) D_{i+1}^-1 O_i^T (slot i, i < N-1)
   const double *F64, *K64;
   const float *F32, *K32;
+  double* hist;            // optional [B][hist_len][3]: per PCG iteration k the relative
+  int hist_len;            // residual of its inner solve, alpha_k and beta_k (null = off)
   int variant;             // kernel: 0 optimum (stored H_opt), 1 general member
                            // (five-array H_ab), 2 optimum with the matrix-free H_opt
   const InstDesc* inst;

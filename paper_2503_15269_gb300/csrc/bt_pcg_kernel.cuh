@@ -1572,8 +1572,15 @@ __device__ void solve_instance(Solver<MT, VAR>& Sv, int inst_id) {
     // ------------------------------ SOLVE ------------------------------
     // Inner PCG on S d = rhs (rhs from src64 * scale or b - S x0), textbook
     // form; returns iterations, sets status, leaves the solution in xvec.
+    // optional history: iteration it_base + k - 1 of this instance gets the
+    // relative residual of this inner solve, alpha_k and beta_k (Lanczos
+    // coefficients of the preconditioned operator)
+    double* const hist = (P.hist && tid == 0 && Sv.g == 0) ? P.hist + (size_t)inst_id * P.hist_len * 3 : nullptr;
+    auto record = [&](int idx, int field, double v) {
+      if (hist && idx >= 0 && idx < P.hist_len) hist[(size_t)idx * 3 + field] = v;
+    };
     auto inner_pcg = [&](const double* src64, double scale, MT* xv, bool from_x0, double tol_rel,
-                         int maxit, int& it_out, int& st_out, double& rr_out) {
+                         int maxit, int& it_out, int& st_out, double& rr_out, int it_base) {
       it_out = 0;
       st_out = kOK;
       // initial residual and z0 = M^-1 r0
@@ -1639,6 +1646,8 @@ __device__ void solve_instance(Solver<MT, VAR>& Sv, int inst_id) {
         if (!isfinite(pq)) { st_out = kErrNonfinite; it_out = k - 1; return; }
         if (!(pq > 0.0)) { st_out = kErrBreakdown; it_out = k - 1; errv = pq; return; }
         const double alpha = sdiv(rho, pq);
+        record(it_base + k - 1, 1, alpha);
+        record(it_base + k - 1, 2, 0.0);
         // B1: r -= alpha q, x += alpha p, y0 = G r
         Sweep<MT> sb = {};
         sb.kind = kKB1; sb.stg = SV_R_UPD; sb.fin = FN_Y0; sb.sgn = MT(-1);
@@ -1652,6 +1661,7 @@ __device__ void solve_instance(Solver<MT, VAR>& Sv, int inst_id) {
         rr = acc[2];
         rr_out = rr;
         it_out = k;
+        record(it_base + k - 1, 0, sqrt(rr) / nrhs);
         if (!isfinite(rr)) { st_out = kErrNonfinite; return; }
         if (rr <= thr2) return;
         if (m > 1) {
@@ -1660,6 +1670,7 @@ __device__ void solve_instance(Solver<MT, VAR>& Sv, int inst_id) {
         }
         const double rz_new = acc[1];
         beta = sdiv(rz_new, rho);
+        record(it_base + k - 1, 2, beta);
         rho = rz_new;
       }
     };
@@ -1669,7 +1680,7 @@ __device__ void solve_instance(Solver<MT, VAR>& Sv, int inst_id) {
       int it, st;
       double rr;
       MT* xv = reinterpret_cast<MT*>(xu);
-      inner_pcg(bu, 1.0, xv, P.use_x0 != 0, P.tol, P.maxit, it, st, rr);
+      inner_pcg(bu, 1.0, xv, P.use_x0 != 0, P.tol, P.maxit, it, st, rr, 0);
       iters_total = it;
       Sv.status = st;
       double t[4] = {Sv.vpass_norm2(bu), 0, 0, 0};
@@ -1719,7 +1730,8 @@ __device__ void solve_instance(Solver<MT, VAR>& Sv, int inst_id) {
           if (t_in > 0.5) t_in = 0.5;
           int it, ist;
           double rr;
-          inner_pcg(have_r64 ? r64 : bu, 1.0 / nr, x_in, false, t_in, P.maxit - iters_total, it, ist, rr);
+          inner_pcg(have_r64 ? r64 : bu, 1.0 / nr, x_in, false, t_in, P.maxit - iters_total, it, ist, rr,
+                    iters_total);
           iters_total += it;
           if (ist == kErrBreakdown || ist == kErrNonfinite || ist == kErrTimeout) { st = ist; break; }
           // x += nr * d over the owned rows, then make it visible to the group

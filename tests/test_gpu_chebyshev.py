@@ -103,3 +103,43 @@ def test_estimate_rho_matrix_free_handle():
         s.ok()
         st, rho = bb.bt_estimate_rho(s.h, 60, 1)
     assert st == bb.BT_OK and abs(rho[0] - ref) <= 1e-9 * ref
+
+
+@pytest.mark.parametrize("precision,tol", [(bb.BT_FP64, 1e-8), (bb.BT_MIXED, 1e-4)])
+def test_ritz_rho_matches_oracle(precision, tol):
+    """bt_ritz_rho per instance of a batched handle against the oracle's
+    Ritz estimate from the same right-hand side and iteration count."""
+    insts = [wl.small_ocp(630 + k, N, n) for k, (N, n) in enumerate([(16, 6), (30, 20), (33, 12)])]
+    Ns, ns, d_off, o_off, v_off, D, O, b = wl.pack_batch(insts)
+    p, keep = bb.make_params(m=2, alpha=[1.0, 7.0], precision=precision)
+    st, h = bb.bt_setup_batched(Ns, ns, d_off, o_off, dev(D), dev(O), p)
+    assert st == bb.BT_OK
+    try:
+        st, rho = bb.bt_ritz_rho(h, dev(b), 40, len(insts))
+    finally:
+        bb.bt_destroy(h)
+    assert st == bb.BT_OK
+    for k, inst in enumerate(insts):
+        ref = orc.ritz_rho(inst.D, inst.O, inst.b, 40)
+        assert abs(rho[k] - ref) <= tol, (k, rho[k], ref)
+
+
+def test_history_records_the_oracle_iterates():
+    """bt_set_history: relative residuals and CG scalars of a float64 solve
+    equal those of the oracle's PCG, iteration by iteration."""
+    inst = wl.config1()
+    ref = orc.pcg_opt(inst.D, inst.O, inst.b, [1.0, 7.0], 1e-10, 2000)
+    L = 64
+    hist = dev(np.full(L * 3, -1.0))
+    with Single(inst, m=2, alpha=[1.0, 7.0]) as s:
+        s.ok()
+        assert bb.bt_set_history(s.h, hist, L) == bb.BT_OK
+        st, it, x = s.solve(inst.b, 1e-10, 2000)
+    assert st == bb.BT_OK
+    hh = host(hist).reshape(L, 3)
+    K = min(it, L)
+    nb = np.linalg.norm(inst.b)
+    np.testing.assert_allclose(hh[:K, 0], np.array(ref.res_history[1:K + 1]) / nb, rtol=1e-8)
+    np.testing.assert_allclose(hh[:K, 1], np.array(ref.alphas[:K]), rtol=1e-8)
+    np.testing.assert_allclose(hh[:K - 1, 2], np.array(ref.betas[:K - 1]), rtol=1e-8)
+    assert (hh[K:, 0] == -1.0).all()

@@ -93,3 +93,19 @@ def test_power_rho_approaches_the_dense_spectral_radius():
     est = [orc.power_rho(inst.D, inst.O, k) for k in (50, 400)]
     assert abs(rho - est[1]) < abs(rho - est[0])
     assert abs(rho - est[1]) < 1e-4
+
+
+def test_ritz_rho_converges_faster_than_power_iteration():
+    """Ritz values from 60 PCG iterations against the dense spectral radius:
+    closer than 400 power-iteration steps (1e-15 vs 5e-6 on this case)."""
+    inst = wl.small_ocp(500, 16, 6)
+    B = orc.opt_blocks(inst.D, inst.O)
+    N, n = 16, 6
+    eye = np.eye(N * n)
+    H = np.column_stack([orc.apply_H_opt(B, eye[:, k].reshape(N, n)).reshape(-1) for k in range(N * n)])
+    rho = np.abs(np.linalg.eigvals(H)).max()
+    b = np.random.default_rng(3).standard_normal((N, n))
+    est = orc.ritz_rho(inst.D, inst.O, b, 60)
+    assert abs(est - rho) < 1e-8
+    assert abs(orc.ritz_rho(inst.D, inst.O, b, 40) - rho) < abs(orc.ritz_rho(inst.D, inst.O, b, 20) - rho)
+    assert abs(est - rho) < abs(orc.power_rho(inst.D, inst.O, 400) - rho)
