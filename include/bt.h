@@ -185,7 +185,8 @@ bt_status bt_solve_info(bt_handle h, int k, int* outer, double* rel_residual);
  * inner solves inside float64 refinement on each column's true residual, as
  * in bt_pcg_solve.  B, X: DEVICE [N*n][nrhs] float64, row-major.  iters and
  * status (HOST arrays of nrhs, may be NULL) receive per-column results; the
- * call returns the first non-OK status.  Requires n % 4 == 0.  The first call
+ * call returns the first non-OK status.  Requires n % 4 == 0 and n <= 64
+ * (else BT_ERR_ARG).  The first call
  * allocates the many-RHS workspace on the handle.  Synchronises the stream. */
 bt_status bt_pcg_solve_multi(bt_handle h, const double* B, double* X, int nrhs, double tol,
                              int maxit, int* iters, int* status);

@@ -1058,7 +1058,7 @@ bt_status bt_pcg_solve_multi(bt_handle h, const double* B, double* X, int nrhs, 
   if (h->variant != 0) return BT_ERR_PARAM;  // the many-RHS engine: the optimum with stored H only
   if (nrhs < 1 || nrhs > 64 || !(tol >= 0.0) || maxit < 0) return BT_ERR_ARG;
   const int N = h->N[0], n = h->n[0];
-  if (n % 4 != 0) return BT_ERR_ARG;
+  if (n % 4 != 0 || n > 64) return BT_ERR_ARG;  // 16 row groups of 4 at most (BT_MAX_BLOCK)
   const int kJ = 64;
   if (!h->mr_vec[0]) {
     const size_t cnt = (size_t)N * n * kJ;

@@ -17,7 +17,10 @@
 // Each row job stages its three blocks and three vector blocks in shared
 // memory with cp.async (double-buffered: the next row loads while the current
 // one computes); the block products are register-tiled, 4 rows x 4 columns of
-// the output per thread.
+// the output per thread.  In the float32 sweeps two thread halves take the
+// two halves of the k range of every product (12 warps busy for n = 48, three
+// per scheduler), and one half adds the other's partial tile through shared
+// memory before the finalize.
 #include <cstdint>
 
 #include "../../include/bt.h"
@@ -26,7 +29,10 @@
 namespace bt {
 
 constexpr int kJ = 64;              // right-hand-side columns per solve
-constexpr int kMThreads = 256;
+constexpr int kMThreads = 384;
+constexpr int kMHalf = 192;         // output tiles one thread half covers (n <= 48 split in k)
+constexpr int kMaxNMulti = 64;      // n <= 64: 16 row groups of 4 at most
+constexpr int kVB = 2;              // float4s a thread loads before storing in the vector passes
 
 struct MParams {
   const float *D32, *O32, *Dinv32, *E32, *Hd32, *Hu32, *Hl32;  // library layout (column-major, padded)
@@ -83,12 +89,13 @@ __device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
   v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
 }
 
-// acc[r][c] += sum_k M(a0+r, k) X(k, j0+c): M column-major n x n, X n x J.
+// acc[r][c] += sum_{k0 <= k < k1} M(a0+r, k) X(k, j0+c): M column-major n x n,
+// X n x J.
 template <typename T>
 __device__ __forceinline__ void prod_direct(const T* __restrict__ M, const T* __restrict__ X, int n, int a0, int j0,
-                                            T acc[4][4]) {
+                                            T acc[4][4], int k0, int k1) {
 #pragma unroll 4
-  for (int k = 0; k < n; ++k) {
+  for (int k = k0; k < k1; ++k) {
     T mv[4], xv[4];
     ld4(M + k * n + a0, mv);
     ld4(X + k * kJ + j0, xv);
@@ -99,11 +106,12 @@ __device__ __forceinline__ void prod_direct(const T* __restrict__ M, const T* __
   }
 }
 
-// acc[r][c] += sum_k M(k, a0+r) X(k, j0+c): the transposed block (n % 4 == 0).
+// acc[r][c] += sum_{k0 <= k < k1} M(k, a0+r) X(k, j0+c): the transposed block
+// (n, k0, k1 multiples of 4).
 template <typename T>
 __device__ __forceinline__ void prod_trans(const T* __restrict__ M, const T* __restrict__ X, int n, int a0, int j0,
-                                           T acc[4][4]) {
-  for (int k = 0; k < n; k += 4) {
+                                           T acc[4][4], int k0, int k1) {
+  for (int k = k0; k < k1; k += 4) {
     T mr[4][4], xr[4][4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) ld4(M + (a0 + r) * n + k, mr[r]);   // M(k..k+3, a0+r)
@@ -163,15 +171,17 @@ struct MSolver {
     // column with independent L2 loads (the barrier above acquired them),
     // then the quarters are added in a fixed order (bitwise reproducible).
     {
-      static_assert(kMThreads == 4 * kJ, "four threads per column");
+      static_assert(kMThreads >= 4 * kJ, "four threads per column");
       double* part = colred;  // [4][kJ] doubles of the CTA's scratch
       const int q = threadIdx.x / kJ, j = threadIdx.x % kJ;
-      const int g0 = q * G / 4, g1 = (q + 1) * G / 4;
-      const double* src = P.red + (size_t)par * G * kJ + j;
-      double t = 0.0;
+      if (q < 4) {
+        const int g0 = q * G / 4, g1 = (q + 1) * G / 4;
+        const double* src = P.red + (size_t)par * G * kJ + j;
+        double t = 0.0;
 #pragma unroll 8
-      for (int gg = g0; gg < g1; ++gg) t += __ldcg(src + (size_t)gg * kJ);
-      part[q * kJ + j] = t;
+        for (int gg = g0; gg < g1; ++gg) t += __ldcg(src + (size_t)gg * kJ);
+        part[q * kJ + j] = t;
+      }
       __syncthreads();
       if (threadIdx.x < kJ) colv[j] = ((part[j] + part[kJ + j]) + part[2 * kJ + j]) + part[3 * kJ + j];
     }
@@ -194,7 +204,7 @@ __device__ __forceinline__ void widen(const Accum<float> (&a)[4], double (&d)[4]
 
 // Reduce per-thread column partials part[jg][4] (threads laid out t = ag*16 + jg)
 // into colv[kJ] over the CTA, fixed order.
-__device__ __forceinline__ void cta_col_reduce(const double (&pv)[4], double* scratch /* [kMThreads/16][kJ] */,
+__device__ __forceinline__ void cta_col_reduce(const double (&pv)[4], double* scratch /* [ngroups][kJ] */,
                                                double* colv, int ngroups) {
   const int t = threadIdx.x;
   const int jg = t & 15, ag = t >> 4;
@@ -223,7 +233,8 @@ constexpr int kColBytes = kJ * 8;
 constexpr int kMSmScalars = 256;
 constexpr int kMNumCols = 13;  // 12 double columns + float alpha/beta copies
 constexpr int kMSmScratch = kMSmScalars + kMNumCols * kColBytes;
-constexpr int kMSmJobs = kMSmScratch + 16 * kJ * 8;
+constexpr int kMSmXch = kMSmScratch + (kMThreads / 16) * kJ * 8;  // float4 [4][kMHalf]
+constexpr int kMSmJobs = kMSmXch + 4 * kMHalf * 16;
 
 __host__ __device__ constexpr int mrhs_job_bytes(int n) {
   // float32 job: 3 blocks + 3 vector blocks; float64 job: same in doubles
@@ -238,19 +249,31 @@ enum MPhase : int { MP_A = 0, MP_B1 = 1, MP_B2 = 2, MP_A64 = 3 };
 // ring of 2k+2 rows in shared memory, each loaded once per sweep (one row
 // ahead, with the blocks of the next job), instead of three copies per row in
 // every job; the ring occupies the room of the second job's vector rows.
+//
+// Thread t covers output tile u (row group u / 16, column group u % 16) over
+// the k range of its half: for n <= 48 the 4n tiles fit one half of the CTA
+// and the second half takes k in [kh, n); for larger n one pass covers all
+// tiles and k.  The partial tiles of the second half go through `xch`.
 template <typename Fin, typename Blk>
 __device__ void msweep_ring(MSolver& Sv, int phase, const float* v_in, Fin fin, Blk blk) {
   const int n = Sv.n, N = Sv.N;
   const int tid = threadIdx.x;
   const int ngroups = n / 4;
-  const int jg = tid & 15, ag = tid >> 4;
-  const bool active = ag < ngroups;
+  const int ntile = ngroups * 16;
+  const bool split = ntile <= kMHalf;
+  const int half = split ? tid / kMHalf : 0;
+  const int u = split ? tid - half * kMHalf : tid;
+  const int jg = u & 15, ag = u >> 4;
+  const bool active = u < ntile;
   const int a0 = 4 * ag, j0 = 4 * jg;
+  const int kh = split ? 4 * ((ngroups + 1) / 2) : n;
+  const int k0 = half ? kh : 0, k1 = half ? n : kh;
   const int bb = n * n, vb = n * kJ;
   const int k = (phase == MP_B2) ? 2 : 1;
   const int kv = 2 * k + 2;
   float* blocks = reinterpret_cast<float*>(Sv.sm + kMSmJobs);  // [2][3 bb]
   float* ring = blocks + 6 * bb;                               // [kv][vb]
+  float4* xch = reinterpret_cast<float4*>(Sv.sm + kMSmXch);    // [4][kMHalf] partial tiles
   const auto slot = [&](int r) { return ring + (size_t)(((r % kv) + kv) % kv) * vb; };
   const auto issue_blocks = [&](int row, int buf) {
     float* m = blocks + (size_t)buf * 3 * bb;
@@ -282,11 +305,11 @@ __device__ void msweep_ring(MSolver& Sv, int phase, const float* v_in, Fin fin, 
     float acc[4][4] = {};
     float acc2[4][4] = {};
     if (active) {
-      prod_direct(m0, xc, n, a0, j0, acc);
-      if (row + k < N) prod_direct(m1, slot(row + k), n, a0, j0, acc2);
+      prod_direct(m0, xc, n, a0, j0, acc, k0, k1);
+      if (row + k < N) prod_direct(m1, slot(row + k), n, a0, j0, acc2, k0, k1);
       if (row - k >= 0) {
-        if (phase == MP_B2) prod_direct(m2, slot(row - k), n, a0, j0, acc2);
-        else prod_trans(m2, slot(row - k), n, a0, j0, acc2);
+        if (phase == MP_B2) prod_direct(m2, slot(row - k), n, a0, j0, acc2, k0, k1);
+        else prod_trans(m2, slot(row - k), n, a0, j0, acc2, k0, k1);
       }
     }
     const float sg = (phase == MP_B1) ? -1.f : 1.f;
@@ -295,9 +318,24 @@ __device__ void msweep_ring(MSolver& Sv, int phase, const float* v_in, Fin fin, 
     for (int r = 0; r < 4; ++r)
 #pragma unroll
       for (int c = 0; c < 4; ++c) out[r][c] = acc[r][c] + sg * acc2[r][c];
-    if (active) fin(row, a0, j0, out, xc);
+    if (split && half == 1 && active)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) xch[r * kMHalf + u] = make_float4(out[r][0], out[r][1], out[r][2], out[r][3]);
+    // After this barrier every product of the row is done: the next row's
+    // copies (into the other block buffer and the ring slot of row - k) may
+    // start while the finalize still reads this row's ring slot.
     __syncthreads();
+    if (half == 0 && active) {
+      if (split)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const float4 q = xch[r * kMHalf + u];
+          out[r][0] += q.x; out[r][1] += q.y; out[r][2] += q.z; out[r][3] += q.w;
+        }
+      fin(row, a0, j0, out, xc);
+    }
   }
+  __syncthreads();
 }
 
 // One sweep over the owned rows of float32 (T = float) or the float64
@@ -383,11 +421,11 @@ __device__ void msweep(MSolver& Sv, int phase, const T* v_in, Fin fin) {
     T acc[4][4] = {};
     T acc2[4][4] = {};  // off-diagonal terms (sign -1 for G)
     if (active) {
-      prod_direct(m0, xc, n, a0, j0, acc);
-      if (row + k < N) prod_direct(m1, xr, n, a0, j0, acc2);
+      prod_direct(m0, xc, n, a0, j0, acc, 0, n);
+      if (row + k < N) prod_direct(m1, xr, n, a0, j0, acc2, 0, n);
       if (row - k >= 0) {
-        if (phase == MP_B2) prod_direct(m2, xl, n, a0, j0, acc2);   // Hl_{i-2} Y_{i-2}
-        else prod_trans(m2, xl, n, a0, j0, acc2);                    // O_{i-1}^T / E_{i-1}^T
+        if (phase == MP_B2) prod_direct(m2, xl, n, a0, j0, acc2, 0, n);   // Hl_{i-2} Y_{i-2}
+        else prod_trans(m2, xl, n, a0, j0, acc2, 0, n);                    // O_{i-1}^T / E_{i-1}^T
       }
     }
     const T sg = (phase == MP_B1) ? T(-1) : T(1);
@@ -544,12 +582,14 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
         float* yout = (jp % 2 == 1) ? P.Ya : P.Yb;
         const float aj = P.alpha[jp];
         const bool lastj = (jp == m - 1);
-        msweep<float>(Sv, MP_B2, yin, [&](int row, int a0, int j0, float (&o)[4][4], const float*) {
+        msweep<float>(Sv, MP_B2, yin, [&](int row, int a0, int j0, float (&o)[4][4], const float* yc) {
           for (int r = 0; r < 4; ++r) {
             const size_t idx = (size_t)row * vb + (size_t)(a0 + r) * J + j0;
             const float4 y = make_float4(o[r][0], o[r][1], o[r][2], o[r][3]);
             if (!lastj) stv4(yout, idx, y);
-            const float4 zp = ldv4((jp == 1) ? P.Y0 : P.Z, idx);
+            // z so far: y0 (this sweep's staged input row) after the first
+            // application of H, else the running sum in Z
+            const float4 zp = (jp == 1) ? *reinterpret_cast<const float4*>(yc + (a0 + r) * J + j0) : ldv4(P.Z, idx);
             const float4 z = make_float4(fmaf(aj, y.x, zp.x), fmaf(aj, y.y, zp.y), fmaf(aj, y.z, zp.z),
                                          fmaf(aj, y.w, zp.w));
             stv4(P.Z, idx, z);
@@ -617,29 +657,43 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
         if (actv[tid] > 0.0) itc[tid] += 1.0;
       }
       __syncthreads();
-      // x += alpha p, r -= alpha q, rr per column
+      // x += alpha p, r -= alpha q, rr per column: the owned rows are one
+      // contiguous range of float4s; thread t takes every kMThreads-th (so
+      // always column group t % 16) and loads a batch of kVB before storing.
       {
         Accum<float> pa[4];
-        const int jg = tid & 15, ag = tid >> 4;
-        const float4 al = *reinterpret_cast<const float4*>(alpf + 4 * jg);
-        if (ag < ngroups)
-          for (int row = Sv.s; row < Sv.e; ++row)
-            for (int r = 0; r < 4; ++r) {
-              const size_t idx = (size_t)row * vb + (size_t)(4 * ag + r) * J + 4 * jg;
-              const float4 pp = ldv4(P.P, idx), qq = ldv4(P.Q, idx), xx = ldv4(P.Xin, idx), rr = ldv4(P.R, idx);
-              stv4(P.Xin, idx, make_float4(fmaf(al.x, pp.x, xx.x), fmaf(al.y, pp.y, xx.y), fmaf(al.z, pp.z, xx.z),
-                                           fmaf(al.w, pp.w, xx.w)));
-              const float4 rv = make_float4(fmaf(-al.x, qq.x, rr.x), fmaf(-al.y, qq.y, rr.y), fmaf(-al.z, qq.z, rr.z),
-                                            fmaf(-al.w, qq.w, rr.w));
-              stv4(P.R, idx, rv);
+        const float4 al = *reinterpret_cast<const float4*>(alpf + 4 * (tid & 15));
+        const float4* Pp = reinterpret_cast<const float4*>(P.P);
+        const float4* Qp = reinterpret_cast<const float4*>(P.Q);
+        float4* Xp = reinterpret_cast<float4*>(P.Xin);
+        float4* Rp = reinterpret_cast<float4*>(P.R);
+        const size_t f1 = (size_t)Sv.e * vb / 4;
+        for (size_t f = (size_t)Sv.s * vb / 4 + tid; f < f1; f += (size_t)kVB * kMThreads) {
+          float4 pp[kVB], qq[kVB], xx[kVB], rr[kVB];
+#pragma unroll
+          for (int b = 0; b < kVB; ++b) {
+            const size_t g = f + (size_t)b * kMThreads;
+            if (g < f1) { pp[b] = Pp[g]; qq[b] = Qp[g]; xx[b] = Xp[g]; rr[b] = Rp[g]; }
+          }
+#pragma unroll
+          for (int b = 0; b < kVB; ++b) {
+            const size_t g = f + (size_t)b * kMThreads;
+            if (g < f1) {
+              Xp[g] = make_float4(fmaf(al.x, pp[b].x, xx[b].x), fmaf(al.y, pp[b].y, xx[b].y),
+                                  fmaf(al.z, pp[b].z, xx[b].z), fmaf(al.w, pp[b].w, xx[b].w));
+              const float4 rv = make_float4(fmaf(-al.x, qq[b].x, rr[b].x), fmaf(-al.y, qq[b].y, rr[b].y),
+                                            fmaf(-al.z, qq[b].z, rr[b].z), fmaf(-al.w, qq[b].w, rr[b].w));
+              Rp[g] = rv;
               pa[0].add(rv.x * rv.x);
               pa[1].add(rv.y * rv.y);
               pa[2].add(rv.z * rv.z);
               pa[3].add(rv.w * rv.w);
             }
+          }
+        }
         double pr[4];
         widen(pa, pr);
-        cta_col_reduce(pr, scratch, colR, ngroups);
+        cta_col_reduce(pr, scratch, colR, kMThreads / 16);
         Sv.grid_reduce(colR);
         if (tid < J) {
           rrv[tid] = colR[tid];
@@ -658,18 +712,27 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
         betf[tid] = (float)b;
       }
       __syncthreads();
-      // p = z + beta p
+      // p = z + beta p, with the access pattern of the x, r update
       {
-        const int jg = tid & 15, ag = tid >> 4;
-        if (ag < ngroups)
-          for (int row = Sv.s; row < Sv.e; ++row)
-            for (int r = 0; r < 4; ++r) {
-              const size_t idx = (size_t)row * vb + (size_t)(4 * ag + r) * J + 4 * jg;
-              const float4 be = *reinterpret_cast<const float4*>(betf + 4 * jg);
-              const float4 pp = ldv4(P.P, idx), zz = ldv4(P.Z, idx);
-              stv4(P.P, idx, make_float4(fmaf(be.x, pp.x, zz.x), fmaf(be.y, pp.y, zz.y), fmaf(be.z, pp.z, zz.z),
-                                         fmaf(be.w, pp.w, zz.w)));
-            }
+        const float4 be = *reinterpret_cast<const float4*>(betf + 4 * (tid & 15));
+        float4* Pp = reinterpret_cast<float4*>(P.P);
+        const float4* Zp = reinterpret_cast<const float4*>(P.Z);
+        const size_t f1 = (size_t)Sv.e * vb / 4;
+        for (size_t f = (size_t)Sv.s * vb / 4 + tid; f < f1; f += (size_t)kVB * kMThreads) {
+          float4 pp[kVB], zz[kVB];
+#pragma unroll
+          for (int b = 0; b < kVB; ++b) {
+            const size_t g = f + (size_t)b * kMThreads;
+            if (g < f1) { pp[b] = Pp[g]; zz[b] = Zp[g]; }
+          }
+#pragma unroll
+          for (int b = 0; b < kVB; ++b) {
+            const size_t g = f + (size_t)b * kMThreads;
+            if (g < f1)
+              Pp[g] = make_float4(fmaf(be.x, pp[b].x, zz[b].x), fmaf(be.y, pp[b].y, zz[b].y),
+                                  fmaf(be.z, pp[b].z, zz[b].z), fmaf(be.w, pp[b].w, zz[b].w));
+          }
+        }
         Sv.barrier();
       }
     }

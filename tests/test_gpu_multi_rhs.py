@@ -34,7 +34,10 @@ def solve_multi(inst, nrhs, tol, maxit=20000, m=2, alpha=(1.0, 7.0)):
     return st, its, sts, host(X).reshape(inst.N, inst.n, nrhs), infos
 
 
-@pytest.mark.parametrize("N,n,nrhs", [(1, 4, 3), (2, 4, 64), (7, 8, 5), (33, 12, 64), (20, 16, 17)])
+# n <= 48: the k range of each product split over two thread halves (n = 4:
+# one half empty; n = 44: an odd number of row groups); n = 52, 64: one pass
+@pytest.mark.parametrize("N,n,nrhs", [(1, 4, 3), (2, 4, 64), (7, 8, 5), (33, 12, 64), (20, 16, 17), (9, 44, 64),
+                                      (5, 52, 7), (6, 64, 64)])
 def test_multi_rhs_matches_direct_solves(N, n, nrhs):
     inst = wl.small_llt(60, N, n, nrhs=nrhs)
     st, its, sts, X, infos = solve_multi(inst, nrhs, 1e-12)
@@ -78,3 +81,4 @@ def test_config3_many_rhs_full_size():
     for j in range(2):
         err = np.linalg.norm(X[:, :, j] - xr[:, :, j]) / np.linalg.norm(xr[:, :, j])
         assert err <= 1e-3, (j, err)
+
