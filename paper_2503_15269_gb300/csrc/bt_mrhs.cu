@@ -32,6 +32,7 @@ constexpr int kJ = 64;              // right-hand-side columns per solve
 constexpr int kMThreads = 384;
 constexpr int kMHalf = 192;         // output tiles one thread half covers (n <= 48 split in k)
 constexpr int kMaxNMulti = 64;      // n <= 64: 16 row groups of 4 at most
+static_assert(kMaxNMulti / 4 * 16 <= kMThreads, "one pass covers every output tile of the largest block");
 constexpr int kVB = 2;              // float4s a thread loads before storing in the vector passes
 
 struct MParams {
@@ -89,9 +90,9 @@ __device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
   v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
 }
 
-// acc[r][c] += sum_{k0 <= k < k1} M(a0+r, k) X(k, j0+c): M column-major n x n,
-// X n x J.
-template <typename T>
+// acc[r][c] (+/-)= sum_{k0 <= k < k1} M(a0+r, k) X(k, j0+c): M column-major
+// n x n, X n x J; NEG subtracts (the negation folds into the FMA).
+template <bool NEG = false, typename T>
 __device__ __forceinline__ void prod_direct(const T* __restrict__ M, const T* __restrict__ X, int n, int a0, int j0,
                                             T acc[4][4], int k0, int k1) {
 #pragma unroll 4
@@ -102,13 +103,13 @@ __device__ __forceinline__ void prod_direct(const T* __restrict__ M, const T* __
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[r][c] = fma(mv[r], xv[c], acc[r][c]);
+      for (int c = 0; c < 4; ++c) acc[r][c] = fma(NEG ? -mv[r] : mv[r], xv[c], acc[r][c]);
   }
 }
 
-// acc[r][c] += sum_{k0 <= k < k1} M(k, a0+r) X(k, j0+c): the transposed block
-// (n, k0, k1 multiples of 4).
-template <typename T>
+// acc[r][c] (+/-)= sum_{k0 <= k < k1} M(k, a0+r) X(k, j0+c): the transposed
+// block (n, k0, k1 multiples of 4).
+template <bool NEG = false, typename T>
 __device__ __forceinline__ void prod_trans(const T* __restrict__ M, const T* __restrict__ X, int n, int a0, int j0,
                                            T acc[4][4], int k0, int k1) {
   for (int k = k0; k < k1; k += 4) {
@@ -122,7 +123,7 @@ __device__ __forceinline__ void prod_trans(const T* __restrict__ M, const T* __r
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = fma(mr[r][q], xr[q][c], acc[r][c]);
+        for (int c = 0; c < 4; ++c) acc[r][c] = fma(NEG ? -mr[r][q] : mr[r][q], xr[q][c], acc[r][c]);
   }
 }
 
@@ -254,8 +255,12 @@ enum MPhase : int { MP_A = 0, MP_B1 = 1, MP_B2 = 2, MP_A64 = 3 };
 // the k range of its half: for n <= 48 the 4n tiles fit one half of the CTA
 // and the second half takes k in [kh, n); for larger n one pass covers all
 // tiles and k.  The partial tiles of the second half go through `xch`.
+// `pre` (may be null): a float32 vector whose tile of the row the finalize
+// needs (passed to it as pf, row r of the tile at pf[r * pstride]).  For n <= 48 each thread
+// copies its tile into shared memory with cp.async before the products, so
+// the load overlaps them; larger blocks leave no room and load it directly.
 template <typename Fin, typename Blk>
-__device__ void msweep_ring(MSolver& Sv, int phase, const float* v_in, Fin fin, Blk blk) {
+__device__ void msweep_ring(MSolver& Sv, int phase, const float* v_in, const float* pre, Fin fin, Blk blk) {
   const int n = Sv.n, N = Sv.N;
   const int tid = threadIdx.x;
   const int ngroups = n / 4;
@@ -274,6 +279,7 @@ __device__ void msweep_ring(MSolver& Sv, int phase, const float* v_in, Fin fin, 
   float* blocks = reinterpret_cast<float*>(Sv.sm + kMSmJobs);  // [2][3 bb]
   float* ring = blocks + 6 * bb;                               // [kv][vb]
   float4* xch = reinterpret_cast<float4*>(Sv.sm + kMSmXch);    // [4][kMHalf] partial tiles
+  float4* pstage = reinterpret_cast<float4*>(Sv.sm + kMSmJobs + mrhs_job_bytes(n));  // [4][kMHalf], n <= 48
   const auto slot = [&](int r) { return ring + (size_t)(((r % kv) + kv) % kv) * vb; };
   const auto issue_blocks = [&](int row, int buf) {
     float* m = blocks + (size_t)buf * 3 * bb;
@@ -302,22 +308,27 @@ __device__ void msweep_ring(MSolver& Sv, int phase, const float* v_in, Fin fin, 
     const float* m1 = m0 + bb;
     const float* m2 = m0 + 2 * bb;
     const float* xc = slot(row);
-    float acc[4][4] = {};
-    float acc2[4][4] = {};
+    if (pre && split) {
+      if (half == 0 && active)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) cp16(pstage + r * kMHalf + u, pre + (size_t)row * vb + (size_t)(a0 + r) * kJ + j0);
+      cp_commit();
+    }
+    // one accumulator: G's off-diagonal blocks enter with a minus sign
+    float out[4][4] = {};
     if (active) {
-      prod_direct(m0, xc, n, a0, j0, acc, k0, k1);
-      if (row + k < N) prod_direct(m1, slot(row + k), n, a0, j0, acc2, k0, k1);
-      if (row - k >= 0) {
-        if (phase == MP_B2) prod_direct(m2, slot(row - k), n, a0, j0, acc2, k0, k1);
-        else prod_trans(m2, slot(row - k), n, a0, j0, acc2, k0, k1);
+      prod_direct(m0, xc, n, a0, j0, out, k0, k1);
+      if (phase == MP_B1) {
+        if (row + k < N) prod_direct<true>(m1, slot(row + k), n, a0, j0, out, k0, k1);
+        if (row - k >= 0) prod_trans<true>(m2, slot(row - k), n, a0, j0, out, k0, k1);
+      } else {
+        if (row + k < N) prod_direct(m1, slot(row + k), n, a0, j0, out, k0, k1);
+        if (row - k >= 0) {
+          if (phase == MP_B2) prod_direct(m2, slot(row - k), n, a0, j0, out, k0, k1);
+          else prod_trans(m2, slot(row - k), n, a0, j0, out, k0, k1);
+        }
       }
     }
-    const float sg = (phase == MP_B1) ? -1.f : 1.f;
-    float out[4][4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) out[r][c] = acc[r][c] + sg * acc2[r][c];
     if (split && half == 1 && active)
 #pragma unroll
       for (int r = 0; r < 4; ++r) xch[r * kMHalf + u] = make_float4(out[r][0], out[r][1], out[r][2], out[r][3]);
@@ -332,17 +343,46 @@ __device__ void msweep_ring(MSolver& Sv, int phase, const float* v_in, Fin fin, 
           const float4 q = xch[r * kMHalf + u];
           out[r][0] += q.x; out[r][1] += q.y; out[r][2] += q.z; out[r][3] += q.w;
         }
-      fin(row, a0, j0, out, xc);
+      // the tile of `pre`: row r of it at pf[r * pstride]
+      const float4* pf = nullptr;
+      int pstride = 0;
+      if (pre) {
+        if (split) {
+          cp_wait<0>();  // this thread's own tile (and the next row's copies, already under way)
+          pf = pstage + u;
+          pstride = kMHalf;
+        } else {
+          pf = reinterpret_cast<const float4*>(pre + (size_t)row * vb + (size_t)a0 * kJ + j0);
+          pstride = kJ / 4;
+        }
+      }
+      fin(row, a0, j0, out, xc, pf, pstride);
     }
   }
   __syncthreads();
 }
 
-// One sweep over the owned rows of float32 (T = float) or the float64
-// refinement residual (T = double).  The finalize functor receives the 4x4
-// tile (rows a0.., columns j0..) of row i.
+// One float32 sweep (A, B1 or B2) over the owned rows, through the ring.
+template <typename Fin>
+__device__ void msweep32(MSolver& Sv, int phase, const float* v_in, const float* pre, Fin fin) {
+  const MParams& P = Sv.P;
+  if (Sv.e <= Sv.s) return;
+  auto blk = [&](int which, int row) -> const float* {
+    // which: 0 = first (D, D^-1, Hd), 1 = second (O, E, Hu), 2 = third (O, E, Hl)
+    const float* A;
+    if (phase == MP_A) A = (which == 0) ? P.D32 : P.O32;
+    else if (phase == MP_B1) A = (which == 0) ? P.Dinv32 : P.E32;
+    else A = (which == 0) ? P.Hd32 : (which == 1 ? P.Hu32 : P.Hl32);
+    return A + (size_t)row * P.bs32;
+  };
+  msweep_ring(Sv, phase, v_in, pre, fin, blk);
+}
+
+// The float64 refinement-residual sweep (T = double; `phase` MP_A64).  The
+// finalize functor receives the 4x4 tile (rows a0.., columns j0..) of row i.
 template <typename T, typename Fin>
 __device__ void msweep(MSolver& Sv, int phase, const T* v_in, Fin fin) {
+  static_assert(sizeof(T) == 8, "float32 sweeps go through msweep32");
   const MParams& P = Sv.P;
   const int n = Sv.n, N = Sv.N;
   const int tid = threadIdx.x;
@@ -391,10 +431,6 @@ __device__ void msweep(MSolver& Sv, int phase, const T* v_in, Fin fin) {
   };
   const int nrows = Sv.e - Sv.s;
   if (nrows <= 0) return;
-  if constexpr (sizeof(T) == 4) {
-    msweep_ring(Sv, phase, v_in, fin, blk);
-    return;
-  }
   if (nbuf == 2) issue(Sv.s, 0);
   for (int it = 0; it < nrows; ++it) {
     const int row = Sv.s + it;
@@ -561,7 +597,7 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
       // r.z per column, summed in the finalize of the sweep that completes z
       Accum<float> pa[4];
       // B1: y0 = G r (r is the staged centre block of this sweep)
-      msweep<float>(Sv, MP_B1, P.R, [&](int row, int a0, int j0, float (&o)[4][4], const float* xc) {
+      msweep32(Sv, MP_B1, P.R, nullptr, [&](int row, int a0, int j0, float (&o)[4][4], const float* xc, const float4*, int) {
         for (int r = 0; r < 4; ++r) {
           const size_t idx = (size_t)row * vb + (size_t)(a0 + r) * J + j0;
           const float4 y = make_float4(o[r][0], o[r][1], o[r][2], o[r][3]);
@@ -582,7 +618,8 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
         float* yout = (jp % 2 == 1) ? P.Ya : P.Yb;
         const float aj = P.alpha[jp];
         const bool lastj = (jp == m - 1);
-        msweep<float>(Sv, MP_B2, yin, [&](int row, int a0, int j0, float (&o)[4][4], const float* yc) {
+        msweep32(Sv, MP_B2, yin, lastj ? P.R : nullptr,
+                 [&](int row, int a0, int j0, float (&o)[4][4], const float* yc, const float4* rpf, int rst) {
           for (int r = 0; r < 4; ++r) {
             const size_t idx = (size_t)row * vb + (size_t)(a0 + r) * J + j0;
             const float4 y = make_float4(o[r][0], o[r][1], o[r][2], o[r][3]);
@@ -594,7 +631,7 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
                                          fmaf(aj, y.w, zp.w));
             stv4(P.Z, idx, z);
             if (lastj) {
-              const float4 rv = ldv4(P.R, idx);
+              const float4 rv = rpf[r * rst];  // r, staged during the products
               pa[0].add(rv.x * z.x);
               pa[1].add(rv.y * z.y);
               pa[2].add(rv.z * z.z);
@@ -629,7 +666,7 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
       ++total_it;
       // A: q = S p, pq per column
       Accum<float> pa[4];
-      msweep<float>(Sv, MP_A, P.P, [&](int row, int a0, int j0, float (&o)[4][4], const float* pc) {
+      msweep32(Sv, MP_A, P.P, nullptr, [&](int row, int a0, int j0, float (&o)[4][4], const float* pc, const float4*, int) {
         for (int r = 0; r < 4; ++r) {
           const size_t idx = (size_t)row * vb + (size_t)(a0 + r) * J + j0;
           stv4(P.Q, idx, make_float4(o[r][0], o[r][1], o[r][2], o[r][3]));
@@ -782,7 +819,8 @@ __global__ void k_mrhs_out(const double* X64, double* X, long long rows, int nrh
 
 }  // namespace bt
 
-extern "C" int bt_mrhs_smem_bytes(int n) { return kMSmJobs + mrhs_job_bytes(n); }
+// jobs, plus the staged finalize tiles when the k range is split (n <= 48)
+extern "C" int bt_mrhs_smem_bytes(int n) { return kMSmJobs + mrhs_job_bytes(n) + (4 * n <= kMHalf ? 4 * kMHalf * 16 : 0); }
 
 extern "C" cudaError_t bt_launch_mrhs(const bt::MParams* P, const double* B, double* X, int smem, cudaStream_t st) {
   const long long rows = (long long)P->N * P->n;
