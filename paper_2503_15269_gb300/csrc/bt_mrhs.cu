@@ -95,7 +95,7 @@ __device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
 template <bool NEG = false, typename T>
 __device__ __forceinline__ void prod_direct(const T* __restrict__ M, const T* __restrict__ X, int n, int a0, int j0,
                                             T acc[4][4], int k0, int k1) {
-#pragma unroll 4
+#pragma unroll 8
   for (int k = k0; k < k1; ++k) {
     T mv[4], xv[4];
     ld4(M + k * n + a0, mv);
