@@ -82,3 +82,19 @@ def test_config3_many_rhs_full_size():
         err = np.linalg.norm(X[:, :, j] - xr[:, :, j]) / np.linalg.norm(xr[:, :, j])
         assert err <= 1e-3, (j, err)
 
+
+
+@pytest.mark.parametrize("m,alpha", [(1, (1.0,)), (3, (1.0, 1.0, 1.0)), (3, (1.0, 2.0, 3.0))])
+@pytest.mark.parametrize("N,n", [(13, 12), (9, 48), (4, 64)])
+def test_multi_rhs_polynomial_orders(m, alpha, N, n):
+    """m = 1 (z from the G sweep alone) and m = 3 (one H sweep summing into z
+    from global memory, then the last one with r staged during the
+    products), on both product layouts (n <= 48 split in k, n = 64 not)."""
+    inst = wl.small_llt(63 + m, N, n, nrhs=9)
+    st, its, sts, X, infos = solve_multi(inst, 9, 1e-12, m=m, alpha=alpha)
+    assert st == bb.BT_OK and (sts == 0).all()
+    xr = orc.direct_solve(inst.D, inst.O, inst.b)
+    for j in range(9):
+        err = np.linalg.norm(X[:, :, j] - xr[:, :, j]) / np.linalg.norm(xr[:, :, j])
+        assert err <= 1e-8, (j, err)
+        assert infos[j][2] <= 1e-12
