@@ -244,7 +244,7 @@ __host__ __device__ constexpr int mrhs_job_bytes(int n) {
 
 namespace bt {
 
-enum MPhase : int { MP_A = 0, MP_B1 = 1, MP_B2 = 2, MP_A64 = 3 };
+enum MPhase : int { MP_A = 0, MP_B1 = 1, MP_B2 = 2 };
 
 // Float32 sweeps: the vector rows a row job reads (i-k, i, i+k) come from a
 // ring of 2k+2 rows in shared memory, each loaded once per sweep (one row
@@ -378,11 +378,13 @@ __device__ void msweep32(MSolver& Sv, int phase, const float* v_in, const float*
   msweep_ring(Sv, phase, v_in, pre, fin, blk);
 }
 
-// The float64 refinement-residual sweep (T = double; `phase` MP_A64).  The
-// finalize functor receives the 4x4 tile (rows a0.., columns j0..) of row i.
-template <typename T, typename Fin>
-__device__ void msweep(MSolver& Sv, int phase, const T* v_in, Fin fin) {
-  static_assert(sizeof(T) == 8, "float32 sweeps go through msweep32");
+// The float64 refinement-residual sweep q = S x (Eq. 1) over the owned rows:
+// one job buffer (three float64 blocks and three vector rows) fills the
+// region the float32 sweeps double-buffer, so each row's copies complete
+// before its products.  It runs once per refinement step.  The finalize
+// functor receives the 4x4 tile (rows a0.., columns j0..) of row i.
+template <typename Fin>
+__device__ void msweep64(MSolver& Sv, const double* v_in, Fin fin) {
   const MParams& P = Sv.P;
   const int n = Sv.n, N = Sv.N;
   const int tid = threadIdx.x;
@@ -391,85 +393,29 @@ __device__ void msweep(MSolver& Sv, int phase, const T* v_in, Fin fin) {
   const bool active = ag < ngroups;
   const int a0 = 4 * ag, j0 = 4 * jg;
   const int bb = n * n, vb = n * kJ;
-  char* jobs = Sv.sm + kMSmJobs;
-  const bool dbl = sizeof(T) == 8;
-  // one float64 job or two float32 jobs (double buffer) in the same region
-  const int jbytes = dbl ? mrhs_job_bytes(n) : mrhs_job_bytes(n) / 2;
-  const int nbuf = dbl ? 1 : 2;   // float64 jobs use one buffer spanning both
-  const int k = (phase == MP_B2) ? 2 : 1;
-  auto blk = [&](int which, int row) -> const T* {
-    // which: 0 = first (D, D^-1, Hd), 1 = second (O, E, Hu), 2 = third (O, E, Hl)
-    if (dbl) {
-      const double* A = (which == 0) ? P.D64 : P.O64;
-      return reinterpret_cast<const T*>(A + (size_t)row * P.bs64);
-    }
-    const float* A;
-    if (phase == MP_A) A = (which == 0) ? P.D32 : P.O32;
-    else if (phase == MP_B1) A = (which == 0) ? P.Dinv32 : P.E32;
-    else A = (which == 0) ? P.Hd32 : (which == 1 ? P.Hu32 : P.Hl32);
-    return reinterpret_cast<const T*>(A + (size_t)row * P.bs32);
-  };
-  auto issue = [&](int row, int buf) {
-    T* base = reinterpret_cast<T*>(jobs + (size_t)buf * jbytes);
-    T* m0 = base;
-    T* m1 = base + bb;
-    T* m2 = base + 2 * bb;
-    T* x0 = base + 3 * bb;   // vector rows row-k, row, row+k
-    // blocks: first(row), second(row), third(row-k) [transposed O/E or Hl]
-    auto cpb = [&](T* dst, const T* src, int cnt) {
-      if (dbl) cp_blockd(reinterpret_cast<double*>(dst), reinterpret_cast<const double*>(src), cnt);
-      else cp_block(reinterpret_cast<float*>(dst), reinterpret_cast<const float*>(src), cnt);
-    };
-    cpb(m0, blk(0, row), bb);
-    if (row + k < N) cpb(m1, blk(1, row), bb);
-    if (row - k >= 0) cpb(m2, blk(2, row - k), bb);
+  double* m0 = reinterpret_cast<double*>(Sv.sm + kMSmJobs);  // D_i
+  double* m1 = m0 + bb;                                        // O_i
+  double* m2 = m0 + 2 * bb;                                    // O_{i-1}
+  double* xl = m0 + 3 * bb;                                    // x rows i-1, i, i+1
+  double* xc = xl + vb;
+  double* xr = xc + vb;
+  for (int row = Sv.s; row < Sv.e; ++row) {
+    cp_blockd(m0, P.D64 + (size_t)row * P.bs64, bb);
+    if (row + 1 < N) cp_blockd(m1, P.O64 + (size_t)row * P.bs64, bb);
+    if (row >= 1) cp_blockd(m2, P.O64 + (size_t)(row - 1) * P.bs64, bb);
     for (int d = -1; d <= 1; ++d) {
-      const int r = row + d * k;
-      if (r >= 0 && r < N) cpb(x0 + (d + 1) * vb, v_in + (size_t)r * vb, vb);
+      const int r = row + d;
+      if (r >= 0 && r < N) cp_blockd(xl + (d + 1) * vb, v_in + (size_t)r * vb, vb);
     }
     cp_commit();
-  };
-  const int nrows = Sv.e - Sv.s;
-  if (nrows <= 0) return;
-  if (nbuf == 2) issue(Sv.s, 0);
-  for (int it = 0; it < nrows; ++it) {
-    const int row = Sv.s + it;
-    const int buf = (nbuf == 2) ? (it & 1) : 0;
-    if (nbuf == 2) {
-      if (it + 1 < nrows) {
-        issue(row + 1, (it + 1) & 1);
-        cp_wait<1>();
-      } else {
-        cp_wait<0>();
-      }
-    } else {
-      issue(row, 0);
-      cp_wait<0>();
-    }
+    cp_wait<0>();
     __syncthreads();
-    const T* base = reinterpret_cast<const T*>(jobs + (size_t)buf * jbytes);
-    const T* m0 = base;
-    const T* m1 = base + bb;
-    const T* m2 = base + 2 * bb;
-    const T* xl = base + 3 * bb;
-    const T* xc = xl + vb;
-    const T* xr = xc + vb;
-    T acc[4][4] = {};
-    T acc2[4][4] = {};  // off-diagonal terms (sign -1 for G)
+    double out[4][4] = {};
     if (active) {
-      prod_direct(m0, xc, n, a0, j0, acc, 0, n);
-      if (row + k < N) prod_direct(m1, xr, n, a0, j0, acc2, 0, n);
-      if (row - k >= 0) {
-        if (phase == MP_B2) prod_direct(m2, xl, n, a0, j0, acc2, 0, n);   // Hl_{i-2} Y_{i-2}
-        else prod_trans(m2, xl, n, a0, j0, acc2, 0, n);                    // O_{i-1}^T / E_{i-1}^T
-      }
+      prod_direct(m0, xc, n, a0, j0, out, 0, n);                // D_i x_i
+      if (row + 1 < N) prod_direct(m1, xr, n, a0, j0, out, 0, n);  // O_i x_{i+1}
+      if (row >= 1) prod_trans(m2, xl, n, a0, j0, out, 0, n);      // O_{i-1}^T x_{i-1}
     }
-    const T sg = (phase == MP_B1) ? T(-1) : T(1);
-    T out[4][4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) out[r][c] = acc[r][c] + sg * acc2[r][c];
     if (active) fin(row, a0, j0, out, xc);
     __syncthreads();
   }
@@ -543,7 +489,7 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
     // ---- refinement residual r64 = b - S x64 (float64), skipped at x = 0
     if (outer > 0) {
       double pv[4] = {0, 0, 0, 0};
-      msweep<double>(Sv, MP_A64, P.X64, [&](int row, int a0, int j0, double (&o)[4][4], const double*) {
+      msweep64(Sv, P.X64, [&](int row, int a0, int j0, double (&o)[4][4], const double*) {
         for (int r = 0; r < 4; ++r)
           for (int c = 0; c < 4; ++c) {
             const size_t idx = (size_t)row * vb + (size_t)(a0 + r) * J + j0 + c;
