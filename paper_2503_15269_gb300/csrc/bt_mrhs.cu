@@ -14,13 +14,15 @@
 // grid barriers (bounded) separate the phases.  Vectors are [N][n][J]
 // (block row i, then its n rows, then the J columns), J = 64.
 //
-// Each row job stages its three blocks and three vector blocks in shared
-// memory with cp.async (double-buffered: the next row loads while the current
-// one computes); the block products are register-tiled, 4 rows x 4 columns of
-// the output per thread.  In the float32 sweeps two thread halves take the
-// two halves of the k range of every product (12 warps busy for n = 48, three
-// per scheduler), and one half adds the other's partial tile through shared
-// memory before the finalize.
+// The float32 sweeps stage each row job's three blocks in shared memory with
+// cp.async (double-buffered: the next row's blocks load while the current
+// one computes) and keep the vector rows in a ring of 2k+2 rows, each loaded
+// once per sweep.  The block products are register-tiled, 4 rows x 4 columns
+// of the output per thread; two thread halves take the two halves of the k
+// range of every product (12 warps busy for n = 48, three per scheduler), and
+// one half adds the other's partial tile through shared memory before the
+// finalize.  The float64 residual sweep (once per refinement step) stages one
+// row job at a time.
 #include <cstdint>
 
 #include "../../include/bt.h"
