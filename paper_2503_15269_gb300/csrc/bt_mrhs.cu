@@ -114,6 +114,7 @@ __device__ __forceinline__ void prod_direct(const T* __restrict__ M, const T* __
 template <bool NEG = false, typename T>
 __device__ __forceinline__ void prod_trans(const T* __restrict__ M, const T* __restrict__ X, int n, int a0, int j0,
                                            T acc[4][4], int k0, int k1) {
+#pragma unroll 2
   for (int k = k0; k < k1; k += 4) {
     T mr[4][4], xr[4][4];
 #pragma unroll
