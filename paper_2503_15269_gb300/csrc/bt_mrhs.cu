@@ -138,7 +138,7 @@ struct MSolver {
   int bar_count;
   bool fail;
   double* colbuf;   // smem [kJ] scratch for reduced values
-  double* colred;   // smem [kMThreads/16... ] partials
+  double* colred;   // smem scratch for the cross-CTA column sums ([kMThreads / kJ][kJ])
 
   __device__ MSolver(const MParams& P_, char* sm_) : P(P_), sm(sm_) {}
 
@@ -171,23 +171,27 @@ struct MSolver {
       fail = true;
       return;
     }
-    // Totals: the 4 x 64 threads each sum a quarter of the G slots of one
+    // Totals: the kQ x 64 threads each sum a kQ-th of the G slots of one
     // column with independent L2 loads (the barrier above acquired them),
-    // then the quarters are added in a fixed order (bitwise reproducible).
+    // then the parts are added in a fixed order (bitwise reproducible).
     {
-      static_assert(kMThreads >= 4 * kJ, "four threads per column");
-      double* part = colred;  // [4][kJ] doubles of the CTA's scratch
+      constexpr int kQ = kMThreads / kJ;
+      static_assert(kMThreads == kQ * kJ, "whole groups of 64 threads");
+      double* part = colred;  // [kQ][kJ] doubles of the CTA's scratch
       const int q = threadIdx.x / kJ, j = threadIdx.x % kJ;
-      if (q < 4) {
-        const int g0 = q * G / 4, g1 = (q + 1) * G / 4;
-        const double* src = P.red + (size_t)par * G * kJ + j;
-        double t = 0.0;
+      const int g0 = q * G / kQ, g1 = (q + 1) * G / kQ;
+      const double* src = P.red + (size_t)par * G * kJ + j;
+      double t = 0.0;
 #pragma unroll 8
-        for (int gg = g0; gg < g1; ++gg) t += __ldcg(src + (size_t)gg * kJ);
-        part[q * kJ + j] = t;
-      }
+      for (int gg = g0; gg < g1; ++gg) t += __ldcg(src + (size_t)gg * kJ);
+      part[q * kJ + j] = t;
       __syncthreads();
-      if (threadIdx.x < kJ) colv[j] = ((part[j] + part[kJ + j]) + part[2 * kJ + j]) + part[3 * kJ + j];
+      if (threadIdx.x < kJ) {
+        double sum = part[j];
+#pragma unroll
+        for (int qq = 1; qq < kQ; ++qq) sum += part[qq * kJ + j];
+        colv[j] = sum;
+      }
     }
     __syncthreads();
   }
