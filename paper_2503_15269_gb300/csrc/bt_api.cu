@@ -1060,7 +1060,7 @@ bt_status bt_pcg_solve_multi(bt_handle h, const double* B, double* X, int nrhs, 
   const int N = h->N[0], n = h->n[0];
   if (n % 4 != 0 || n > 64) return BT_ERR_ARG;  // 16 row groups of 4 at most (BT_MAX_BLOCK)
   const int kJ = 64;
-  if (!h->mr_vec[0]) {
+  if (!h->mr_vec[15]) {  // the last entry: a partly allocated workspace is allocated again
     const size_t cnt = (size_t)N * n * kJ;
     bt_status s;
     double* d = nullptr;
@@ -1089,6 +1089,8 @@ bt_status bt_pcg_solve_multi(bt_handle h, const double* B, double* X, int nrhs, 
     double* res_d = nullptr;
     if ((s = dalloc(h, &res_d, kJ)) != BT_OK) return s;
     h->mr_vec[14] = res_d;
+    if ((s = dalloc(h, &f, cnt)) != BT_OK) return s;  // second p buffer
+    h->mr_vec[15] = f;
   }
   if (cudaMemsetAsync(h->mr_vec[12], 0, 64 * sizeof(int), h->stream)) return BT_ERR_CUDA;
   const float* blk32[7] = {h->D32, h->O32, h->Dinv32, h->E32, h->Hd32, h->Hu32, h->Hl32};

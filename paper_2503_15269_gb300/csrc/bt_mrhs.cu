@@ -48,6 +48,7 @@ struct MParams {
   double* R64;
   // float32 vectors [N][n][J]
   float *Xin, *R, *P, *Q, *Y0, *Ya, *Yb, *Z;
+  float* P2;            // second p buffer: the A sweep writes the new p there (n <= 48)
   double* red;          // [2][G][kJ]
   unsigned* bar;
   int* abort_flag;
@@ -253,6 +254,16 @@ namespace bt {
 
 enum MPhase : int { MP_A = 0, MP_B1 = 1, MP_B2 = 2 };
 
+// The p update p = z + beta p folded into the A sweep (z null: off).  The
+// ring stages the old p; each ring row, once its copy has landed, becomes
+// z + beta p in place (z staged beside it), and the owned rows are also
+// written to `pout`.  `beta`: the per-column float beta in shared memory.
+struct Fold {
+  const float* z;
+  float* pout;
+  const float* beta;
+};
+
 // Float32 sweeps: the vector rows a row job reads (i-k, i, i+k) come from a
 // ring of 2k+2 rows in shared memory, each loaded once per sweep (one row
 // ahead, with the blocks of the next job), instead of three copies per row in
@@ -266,8 +277,16 @@ enum MPhase : int { MP_A = 0, MP_B1 = 1, MP_B2 = 2 };
 // needs (passed to it as pf, row r of the tile at pf[r * pstride]).  For n <= 48 each thread
 // copies its tile into shared memory with cp.async before the products, so
 // the load overlaps them; larger blocks leave no room and load it directly.
+//
+// `fd` (A sweep, n <= 48 only): the p update folded in.  The prologue rows are
+// updated by all threads before the first products; every later row by the
+// second thread half while the first runs the finalize, between the row's
+// two barriers, so that the next row's products see it.  Its z rows use the
+// ring's two spare slots (A keeps 4 of 6) and the staged-tile region: three
+// slots, row r in slot r % 3.
 template <typename Fin, typename Blk>
-__device__ void msweep_ring(MSolver& Sv, int phase, const float* v_in, const float* pre, Fin fin, Blk blk) {
+__device__ void msweep_ring(MSolver& Sv, int phase, const float* v_in, const float* pre, const Fold& fd, Fin fin,
+                            Blk blk) {
   const int n = Sv.n, N = Sv.N;
   const int tid = threadIdx.x;
   const int ngroups = n / 4;
@@ -288,6 +307,25 @@ __device__ void msweep_ring(MSolver& Sv, int phase, const float* v_in, const flo
   float4* xch = reinterpret_cast<float4*>(Sv.sm + kMSmXch);    // [4][kMHalf] partial tiles
   float4* pstage = reinterpret_cast<float4*>(Sv.sm + kMSmJobs + mrhs_job_bytes(n));  // [4][kMHalf], n <= 48
   const auto slot = [&](int r) { return ring + (size_t)(((r % kv) + kv) % kv) * vb; };
+  const bool fold = fd.z != nullptr && split && phase == MP_A;
+  const auto zslot = [&](int r) {
+    const int j = r % 3;  // r >= 0
+    return j < 2 ? ring + (size_t)(4 + j) * vb : reinterpret_cast<float*>(pstage);
+  };
+  const auto fold_row = [&](int r, int t0, int nt) {  // ring row r := z_r + beta p_r
+    float4* ps = reinterpret_cast<float4*>(slot(r));
+    const float4* zs = reinterpret_cast<const float4*>(zslot(r));
+    const float4* b4 = reinterpret_cast<const float4*>(fd.beta);
+    float4* po = reinterpret_cast<float4*>(fd.pout + (size_t)r * vb);
+    const bool own = r >= Sv.s && r < Sv.e;
+    for (int q = t0; q < vb / 4; q += nt) {
+      const float4 b = b4[q & 15], pp = ps[q], zz = zs[q];
+      const float4 w = make_float4(fmaf(b.x, pp.x, zz.x), fmaf(b.y, pp.y, zz.y), fmaf(b.z, pp.z, zz.z),
+                                   fmaf(b.w, pp.w, zz.w));
+      ps[q] = w;
+      if (own) po[q] = w;
+    }
+  };
   const auto issue_blocks = [&](int row, int buf) {
     float* m = blocks + (size_t)buf * 3 * bb;
     cp_block(m, blk(0, row), bb);
@@ -297,14 +335,26 @@ __device__ void msweep_ring(MSolver& Sv, int phase, const float* v_in, const flo
   const int s = Sv.s, e = Sv.e;
   // prologue: the first job's blocks and vector rows s-k .. s+k
   issue_blocks(s, 0);
-  for (int r = max(0, s - k); r <= min(N - 1, s + k); ++r) cp_block(slot(r), v_in + (size_t)r * vb, vb);
+  for (int r = max(0, s - k); r <= min(N - 1, s + k); ++r) {
+    cp_block(slot(r), v_in + (size_t)r * vb, vb);
+    if (fold) cp_block(zslot(r), fd.z + (size_t)r * vb, vb);
+  }
   cp_commit();
+  if (fold) {  // the prologue rows, before any later copy can reuse their z slots
+    cp_wait<0>();
+    __syncthreads();
+    for (int r = max(0, s - k); r <= min(N - 1, s + k); ++r) fold_row(r, tid, kMThreads);
+    __syncthreads();
+  }
   for (int row = s; row < e; ++row) {
     const int it = row - s;
     if (row + 1 < e) {  // the next job: its blocks and its one new vector row
       issue_blocks(row + 1, (it + 1) & 1);
       const int nr = row + 1 + k;
-      if (nr < N) cp_block(slot(nr), v_in + (size_t)nr * vb, vb);
+      if (nr < N) {
+        cp_block(slot(nr), v_in + (size_t)nr * vb, vb);
+        if (fold) cp_block(zslot(nr), fd.z + (size_t)nr * vb, vb);
+      }
       cp_commit();
       cp_wait<1>();
     } else {
@@ -339,10 +389,12 @@ __device__ void msweep_ring(MSolver& Sv, int phase, const float* v_in, const flo
     if (split && half == 1 && active)
 #pragma unroll
       for (int r = 0; r < 4; ++r) xch[r * kMHalf + u] = make_float4(out[r][0], out[r][1], out[r][2], out[r][3]);
+    if (fold) cp_wait<0>();  // the next row's new ring row (and its z) has landed
     // After this barrier every product of the row is done: the next row's
     // copies (into the other block buffer and the ring slot of row - k) may
     // start while the finalize still reads this row's ring slot.
     __syncthreads();
+    if (fold && half == 1 && row + 1 < e && row + 1 + k < N) fold_row(row + 1 + k, u, kMHalf);
     if (half == 0 && active) {
       if (split)
 #pragma unroll
@@ -371,7 +423,8 @@ __device__ void msweep_ring(MSolver& Sv, int phase, const float* v_in, const flo
 
 // One float32 sweep (A, B1 or B2) over the owned rows, through the ring.
 template <typename Fin>
-__device__ void msweep32(MSolver& Sv, int phase, const float* v_in, const float* pre, Fin fin) {
+__device__ void msweep32(MSolver& Sv, int phase, const float* v_in, const float* pre, Fin fin,
+                         const Fold& fd = Fold{nullptr, nullptr, nullptr}) {
   const MParams& P = Sv.P;
   if (Sv.e <= Sv.s) return;
   auto blk = [&](int which, int row) -> const float* {
@@ -382,7 +435,7 @@ __device__ void msweep32(MSolver& Sv, int phase, const float* v_in, const float*
     else A = (which == 0) ? P.Hd32 : (which == 1 ? P.Hu32 : P.Hl32);
     return A + (size_t)row * P.bs32;
   };
-  msweep_ring(Sv, phase, v_in, pre, fin, blk);
+  msweep_ring(Sv, phase, v_in, pre, fd, fin, blk);
 }
 
 // The float64 refinement-residual sweep q = S x (Eq. 1) over the owned rows:
@@ -465,6 +518,7 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
   const size_t vb = (size_t)n * kJ;
   const int J = kJ;
   const int m = P.m;
+  const bool fold = 4 * n <= kMHalf;  // p update folded into the A sweep (the k-split layout)
 
   // ||b_j||^2 and x64 = 0 over the owned rows
   {
@@ -601,7 +655,10 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
       __syncthreads();
     };
     apply_precond(rho);
-    // p = z
+    // p = z; beta = 0 (with the folded update the first A sweep forms
+    // z + 0 p from this copy)
+    float* Pc = P.P;   // the current p (the old one while an A sweep folds the update in)
+    float* Pn = P.P2;  // where a folding A sweep writes the new p
     {
       const int jg = tid & 15, ag = tid >> 4;
       if (ag < ngroups)
@@ -610,6 +667,7 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
             const size_t idx = (size_t)row * vb + (size_t)(4 * ag + r) * J + 4 * jg;
             stv4(P.P, idx, ldv4(P.Z, idx));
           }
+      if (tid < J) betf[tid] = 0.f;
       Sv.barrier();
     }
     // inner iterations
@@ -619,7 +677,7 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
       ++total_it;
       // A: q = S p, pq per column
       Accum<float> pa[4];
-      msweep32(Sv, MP_A, P.P, nullptr, [&](int row, int a0, int j0, float (&o)[4][4], const float* pc, const float4*, int) {
+      msweep32(Sv, MP_A, Pc, nullptr, [&](int row, int a0, int j0, float (&o)[4][4], const float* pc, const float4*, int) {
         for (int r = 0; r < 4; ++r) {
           const size_t idx = (size_t)row * vb + (size_t)(a0 + r) * J + j0;
           stv4(P.Q, idx, make_float4(o[r][0], o[r][1], o[r][2], o[r][3]));
@@ -629,7 +687,12 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
           pa[2].add(pp.z * o[r][2]);
           pa[3].add(pp.w * o[r][3]);
         }
-      });
+      }, fold ? Fold{P.Z, Pn, betf} : Fold{nullptr, nullptr, nullptr});
+      if (fold) {  // the p just formed is the current one
+        float* t = Pc;
+        Pc = Pn;
+        Pn = t;
+      }
       double pv[4];
       widen(pa, pv);
       cta_col_reduce(pv, scratch, colR, ngroups);
@@ -653,7 +716,7 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
       {
         Accum<float> pa[4];
         const float4 al = *reinterpret_cast<const float4*>(alpf + 4 * (tid & 15));
-        const float4* Pp = reinterpret_cast<const float4*>(P.P);
+        const float4* Pp = reinterpret_cast<const float4*>(Pc);
         const float4* Qp = reinterpret_cast<const float4*>(P.Q);
         float4* Xp = reinterpret_cast<float4*>(P.Xin);
         float4* Rp = reinterpret_cast<float4*>(P.R);
@@ -702,10 +765,11 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
         betf[tid] = (float)b;
       }
       __syncthreads();
-      // p = z + beta p, with the access pattern of the x, r update
-      {
+      // p = z + beta p, with the access pattern of the x, r update (n > 48;
+      // smaller blocks fold it into the next A sweep)
+      if (!fold) {
         const float4 be = *reinterpret_cast<const float4*>(betf + 4 * (tid & 15));
-        float4* Pp = reinterpret_cast<float4*>(P.P);
+        float4* Pp = reinterpret_cast<float4*>(Pc);
         const float4* Zp = reinterpret_cast<const float4*>(P.Z);
         const size_t f1 = (size_t)Sv.e * vb / 4;
         for (size_t f = (size_t)Sv.s * vb / 4 + tid; f < f1; f += (size_t)kVB * kMThreads) {
@@ -799,7 +863,7 @@ extern "C" cudaError_t bt_mrhs_occupancy(int smem, int* blocks) {
 
 // Host launcher: fills the kernel parameters from plain pointers (the
 // workspace vector list is B64, X64, R64, Xin, R, P, Q, Y0, Ya, Yb, Z, red,
-// ctl, int results [iters | status | outer], double results [resid]).
+// ctl, int results [iters | status | outer], double results [resid], P2).
 extern "C" cudaError_t bt_mrhs_solve_launch(int N, int n, int m, const double* alpha, const float* const* blk32,
                                             const double* D64, const double* O64, int bs32, int bs64,
                                             void* const* vec, double tol, double tol_inner, int maxit,
@@ -823,6 +887,7 @@ extern "C" cudaError_t bt_mrhs_solve_launch(int N, int n, int m, const double* a
   P.Ya = static_cast<float*>(vec[8]);
   P.Yb = static_cast<float*>(vec[9]);
   P.Z = static_cast<float*>(vec[10]);
+  P.P2 = static_cast<float*>(vec[15]);
   P.red = static_cast<double*>(vec[11]);
   int* ctl = static_cast<int*>(vec[12]);
   P.abort_flag = ctl + 1;
