@@ -348,15 +348,16 @@ __device__ void msweep_ring(MSolver& Sv, int phase, const float* v_in, const flo
   }
   for (int row = s; row < e; ++row) {
     const int it = row - s;
-    if (row + 1 < e) {  // the next job: its blocks and its one new vector row
-      issue_blocks(row + 1, (it + 1) & 1);
+    if (row + 1 < e) {  // the next job: its one new vector row, then its blocks (two groups)
       const int nr = row + 1 + k;
       if (nr < N) {
         cp_block(slot(nr), v_in + (size_t)nr * vb, vb);
         if (fold) cp_block(zslot(nr), fd.z + (size_t)nr * vb, vb);
       }
       cp_commit();
-      cp_wait<1>();
+      issue_blocks(row + 1, (it + 1) & 1);
+      cp_commit();
+      cp_wait<2>();  // everything but the two groups just issued
     } else {
       cp_wait<0>();
     }
@@ -389,7 +390,7 @@ __device__ void msweep_ring(MSolver& Sv, int phase, const float* v_in, const flo
     if (split && half == 1 && active)
 #pragma unroll
       for (int r = 0; r < 4; ++r) xch[r * kMHalf + u] = make_float4(out[r][0], out[r][1], out[r][2], out[r][3]);
-    if (fold) cp_wait<0>();  // the next row's new ring row (and its z) has landed
+    if (fold) cp_wait<1>();  // the next row's new ring row (and its z) has landed; its blocks may not
     // After this barrier every product of the row is done: the next row's
     // copies (into the other block buffer and the ring slot of row - k) may
     // start while the finalize still reads this row's ring slot.
