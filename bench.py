@@ -71,14 +71,17 @@ def parse():
 # CPU oracle (baseline leg and the reference arm)
 # ---------------------------------------------------------------------------
 def _oracle_job(args):
-    idx, tol = args
+    """One instance of the sample: the oracle's PCG (timed: the CPU baseline)
+    and, untimed, its direct solve (the reference for the GPU's error)."""
+    idx, tol, want_x = args
     from oracle import bt_oracle as orc
     from paper_2503_15269_gb300 import workloads as wl
     inst = wl.config2(indices=[idx])[0]
     t0 = time.perf_counter()
     res = orc.pcg_opt(inst.D, inst.O, inst.b, list(ALPHA), tol, 5000)
     dt = time.perf_counter() - t0
-    return idx, dt, res.iters, res.status
+    xd = orc.direct_solve(inst.D, inst.O, inst.b).reshape(-1) if want_x else None
+    return idx, dt, res.iters, res.status, (res.x.reshape(-1) if want_x else None), xd
 
 
 def sample_indices(batch: int, count: int):
@@ -86,15 +89,36 @@ def sample_indices(batch: int, count: int):
     return list(range(0, batch, step))[:count]
 
 
-def run_oracle(indices, procs):
+def run_oracle(indices, procs, want_x=False):
+    """The oracle over a sample of instances in `procs` spawned processes;
+    wall time of the timed PCG leg (with want_x the workers also return the
+    PCG and direct-solve x of each instance, computed after the timed leg)."""
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     with ctx.Pool(procs) as pool:
-        pool.map(_oracle_job, [(indices[0], TOL)])  # warm the workers (imports)
+        pool.map(_oracle_job, [(indices[0], TOL, False)])  # warm the workers (imports)
         t0 = time.perf_counter()
-        out = pool.map(_oracle_job, [(i, TOL) for i in indices], chunksize=1)
+        out = pool.map(_oracle_job, [(i, TOL, False) for i in indices], chunksize=1)
         wall = time.perf_counter() - t0
+        if want_x:
+            xs = pool.map(_oracle_job, [(i, TOL, True) for i in indices], chunksize=1)
+            out = [(o[0], o[1], o[2], o[3], x[4], x[5]) for o, x in zip(out, xs)]
     return wall, out
+
+
+def err_vs_oracle(x_gpu, v_off, Ns, ns, out):
+    """Largest relative error, over the sampled instances, of the GPU's x
+    against the oracle's direct solve (float64 block Cholesky) and against the
+    oracle's PCG x at the same tolerance."""
+    import numpy as np
+    e_dir, e_pcg = 0.0, 0.0
+    for o in out:
+        k = o[0]
+        xk = x_gpu[v_off[k]:v_off[k] + int(Ns[k]) * int(ns[k])]
+        e_dir = max(e_dir, float(np.linalg.norm(xk - o[5]) / np.linalg.norm(o[5])))
+        e_pcg = max(e_pcg, float(np.linalg.norm(xk - o[4]) / np.linalg.norm(o[4])))
+    return {"max_rel_err_vs_direct": e_dir, "max_rel_err_vs_oracle_pcg": e_pcg, "instances": len(out),
+            "reference": "oracle direct solve (float64 block Cholesky) and oracle PCG at the same tol"}
 
 
 def max_over_ranks(ms, dist, device):
@@ -327,6 +351,15 @@ def main():
     assert max(resid) <= TOL, max(resid)
 
     # ---- device-timed steps ----
+    # The timed region replays one CUDA graph per step: the refactor kernels
+    # and the persistent solve, captured once (bt_graph_capture_refactor_solve).
+    # A second pass launches the same kernels directly with events between
+    # them, for the per-kernel durations behind the roofline.
+    assert bb.bt_graph_capture_refactor_solve(h, dD, dO, db, dx, TOL, 5000, d_it[:B], d_it[B:]) == bb.BT_OK
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            assert bb.bt_graph_launch(h) == bb.BT_OK
+    torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -339,17 +372,23 @@ def main():
     with torch.cuda.stream(stream):
         e0.record(stream)
         for k in range(a.steps):
+            assert bb.bt_graph_launch(h) == bb.BT_OK
+        e1.record(stream)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for k in range(a.steps):
             ev[k][0].record(stream)
             assert bb.bt_refactor(h, dD, dO) == bb.BT_OK
             ev[k][1].record(stream)
             assert bb.bt_pcg_solve_batched_async(h, db, dx, TOL, 5000, d_it[:B], d_it[B:]) == bb.BT_OK
             ev[k][2].record(stream)
-        e1.record(stream)
     torch.cuda.synchronize()
     if clocks:
         clocks.__exit__()
     if dist:
         dist.barrier()
+    assert (d_it[B:] == 0).all()
+    x_gpu = dx.double().cpu().numpy().copy()
     ms = e0.elapsed_time(e1)
     ms_setup = sum(x[0].elapsed_time(x[1]) for x in ev) / a.steps
     ms_solve = sum(x[1].elapsed_time(x[2]) for x in ev) / a.steps
@@ -432,7 +471,9 @@ def main():
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": stored_traffic(abytes), "peak_source": peak_kind,
             "kernel": "bt_persistent_kernel<float, 0> (batched mixed solve)",
-            "alg_bytes_per_launch": abytes, "ms_per_launch": ms_solve}
+            "alg_bytes_per_launch": abytes, "ms_per_launch": ms_solve,
+            "timing": "CUDA events around the solve launches of the direct-launch pass (same kernels as the "
+                      "graph replays that give value)"}
 
     # ---- plain FP64 single-instance PCG, one instance at a time ----
     fp64 = None
@@ -440,14 +481,17 @@ def main():
         fp64 = fp64_one_at_a_time(bb, torch, dev, stream, Ns, ns, d_off, o_off, v_off, dD, dO, db)
 
     cpu = None
+    err = None
     if rank == 0 and world == 1 and not a.no_cpu:
         procs = min(cpu_cores(), 16)
         idx = sample_indices(B, min(a.cpu_sample, B))
-        wall, out = run_oracle(idx, procs)
+        wall, out = run_oracle(idx, procs, want_x=True)
+        err = err_vs_oracle(x_gpu, v_off, Ns, ns, out)
         cpu = {"value": len(out) / wall, "unit": UNIT, "cores": procs, "kind": "oracle",
                "sample": f"{len(idx)} of the {B} instances (every {max(1, B // len(idx))}th), "
                          f"numpy float64 oracle PCG incl. its setup, {procs} spawn processes",
-               "wall_s": wall, "oracle_iters_mean": float(np.mean([o[2] for o in out]))}
+               "wall_s": wall, "oracle_iters_mean": float(np.mean([o[2] for o in out])),
+               "err_vs_oracle": err}
 
     if rank == 0:
         line = {
@@ -457,11 +501,13 @@ def main():
             "config": {"workload": f"ocp batch of {B}: N~U{{32..512}}, n in {{12,24,36}}, m=n/3, "
                                    "mixed precision, one persistent launch",
                        "preconditioner": "a=1, m=2, alpha=(1,7)", "tol": TOL,
-                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}",
+                       "graph": True},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             # per step: k_factor32, k_factor_retry, k_EH (refactor) and the persistent solve kernel
             "gpu_launches": 4 * a.steps,
             "roofline": roof,
+            "err_vs_oracle": err,
             "cpu_baseline": cpu,
             "clocks": clocks.summary() if clocks else None,
             "detail": {"ms_setup": ms_setup, "ms_solve": ms_solve, "iters_mean": float(np.mean(iters)),
@@ -512,6 +558,18 @@ def other_workload(a):
         ms = e0.elapsed_time(e1) / a.steps
         outers = [bb.bt_multi_info(h, j)[1] for j in range(J)]
         bb.bt_destroy(h)
+        # error against the float64 oracle: every column's true residual
+        # (oracle SpMV) and four sampled columns against its direct solve
+        from oracle import bt_oracle as orc
+        Xh = dX.cpu().numpy().reshape(N, n, J)
+        R = orc.spmv(inst.D, inst.O, Xh) - inst.b
+        res_max = max(float(np.linalg.norm(R[:, :, j]) / np.linalg.norm(inst.b[:, :, j])) for j in range(J))
+        cols = [0, 21, 42, 63]
+        xr = orc.direct_solve(inst.D, inst.O, inst.b[:, :, cols])
+        e_dir = max(float(np.linalg.norm(Xh[:, :, j] - xr[:, :, c]) / np.linalg.norm(xr[:, :, c]))
+                    for c, j in enumerate(cols))
+        err = {"max_rel_err_vs_direct": e_dir, "columns": cols, "max_true_rel_residual": res_max,
+               "reference": "oracle direct solve (float64 block Cholesky); residuals by the oracle's SpMV"}
         # bytes: every shared sweep streams the blocks once for all 64 columns;
         # the sweeps of an outer step run until its slowest column converges
         n2 = n * n
@@ -529,6 +587,7 @@ def other_workload(a):
               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                            "frac": achieved / peak, "traffic": None, "peak_source": kind,
                            "kernel": "bt_mrhs_kernel", "alg_bytes_per_launch": abytes},
+              "err_vs_oracle": err,
               "detail": {"iters_max": it_max, "iters_mean": float(np.mean(its)), "outer_max": o_max}})
         return
     if a.workload == "family":
@@ -575,33 +634,114 @@ def other_workload(a):
               "data": "synthetic (seeded)", "config": {"workload": "single instances, one persistent launch each"},
               "rows": rows})
         return
+    adjoint_workload(a, bb, wl, torch, dev)
+
+
+def adjoint_workload(a, bb, wl, torch, dev):
+    """Forward + adjoint on 256 LQR instances, N = 256, n = 24 (input 8),
+    mixed, tol 1e-8.  value: through the public API (bt_solve, a
+    torch.autograd.Function: setup, forward solve, backward solve, gradient
+    blocks) per step.  roofline: a second pass through the C ABI on one
+    handle (refactor, forward batched solve, adjoint solve with the same
+    preconditioner, bt_adjoint_blocks), CUDA events around each launch; the
+    solve kernel's algorithmic bytes (forward + adjoint solves, the per
+    instance iteration and refinement counts) over its event time.  Error
+    against the oracle on sampled instances: x and dL/db against its direct
+    solve and adjoint."""
+    import numpy as np
+    from oracle import bt_oracle as orc
     from paper_2503_15269_gb300.autograd import bt_solve
     insts = wl.config4()
-    Ns, ns, d_off, o_off, v_off, D, O, b = wl.pack_batch(insts)
-    D = torch.tensor(D, device=dev, requires_grad=True)
-    O = torch.tensor(O, device=dev, requires_grad=True)
-    b = torch.tensor(b, device=dev, requires_grad=True)
+    Ns, ns, d_off, o_off, v_off, D_, O_, b_ = wl.pack_batch(insts)
+    D = torch.tensor(D_, device=dev, requires_grad=True)
+    O = torch.tensor(O_, device=dev, requires_grad=True)
+    b = torch.tensor(b_, device=dev, requires_grad=True)
     w = torch.tensor(np.random.default_rng(5).standard_normal(b.numel()), device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     def step():
         D.grad = O.grad = b.grad = None
         x = bt_solve(D, O, b, Ns, ns, d_off, o_off, precision=bb.BT_MIXED, tol=TOL)
         (x * w).sum().backward()
+        return x
 
     for _ in range(a.warmup):
         step()
     torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.__enter__()
     e0.record()
     for _ in range(a.steps):
-        step()
+        x = step()
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / a.steps
     B = len(insts)
+    xs, gb = x.detach().cpu().numpy(), b.grad.cpu().numpy()
+
+    # ---- the same work through the C ABI on one handle, per-launch events ----
+    stream = torch.cuda.Stream(device=dev)
+    p, keep = bb.make_params(m=M, alpha=ALPHA, precision=bb.BT_MIXED, stream=stream)
+    Dd, Od, bd = D.detach(), O.detach(), b.detach()
+    st, h = bb.bt_setup_batched(Ns, ns, d_off, o_off, Dd, Od, p)
+    assert st == bb.BT_OK, bb.status_string(st)
+    xd, gd = torch.zeros_like(bd), torch.zeros_like(bd)
+    gD, gO = torch.empty_like(Dd), torch.empty_like(Od)
+    st, it_f, sts = bb.bt_pcg_solve_batched(h, bd, xd, B, TOL, 10000)
+    assert st == bb.BT_OK and (sts == 0).all()
+    out_f = [bb.bt_solve_info(h, k)[1] for k in range(B)]
+    st, it_b, sts = bb.bt_pcg_solve_batched(h, w, gd, B, TOL, 10000)
+    assert st == bb.BT_OK and (sts == 0).all()
+    out_b = [bb.bt_solve_info(h, k)[1] for k in range(B)]
+    d_it = torch.zeros(2 * B, dtype=torch.int32, device=dev)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(a.steps)]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for k in range(a.steps):
+            ev[k][0].record(stream)
+            assert bb.bt_refactor(h, Dd, Od) == bb.BT_OK
+            ev[k][1].record(stream)
+            assert bb.bt_pcg_solve_batched_async(h, bd, xd, TOL, 10000, d_it[:B], d_it[B:]) == bb.BT_OK
+            ev[k][2].record(stream)
+            assert bb.bt_pcg_solve_batched_async(h, w, gd, TOL, 10000, d_it[:B], d_it[B:]) == bb.BT_OK
+            ev[k][3].record(stream)
+            assert bb.bt_adjoint_blocks(h, xd, gd, gD, gO) == bb.BT_OK
+            ev[k][4].record(stream)
+    torch.cuda.synchronize()
+    clocks.__exit__()
+    bb.bt_destroy(h)
+    t = [sum(e[i].elapsed_time(e[i + 1]) for e in ev) / a.steps for i in range(4)]
+    ms_refactor, ms_fwd, ms_bwd, ms_adj = t
+    abytes = alg_bytes(Ns, ns, it_f, out_f) + alg_bytes(Ns, ns, it_b, out_b)
+    achieved = abytes / ((ms_fwd + ms_bwd) / 1e3) / 1e9
+    peak, kind = measured_peak()
+    adj_bytes = sum(8 * ((2 * int(N) - 1) * int(n) ** 2 + 2 * int(N) * int(n)) for N, n in zip(Ns, ns))
+    # error against the oracle on sampled instances
+    e_x, e_g = 0.0, 0.0
+    wn = w.cpu().numpy()
+    samples = (0, 77, 255)
+    for k in samples:
+        inst = insts[k]
+        sl = slice(v_off[k], v_off[k] + inst.N * inst.n)
+        xr = orc.direct_solve(inst.D, inst.O, inst.b)
+        g, _, _ = orc.adjoint(inst.D, inst.O, xr, wn[sl].reshape(inst.N, inst.n))
+        e_x = max(e_x, float(np.linalg.norm(xs[sl].reshape(inst.N, inst.n) - xr) / np.linalg.norm(xr)))
+        e_g = max(e_g, float(np.linalg.norm(gb[sl].reshape(inst.N, inst.n) - g) / np.linalg.norm(g)))
     emit({"metric": "forward + adjoint solves per second (x = S^-1 b and dL/d(D, O, b)), rel. residual 1e-8",
           "value": B / (ms / 1e3), "unit": "instances/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
           "ms_per_step": ms, "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic (seeded LQR)",
-          "config": {"workload": "256 LQR instances N=256 n=24 (input size 8), setup + forward + adjoint per step"}})
+          "config": {"workload": "256 LQR instances N=256 n=24 (input size 8), setup + forward + adjoint per step"},
+          "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                       "traffic": None, "peak_source": kind,
+                       "kernel": "bt_persistent_kernel<float, 0> (forward and adjoint batched solves)",
+                       "alg_bytes_per_launch": abytes / 2, "ms_per_launch": (ms_fwd + ms_bwd) / 2},
+          "err_vs_oracle": {"max_rel_err_x_vs_direct": e_x, "max_rel_err_grad_b_vs_oracle_adjoint": e_g,
+                            "instances": list(samples),
+                            "reference": "oracle direct solve and oracle adjoint (float64)"},
+          "clocks": clocks.summary(),
+          "detail": {"ms_refactor": ms_refactor, "ms_forward_solve": ms_fwd, "ms_adjoint_solve": ms_bwd,
+                     "ms_adjoint_blocks": ms_adj, "adjoint_blocks_gbs": adj_bytes / (ms_adj / 1e3) / 1e9,
+                     "iters_mean_forward": float(np.mean(it_f)), "iters_mean_adjoint": float(np.mean(it_b))}})
 
 
 def family_protocol(a, bb, wl, torch, dev):

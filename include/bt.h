@@ -223,6 +223,18 @@ bt_status bt_pcg_solve_batched_async(bt_handle h, const double* b, double* x, do
  * the handle's stream.  A new capture replaces the previous one. */
 bt_status bt_graph_capture_batched(bt_handle h, const double* b, double* x, double tol,
                                    int maxit, int* d_iters, int* d_status);
+
+/* Capture one whole step of a batched workload -- bt_refactor(h, D, O)
+ * followed by bt_pcg_solve_batched_async(h, b, x, tol, maxit, d_iters,
+ * d_status) -- into the handle's CUDA graph (replacing any earlier capture).
+ * Each bt_graph_launch then re-forms every preconditioner block (Sec. 4.1)
+ * from the values D, O hold at that moment and solves all instances, with no
+ * host work between the setup kernels and the persistent solve.  D, O, b, x
+ * (DEVICE) must keep their addresses and the packing given at setup; a
+ * non-SPD block is reported by bt_setup_status after the replay. */
+bt_status bt_graph_capture_refactor_solve(bt_handle h, const double* D, const double* O,
+                                          const double* b, double* x, double tol, int maxit,
+                                          int* d_iters, int* d_status);
 bt_status bt_graph_launch(bt_handle h);
 
 /* Adjoint of x = S^-1 b (kernel only): given x and g = S^-1 (dL/dx) for each
@@ -250,9 +262,13 @@ bt_status bt_adjoint_blocks(bt_handle h, const double* x, const double* g, doubl
  *   - Sizes whose buffers do not fit in the array are rejected with
  *     BT_ERR_ARG before anything runs: for BT_FP64 with m = 2 the limit is
  *     about 56 N n^2 + 88 N n bytes <= 16 MiB (N = 128, n = 32 fits).
- *   - The first call on a device looks up the array's device address (once
- *     per device, with that device current); make that first call before any
- *     stream capture.
+ *   - The first call in each CUDA context of a device looks up the array's
+ *     device address (with that device current) and keeps it for later calls
+ *     in the same context; after cudaDeviceReset, or when the device's primary
+ *     context is destroyed and made anew, the module is loaded again and the
+ *     next call looks the address up afresh.  The lookup may load the module,
+ *     so make a device's first call while no CUDA stream capture is under way
+ *     in the process.
  *   - Every call shares the array, which keeps the last call's contents; each
  *     call clears what must start at zero.  Calls that overlap on the GPU race
  *     on the array: issue them one after another.

@@ -75,6 +75,7 @@ def lib() -> C.CDLL:
         "bt_pcg_solve_batched": (C.c_int, [H, dp, dp, llp, C.c_double, C.c_int, ip, ip]),
         "bt_pcg_solve_batched_async": (C.c_int, [H, dp, dp, C.c_double, C.c_int, vp, vp]),
         "bt_graph_capture_batched": (C.c_int, [H, dp, dp, C.c_double, C.c_int, vp, vp]),
+        "bt_graph_capture_refactor_solve": (C.c_int, [H, dp, dp, dp, dp, C.c_double, C.c_int, vp, vp]),
         "bt_graph_launch": (C.c_int, [H]),
         "bt_adjoint_blocks": (C.c_int, [H, dp, dp, dp, dp]),
         "bt_pcg_solve_noalloc": (C.c_int, [C.c_int, C.c_int, dp, dp, dp, dp, C.c_double, C.c_int,
@@ -241,6 +242,11 @@ def bt_pcg_solve_batched_async(h, b, x, tol: float, maxit: int, d_iters=None, d_
 def bt_graph_capture_batched(h, b, x, tol: float, maxit: int, d_iters=None, d_status=None) -> int:
     return lib().bt_graph_capture_batched(h, _ptr(b), _ptr(x), float(tol), int(maxit), _ptr(d_iters),
                                           _ptr(d_status))
+
+
+def bt_graph_capture_refactor_solve(h, D, O, b, x, tol: float, maxit: int, d_iters=None, d_status=None) -> int:
+    return lib().bt_graph_capture_refactor_solve(h, _ptr(D), _ptr(O), _ptr(b), _ptr(x), float(tol), int(maxit),
+                                                 _ptr(d_iters), _ptr(d_status))
 
 
 def bt_graph_launch(h) -> int:

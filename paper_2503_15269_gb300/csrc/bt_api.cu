@@ -1019,6 +1019,34 @@ bt_status bt_graph_capture_batched(bt_handle h, const double* b, double* x, doub
   return BT_OK;
 }
 
+bt_status bt_graph_capture_refactor_solve(bt_handle h, const double* D, const double* O, const double* b, double* x,
+                                          double tol, int maxit, int* d_iters, int* d_status) {
+  Range nvtx_range("bt_graph_capture_refactor_solve");
+  if (!h || !D || (h->maxN > 1 && !O)) return BT_ERR_ARG;
+  if (!h->batched) return BT_ERR_STATE;
+  if (!h->stream) return BT_ERR_ARG;  // the legacy default stream cannot be captured
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->graph_src) cudaGraphDestroy(h->graph_src);
+  h->graph = nullptr;
+  h->graph_src = nullptr;
+  // kernel attributes were set when bt_setup_batched launched the same kernels
+  int occ = 0;
+  bt_persistent_occupancy(h->mixed, h->variant, h->smem, &occ);
+  if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal)) return BT_ERR_CUDA;
+  bt_status s = launch_setup_kernels(h, D, O);
+  if (s == BT_OK) s = bt_pcg_solve_batched_async(h, b, x, tol, maxit, d_iters, d_status);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  if (s != BT_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e) return BT_ERR_CUDA;
+  h->graph_src = g;
+  if (cudaGraphInstantiate(&h->graph, g, 0)) return BT_ERR_CUDA;
+  return BT_OK;
+}
+
 bt_status bt_graph_launch(bt_handle h) {
   if (!h || !h->graph) return BT_ERR_STATE;
   return cuda_st(cudaGraphLaunch(h->graph, h->stream));

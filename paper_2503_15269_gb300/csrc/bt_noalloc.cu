@@ -18,6 +18,8 @@
 // padding slots of the block arrays) is cleared at the start of each call.
 // Calls that overlap on the GPU (two streams, or two host threads) race on
 // the array: issue them one after another.
+#include <cuda.h>
+
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -39,20 +41,51 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned char* g_addr[kMaxDevices] = {};
+unsigned long long g_ctx_id[kMaxDevices] = {};
 
-// Device address of the scratch array for the current device; looked up
-// once per device (cudaGetSymbolAddress), with that device current.
+// Device address of the scratch array for the current device, looked up
+// (cudaGetSymbolAddress, with that device current) on the first call in each
+// CUDA context of the device and cached under the context's unique id: a
+// cudaDeviceReset or a new primary context loads the module afresh, and the
+// next call then looks the address up again instead of using a stale one.
 cudaError_t scratch_address(unsigned char** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  e = cudaSetDevice(dev);  // initialises the device's primary context and makes it current
+  if (e != cudaSuccess) return e;
+  // the driver API through the runtime's entry-point lookup (no link-time
+  // dependency on the driver library)
+  using CtxGetCurrent = CUresult (*)(CUcontext*);
+  using CtxGetId = CUresult (*)(CUcontext, unsigned long long*);
+  static CtxGetCurrent get_current = nullptr;
+  static CtxGetId get_id = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!get_current || !get_id) {
+      void* f1 = nullptr;
+      void* f2 = nullptr;
+      cudaDriverEntryPointQueryResult q1{}, q2{};
+      if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+          cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+          q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+        return cudaErrorSymbolNotFound;
+      get_current = reinterpret_cast<CtxGetCurrent>(f1);
+      get_id = reinterpret_cast<CtxGetId>(f2);
+    }
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return cudaErrorDeviceUninitialized;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
+  if (!g_addr[dev] || g_ctx_id[dev] != id) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_bt_noalloc_scratch);
     if (e != cudaSuccess) return e;
     g_addr[dev] = static_cast<unsigned char*>(p);
+    g_ctx_id[dev] = id;
   }
   *out = g_addr[dev];
   return cudaSuccess;
@@ -128,7 +161,7 @@ extern "C" bt_status bt_pcg_solve_noalloc(int N, int n, const double* D, const d
   const int fixed = bt_persistent_smem_fixed(0);
   int vslot = mixed ? 9 * 1024 : 18 * 1024;
   const long long per_cta = std::min<long long>(smem_optin, 228 * 1024 - 1024);
-  const int vslots = (0) == 1 ? 3 : 4;  // vector ring slots of the kernel variant
+  const int vslots = 4;  // vector ring slots of the optimum's kernel variant
   int S = (int)((per_cta - fixed - vslots * vslot) / sb);
   if (S < 2) {
     vslot = 0;
@@ -193,8 +226,11 @@ extern "C" bt_status bt_pcg_solve_noalloc(int N, int n, const double* D, const d
   char* ws = c.take<char>(base, ws_stride);
   if (c.off > (size_t)BT_NOALLOC_SCRATCH_BYTES) return BT_ERR_ARG;  // instance too large for the scratch
 
-  // clear what must start at zero, then set up and solve
+  // clear what must start at zero (block arrays with their padding slots, and
+  // the PCG workspace, whose padding an earlier call -- one that diverged or
+  // had non-finite input -- may have left non-finite), then set up and solve
   if (cudaMemsetAsync(base + blocks_begin, 0, blocks_end - blocks_begin, st)) return BT_ERR_CUDA;
+  if (cudaMemsetAsync(ws, 0, ws_stride, st)) return BT_ERR_CUDA;
   k_noalloc_init<<<std::max(1, (N + 255) / 256), 256, 0, st>>>(inst, rows, offs, order, N, n, bs32, bs64, ctl,
                                                               64, fail_key);
   if (cudaGetLastError() != cudaSuccess) return BT_ERR_CUDA;

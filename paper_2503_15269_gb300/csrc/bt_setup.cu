@@ -767,26 +767,48 @@ __global__ void __launch_bounds__(256, 2) k_EH(const __grid_constant__ SetupPara
 }
 
 // ---------------------------------------------------------------- adjoint
-// gD_i = -g_i x_i^T, gO_i = -(g_i x_{i+1}^T + x_i g_{i+1}^T), caller layout.
-__global__ void k_adjoint(const __grid_constant__ AdjParams P) {
-  const long long gr = blockIdx.x;
+// gD_i = -g_i x_i^T, gO_i = -(g_i x_{i+1}^T + x_i g_{i+1}^T), caller layout
+// (row-major blocks).  One warp per block row: lane l holds entries l and
+// l + 32 of x_i, g_i, x_{i+1}, g_{i+1}; output row a takes g_i[a] and x_i[a]
+// from lane a % 32 by shuffle, and the warp writes the row's n contiguous
+// doubles (streaming stores: the gradients are the caller's, not re-read
+// here).  Bound by the (2N-1) n^2 doubles it writes.
+constexpr int kAdjWarps = 8;
+
+__global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint(const __grid_constant__ AdjParams P) {
+  const int lane = threadIdx.x & 31;
+  const long long gr = (long long)blockIdx.x * kAdjWarps + (threadIdx.x >> 5);
   if (gr >= P.nrows) return;
   const RowRef rr = P.rows[gr];
   const InstDesc d = P.inst[rr.inst];
   const int n = d.n, i = rr.row;
-  const double* x = P.x + d.vec;
-  const double* g = P.g + d.vec;
-  double* gD = P.gD + P.d_off[rr.inst] + (long long)i * n * n;
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-    const int a = t / n, c = t % n;
-    gD[t] = -g[(long long)i * n + a] * x[(long long)i * n + c];
+  const bool has_next = i < d.N - 1;
+  const double* xi = P.x + d.vec + (long long)i * n;
+  const double* gi = P.g + d.vec + (long long)i * n;
+  const int c0 = lane, c1 = lane + 32;
+  const bool v0 = c0 < n, v1 = c1 < n;
+  const double x0 = v0 ? xi[c0] : 0.0, x1 = v1 ? xi[c1] : 0.0;
+  const double g0 = v0 ? gi[c0] : 0.0, g1 = v1 ? gi[c1] : 0.0;
+  double xn0 = 0.0, xn1 = 0.0, gn0 = 0.0, gn1 = 0.0;
+  if (has_next) {
+    xn0 = v0 ? xi[n + c0] : 0.0;
+    xn1 = v1 ? xi[n + c1] : 0.0;
+    gn0 = v0 ? gi[n + c0] : 0.0;
+    gn1 = v1 ? gi[n + c1] : 0.0;
   }
-  if (i < d.N - 1) {
-    double* gO = P.gO + P.o_off[rr.inst] + (long long)i * n * n;
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-      const int a = t / n, c = t % n;
-      gO[t] = -(g[(long long)i * n + a] * x[(long long)(i + 1) * n + c] +
-                x[(long long)i * n + a] * g[(long long)(i + 1) * n + c]);
+  double* gD = P.gD + P.d_off[rr.inst] + (long long)i * n * n;
+  double* gO = has_next ? P.gO + P.o_off[rr.inst] + (long long)i * n * n : nullptr;
+  for (int a = 0; a < n; ++a) {
+    const int src = a & 31;
+    const double ga = __shfl_sync(0xffffffffu, a < 32 ? g0 : g1, src);
+    const double xa = __shfl_sync(0xffffffffu, a < 32 ? x0 : x1, src);
+    double* dr = gD + a * n;
+    if (v0) __stcs(dr + c0, -ga * x0);
+    if (v1) __stcs(dr + c1, -ga * x1);
+    if (has_next) {
+      double* orow = gO + a * n;
+      if (v0) __stcs(orow + c0, -fma(ga, xn0, xa * gn0));
+      if (v1) __stcs(orow + c1, -fma(ga, xn1, xa * gn1));
     }
   }
 }
@@ -872,6 +894,7 @@ extern "C" cudaError_t bt_launch_setup(const bt::SetupParams* P, int mixed, int 
 
 extern "C" cudaError_t bt_launch_adjoint(const bt::AdjParams* P, cudaStream_t st) {
   if (P->nrows == 0) return cudaSuccess;
-  bt::k_adjoint<<<(unsigned)P->nrows, 128, 0, st>>>(*P);
+  const long long grid = (P->nrows + bt::kAdjWarps - 1) / bt::kAdjWarps;
+  bt::k_adjoint<<<(unsigned)grid, bt::kAdjWarps * 32, 0, st>>>(*P);
   return cudaGetLastError();
 }

@@ -1,4 +1,4 @@
-"""Helpers shared by the GPU tests (marshalling only)."""
+"""Helpers shared by the GPU tests (marshalling, and the oracle-side condition estimate)."""
 import numpy as np
 
 from paper_2503_15269_gb300 import binding as bb
@@ -65,3 +65,14 @@ def rel(a, b):
 
 def maxrel(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def cond_estimate(D, O, b, maxit=20000):
+    """kappa(S) of one system, from the oracle: the extreme Ritz values of
+    the Lanczos tridiagonal of an unpreconditioned CG run (M = I) on b to a
+    relative residual of 1e-12 (oracle.lanczos_cond, textbook relation).
+    The relative error of a solve stopped at relative residual tol is at
+    most kappa(S) * tol."""
+    from oracle import bt_oracle as orc
+    res = orc.pcg(D, O, b, lambda r: r, 1e-12, maxit)
+    return orc.lanczos_cond(res.alphas, res.betas)

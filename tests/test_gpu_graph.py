@@ -79,3 +79,56 @@ def test_refactor_and_async_single_solve():
         assert blk == 7
     finally:
         bb.bt_destroy(h)
+
+
+def test_graph_of_refactor_and_solve_follows_new_values():
+    """bt_graph_capture_refactor_solve: one replay re-forms every block from
+    the values D, O hold at replay time and solves; after overwriting the
+    captured buffers with another batch of the same shapes, a replay equals
+    bt_refactor + bt_pcg_solve_batched on the new values, bit for bit, and
+    each instance satisfies the oracle's residual test."""
+    idx_a = [5, 11, 48, 300, 700, 1001]
+    insts_a = wl.config2(indices=idx_a)
+    shapes = [(i.N, i.n) for i in insts_a]
+    insts_b = [wl.small_ocp(120 + k, N, n) for k, (N, n) in enumerate(shapes)]
+    Ns, ns, d_off, o_off, v_off, Da, Oa, ba = wl.pack_batch(insts_a)
+    _, _, _, _, _, Db, Ob, bb_ = wl.pack_batch(insts_b)
+    B = len(insts_a)
+    stream = torch.cuda.Stream()
+    p, keep = bb.make_params(m=2, alpha=[1.0, 7.0], precision=bb.BT_MIXED, stream=stream)
+    dD, dO, db = dev(Da), dev(Oa), dev(ba)
+    st, h = bb.bt_setup_batched(Ns, ns, d_off, o_off, dD, dO, p)
+    assert st == bb.BT_OK
+    try:
+        x = dev(np.zeros(ba.size))
+        d_it = torch.zeros(B, dtype=torch.int32, device="cuda")
+        d_st = torch.full((B,), -1, dtype=torch.int32, device="cuda")
+        assert bb.bt_graph_capture_refactor_solve(h, dD, dO, db, x, 1e-8, 5000, d_it, d_st) == bb.BT_OK
+        results = []
+        for D_, O_, b_ in ((Da, Oa, ba), (Db, Ob, bb_)):
+            with torch.cuda.stream(stream):
+                dD.copy_(dev(D_))
+                dO.copy_(dev(O_))
+                db.copy_(dev(b_))
+                x.zero_()
+            assert bb.bt_graph_launch(h) == bb.BT_OK
+            stream.synchronize()
+            assert bb.bt_setup_status(h) == bb.BT_OK
+            assert (host(d_st) == 0).all()
+            results.append((host(x).copy(), host(d_it).copy()))
+        # the same steps through the direct calls
+        for (D_, O_, b_, insts), (xg, itg) in zip(((Da, Oa, ba, insts_a), (Db, Ob, bb_, insts_b)), results):
+            dD.copy_(dev(D_))
+            dO.copy_(dev(O_))
+            torch.cuda.synchronize()
+            assert bb.bt_refactor(h, dD, dO) == bb.BT_OK
+            x_ref = dev(np.zeros(b_.size))
+            st, it_ref, st_ref = bb.bt_pcg_solve_batched(h, dev(b_), x_ref, B, 1e-8, 5000)
+            assert st == bb.BT_OK
+            assert np.array_equal(xg, host(x_ref))
+            assert np.array_equal(itg, it_ref.astype(np.int32))
+            for k, inst in enumerate(insts):
+                xk = xg[v_off[k]:v_off[k] + inst.N * inst.n].reshape(inst.N, inst.n)
+                assert np.linalg.norm(orc.spmv(inst.D, inst.O, xk) - inst.b) <= 1e-8 * np.linalg.norm(inst.b)
+    finally:
+        bb.bt_destroy(h)

@@ -1,6 +1,8 @@
 """Many right-hand sides (64 columns sharing each block sweep) against the
 oracle: per-column direct solves on small cases, and the 2048 x 48 workload
 through every column's true residual plus sampled direct solves."""
+import functools
+
 import numpy as np
 import pytest
 
@@ -8,7 +10,7 @@ from oracle import bt_oracle as orc
 from paper_2503_15269_gb300 import binding as bb
 from paper_2503_15269_gb300 import workloads as wl
 
-from _util import dev, host
+from _util import cond_estimate, dev, host
 
 pytestmark = pytest.mark.gpu
 
@@ -66,10 +68,16 @@ def test_multi_rhs_columns_match_single_solves():
     assert st == bb.BT_OK and its[2] == 0 and np.all(X[:, :, 2] == 0)
 
 
+@functools.lru_cache(maxsize=1)
+def config3_cond():
+    inst = wl.config3()
+    return cond_estimate(inst.D, inst.O, inst.b[:, :, 0])
+
+
 def test_config3_many_rhs_full_size():
-    """LL^T, N = 2048, n = 48, 64 right-hand sides: every column's float64
-    true residual <= 1e-8; two sampled columns against direct solves within
-    cond * tol."""
+    """LL^T, N = 2048, n = 48, 64 right-hand sides at the benchmark's
+    tol = 1e-8: every column's float64 true residual <= 1e-8, and sampled
+    columns against direct solves within cond(S) * tol."""
     inst = wl.config3()
     st, its, sts, X, infos = solve_multi(inst, 64, 1e-8)
     assert st == bb.BT_OK and (sts == 0).all()
@@ -77,11 +85,33 @@ def test_config3_many_rhs_full_size():
     for j in range(64):
         res = np.linalg.norm(R[:, :, j]) / np.linalg.norm(inst.b[:, :, j])
         assert res <= 1e-8, (j, res)
+    cond = config3_cond()
     xr = orc.direct_solve(inst.D, inst.O, inst.b[:, :, :2])
     for j in range(2):
         err = np.linalg.norm(X[:, :, j] - xr[:, :, j]) / np.linalg.norm(xr[:, :, j])
-        assert err <= 1e-3, (j, err)
+        assert err <= cond * 1e-8, (j, err, cond)
 
+
+def test_config3_many_rhs_full_size_error_1e8():
+    """The same system solved to tol = min(1e-8, 1e-8 / cond(S)) (cond from
+    the oracle's Lanczos estimate, about 6.6e4), so that the mixed path's
+    solution error is bounded by 1e-8: four sampled columns (first, last and
+    two inside) against the oracle's direct solve at <= 1e-8, every column's
+    true residual at <= tol."""
+    inst = wl.config3()
+    cond = config3_cond()
+    tol = min(1e-8, 1e-8 / cond)
+    st, its, sts, X, infos = solve_multi(inst, 64, tol)
+    assert st == bb.BT_OK and (sts == 0).all(), (st, sts)
+    R = orc.spmv(inst.D, inst.O, X) - inst.b
+    for j in range(64):
+        res = np.linalg.norm(R[:, :, j]) / np.linalg.norm(inst.b[:, :, j])
+        assert res <= tol, (j, res, tol)
+    cols = [0, 21, 42, 63]
+    xr = orc.direct_solve(inst.D, inst.O, inst.b[:, :, cols])
+    for c, j in enumerate(cols):
+        err = np.linalg.norm(X[:, :, j] - xr[:, :, c]) / np.linalg.norm(xr[:, :, c])
+        assert err <= 1e-8, (j, err, tol)
 
 
 @pytest.mark.parametrize("m,alpha", [(1, (1.0,)), (3, (1.0, 1.0, 1.0)), (3, (1.0, 2.0, 3.0))])

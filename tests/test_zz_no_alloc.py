@@ -5,17 +5,26 @@ cudaMalloc's device synchronisation and unbounded latency are not allowed).
 It must give the same answer as the allocating path (bt_setup +
 bt_pcg_solve) through the C ABI, on two calls in a row -- the second call
 reuses the static scratch array the first one left behind, so it also checks
-that each call clears what must start at zero.  Runs on its own in a fresh
-process and after the rest of the suite (this file is collected last)."""
+that each call clears what must start at zero -- and the oracle's answer.
+This file is collected last, so it runs after the rest of the suite; one test
+repeats the two-call check in a child process of its own, where the first
+call meets the array as the module loaded it."""
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
+from oracle import bt_oracle as orc
 from paper_2503_15269_gb300 import binding as bb
 from paper_2503_15269_gb300 import workloads as wl
 
 from _util import dev, host, rel
 
 pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -36,15 +45,17 @@ def allocating_solve(inst, params, tol, maxit):
     return st, it, host(x)
 
 
-def noalloc_solve(inst, params, tol, maxit, x_init=None):
+def noalloc_solve(inst, params, tol, maxit, x_init=None, b=None):
     x = dev(np.zeros(inst.N * inst.n) if x_init is None else x_init)
-    st, it = bb.bt_pcg_solve_noalloc(inst.N, inst.n, dev(inst.D), dev(inst.O), dev(inst.b.reshape(-1)), x,
-                                     tol, maxit, params)
+    bv = inst.b.reshape(-1) if b is None else b
+    st, it = bb.bt_pcg_solve_noalloc(inst.N, inst.n, dev(inst.D), dev(inst.O), dev(bv), x, tol, maxit, params)
     return st, it, host(x)
 
 
-@pytest.mark.parametrize("precision,tol", [(bb.BT_FP64, 1e-10), (bb.BT_MIXED, 1e-10)])
-def test_noalloc_matches_allocating_path_two_calls(precision, tol):
+def two_calls(precision, tol):
+    """Two no-allocation solves of different shapes in a row, each against the
+    allocating path (same status, iterations within 1, x within 1e-10) and
+    against the oracle's direct solve (within cond(S) * tol, cond ~ 1e3)."""
     params, keep = bb.make_params(m=2, alpha=[1.0, 7.0], precision=precision)
     first = wl.config1()                 # N = 128, n = 12
     second = wl.small_llt(7, 37, 9)      # different shape: odd N, odd n
@@ -54,6 +65,38 @@ def test_noalloc_matches_allocating_path_two_calls(precision, tol):
         assert st_a == bb.BT_OK and st_b == bb.BT_OK
         assert abs(it_a - it_b) <= 1
         assert rel(x_b, x_a) <= 1e-10
+        xr = orc.direct_solve(inst.D, inst.O, inst.b).reshape(-1)
+        assert rel(x_b, xr) <= 1e-6, rel(x_b, xr)
+
+
+@pytest.mark.parametrize("precision,tol", [(bb.BT_FP64, 1e-10), (bb.BT_MIXED, 1e-10)])
+def test_noalloc_matches_allocating_path_two_calls(precision, tol):
+    two_calls(precision, tol)
+
+
+def test_noalloc_clean_call_after_nonfinite_input():
+    """A call whose b holds a NaN (status BT_ERR_NONFINITE) leaves non-finite
+    values in the shared array; the next, smaller call must not see them."""
+    params, keep = bb.make_params(m=2, alpha=[1.0, 7.0], precision=bb.BT_MIXED)
+    big = wl.config1()
+    b = big.b.reshape(-1).copy()
+    b[17] = np.nan
+    st, it, _ = noalloc_solve(big, params, 1e-10, 2000, b=b)
+    assert st == bb.BT_ERR_NONFINITE
+    small = wl.small_llt(8, 21, 7)
+    st_a, it_a, x_a = allocating_solve(small, params, 1e-10, 2000)
+    st_b, it_b, x_b = noalloc_solve(small, params, 1e-10, 2000)
+    assert st_a == bb.BT_OK and st_b == bb.BT_OK
+    assert abs(it_a - it_b) <= 1 and rel(x_b, x_a) <= 1e-10
+
+
+def test_noalloc_two_calls_in_a_fresh_process():
+    code = ("import sys; sys.path[:0] = [%r, %r]; import test_zz_no_alloc as t; "
+            "from paper_2503_15269_gb300 import binding as bb; bb.lib(); "
+            "t.two_calls(bb.BT_MIXED, 1e-10); t.two_calls(bb.BT_FP64, 1e-10); print('fresh ok')"
+            % (ROOT, os.path.join(ROOT, "tests")))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0 and "fresh ok" in r.stdout, r.stdout[-2000:] + r.stderr[-2000:]
 
 
 def test_noalloc_rejects_sizes_beyond_the_scratch():
