@@ -113,6 +113,14 @@ typedef struct bt_params {
                           problems bound by memory capacity), 4 instead of 3 block
                           reads per application.  a = 1 only; not for
                           bt_pcg_solve_multi or bt_pcg_solve_noalloc (BT_ERR_PARAM). */
+  int mrhs_engine;     /* bt_pcg_solve_multi's block products: 0 = automatic (tensor
+                          cores where supported: n a multiple of 8, n <= 48; float32
+                          SIMT otherwise), 1 = float32 SIMT, 2 = tensor cores (3xTF32
+                          split, float32 accumulation; BT_ERR_ARG where unsupported). */
+  int mixed_fp64_factor; /* BT_MIXED: 1 = factor every D_i in float64 (then round
+                          D_i^-1 and the E, H blocks to float32), 0 = float32 factor
+                          with a float64 refactor of the blocks whose pivots show
+                          cond(D_i) > 1e3.                                          */
 } bt_params;
 
 typedef struct bt_ctx* bt_handle;

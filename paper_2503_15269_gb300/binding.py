@@ -43,6 +43,8 @@ class bt_params(C.Structure):
         ("group_ctas", C.c_int),
         ("stage_kb", C.c_int),
         ("h_matrix_free", C.c_int),
+        ("mrhs_engine", C.c_int),
+        ("mixed_fp64_factor", C.c_int),
     ]
 
 
@@ -144,7 +146,8 @@ def polycoeff_alpha(m: int, last: float = 7.0) -> list:
 def make_params(m: int = 2, alpha: Optional[Sequence[float]] = None, precision: int = BT_FP64,
                 tol_inner: float = 0.0, max_outer: int = 0, use_x0: bool = False, cycle_budget: int = 0,
                 stream=None, ctas_per_sm: int = 0, group_ctas: int = 0, stage_kb: int = 0,
-                a: float = 1.0, h_matrix_free: bool = False):
+                a: float = 1.0, h_matrix_free: bool = False, mrhs_engine: int = 0,
+                mixed_fp64_factor: bool = False):
     """Build a bt_params; returns (params, keepalive)."""
     p = bt_params()
     lib().bt_params_init(C.byref(p))
@@ -164,6 +167,8 @@ def make_params(m: int = 2, alpha: Optional[Sequence[float]] = None, precision: 
     p.group_ctas = group_ctas
     p.stage_kb = stage_kb
     p.h_matrix_free = 1 if h_matrix_free else 0
+    p.mrhs_engine = mrhs_engine
+    p.mixed_fp64_factor = 1 if mixed_fp64_factor else 0
     return p, keep
 
 

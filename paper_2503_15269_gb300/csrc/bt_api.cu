@@ -22,13 +22,16 @@ extern "C" cudaError_t bt_persistent_occupancy(int mt_is_float, int variant, int
 extern "C" cudaError_t bt_launch_setup(const bt::SetupParams* P, int mixed, int m, int maxn, cudaStream_t st);
 extern "C" cudaError_t bt_launch_adjoint(const bt::AdjParams* P, cudaStream_t st);
 namespace bt { struct MParams; }
-extern "C" int bt_mrhs_smem_bytes(int n);
-extern "C" cudaError_t bt_mrhs_occupancy(int smem, int* blocks);
+extern "C" int bt_mrhs_smem_bytes(int n, int tc);
+extern "C" int bt_mrhs_tc_supported(int n);
+extern "C" cudaError_t bt_mrhs_occupancy(int smem, int tc, int* blocks);
+extern "C" cudaError_t bt_mrhs_images(int N, int n, int m, const float* const* blk32, int bs32, float* const* img,
+                                      cudaStream_t st);
 extern "C" cudaError_t bt_mrhs_solve_launch(int N, int n, int m, const double* alpha, const float* const* blk32,
                                             const double* D64, const double* O64, int bs32, int bs64,
-                                            void* const* vec, double tol, double tol_inner, int maxit,
-                                            int max_outer, long long budget, int G, int nrhs, const double* B,
-                                            double* X, int smem, cudaStream_t st);
+                                            void* const* vec, const float* const* img, double tol, double tol_inner,
+                                            int maxit, int max_outer, long long budget, int G, int nrhs,
+                                            const double* B, double* X, int smem, cudaStream_t st);
 
 namespace {
 
@@ -95,6 +98,7 @@ struct bt_ctx {
   // many-right-hand-side workspace (allocated on the first bt_pcg_solve_multi)
   void* mr_vec[16] = {};
   int mr_G = 0, mr_smem = 0, mr_outer = 0;
+  float* mr_img[9] = {};  // block images of the tensor-core many-RHS engine
   std::vector<double> mr_resid;
 };
 
@@ -188,6 +192,8 @@ bt_status check_params(const bt_params* p, double* alpha_out) {
     return BT_ERR_PARAM;
   // the matrix-free H applies H_opt = H_J^2: the optimum only
   if (p->h_matrix_free != 0 && (p->h_matrix_free != 1 || p->a != 1.0)) return BT_ERR_PARAM;
+  if (p->mrhs_engine < 0 || p->mrhs_engine > 2) return BT_ERR_PARAM;
+  if (p->mixed_fp64_factor != 0 && p->mixed_fp64_factor != 1) return BT_ERR_PARAM;
   return BT_OK;
 }
 
@@ -1101,10 +1107,8 @@ bt_status bt_pcg_solve_multi(bt_handle h, const double* B, double* X, int nrhs, 
       if ((s = dalloc(h, &f, cnt)) != BT_OK) return s;
       h->mr_vec[i] = f;
     }
-    h->mr_smem = bt_mrhs_smem_bytes(n);
-    int occ = 0;
-    if (bt_mrhs_occupancy(h->mr_smem, &occ) != cudaSuccess || occ < 1) return BT_ERR_CUDA;
-    h->mr_G = std::max(1, std::min(h->sms * occ, N));
+    // one CTA per SM in either engine (both need more than half the shared memory)
+    h->mr_G = std::max(1, std::min(h->sms, N));
     double* red = nullptr;
     if ((s = dalloc(h, &red, (size_t)2 * h->mr_G * kJ)) != BT_OK) return s;
     h->mr_vec[11] = red;
@@ -1120,14 +1124,35 @@ bt_status bt_pcg_solve_multi(bt_handle h, const double* B, double* X, int nrhs, 
     if ((s = dalloc(h, &f, cnt)) != BT_OK) return s;  // second p buffer
     h->mr_vec[15] = f;
   }
-  if (cudaMemsetAsync(h->mr_vec[12], 0, 64 * sizeof(int), h->stream)) return BT_ERR_CUDA;
+  // engine: tensor cores (3xTF32) where supported, unless the caller asks for SIMT
+  const int tc_ok = bt_mrhs_tc_supported(n);
+  if (h->prm.mrhs_engine == 2 && !tc_ok) return BT_ERR_ARG;
+  const int tc = (h->prm.mrhs_engine == 2 || (h->prm.mrhs_engine == 0 && tc_ok)) ? 1 : 0;
   const float* blk32[7] = {h->D32, h->O32, h->Dinv32, h->E32, h->Hd32, h->Hu32, h->Hl32};
+  const int bs32 = bt::slot32(n), bs64 = (int)rup((long long)n * n, 2);
+  if (tc) {
+    if (!h->mr_img[8]) {
+      for (int i = 0; i < 9; ++i) {
+        bt_status s2 = dalloc(h, &h->mr_img[i], (size_t)N * n * n);
+        if (s2 != BT_OK) return s2;
+      }
+    }
+    // the images follow the handle's current blocks (a refactor may have changed them)
+    if (bt_mrhs_images(N, n, h->prm.m, blk32, bs32, h->mr_img, h->stream) != cudaSuccess) return BT_ERR_CUDA;
+  }
+  h->mr_smem = bt_mrhs_smem_bytes(n, tc);
+  {
+    int occ = 0;
+    if (bt_mrhs_occupancy(h->mr_smem, tc, &occ) != cudaSuccess || occ < 1) return BT_ERR_CUDA;
+    if (h->mr_G > h->sms * occ) return BT_ERR_CUDA;
+  }
+  if (cudaMemsetAsync(h->mr_vec[12], 0, 64 * sizeof(int), h->stream)) return BT_ERR_CUDA;
   const double tin = h->prm.tol_inner > 0 ? h->prm.tol_inner : 1e-5;  // measured best for the 64-column solve
   const int mo = h->prm.max_outer > 0 ? h->prm.max_outer : 30;
   const long long budget = h->prm.cycle_budget > 0 ? h->prm.cycle_budget : (1ll << 36);
-  const int bs32 = bt::slot32(n), bs64 = (int)rup((long long)n * n, 2);
-  cudaError_t e = bt_mrhs_solve_launch(N, n, h->prm.m, h->alpha, blk32, h->D64, h->O64, bs32, bs64, h->mr_vec, tol,
-                                       tin, maxit, mo, budget, h->mr_G, nrhs, B, X, h->mr_smem, h->stream);
+  cudaError_t e = bt_mrhs_solve_launch(N, n, h->prm.m, h->alpha, blk32, h->D64, h->O64, bs32, bs64, h->mr_vec,
+                                       tc ? h->mr_img : nullptr, tol, tin, maxit, mo, budget, h->mr_G, nrhs, B, X,
+                                       h->mr_smem, h->stream);
   if (e != cudaSuccess) return BT_ERR_CUDA;
   std::vector<int> ri(3 * kJ);
   std::vector<double> rd(kJ);

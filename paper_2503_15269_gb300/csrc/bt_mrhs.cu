@@ -40,6 +40,11 @@ constexpr int kVB = 2;              // float4s a thread loads before storing in 
 struct MParams {
   const float *D32, *O32, *Dinv32, *E32, *Hd32, *Hu32, *Hl32;  // library layout (column-major, padded)
   const double *D64, *O64;
+  // Tensor-core engine: per block row, the block Q of each product out = Q x
+  // as a K-major core-matrix image (see k_mrhs_image), n*n floats per row:
+  // role 0 (block (c, c)): D, D^-1, Hd; role 1 (block (c+k, c)): O^T, -E^T, Hl;
+  // role 2 (block (c-k, c), stored at index c-k): O, -E, Hu.
+  const float *img_d, *img_dinv, *img_hd, *img_ot, *img_et, *img_hl, *img_o, *img_e, *img_hu;
   int N, n, bs32, bs64, m;
   float alpha[kMaxM];
   // float64 vectors [N][n][J]
@@ -140,6 +145,11 @@ struct MSolver {
   bool fail;
   double* colbuf;   // smem [kJ] scratch for reduced values
   double* colred;   // smem scratch for the cross-CTA column sums ([kMThreads / kJ][kJ])
+  // tensor-core engine: TMEM base address, and the counts behind the mbarrier
+  // phases (identical in every thread): columns whose data was waited for /
+  // issued, MMA commits waited for / issued
+  unsigned tmem;
+  int gcol, iss, mma_done, mma_iss;
 
   __device__ MSolver(const MParams& P_, char* sm_) : P(P_), sm(sm_) {}
 
@@ -439,6 +449,286 @@ __device__ void msweep32(MSolver& Sv, int phase, const float* v_in, const float*
   msweep_ring(Sv, phase, v_in, pre, fd, fin, blk);
 }
 
+// ------------------------------------------------------------ tensor cores
+// The tensor-core engine (row of the many-RHS path where the work is a dense
+// contraction): every product out = Q x of a sweep is an n x n by n x 64
+// contraction, computed transposed, out^T = x^T Q^T, by tcgen05.mma kind::tf32
+// with M = 64 (the right-hand-side columns), N = n, K = 8 per instruction,
+// accumulating in tensor memory (TMEM).  Both operands are K-major
+// SWIZZLE_NONE core-matrix images in shared memory: 8 rows x 16 bytes per core
+// matrix, element (row a, k) of an operand at
+//     ((a / 8) * (n / 4) + k / 4) * 32 + (a % 8) * 4 + k % 4     (floats),
+// so the K-direction core stride (LBO) is 128 bytes and the 8-row stride
+// (SBO) 32 n bytes.  Float32 accuracy from TF32 units: each operand is split
+// x = hi + lo with hi = tf32(x) and lo = tf32(x - hi) (rounded: the tensor
+// cores read the top 19 bits of each operand and drop the rest), and each
+// product takes three MMAs, hi.hi + hi.lo + lo.hi, in float32 accumulation.
+// The M = 64 accumulator keeps rows 16 q .. 16 q + 15 in TMEM lanes
+// 32 q .. 32 q + 15 (q = 0..3), column r of out^T in TMEM column r.
+constexpr int kTcMaxN = 48;
+constexpr unsigned kTmemCols = 512;
+constexpr int kTcRing = 5;  // raw vector rows held: k + 3 for the H sweeps (k = 2)
+
+__device__ __forceinline__ uint64_t tc_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+// instruction descriptor: D float32, A and B tf32, both K-major, M = 64, N = n
+__device__ __forceinline__ unsigned tc_idesc(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(n >> 3) << 17) | (4u << 24);
+}
+__device__ __forceinline__ void tc_mma(unsigned d, uint64_t a, uint64_t b, unsigned id, unsigned acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(id), "r"(acc)
+      : "memory");
+}
+// the mbarrier completes once every MMA this thread issued before it has finished
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// 8 consecutive TMEM columns of the warp's 32 lanes (lane = thread)
+__device__ __forceinline__ void tc_ld8(unsigned ta, float (&v)[8]) {
+  unsigned r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(ta)
+               : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tc_alloc(unsigned* slot) {  // one warp
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+               "r"(kTmemCols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc_dealloc(unsigned taddr) {  // one warp
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTmemCols) : "memory");
+}
+// x rounded to TF32 (11 significant bits, ties away from zero) on its bit pattern
+__device__ __forceinline__ float tf32_round(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xffffe000u);
+}
+__device__ __forceinline__ void split4(const float4 v, float4& h, float4& l) {
+  h = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
+  l = make_float4(tf32_round(v.x - h.x), tf32_round(v.y - h.y), tf32_round(v.z - h.z), tf32_round(v.w - h.w));
+}
+__device__ __forceinline__ float comp(const float4& v, int i) { return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w)); }
+
+// Shared memory of the tensor-core sweeps (floats, after the common prefix):
+//   blk   [2][3][n n]  block images of two columns (split to hi in place)
+//   blo   [3][n n]     their lo parts
+//   ahi, alo [64 n]    the column's vector row as the A image
+//   ring  [5][n 64]    raw vector rows (the finalize reads its row's)
+//   stage [n 64]       the finished row, [n][64]
+__host__ __device__ constexpr int mrhs_tc_floats(int n) { return 9 * n * n + (3 + kTcRing) * n * kJ; }
+constexpr int kTcBarOff = 64;  // bytes: full[2], mma, TMEM slot (in the flag words)
+
+// One sweep (A, B1 or B2) on the tensor cores, in column form: column c's
+// vector row x_c multiplies the three blocks of block column c, accumulating
+// into rows c - k, c, c + k (k = 2 for H, else 1), each row in its own TMEM
+// accumulator (2k + 2 of them, row t in slot t % (2k + 2)).  Row t is finished
+// -- TMEM to shared memory, then the finalize functor per 4x4 tile -- one
+// column after its last product (column t + k).  A CTA processes the columns
+// s - k .. e + k - 1 of its rows [s, e); a halo column contributes to the
+// owned rows only.  Thread 0 issues the bulk copies of column c + 2 once the
+// MMAs of column c (which read its buffers) are done, and the MMAs of each
+// column; the split into TF32 parts, the finalize and the TMEM reads run on
+// all threads, the finalize of row c - 1 - k overlapping the MMAs of column c.
+template <typename Fin>
+__device__ void msweep_tc(MSolver& Sv, int phase, const float* v_in, const float* pre, Fin fin) {
+  const MParams& P = Sv.P;
+  const int n = Sv.n, N = Sv.N, s = Sv.s, e = Sv.e;
+  __syncthreads();
+  if (e <= s || Sv.fail) return;
+  const int tid = threadIdx.x;
+  const int k = (phase == MP_B2) ? 2 : 1;
+  const int R = k + 3, S = 2 * k + 2;
+  const int bb = n * n, vb = n * kJ, nk4 = n / 4;
+  const int c_lo = max(0, s - k), c_hi = min(N, e + k);
+  const float* img0 = phase == MP_A ? P.img_d : (phase == MP_B1 ? P.img_dinv : P.img_hd);
+  const float* img1 = phase == MP_A ? P.img_ot : (phase == MP_B1 ? P.img_et : P.img_hl);
+  const float* img2 = phase == MP_A ? P.img_o : (phase == MP_B1 ? P.img_e : P.img_hu);
+  float* blk = reinterpret_cast<float*>(Sv.sm + kMSmJobs);
+  float* blo = blk + 6 * bb;
+  float* ahi = blk + 9 * bb;
+  float* alo = ahi + vb;
+  float* ring = alo + vb;
+  float* stage = ring + kTcRing * vb;
+  uint64_t* full = reinterpret_cast<uint64_t*>(Sv.sm + kTcBarOff);
+  uint64_t* mbar = full + 2;
+  const auto slot = [&](int r) { return ring + (size_t)(r % R) * vb; };
+  // role 0: row c (block (c, c)); 1: row c + k; 2: row c - k
+  const auto target = [&](int c, int role) { return role == 0 ? c : (role == 1 ? c + k : c - k); };
+  const auto role_ok = [&](int c, int role) {
+    const int t = target(c, role);
+    return t >= s && t < e && t < N;
+  };
+  const auto issue = [&](int c, int buf) {  // thread 0
+    unsigned bytes = (unsigned)vb * 4u;
+    for (int r = 0; r < 3; ++r)
+      if (role_ok(c, r)) bytes += (unsigned)bb * 4u;
+    mbar_arrive_expect_tx(full + buf, bytes);
+    for (int r = 0; r < 3; ++r) {
+      if (!role_ok(c, r)) continue;
+      const float* src = r == 0 ? img0 + (size_t)c * bb : (r == 1 ? img1 + (size_t)c * bb : img2 + (size_t)(c - k) * bb);
+      bulk_g2s(blk + (size_t)(buf * 3 + r) * bb, src, (unsigned)bb * 4u, full + buf);
+    }
+    bulk_g2s(slot(c), v_in + (size_t)c * vb, (unsigned)vb * 4u, full + buf);
+  };
+  if (tid == 0) {
+    fence_proxy_async_smem();
+    if (c_lo < c_hi) issue(c_lo, Sv.gcol & 1);
+    if (c_lo + 1 < c_hi) issue(c_lo + 1, (Sv.gcol + 1) & 1);
+  }
+  Sv.iss = Sv.gcol + min(2, c_hi - c_lo);
+  bool bad = false;
+  for (int c = c_lo; c <= e + k && !bad; ++c) {  // step e + k finishes row e - 1
+    const bool proc = c < c_hi;
+    const int buf = Sv.gcol & 1;
+    if (proc) {
+      const bool ok = mbar_wait(full + buf, (unsigned)((Sv.gcol >> 1) & 1), Sv.deadline);
+      if (__syncthreads_or(!ok)) {
+        bad = true;
+        break;
+      }
+      // split the blocks (hi in place, lo beside) and the vector row (transposed into the A image)
+      for (int r = 0; r < 3; ++r) {
+        if (!role_ok(c, r)) continue;
+        float4* h4 = reinterpret_cast<float4*>(blk + (size_t)(buf * 3 + r) * bb);
+        float4* l4 = reinterpret_cast<float4*>(blo + (size_t)r * bb);
+        for (int q = tid; q < bb / 4; q += kMThreads) {
+          float4 h, l;
+          split4(h4[q], h, l);
+          h4[q] = h;
+          l4[q] = l;
+        }
+      }
+      {
+        const float* xr = slot(c);
+        for (int q = tid; q < nk4 * 16; q += kMThreads) {
+          const int k4 = q >> 4, j4 = q & 15;
+          float4 rv[4];
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) rv[kk] = *reinterpret_cast<const float4*>(xr + (4 * k4 + kk) * kJ + 4 * j4);
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const int j = 4 * j4 + jj;
+            float4 h, l;
+            split4(make_float4(comp(rv[0], jj), comp(rv[1], jj), comp(rv[2], jj), comp(rv[3], jj)), h, l);
+            const int off = ((j >> 3) * nk4 + k4) * 32 + (j & 7) * 4;
+            *reinterpret_cast<float4*>(ahi + off) = h;
+            *reinterpret_cast<float4*>(alo + off) = l;
+          }
+        }
+      }
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        const unsigned id = tc_idesc(n);
+        const unsigned sbo = 32u * (unsigned)n;
+        const unsigned a_hi = smem_u32(ahi), a_lo = smem_u32(alo);
+        for (int r = 0; r < 3; ++r) {
+          if (!role_ok(c, r)) continue;
+          const int t = target(c, r);
+          // the first product into a row: role 1, or role 0 when column c - k does not exist
+          const bool first = (r == 1) || (r == 0 && c - k < 0);
+          const unsigned d = Sv.tmem + (unsigned)((t % S) * 64);
+          const unsigned b_hi = smem_u32(blk + (size_t)(buf * 3 + r) * bb);
+          const unsigned b_lo = smem_u32(blo + (size_t)r * bb);
+          unsigned acc = first ? 0u : 1u;
+          for (int ks = 0; ks < n / 8; ++ks) {
+            const unsigned o = 256u * (unsigned)ks;
+            tc_mma(d, tc_desc(a_hi + o, 128, sbo), tc_desc(b_hi + o, 128, sbo), id, acc);
+            acc = 1u;
+            tc_mma(d, tc_desc(a_hi + o, 128, sbo), tc_desc(b_lo + o, 128, sbo), id, 1u);
+            tc_mma(d, tc_desc(a_lo + o, 128, sbo), tc_desc(b_hi + o, 128, sbo), id, 1u);
+          }
+        }
+        tc_commit(mbar);
+      }
+      ++Sv.mma_iss;
+    }
+    // finish row t = c - 1 - k (its last product came from column <= c - 1)
+    const int t = c - 1 - k;
+    if (t >= s && t < e) {
+      tc_fence_after();
+      const int warp = tid >> 5, lane = tid & 31, q = warp & 3;
+      const unsigned base = Sv.tmem + (unsigned)((t % S) * 64) + ((unsigned)(32 * q) << 16);
+      for (int ch = warp >> 2; ch < n / 8; ch += kMThreads / 128) {
+        float v[8];
+        tc_ld8(base + 8u * (unsigned)ch, v);
+        if (lane < 16) {
+          const int j = 16 * q + lane;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) stage[(8 * ch + i) * kJ + j] = v[i];
+        }
+      }
+      tc_fence_before();
+      __syncthreads();
+      if (tid < 4 * n) {
+        const int a0 = 4 * (tid >> 4), j0 = 4 * (tid & 15);
+        float out[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const float4 w = *reinterpret_cast<const float4*>(stage + (a0 + r) * kJ + j0);
+          out[r][0] = w.x; out[r][1] = w.y; out[r][2] = w.z; out[r][3] = w.w;
+        }
+        const float4* pf = nullptr;
+        int pstride = 0;
+        if (pre) {
+          pf = reinterpret_cast<const float4*>(pre + (size_t)t * vb + (size_t)a0 * kJ + j0);
+          pstride = kJ / 4;
+        }
+        fin(t, a0, j0, out, slot(t), pf, pstride);
+      }
+      __syncthreads();
+    }
+    if (proc) {
+      const bool ok = mbar_wait(mbar, (unsigned)(Sv.mma_done & 1), Sv.deadline);
+      if (__syncthreads_or(!ok)) {
+        bad = true;
+        break;
+      }
+      ++Sv.mma_done;
+      ++Sv.gcol;
+      if (c + 2 < c_hi) {
+        if (tid == 0) {
+          fence_proxy_async_smem();
+          issue(c + 2, buf);
+        }
+        ++Sv.iss;
+      }
+    }
+  }
+  if (bad) {
+    // let every copy and MMA this CTA started finish (bounded) before the
+    // kernel goes on to release TMEM and exit
+    const long long lim = clock64() + (1ll << 31);
+    for (int gc = Sv.gcol; gc < Sv.iss; ++gc) mbar_wait(full + (gc & 1), (unsigned)((gc >> 1) & 1), lim);
+    for (int m = Sv.mma_done; m < Sv.mma_iss; ++m) mbar_wait(mbar, (unsigned)(m & 1), lim);
+    Sv.gcol = Sv.iss;
+    Sv.mma_done = Sv.mma_iss;
+    Sv.fail = true;
+    if (tid == 0) atomicExch(P.abort_flag, 1);
+  }
+  __syncthreads();
+}
+
+template <bool TC, typename Fin>
+__device__ __forceinline__ void msweep(MSolver& Sv, int phase, const float* v_in, const float* pre, Fin fin,
+                                       const Fold& fd = Fold{nullptr, nullptr, nullptr}) {
+  if constexpr (TC) msweep_tc(Sv, phase, v_in, pre, fin);
+  else msweep32(Sv, phase, v_in, pre, fin, fd);
+}
+
 // The float64 refinement-residual sweep q = S x (Eq. 1) over the owned rows:
 // one job buffer (three float64 blocks and three vector rows) fills the
 // region the float32 sweeps double-buffer, so each row's copies complete
@@ -483,9 +773,26 @@ __device__ void msweep64(MSolver& Sv, const double* v_in, Fin fin) {
 }
 
 // The kernel: mixed-precision refinement around float32 PCG, all columns.
+// TC: block products on the tensor cores (msweep_tc), else float32 SIMT tiles.
+template <bool TC>
 __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_constant__ MParams P) {
   extern __shared__ __align__(128) char smem[];
   MSolver Sv(P, smem);
+  Sv.tmem = 0;
+  Sv.gcol = Sv.iss = Sv.mma_done = Sv.mma_iss = 0;
+  if constexpr (TC) {
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kTcBarOff);
+    unsigned* tslot = reinterpret_cast<unsigned*>(smem + kTcBarOff + 24);
+    if (threadIdx.x == 0) {
+      for (int b = 0; b < 3; ++b) mbar_init(bars + b, 1);
+      fence_mbar_init();
+    }
+    if (threadIdx.x < 32) tc_alloc(tslot);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    Sv.tmem = *tslot;
+  }
   Sv.g = blockIdx.x;
   Sv.G = P.G;
   Sv.N = P.N;
@@ -519,7 +826,7 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
   const size_t vb = (size_t)n * kJ;
   const int J = kJ;
   const int m = P.m;
-  const bool fold = 4 * n <= kMHalf;  // p update folded into the A sweep (the k-split layout)
+  const bool fold = !TC && 4 * n <= kMHalf;  // p update folded into the A sweep (the k-split layout)
 
   // ||b_j||^2 and x64 = 0 over the owned rows
   {
@@ -605,7 +912,7 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
       // r.z per column, summed in the finalize of the sweep that completes z
       Accum<float> pa[4];
       // B1: y0 = G r (r is the staged centre block of this sweep)
-      msweep32(Sv, MP_B1, P.R, nullptr, [&](int row, int a0, int j0, float (&o)[4][4], const float* xc, const float4*, int) {
+      msweep<TC>(Sv, MP_B1, P.R, nullptr, [&](int row, int a0, int j0, float (&o)[4][4], const float* xc, const float4*, int) {
         for (int r = 0; r < 4; ++r) {
           const size_t idx = (size_t)row * vb + (size_t)(a0 + r) * J + j0;
           const float4 y = make_float4(o[r][0], o[r][1], o[r][2], o[r][3]);
@@ -626,7 +933,7 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
         float* yout = (jp % 2 == 1) ? P.Ya : P.Yb;
         const float aj = P.alpha[jp];
         const bool lastj = (jp == m - 1);
-        msweep32(Sv, MP_B2, yin, lastj ? P.R : nullptr,
+        msweep<TC>(Sv, MP_B2, yin, lastj ? P.R : nullptr,
                  [&](int row, int a0, int j0, float (&o)[4][4], const float* yc, const float4* rpf, int rst) {
           for (int r = 0; r < 4; ++r) {
             const size_t idx = (size_t)row * vb + (size_t)(a0 + r) * J + j0;
@@ -678,7 +985,7 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
       ++total_it;
       // A: q = S p, pq per column
       Accum<float> pa[4];
-      msweep32(Sv, MP_A, Pc, nullptr, [&](int row, int a0, int j0, float (&o)[4][4], const float* pc, const float4*, int) {
+      msweep<TC>(Sv, MP_A, Pc, nullptr, [&](int row, int a0, int j0, float (&o)[4][4], const float* pc, const float4*, int) {
         for (int r = 0; r < 4; ++r) {
           const size_t idx = (size_t)row * vb + (size_t)(a0 + r) * J + j0;
           stv4(P.Q, idx, make_float4(o[r][0], o[r][1], o[r][2], o[r][3]));
@@ -817,6 +1124,14 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
     P.resid[tid] = nbv[tid] > 0.0 ? nrv[tid] / nbv[tid] : 0.0;
     P.outer[tid] = outer;
   }
+  if constexpr (TC) {  // every MMA was waited for (or drained after a timeout)
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      tc_fence_after();
+      tc_dealloc(Sv.tmem);
+    }
+  }
 }
 
 // Layout conversion: caller [N*n][nrhs] (row-major) <-> internal [N][n][kJ].
@@ -835,46 +1150,99 @@ __global__ void k_mrhs_out(const double* X64, double* X, long long rows, int nrh
   X[t] = X64[r * kJ + j];
 }
 
+// Q_i as the K-major core-matrix image of the tensor-core engine: element
+// (a, b) of Q_i at ((a / 8) * (n / 4) + b / 4) * 32 + (a % 8) * 4 + b % 4,
+// Q_i = sign * M_i (trans = 0) or sign * M_i^T (trans = 1), M_i read from the
+// library's column-major float32 slot (M_i(a, b) at b * n + a).
+__global__ void k_mrhs_image(const float* src, int bs32, float* dst, int N, int n, int trans, float sign) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long bb = (long long)n * n;
+  if (t >= (long long)N * bb) return;
+  const long long i = t / bb;
+  const int w = (int)(t - i * bb);
+  const int a = w / n, b = w - (w / n) * n;
+  const float v = trans ? src[i * bs32 + (long long)a * n + b] : src[i * bs32 + (long long)b * n + a];
+  dst[i * bb + ((a >> 3) * (n >> 2) + (b >> 2)) * 32 + (a & 7) * 4 + (b & 3)] = sign * v;
+}
+
 }  // namespace bt
 
-// jobs, plus the staged finalize tiles when the k range is split (n <= 48)
-extern "C" int bt_mrhs_smem_bytes(int n) { return kMSmJobs + mrhs_job_bytes(n) + (4 * n <= kMHalf ? 4 * kMHalf * 16 : 0); }
+// Shared memory of the many-RHS kernel: the common prefix, then the jobs (plus
+// the staged finalize tiles when the k range is split, n <= 48) for the SIMT
+// engine, or the tensor-core sweep buffers (which also hold the float64
+// residual sweep's job).
+extern "C" int bt_mrhs_smem_bytes(int n, int tc) {
+  if (tc) return kMSmJobs + bt::mrhs_tc_floats(n) * 4;
+  return kMSmJobs + mrhs_job_bytes(n) + (4 * n <= kMHalf ? 4 * kMHalf * 16 : 0);
+}
 
-extern "C" cudaError_t bt_launch_mrhs(const bt::MParams* P, const double* B, double* X, int smem, cudaStream_t st) {
+extern "C" int bt_mrhs_tc_supported(int n) { return n % 8 == 0 && n >= 8 && n <= bt::kTcMaxN; }
+
+static const void* mrhs_kernel(int tc) {
+  return tc ? (const void*)bt::bt_mrhs_kernel<true> : (const void*)bt::bt_mrhs_kernel<false>;
+}
+
+extern "C" cudaError_t bt_launch_mrhs(const bt::MParams* P, const double* B, double* X, int smem, int tc,
+                                      cudaStream_t st) {
   const long long rows = (long long)P->N * P->n;
   const int tb = 256;
   bt::k_mrhs_in<<<(unsigned)((rows * bt::kJ + tb - 1) / tb), tb, 0, st>>>(B, const_cast<double*>(P->B64), rows,
                                                                          P->nrhs);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(bt::bt_mrhs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const void* kern = mrhs_kernel(tc);
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)P};
-  e = cudaLaunchCooperativeKernel((const void*)bt::bt_mrhs_kernel, dim3(P->G), dim3(bt::kMThreads), args, smem, st);
+  e = cudaLaunchCooperativeKernel(kern, dim3(P->G), dim3(bt::kMThreads), args, smem, st);
   if (e != cudaSuccess) return e;
   bt::k_mrhs_out<<<(unsigned)((rows * P->nrhs + tb - 1) / tb), tb, 0, st>>>(P->X64, X, rows, P->nrhs);
   return cudaGetLastError();
 }
 
-extern "C" cudaError_t bt_mrhs_occupancy(int smem, int* blocks) {
-  cudaError_t e = cudaFuncSetAttribute(bt::bt_mrhs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+extern "C" cudaError_t bt_mrhs_occupancy(int smem, int tc, int* blocks) {
+  const void* kern = mrhs_kernel(tc);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, bt::bt_mrhs_kernel, bt::kMThreads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, bt::kMThreads, smem);
+}
+
+// The nine block images of the tensor-core engine from the float32 slots
+// (img: D, D^-1, Hd, O^T, -E^T, Hl, O, -E, Hu; H images only for m >= 2).
+extern "C" cudaError_t bt_mrhs_images(int N, int n, int m, const float* const* blk32, int bs32, float* const* img,
+                                      cudaStream_t st) {
+  // blk32: D, O, D^-1, E, Hd, Hu, Hl
+  const float* src[9] = {blk32[0], blk32[2], blk32[4], blk32[1], blk32[3], blk32[6], blk32[1], blk32[3], blk32[5]};
+  const int trans[9] = {0, 0, 0, 1, 1, 0, 0, 0, 0};
+  const float sign[9] = {1.f, 1.f, 1.f, 1.f, -1.f, 1.f, 1.f, -1.f, 1.f};
+  const long long tot = (long long)N * n * n;
+  const int tb = 256;
+  for (int i = 0; i < 9; ++i) {
+    if ((i == 2 || i == 5 || i == 8) && m < 2) continue;
+    bt::k_mrhs_image<<<(unsigned)((tot + tb - 1) / tb), tb, 0, st>>>(src[i], bs32, img[i], N, n, trans[i], sign[i]);
+  }
+  return cudaGetLastError();
 }
 
 // Host launcher: fills the kernel parameters from plain pointers (the
 // workspace vector list is B64, X64, R64, Xin, R, P, Q, Y0, Ya, Yb, Z, red,
-// ctl, int results [iters | status | outer], double results [resid], P2).
+// ctl, int results [iters | status | outer], double results [resid], P2;
+// img: the nine block images for the tensor-core engine, or null).
 extern "C" cudaError_t bt_mrhs_solve_launch(int N, int n, int m, const double* alpha, const float* const* blk32,
                                             const double* D64, const double* O64, int bs32, int bs64,
-                                            void* const* vec, double tol, double tol_inner, int maxit,
-                                            int max_outer, long long budget, int G, int nrhs, const double* B,
-                                            double* X, int smem, cudaStream_t st) {
+                                            void* const* vec, const float* const* img, double tol, double tol_inner,
+                                            int maxit, int max_outer, long long budget, int G, int nrhs,
+                                            const double* B, double* X, int smem, cudaStream_t st) {
   bt::MParams P{};
   P.D32 = blk32[0]; P.O32 = blk32[1]; P.Dinv32 = blk32[2]; P.E32 = blk32[3];
   P.Hd32 = blk32[4]; P.Hu32 = blk32[5]; P.Hl32 = blk32[6];
   P.D64 = D64;
   P.O64 = O64;
+  if (img) {
+    P.img_d = img[0]; P.img_dinv = img[1]; P.img_hd = img[2];
+    P.img_ot = img[3]; P.img_et = img[4]; P.img_hl = img[5];
+    P.img_o = img[6]; P.img_e = img[7]; P.img_hu = img[8];
+  }
   P.N = N; P.n = n; P.bs32 = bs32; P.bs64 = bs64; P.m = m;
   for (int j = 0; j < bt::kMaxM; ++j) P.alpha[j] = j < m ? (float)alpha[j] : 0.0f;
   P.B64 = static_cast<const double*>(vec[0]);
@@ -905,5 +1273,5 @@ extern "C" cudaError_t bt_mrhs_solve_launch(int N, int n, int m, const double* a
   P.budget = budget;
   P.G = G;
   P.nrhs = nrhs;
-  return bt_launch_mrhs(&P, B, X, smem, st);
+  return bt_launch_mrhs(&P, B, X, smem, img ? 1 : 0, st);
 }

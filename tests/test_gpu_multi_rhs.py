@@ -22,8 +22,8 @@ def _lib():
     bb.lib()
 
 
-def solve_multi(inst, nrhs, tol, maxit=20000, m=2, alpha=(1.0, 7.0)):
-    p, keep = bb.make_params(m=m, alpha=list(alpha), precision=bb.BT_MIXED)
+def solve_multi(inst, nrhs, tol, maxit=20000, m=2, alpha=(1.0, 7.0), engine=0):
+    p, keep = bb.make_params(m=m, alpha=list(alpha), precision=bb.BT_MIXED, mrhs_engine=engine)
     st, h = bb.bt_setup(inst.N, inst.n, dev(inst.D), dev(inst.O), p)
     assert st == bb.BT_OK
     try:
@@ -36,13 +36,33 @@ def solve_multi(inst, nrhs, tol, maxit=20000, m=2, alpha=(1.0, 7.0)):
     return st, its, sts, host(X).reshape(inst.N, inst.n, nrhs), infos
 
 
-# n <= 48: the k range of each product split over two thread halves (n = 4:
-# one half empty; n = 44: an odd number of row groups); n = 52, 64: one pass
+SIMT, TC = 1, 2  # mrhs_engine: float32 SIMT tiles, tensor cores (3xTF32)
+
+
+# SIMT, n <= 48: the k range of each product split over two thread halves (n =
+# 4: one half empty; n = 44: an odd number of row groups); n = 52, 64: one pass
+
 @pytest.mark.parametrize("N,n,nrhs", [(1, 4, 3), (2, 4, 64), (7, 8, 5), (33, 12, 64), (20, 16, 17), (9, 44, 64),
                                       (5, 52, 7), (6, 64, 64)])
 def test_multi_rhs_matches_direct_solves(N, n, nrhs):
     inst = wl.small_llt(60, N, n, nrhs=nrhs)
-    st, its, sts, X, infos = solve_multi(inst, nrhs, 1e-12)
+    st, its, sts, X, infos = solve_multi(inst, nrhs, 1e-12, engine=SIMT)
+    assert st == bb.BT_OK and (sts == 0).all()
+    xr = orc.direct_solve(inst.D, inst.O, inst.b)
+    for j in range(nrhs):
+        err = np.linalg.norm(X[:, :, j] - xr[:, :, j]) / np.linalg.norm(xr[:, :, j])
+        assert err <= 1e-8, (j, err)
+        assert infos[j][2] <= 1e-12
+
+
+# tensor-core engine (n a multiple of 8, n <= 48): one CTA (N = 1, 2: no
+# neighbours), rows split over many CTAs with halo columns on both sides (N
+# small against the 152 CTAs: CTAs of one row), ragged column counts
+@pytest.mark.parametrize("N,n,nrhs", [(1, 8, 3), (2, 8, 64), (3, 16, 64), (7, 8, 5), (40, 24, 64), (17, 40, 33),
+                                      (9, 48, 64), (300, 16, 64), (5, 32, 1)])
+def test_multi_rhs_tensor_cores_match_direct_solves(N, n, nrhs):
+    inst = wl.small_llt(70, N, n, nrhs=nrhs)
+    st, its, sts, X, infos = solve_multi(inst, nrhs, 1e-12, engine=TC)
     assert st == bb.BT_OK and (sts == 0).all()
     xr = orc.direct_solve(inst.D, inst.O, inst.b)
     for j in range(nrhs):
@@ -115,16 +135,48 @@ def test_config3_many_rhs_full_size_error_1e8():
 
 
 @pytest.mark.parametrize("m,alpha", [(1, (1.0,)), (3, (1.0, 1.0, 1.0)), (3, (1.0, 2.0, 3.0))])
-@pytest.mark.parametrize("N,n", [(13, 12), (9, 48), (4, 64)])
-def test_multi_rhs_polynomial_orders(m, alpha, N, n):
+@pytest.mark.parametrize("N,n,engine", [(13, 12, SIMT), (9, 48, SIMT), (4, 64, SIMT), (9, 48, TC), (31, 16, TC)])
+def test_multi_rhs_polynomial_orders(m, alpha, N, n, engine):
     """m = 1 (z from the G sweep alone) and m = 3 (one H sweep summing into z
     from global memory, then the last one with r staged during the
-    products), on both product layouts (n <= 48 split in k, n = 64 not)."""
+    products), on both SIMT product layouts (n <= 48 split in k, n = 64 not)
+    and on the tensor cores."""
     inst = wl.small_llt(63 + m, N, n, nrhs=9)
-    st, its, sts, X, infos = solve_multi(inst, 9, 1e-12, m=m, alpha=alpha)
+    st, its, sts, X, infos = solve_multi(inst, 9, 1e-12, m=m, alpha=alpha, engine=engine)
     assert st == bb.BT_OK and (sts == 0).all()
     xr = orc.direct_solve(inst.D, inst.O, inst.b)
     for j in range(9):
         err = np.linalg.norm(X[:, :, j] - xr[:, :, j]) / np.linalg.norm(xr[:, :, j])
         assert err <= 1e-8, (j, err)
         assert infos[j][2] <= 1e-12
+
+
+def test_multi_rhs_engines_agree_and_tc_rejects_unsupported_n():
+    """Both engines on one LQR system (n = 24): the same solutions to the
+    tolerance, iteration counts within a few; the tensor-core engine asked for
+    n = 12 (not a multiple of 8) returns BT_ERR_ARG."""
+    inst = wl.small_ocp(62, 200, 24)
+    rng = np.random.default_rng(3)
+    b = rng.standard_normal((inst.N, inst.n, 64))
+    multi = wl.Instance(D=inst.D, O=inst.O, b=b)
+    res = {}
+    for eng in (SIMT, TC):
+        st, its, sts, X, _ = solve_multi(multi, 64, 1e-10, engine=eng)
+        assert st == bb.BT_OK and (sts == 0).all()
+        res[eng] = (its, X)
+    assert np.abs(res[SIMT][0] - res[TC][0]).max() <= 3
+    xr = orc.direct_solve(inst.D, inst.O, b)
+    for eng in (SIMT, TC):
+        err = np.linalg.norm(res[eng][1] - xr) / np.linalg.norm(xr)
+        assert err <= 1e-8, (eng, err)
+    small = wl.small_ocp(63, 10, 12)
+    p, keep = bb.make_params(m=2, alpha=[1.0, 7.0], precision=bb.BT_MIXED, mrhs_engine=TC)
+    st, h = bb.bt_setup(small.N, small.n, dev(small.D), dev(small.O), p)
+    assert st == bb.BT_OK
+    try:
+        B = dev(np.ones(small.N * small.n * 4))
+        X = dev(np.zeros(small.N * small.n * 4))
+        st, its, sts = bb.bt_pcg_solve_multi(h, B, X, 4, 1e-8, 100)
+        assert st == bb.BT_ERR_ARG
+    finally:
+        bb.bt_destroy(h)
