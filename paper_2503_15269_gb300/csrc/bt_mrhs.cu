@@ -23,6 +23,7 @@
 // one half adds the other's partial tile through shared memory before the
 // finalize.  The float64 residual sweep (once per refinement step) stages one
 // row job at a time.
+#include <algorithm>
 #include <cstdint>
 
 #include "../../include/bt.h"
@@ -453,30 +454,35 @@ __device__ void msweep32(MSolver& Sv, int phase, const float* v_in, const float*
 // The tensor-core engine (row of the many-RHS path where the work is a dense
 // contraction): every product out = Q x of a sweep is an n x n by n x 64
 // contraction, computed transposed, out^T = x^T Q^T, by tcgen05.mma kind::tf32
-// with M = 64 (the right-hand-side columns), N = n, K = 8 per instruction,
-// accumulating in tensor memory (TMEM).  Both operands are K-major
+// with N = n and K = 8 per instruction, accumulating in tensor memory (TMEM).
+// Both operands are K-major
 // SWIZZLE_NONE core-matrix images in shared memory: 8 rows x 16 bytes per core
 // matrix, element (row a, k) of an operand at
 //     ((a / 8) * (n / 4) + k / 4) * 32 + (a % 8) * 4 + k % 4     (floats),
 // so the K-direction core stride (LBO) is 128 bytes and the 8-row stride
 // (SBO) 32 n bytes.  Float32 accuracy from TF32 units: each operand is split
 // x = hi + lo with hi = tf32(x) and lo = tf32(x - hi) (rounded: the tensor
-// cores read the top 19 bits of each operand and drop the rest), and each
-// product takes three MMAs, hi.hi + hi.lo + lo.hi, in float32 accumulation.
-// The M = 64 accumulator keeps rows 16 q .. 16 q + 15 in TMEM lanes
-// 32 q .. 32 q + 15 (q = 0..3), column r of out^T in TMEM column r.
+// cores read the top 19 bits of each operand and drop the rest).  The A
+// operand stacks the two parts of the vector row, [x_hi^T; x_lo^T], into
+// M = 128 rows, so that per K step two MMAs (with Q_hi and Q_lo) form all four
+// partial products: TMEM lane j < 64 accumulates x_hi^T Q^T + x_hi^T Q_lo^T
+// for right-hand side j, lane 64 + j the x_lo terms; the finalize adds the two
+// (float32 accumulation throughout).  Row i of the M = 128 accumulator is
+// TMEM lane i, column r of out^T TMEM column r.
 constexpr int kTcMaxN = 48;
 constexpr unsigned kTmemCols = 512;
-constexpr int kTcRing = 5;  // raw vector rows held: k + 3 for the H sweeps (k = 2)
 
 __device__ __forceinline__ uint64_t tc_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
   return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
-// instruction descriptor: D float32, A and B tf32, both K-major, M = 64, N = n
+// instruction descriptor: D float32, A and B tf32, both K-major, M = 128, N = n
 __device__ __forceinline__ unsigned tc_idesc(int n) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(n >> 3) << 17) | (4u << 24);
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(n >> 3) << 17) | (8u << 24);
 }
+// thread that issues the MMAs and the bulk copies: lane 0 of the last warp,
+// which holds no finalize tile and reads no TMEM
+constexpr int kTcIssuer = kMThreads - 32;
 __device__ __forceinline__ void tc_mma(unsigned d, uint64_t a, uint64_t b, unsigned id, unsigned acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -521,26 +527,36 @@ __device__ __forceinline__ void split4(const float4 v, float4& h, float4& l) {
 }
 __device__ __forceinline__ float comp(const float4& v, int i) { return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w)); }
 
-// Shared memory of the tensor-core sweeps (floats, after the common prefix):
-//   blk   [2][3][n n]  block images of two columns (split to hi in place)
-//   blo   [3][n n]     their lo parts
-//   ahi, alo [64 n]    the column's vector row as the A image
-//   ring  [5][n 64]    raw vector rows (the finalize reads its row's)
-//   stage [n 64]       the finished row, [n][64]
-__host__ __device__ constexpr int mrhs_tc_floats(int n) { return 9 * n * n + (3 + kTcRing) * n * kJ; }
+// Shared memory of the tensor-core sweeps (floats, from kTcBase: the column
+// sums' scratch and the SIMT exchange tiles are idle during a sweep):
+//   bimg  [2][3][2][n n]  per column buffer and block: [hi | lo] B images (the
+//                         bulk copy lands in hi, the split writes lo)
+//   aimg  [2][64 n]       [hi; lo] A image of the column's vector row
+//   ring  [3][n 64]       raw vector rows (columns c .. c + 2)
+//   stage [2][n 64]       the finished row, [n][64]: x_hi and x_lo partial sums
+//   fbuf  [2][n 64]       the finished row's input and `pre` tiles ([n][64],
+//                         each finalize thread copies and reads its own tile)
+constexpr int kTcBase = kMSmScratch;
+__host__ __device__ constexpr int mrhs_tc_floats(int n) { return 12 * n * n + 9 * n * kJ; }
 constexpr int kTcBarOff = 64;  // bytes: full[2], mma, TMEM slot (in the flag words)
 
 // One sweep (A, B1 or B2) on the tensor cores, in column form: column c's
 // vector row x_c multiplies the three blocks of block column c, accumulating
-// into rows c - k, c, c + k (k = 2 for H, else 1), each row in its own TMEM
-// accumulator (2k + 2 of them, row t in slot t % (2k + 2)).  Row t is finished
-// -- TMEM to shared memory, then the finalize functor per 4x4 tile -- one
-// column after its last product (column t + k).  A CTA processes the columns
-// s - k .. e + k - 1 of its rows [s, e); a halo column contributes to the
-// owned rows only.  Thread 0 issues the bulk copies of column c + 2 once the
-// MMAs of column c (which read its buffers) are done, and the MMAs of each
-// column; the split into TF32 parts, the finalize and the TMEM reads run on
-// all threads, the finalize of row c - 1 - k overlapping the MMAs of column c.
+// into rows c - k, c, c + k (k = 2 for H, else 1).  Per block and K step one
+// MMA with A = [x_hi; x_lo] (M = 128) and B = [Q_hi | Q_lo] (N = 2n) forms the
+// four partial products of x^T Q^T into the row's TMEM accumulator (2k + 1 of
+// them, row t in slot t % (2k + 1), 2n columns each).  Step c of the loop:
+//   the finalize threads start copying the input (and `pre`) tiles of row
+//   t = c - 1 - k; wait for column c's data (issued two steps earlier); split
+//   it into TF32 parts; read row t (complete since column c - 1's MMAs, the
+//   last with a product into it, were waited for) from TMEM; issue the MMAs
+//   of column c (whose new row c + k reuses row t's slot); finalize row t
+//   from shared memory while they run; wait for them and issue the bulk
+//   copies of column c + 2 into the buffers they released.
+// A CTA processes the columns s - k .. e + k - 1 of its rows [s, e); a halo
+// column contributes to the owned rows only.  One thread (kTcIssuer) issues
+// the bulk copies and the MMAs; warps 0-7 read TMEM; the finalize tiles run on
+// threads < 4n.
 template <typename Fin>
 __device__ void msweep_tc(MSolver& Sv, int phase, const float* v_in, const float* pre, Fin fin) {
   const MParams& P = Sv.P;
@@ -549,28 +565,30 @@ __device__ void msweep_tc(MSolver& Sv, int phase, const float* v_in, const float
   if (e <= s || Sv.fail) return;
   const int tid = threadIdx.x;
   const int k = (phase == MP_B2) ? 2 : 1;
-  const int R = k + 3, S = 2 * k + 2;
+  const int S = 2 * k + 1;
+  const int slot_cols = (2 * n + 31) / 32 * 32;
   const int bb = n * n, vb = n * kJ, nk4 = n / 4;
   const int c_lo = max(0, s - k), c_hi = min(N, e + k);
   const float* img0 = phase == MP_A ? P.img_d : (phase == MP_B1 ? P.img_dinv : P.img_hd);
   const float* img1 = phase == MP_A ? P.img_ot : (phase == MP_B1 ? P.img_et : P.img_hl);
   const float* img2 = phase == MP_A ? P.img_o : (phase == MP_B1 ? P.img_e : P.img_hu);
-  float* blk = reinterpret_cast<float*>(Sv.sm + kMSmJobs);
-  float* blo = blk + 6 * bb;
-  float* ahi = blk + 9 * bb;
-  float* alo = ahi + vb;
-  float* ring = alo + vb;
-  float* stage = ring + kTcRing * vb;
+  float* bimg = reinterpret_cast<float*>(Sv.sm + kTcBase);
+  float* aimg = bimg + 12 * bb;
+  float* ring = aimg + 2 * vb;
+  float* stage = ring + 3 * vb;
+  float* xbuf = stage + 2 * vb;
+  float* pbuf = xbuf + vb;
   uint64_t* full = reinterpret_cast<uint64_t*>(Sv.sm + kTcBarOff);
   uint64_t* mbar = full + 2;
-  const auto slot = [&](int r) { return ring + (size_t)(r % R) * vb; };
+  const auto bptr = [&](int buf, int role) { return bimg + (size_t)(buf * 3 + role) * 2 * bb; };
+  const auto slot = [&](int r) { return ring + (size_t)(r % 3) * vb; };
   // role 0: row c (block (c, c)); 1: row c + k; 2: row c - k
   const auto target = [&](int c, int role) { return role == 0 ? c : (role == 1 ? c + k : c - k); };
   const auto role_ok = [&](int c, int role) {
     const int t = target(c, role);
     return t >= s && t < e && t < N;
   };
-  const auto issue = [&](int c, int buf) {  // thread 0
+  const auto issue = [&](int c, int buf) {  // kTcIssuer
     unsigned bytes = (unsigned)vb * 4u;
     for (int r = 0; r < 3; ++r)
       if (role_ok(c, r)) bytes += (unsigned)bb * 4u;
@@ -578,31 +596,44 @@ __device__ void msweep_tc(MSolver& Sv, int phase, const float* v_in, const float
     for (int r = 0; r < 3; ++r) {
       if (!role_ok(c, r)) continue;
       const float* src = r == 0 ? img0 + (size_t)c * bb : (r == 1 ? img1 + (size_t)c * bb : img2 + (size_t)(c - k) * bb);
-      bulk_g2s(blk + (size_t)(buf * 3 + r) * bb, src, (unsigned)bb * 4u, full + buf);
+      bulk_g2s(bptr(buf, r), src, (unsigned)bb * 4u, full + buf);
     }
     bulk_g2s(slot(c), v_in + (size_t)c * vb, (unsigned)vb * 4u, full + buf);
   };
-  if (tid == 0) {
+  if (tid == kTcIssuer) {
     fence_proxy_async_smem();
     if (c_lo < c_hi) issue(c_lo, Sv.gcol & 1);
     if (c_lo + 1 < c_hi) issue(c_lo + 1, (Sv.gcol + 1) & 1);
   }
   Sv.iss = Sv.gcol + min(2, c_hi - c_lo);
+  const int a0 = 4 * (tid >> 4), j0 = 4 * (tid & 15);  // finalize tile of threads < 4n
   bool bad = false;
-  for (int c = c_lo; c <= e + k && !bad; ++c) {  // step e + k finishes row e - 1
+  for (int c = c_lo; c <= e + k; ++c) {  // step e + k finishes row e - 1
     const bool proc = c < c_hi;
-    const int buf = Sv.gcol & 1;
+    const int buf = Sv.gcol & 1;  // buffers of column c (global column index gcol)
+    const int t = c - 1 - k;      // the row this step finishes
+    const bool fin_t = t >= s && t < e;
+    if (fin_t && tid < 4 * n) {  // this thread's input (and pre) tile of row t
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const size_t g = (size_t)t * vb + (size_t)(a0 + r) * kJ + j0;
+        cp16(xbuf + (a0 + r) * kJ + j0, v_in + g);
+        if (pre) cp16(pbuf + (a0 + r) * kJ + j0, pre + g);
+      }
+      cp_commit();
+    }
     if (proc) {
       const bool ok = mbar_wait(full + buf, (unsigned)((Sv.gcol >> 1) & 1), Sv.deadline);
       if (__syncthreads_or(!ok)) {
         bad = true;
         break;
       }
-      // split the blocks (hi in place, lo beside) and the vector row (transposed into the A image)
+      // split the blocks (hi in place, lo beside) and the vector row (transposed
+      // into the A image: one right-hand side j and four k per task)
       for (int r = 0; r < 3; ++r) {
         if (!role_ok(c, r)) continue;
-        float4* h4 = reinterpret_cast<float4*>(blk + (size_t)(buf * 3 + r) * bb);
-        float4* l4 = reinterpret_cast<float4*>(blo + (size_t)r * bb);
+        float4* h4 = reinterpret_cast<float4*>(bptr(buf, r));
+        float4* l4 = h4 + bb / 4;
         for (int q = tid; q < bb / 4; q += kMThreads) {
           float4 h, l;
           split4(h4[q], h, l);
@@ -610,86 +641,74 @@ __device__ void msweep_tc(MSolver& Sv, int phase, const float* v_in, const float
           l4[q] = l;
         }
       }
-      {
-        const float* xr = slot(c);
-        for (int q = tid; q < nk4 * 16; q += kMThreads) {
-          const int k4 = q >> 4, j4 = q & 15;
-          float4 rv[4];
+      const float* xr = slot(c);
+      for (int q = tid; q < 16 * n; q += kMThreads) {
+        const int j = q & 63, k4 = q >> 6;
+        float4 h, l;
+        split4(make_float4(xr[(4 * k4) * kJ + j], xr[(4 * k4 + 1) * kJ + j], xr[(4 * k4 + 2) * kJ + j],
+                           xr[(4 * k4 + 3) * kJ + j]),
+               h, l);
+        const int off = ((j >> 3) * nk4 + k4) * 32 + (j & 7) * 4;
+        *reinterpret_cast<float4*>(aimg + off) = h;
+        *reinterpret_cast<float4*>(aimg + vb + off) = l;
+      }
+    } else if (fin_t) {
+      __syncthreads();  // the previous finalize has read the stage
+    }
+    if (fin_t) {  // read row t from TMEM
+      tc_fence_after();
+      const int warp = tid >> 5, lane = tid & 31, q = warp & 3;
+      if (warp < 8) {  // lanes 0-63: x_hi terms of column j = lane + 32 q; 64-127: x_lo terms
+        const unsigned base = Sv.tmem + (unsigned)((t % S) * slot_cols) + ((unsigned)(32 * q) << 16);
+        float* st = stage + (q >> 1) * vb + 32 * (q & 1) + lane;
+        for (int ch = warp >> 2; ch < n / 8; ch += 2) {
+          float v[8], w[8];
+          tc_ld8(base + 8u * (unsigned)ch, v);                // x Q_hi^T
+          tc_ld8(base + (unsigned)n + 8u * (unsigned)ch, w);  // x Q_lo^T
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) rv[kk] = *reinterpret_cast<const float4*>(xr + (4 * k4 + kk) * kJ + 4 * j4);
-#pragma unroll
-          for (int jj = 0; jj < 4; ++jj) {
-            const int j = 4 * j4 + jj;
-            float4 h, l;
-            split4(make_float4(comp(rv[0], jj), comp(rv[1], jj), comp(rv[2], jj), comp(rv[3], jj)), h, l);
-            const int off = ((j >> 3) * nk4 + k4) * 32 + (j & 7) * 4;
-            *reinterpret_cast<float4*>(ahi + off) = h;
-            *reinterpret_cast<float4*>(alo + off) = l;
-          }
+          for (int i = 0; i < 8; ++i) st[(8 * ch + i) * kJ] = v[i] + w[i];
         }
       }
+    }
+    if (proc || fin_t) {
       fence_proxy_async_smem();
+      tc_fence_before();
       __syncthreads();
-      if (tid == 0) {
+    }
+    if (proc) {
+      if (tid == kTcIssuer) {
         tc_fence_after();
-        const unsigned id = tc_idesc(n);
+        const unsigned id = tc_idesc(2 * n);
         const unsigned sbo = 32u * (unsigned)n;
-        const unsigned a_hi = smem_u32(ahi), a_lo = smem_u32(alo);
+        // descriptors of K step 0; step ks starts 256 ks bytes later (16 ks in
+        // the address field)
+        const uint64_t da = tc_desc(smem_u32(aimg), 128, sbo);  // [x_hi; x_lo]
         for (int r = 0; r < 3; ++r) {
           if (!role_ok(c, r)) continue;
-          const int t = target(c, r);
+          const int tr = target(c, r);
           // the first product into a row: role 1, or role 0 when column c - k does not exist
           const bool first = (r == 1) || (r == 0 && c - k < 0);
-          const unsigned d = Sv.tmem + (unsigned)((t % S) * 64);
-          const unsigned b_hi = smem_u32(blk + (size_t)(buf * 3 + r) * bb);
-          const unsigned b_lo = smem_u32(blo + (size_t)r * bb);
-          unsigned acc = first ? 0u : 1u;
+          const unsigned d = Sv.tmem + (unsigned)((tr % S) * slot_cols);
+          const uint64_t db = tc_desc(smem_u32(bptr(buf, r)), 128, sbo);  // [Q_hi | Q_lo]
           for (int ks = 0; ks < n / 8; ++ks) {
-            const unsigned o = 256u * (unsigned)ks;
-            tc_mma(d, tc_desc(a_hi + o, 128, sbo), tc_desc(b_hi + o, 128, sbo), id, acc);
-            acc = 1u;
-            tc_mma(d, tc_desc(a_hi + o, 128, sbo), tc_desc(b_lo + o, 128, sbo), id, 1u);
-            tc_mma(d, tc_desc(a_lo + o, 128, sbo), tc_desc(b_hi + o, 128, sbo), id, 1u);
+            const uint64_t o = 16ull * (unsigned)ks;
+            tc_mma(d, da + o, db + o, id, (first && ks == 0) ? 0u : 1u);
           }
         }
         tc_commit(mbar);
       }
       ++Sv.mma_iss;
     }
-    // finish row t = c - 1 - k (its last product came from column <= c - 1)
-    const int t = c - 1 - k;
-    if (t >= s && t < e) {
-      tc_fence_after();
-      const int warp = tid >> 5, lane = tid & 31, q = warp & 3;
-      const unsigned base = Sv.tmem + (unsigned)((t % S) * 64) + ((unsigned)(32 * q) << 16);
-      for (int ch = warp >> 2; ch < n / 8; ch += kMThreads / 128) {
-        float v[8];
-        tc_ld8(base + 8u * (unsigned)ch, v);
-        if (lane < 16) {
-          const int j = 16 * q + lane;
+    if (fin_t && tid < 4 * n) {
+      cp_wait<0>();  // this thread's own tiles
+      float out[4][4];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) stage[(8 * ch + i) * kJ + j] = v[i];
-        }
+      for (int r = 0; r < 4; ++r) {
+        const float4 w = *reinterpret_cast<const float4*>(stage + (a0 + r) * kJ + j0);
+        const float4 x = *reinterpret_cast<const float4*>(stage + vb + (a0 + r) * kJ + j0);
+        out[r][0] = w.x + x.x; out[r][1] = w.y + x.y; out[r][2] = w.z + x.z; out[r][3] = w.w + x.w;
       }
-      tc_fence_before();
-      __syncthreads();
-      if (tid < 4 * n) {
-        const int a0 = 4 * (tid >> 4), j0 = 4 * (tid & 15);
-        float out[4][4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const float4 w = *reinterpret_cast<const float4*>(stage + (a0 + r) * kJ + j0);
-          out[r][0] = w.x; out[r][1] = w.y; out[r][2] = w.z; out[r][3] = w.w;
-        }
-        const float4* pf = nullptr;
-        int pstride = 0;
-        if (pre) {
-          pf = reinterpret_cast<const float4*>(pre + (size_t)t * vb + (size_t)a0 * kJ + j0);
-          pstride = kJ / 4;
-        }
-        fin(t, a0, j0, out, slot(t), pf, pstride);
-      }
-      __syncthreads();
+      fin(t, a0, j0, out, xbuf, pre ? reinterpret_cast<const float4*>(pbuf + a0 * kJ + j0) : nullptr, kJ / 4);
     }
     if (proc) {
       const bool ok = mbar_wait(mbar, (unsigned)(Sv.mma_done & 1), Sv.deadline);
@@ -699,8 +718,8 @@ __device__ void msweep_tc(MSolver& Sv, int phase, const float* v_in, const float
       }
       ++Sv.mma_done;
       ++Sv.gcol;
-      if (c + 2 < c_hi) {
-        if (tid == 0) {
+      if (c + 2 < c_hi) {  // column c + 2 into the buffers column c released
+        if (tid == kTcIssuer) {
           fence_proxy_async_smem();
           issue(c + 2, buf);
         }
@@ -712,6 +731,7 @@ __device__ void msweep_tc(MSolver& Sv, int phase, const float* v_in, const float
     // let every copy and MMA this CTA started finish (bounded) before the
     // kernel goes on to release TMEM and exit
     const long long lim = clock64() + (1ll << 31);
+    cp_wait<0>();
     for (int gc = Sv.gcol; gc < Sv.iss; ++gc) mbar_wait(full + (gc & 1), (unsigned)((gc >> 1) & 1), lim);
     for (int m = Sv.mma_done; m < Sv.mma_iss; ++m) mbar_wait(mbar, (unsigned)(m & 1), lim);
     Sv.gcol = Sv.iss;
@@ -1172,7 +1192,7 @@ __global__ void k_mrhs_image(const float* src, int bs32, float* dst, int N, int 
 // engine, or the tensor-core sweep buffers (which also hold the float64
 // residual sweep's job).
 extern "C" int bt_mrhs_smem_bytes(int n, int tc) {
-  if (tc) return kMSmJobs + bt::mrhs_tc_floats(n) * 4;
+  if (tc) return std::max(kTcBase + bt::mrhs_tc_floats(n) * 4, kMSmJobs + mrhs_job_bytes(n));
   return kMSmJobs + mrhs_job_bytes(n) + (4 * n <= kMHalf ? 4 * kMHalf * 16 : 0);
 }
 
