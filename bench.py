@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 one-at-a-time comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-sample", type=int, default=48, help="instances in the oracle CPU sample")
+    ap.add_argument("--maxit", type=int, default=20000,
+                    help="many_rhs: iteration limit (with --profile a short capture may stop early)")
+    ap.add_argument("--mrhs-engine", type=int, default=0, choices=[0, 1, 2],
+                    help="many_rhs: 0 automatic (tensor cores for n = 48), 1 float32 SIMT, 2 tensor cores")
     ap.add_argument("--workload", choices=["ocp_batch", "many_rhs", "adjoint", "small", "family", "lqr", "alpha", "matrix_free"],
                     default="ocp_batch",
                     help="ocp_batch: the headline workload (default); many_rhs: one LL^T system, N=2048, "
@@ -543,21 +547,34 @@ def other_workload(a):
         dO = torch.tensor(inst.O, device=dev)
         dB = torch.tensor(inst.b.reshape(N * n, J), device=dev)
         dX = torch.zeros_like(dB)
-        p, keep = bb.make_params(m=M, alpha=ALPHA, precision=bb.BT_MIXED)
-        st, h = bb.bt_setup(N, n, dD, dO, p)
-        assert st == bb.BT_OK, bb.status_string(st)
-        for _ in range(a.warmup):
-            st, its, sts = bb.bt_pcg_solve_multi(h, dB, dX, J, TOL, 20000)
-            assert st == bb.BT_OK and (sts == 0).all()
-        torch.cuda.synchronize()
-        e0.record()
-        for _ in range(a.steps):
-            st, its, sts = bb.bt_pcg_solve_multi(h, dB, dX, J, TOL, 20000)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / a.steps
-        outers = [bb.bt_multi_info(h, j)[1] for j in range(J)]
-        bb.bt_destroy(h)
+
+        def timed(engine):
+            p, keep = bb.make_params(m=M, alpha=ALPHA, precision=bb.BT_MIXED, mrhs_engine=engine)
+            st, h = bb.bt_setup(N, n, dD, dO, p)
+            assert st == bb.BT_OK, bb.status_string(st)
+            for _ in range(a.warmup):
+                st, its, sts = bb.bt_pcg_solve_multi(h, dB, dX, J, TOL, a.maxit)
+                assert st == bb.BT_OK and (sts == 0).all()
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(a.steps):
+                st, its, sts = bb.bt_pcg_solve_multi(h, dB, dX, J, TOL, a.maxit)
+            e1.record()
+            torch.cuda.synchronize()
+            outers = [bb.bt_multi_info(h, j)[1] for j in range(J)]
+            bb.bt_destroy(h)
+            return e0.elapsed_time(e1) / a.steps, its, sts, outers
+
+        if a.profile:  # one short call for a profiler capture: no checks, no baselines
+            ms, its, sts, outers = timed(a.mrhs_engine)
+            emit({"workload": "many_rhs", "profile": True, "ms": ms, "iters_max": int(np.max(its))})
+            return
+        clocks = Clocks(0)
+        clocks.__enter__()
+        ms_simt = timed(1)[0] if a.mrhs_engine == 0 else None
+        ms, its, sts, outers = timed(a.mrhs_engine)
+        clocks.__exit__()
+        assert (sts == 0).all()
         # error against the float64 oracle: every column's true residual
         # (oracle SpMV) and four sampled columns against its direct solve
         from oracle import bt_oracle as orc
@@ -586,9 +603,13 @@ def other_workload(a):
               "config": {"workload": "LL^T N=2048 n=48, 64 right-hand sides, mixed, a=1 m=2 alpha=(1,7)"},
               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                            "frac": achieved / peak, "traffic": None, "peak_source": kind,
-                           "kernel": "bt_mrhs_kernel", "alg_bytes_per_launch": abytes},
-              "err_vs_oracle": err,
-              "detail": {"iters_max": it_max, "iters_mean": float(np.mean(its)), "outer_max": o_max}})
+                           "kernel": "bt_mrhs_kernel<true>" if a.mrhs_engine != 1 else "bt_mrhs_kernel<false>",
+                           "alg_bytes_per_launch": abytes, "ms_per_launch": ms},
+              "err_vs_oracle": err, "clocks": clocks.summary(),
+              "detail": {"iters_max": it_max, "iters_mean": float(np.mean(its)), "outer_max": o_max,
+                         "engine": {0: "tensor cores (3xTF32, tcgen05)", 1: "float32 SIMT",
+                                    2: "tensor cores (3xTF32, tcgen05)"}[a.mrhs_engine],
+                         "ms_float32_simt_engine": ms_simt}})
         return
     if a.workload == "family":
         family_protocol(a, bb, wl, torch, dev)
