@@ -63,7 +63,8 @@ def parse():
                     help="many_rhs: iteration limit (with --profile a short capture may stop early)")
     ap.add_argument("--mrhs-engine", type=int, default=0, choices=[0, 1, 2],
                     help="many_rhs: 0 automatic (tensor cores for n = 48), 1 float32 SIMT, 2 tensor cores")
-    ap.add_argument("--workload", choices=["ocp_batch", "many_rhs", "adjoint", "small", "family", "lqr", "alpha", "matrix_free"],
+    ap.add_argument("--workload", choices=["ocp_batch", "many_rhs", "adjoint", "small", "family", "lqr", "alpha",
+                                           "matrix_free", "precision"],
                     default="ocp_batch",
                     help="ocp_batch: the headline workload (default); many_rhs: one LL^T system, N=2048, "
                          "n=48, 64 right-hand sides; adjoint: 256 LQR instances, N=256, n=24, forward + adjoint; "
@@ -623,6 +624,9 @@ def other_workload(a):
     if a.workload == "matrix_free":
         matrix_free(a, bb, wl, torch, dev)
         return
+    if a.workload == "precision":
+        precision_split(a, bb, wl, torch, dev)
+        return
     if a.workload == "small":
         # latency-bound single instances: microseconds per solve and per PCG
         # iteration (one persistent launch per solve, setup excluded)
@@ -886,6 +890,69 @@ def matrix_free(a, bb, wl, torch, dev):
           "config": {"workload": "ocp batch of 1024, a=1 m=2 alpha=(1,7), H_opt matrix-free"},
           "roofline": {"bound": "hbm", "achieved": r["hbm_gbs"], "peak": peak, "unit": "GB/s", "frac": r["frac"],
                        "traffic": None, "peak_source": kind, "kernel": "bt_persistent_kernel<float, 2>"},
+          "rows": rows})
+
+
+def precision_split(a, bb, wl, torch, dev):
+    """The headline step (refactor + batched mixed solve of the 1024 LQR
+    instances to 1e-8) under the two precision splits of the mixed path:
+    default (float32 factor of each D_i, float64 refactor of blocks with
+    cond(D_i) > 1e3, float32 divisions of the inner step scalars) and strict
+    (every D_i factored in float64, step scalars divided in float64).  Per row
+    the refactor and solve times, iterations and the error against the
+    oracle's direct solve on a sample of 48 instances."""
+    import numpy as np
+    from oracle import bt_oracle as orc
+    insts = wl.config2()
+    Ns, ns, d_off, o_off, v_off, D, O, b = wl.pack_batch(insts)
+    dD, dO, db = (torch.tensor(v, device=dev) for v in (D, O, b))
+    dx = torch.zeros_like(db)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    sample = sample_indices(len(insts), 48)
+    xref = {k: orc.direct_solve(insts[k].D, insts[k].O, insts[k].b) for k in sample}
+    peak, kind = measured_peak()
+    rows = []
+    for strict in (False, True):
+        p, keep = bb.make_params(m=M, alpha=ALPHA, precision=bb.BT_MIXED, mixed_strict_fp64=strict)
+        st, h = bb.bt_setup_batched(Ns, ns, d_off, o_off, dD, dO, p)
+        assert st == bb.BT_OK, bb.status_string(st)
+        for _ in range(a.warmup):
+            assert bb.bt_refactor(h, dD, dO) == bb.BT_OK
+            st, its, sts = bb.bt_pcg_solve_batched(h, db, dx, len(insts), TOL, 5000)
+            assert st == bb.BT_OK and (sts == 0).all()
+        outers = [bb.bt_solve_info(h, k)[1] for k in range(len(insts))]
+        resid = max(bb.bt_solve_info(h, k)[2] for k in range(len(insts)))
+        t_set = t_sol = 0.0
+        for _ in range(a.steps):
+            torch.cuda.synchronize()
+            ev[0].record()
+            bb.bt_refactor(h, dD, dO)
+            ev[1].record()
+            bb.bt_pcg_solve_batched_async(h, db, dx, TOL, 5000)
+            ev[2].record()
+            torch.cuda.synchronize()
+            t_set += ev[0].elapsed_time(ev[1])
+            t_sol += ev[1].elapsed_time(ev[2])
+        bb.bt_destroy(h)
+        xs = dx.cpu().numpy()
+        err = max(float(np.linalg.norm(xs[v_off[k]:v_off[k] + Ns[k] * ns[k]].reshape(Ns[k], ns[k]) - xref[k])
+                        / np.linalg.norm(xref[k])) for k in sample)
+        ms_set, ms_sol = t_set / a.steps, t_sol / a.steps
+        gbs = alg_bytes(Ns, ns, its, outers) / (ms_sol / 1e3) / 1e9
+        rows.append({"split": "strict float64 factor and step scalars" if strict else "default",
+                     "ms_refactor": ms_set, "ms_solve": ms_sol,
+                     "solves_per_s": len(insts) / ((ms_set + ms_sol) / 1e3), "iters_mean": float(np.mean(its)),
+                     "outer_mean": float(np.mean(outers)), "max_true_rel_residual": resid,
+                     "max_rel_err_vs_direct_sample48": err, "solve_hbm_frac": gbs / peak})
+    r = rows[1]
+    emit({"metric": "solves/s at rel. residual 1e-8 under the strict float64 split (refactor + solve per step)",
+          "value": r["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+          "ms_per_step": r["ms_refactor"] + r["ms_solve"], "higher_is_better": True, "dtype": "f32+f64",
+          "data": "synthetic (seeded LQR Schur complements)",
+          "config": {"workload": "ocp batch of 1024, a=1 m=2 alpha=(1,7), default vs strict precision split"},
+          "err_vs_oracle": {"default": rows[0]["max_rel_err_vs_direct_sample48"],
+                            "strict": rows[1]["max_rel_err_vs_direct_sample48"],
+                            "reference": "oracle direct solve, 48 sampled instances"},
           "rows": rows})
 
 

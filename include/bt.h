@@ -117,10 +117,14 @@ typedef struct bt_params {
                           cores where supported: n a multiple of 8, n <= 48; float32
                           SIMT otherwise), 1 = float32 SIMT, 2 = tensor cores (3xTF32
                           split, float32 accumulation; BT_ERR_ARG where unsupported). */
-  int mixed_fp64_factor; /* BT_MIXED: 1 = factor every D_i in float64 (then round
-                          D_i^-1 and the E, H blocks to float32), 0 = float32 factor
-                          with a float64 refactor of the blocks whose pivots show
-                          cond(D_i) > 1e3.                                          */
+  int mixed_strict_fp64; /* BT_MIXED: 1 = float64 where the mixed method needs it
+                          most: every D_i factored (Cholesky, D_i^-1) in float64,
+                          then rounded to float32 with the E and H blocks formed
+                          from it, and the inner CG step scalars (alpha = rho / p.q,
+                          beta = rho' / rho) divided in float64.  0 (default) =
+                          float32 factor with a float64 refactor of the blocks
+                          whose pivots show cond(D_i) > 1e3, float32 divisions of
+                          the step scalars (float64 dot products either way).     */
 } bt_params;
 
 typedef struct bt_ctx* bt_handle;

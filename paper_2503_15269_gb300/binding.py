@@ -44,7 +44,7 @@ class bt_params(C.Structure):
         ("stage_kb", C.c_int),
         ("h_matrix_free", C.c_int),
         ("mrhs_engine", C.c_int),
-        ("mixed_fp64_factor", C.c_int),
+        ("mixed_strict_fp64", C.c_int),
     ]
 
 
@@ -147,7 +147,7 @@ def make_params(m: int = 2, alpha: Optional[Sequence[float]] = None, precision: 
                 tol_inner: float = 0.0, max_outer: int = 0, use_x0: bool = False, cycle_budget: int = 0,
                 stream=None, ctas_per_sm: int = 0, group_ctas: int = 0, stage_kb: int = 0,
                 a: float = 1.0, h_matrix_free: bool = False, mrhs_engine: int = 0,
-                mixed_fp64_factor: bool = False):
+                mixed_strict_fp64: bool = False):
     """Build a bt_params; returns (params, keepalive)."""
     p = bt_params()
     lib().bt_params_init(C.byref(p))
@@ -168,7 +168,7 @@ def make_params(m: int = 2, alpha: Optional[Sequence[float]] = None, precision: 
     p.stage_kb = stage_kb
     p.h_matrix_free = 1 if h_matrix_free else 0
     p.mrhs_engine = mrhs_engine
-    p.mixed_fp64_factor = 1 if mixed_fp64_factor else 0
+    p.mixed_strict_fp64 = 1 if mixed_strict_fp64 else 0
     return p, keep
 
 

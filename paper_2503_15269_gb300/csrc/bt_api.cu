@@ -193,7 +193,7 @@ bt_status check_params(const bt_params* p, double* alpha_out) {
   // the matrix-free H applies H_opt = H_J^2: the optimum only
   if (p->h_matrix_free != 0 && (p->h_matrix_free != 1 || p->a != 1.0)) return BT_ERR_PARAM;
   if (p->mrhs_engine < 0 || p->mrhs_engine > 2) return BT_ERR_PARAM;
-  if (p->mixed_fp64_factor != 0 && p->mixed_fp64_factor != 1) return BT_ERR_PARAM;
+  if (p->mixed_strict_fp64 != 0 && p->mixed_strict_fp64 != 1) return BT_ERR_PARAM;
   return BT_OK;
 }
 
@@ -221,7 +221,8 @@ bt_status launch_setup_kernels(bt_ctx* h, const double* D, const double* O) {
   sp.want64 = 1;
   sp.fail_key = h->d_fail_key;
   sp.fail_piv = h->d_fail_piv;
-  sp.retry = h->d_retry;
+  // the strict float64 split factors every D_i in float64 (no float32 factor to refuse)
+  sp.retry = h->prm.mixed_strict_fp64 ? nullptr : h->d_retry;
   sp.segs = h->d_segs;
   sp.nsegs = h->nsegs;
   // the matrix-free variant forms no H blocks
@@ -468,6 +469,7 @@ bt::KParams base_kparams(bt_ctx* h) {
   P.bar = reinterpret_cast<unsigned*>(h->d_ctl + 2);
   P.red = h->d_red;
   P.mixed = h->mixed;
+  P.scal64 = h->prm.mixed_strict_fp64;
   P.m = h->prm.m;
   for (int j = 0; j < BT_MAX_M; ++j) P.alpha[j] = j < h->prm.m ? h->alpha[j] : 0.0;
   P.tol_inner = h->prm.tol_inner;  // 0: the kernel derives it from tol

@@ -61,6 +61,7 @@ struct KParams {
   const double* bvec;      // SOLVE: b;  SPMV: x;  APPLY: r
   double* xvec;            // SOLVE: x;  SPMV: y;  APPLY: z
   int op, mixed, m;
+  int scal64;              // mixed: divide the inner CG step scalars in float64 (else float32)
   double alpha[kMaxM];
   double tol, tol_inner;
   int maxit, max_outer, use_x0;

@@ -135,6 +135,7 @@ extern "C" bt_status bt_pcg_solve_noalloc(int N, int n, const double* D, const d
   if (p->a != 1.0 || p->h_matrix_free != 0 || p->m < 1 || p->m > BT_MAX_M) return BT_ERR_PARAM;
   if (p->precision != BT_FP64 && p->precision != BT_MIXED) return BT_ERR_PARAM;
   if (p->tol_inner < 0.0 || p->tol_inner >= 1.0 || p->max_outer < 0 || p->cycle_budget < 0) return BT_ERR_PARAM;
+  if (p->mixed_strict_fp64 != 0 && p->mixed_strict_fp64 != 1) return BT_ERR_PARAM;
   double alpha[BT_MAX_M] = {0};
   for (int j = 0; j < p->m; ++j) {
     const double a = p->alpha ? p->alpha[j] : 1.0;
@@ -249,7 +250,7 @@ extern "C" bt_status bt_pcg_solve_noalloc(int N, int n, const double* D, const d
   sp.want64 = 1;
   sp.fail_key = fail_key;
   sp.fail_piv = fail_piv;
-  sp.retry = retry;
+  sp.retry = p->mixed_strict_fp64 ? nullptr : retry;  // strict: every D_i factored in float64
   if (bt_launch_setup(&sp, mixed ? 1 : 0, m, n, st) != cudaSuccess) return BT_ERR_CUDA;
 
   bt::KParams P{};
@@ -266,6 +267,7 @@ extern "C" bt_status bt_pcg_solve_noalloc(int N, int n, const double* D, const d
   P.xvec = x;
   P.op = bt::kOpSolve;
   P.mixed = mixed ? 1 : 0;
+  P.scal64 = p->mixed_strict_fp64;
   P.m = m;
   for (int j = 0; j < BT_MAX_M; ++j) P.alpha[j] = alpha[j];
   P.tol = tol;

@@ -1499,10 +1499,12 @@ __device__ void solve_instance(Solver<MT, VAR>& Sv, int inst_id) {
   double acc[4];
   auto zero_acc = [&]() { acc[0] = acc[1] = acc[2] = acc[3] = 0.0; };
   // PCG step scalars: the float32 inner iteration uses them rounded to float,
-  // so it divides in float32 (a float64 division is a dozen float64
-  // instructions on every thread); the float64 path divides in float64.
-  auto sdiv = [](double a, double b) -> double {
-    if constexpr (sizeof(MT) == 4) return (double)__fdiv_rn((float)a, (float)b);
+  // so by default it divides in float32 (a float64 division is a dozen
+  // float64 instructions on every thread); with P.scal64 (the strict float64
+  // split) and on the float64 path it divides in float64.
+  const bool scal64 = P.scal64 != 0;
+  auto sdiv = [scal64](double a, double b) -> double {
+    if constexpr (sizeof(MT) == 4) return scal64 ? a / b : (double)__fdiv_rn((float)a, (float)b);
     else return a / b;
   };
 

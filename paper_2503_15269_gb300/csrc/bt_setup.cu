@@ -93,20 +93,17 @@ __device__ void factor_row64(const SetupParams& P, long long gr, char* wsm) {
     }
     __syncwarp();
   }
-  // W = L^-1 (one column per lane, forward substitution in MT); the
-  // reciprocals of the diagonal are formed once, into the warp's tail region.
-  MT* W = reinterpret_cast<MT*>(T);
-  // 1 / L[r][r] from the Cholesky; float32 copies sit behind W's float32 data
-  MT* dv = (sizeof(MT) == 4) ? reinterpret_cast<MT*>(T) + nn : reinterpret_cast<MT*>(rinv_col);
-  if (sizeof(MT) == 4)
-    for (int r = lane; r < n; r += 32) dv[r] = (MT)rinv_col[r];
-  __syncwarp();
+  // W = L^-1 (one column per lane, forward substitution) and D_i^-1 = W^T W,
+  // both in float64 (the reciprocals of the diagonal of L come from the
+  // Cholesky); the result is rounded to MT once, on the store.
+  double* W = T;
+  const double* dv = rinv_col;
   for (int c = lane; c < n; c += 32) {
-    for (int r = 0; r < c; ++r) W[r * n + c] = MT(0);
+    for (int r = 0; r < c; ++r) W[r * n + c] = 0.0;
     W[c * n + c] = dv[c];
     for (int r = c + 1; r < n; ++r) {
-      MT acc = MT(0);
-      for (int t = c; t < r; ++t) acc = fma((MT)A[r * n + t], W[t * n + c], acc);
+      double acc = 0.0;
+      for (int t = c; t < r; ++t) acc = fma(A[r * n + t], W[t * n + c], acc);
       W[r * n + c] = -acc * dv[r];
     }
   }
@@ -116,10 +113,10 @@ __device__ void factor_row64(const SetupParams& P, long long gr, char* wsm) {
   for (int t = lane; t < nn; t += 32) {
     const int a = qdiv(t, inv_n), b = t - a * n;
     if (a < b) continue;
-    MT acc = MT(0);
+    double acc = 0.0;
     for (int r = a; r < n; ++r) acc = fma(W[r * n + a], W[r * n + b], acc);
-    out[(long long)b * n + a] = acc;
-    out[(long long)a * n + b] = acc;
+    out[(long long)b * n + a] = (MT)acc;
+    out[(long long)a * n + b] = (MT)acc;
   }
 }
 
@@ -768,48 +765,69 @@ __global__ void __launch_bounds__(256, 2) k_EH(const __grid_constant__ SetupPara
 
 // ---------------------------------------------------------------- adjoint
 // gD_i = -g_i x_i^T, gO_i = -(g_i x_{i+1}^T + x_i g_{i+1}^T), caller layout
-// (row-major blocks).  One warp per block row: lane l holds entries l and
-// l + 32 of x_i, g_i, x_{i+1}, g_{i+1}; output row a takes g_i[a] and x_i[a]
-// from lane a % 32 by shuffle, and the warp writes the row's n contiguous
-// doubles (streaming stores: the gradients are the caller's, not re-read
-// here).  Bound by the (2N-1) n^2 doubles it writes.
+// (row-major blocks).  One warp per block row: x_i, g_i, x_{i+1}, g_{i+1} are
+// staged in shared memory, then the warp writes each n x n block as one flat
+// range -- element f = a n + c, the lanes on consecutive pairs (f, f + 1)
+// with 16-byte streaming stores when n is even and the block 16-byte
+// aligned, single elements otherwise -- stepping (a, c) by carries instead of
+// a division per element.  Bound by the (2N-1) n^2 doubles it writes.
 constexpr int kAdjWarps = 8;
 
+template <int W>  // elements per lane and store: 2 (double2) or 1
+__device__ __forceinline__ void adj_block(double* dst, int n, const double* xa, const double* ga, const double* xb,
+                                          const double* gb, bool off_diag, int lane) {
+  const int nn = n * n, step = 32 * W;
+  const int da = step / n, dc = step - da * n;
+  int f = W * lane;
+  int a = f / n, c = f - a * n;
+  for (; f < nn; f += step) {
+    double v[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+      v[w] = off_diag ? -fma(ga[a], xb[c + w], xa[a] * gb[c + w]) : -ga[a] * xa[c + w];
+    if constexpr (W == 2) __stcs(reinterpret_cast<double2*>(dst + f), make_double2(v[0], v[1]));
+    else __stcs(dst + f, v[0]);
+    a += da;
+    c += dc;
+    if (c >= n) {
+      c -= n;
+      ++a;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint(const __grid_constant__ AdjParams P) {
-  const int lane = threadIdx.x & 31;
-  const long long gr = (long long)blockIdx.x * kAdjWarps + (threadIdx.x >> 5);
+  __shared__ double stage[kAdjWarps][4][kMaxBlock];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long gr = (long long)blockIdx.x * kAdjWarps + warp;
   if (gr >= P.nrows) return;
   const RowRef rr = P.rows[gr];
   const InstDesc d = P.inst[rr.inst];
   const int n = d.n, i = rr.row;
   const bool has_next = i < d.N - 1;
+  double* xs = stage[warp][0];  // x_i, g_i, x_{i+1}, g_{i+1}
+  double* gs = stage[warp][1];
+  double* xn = stage[warp][2];
+  double* gn = stage[warp][3];
   const double* xi = P.x + d.vec + (long long)i * n;
   const double* gi = P.g + d.vec + (long long)i * n;
-  const int c0 = lane, c1 = lane + 32;
-  const bool v0 = c0 < n, v1 = c1 < n;
-  const double x0 = v0 ? xi[c0] : 0.0, x1 = v1 ? xi[c1] : 0.0;
-  const double g0 = v0 ? gi[c0] : 0.0, g1 = v1 ? gi[c1] : 0.0;
-  double xn0 = 0.0, xn1 = 0.0, gn0 = 0.0, gn1 = 0.0;
-  if (has_next) {
-    xn0 = v0 ? xi[n + c0] : 0.0;
-    xn1 = v1 ? xi[n + c1] : 0.0;
-    gn0 = v0 ? gi[n + c0] : 0.0;
-    gn1 = v1 ? gi[n + c1] : 0.0;
-  }
-  double* gD = P.gD + P.d_off[rr.inst] + (long long)i * n * n;
-  double* gO = has_next ? P.gO + P.o_off[rr.inst] + (long long)i * n * n : nullptr;
-  for (int a = 0; a < n; ++a) {
-    const int src = a & 31;
-    const double ga = __shfl_sync(0xffffffffu, a < 32 ? g0 : g1, src);
-    const double xa = __shfl_sync(0xffffffffu, a < 32 ? x0 : x1, src);
-    double* dr = gD + a * n;
-    if (v0) __stcs(dr + c0, -ga * x0);
-    if (v1) __stcs(dr + c1, -ga * x1);
+  for (int t = lane; t < n; t += 32) {
+    xs[t] = xi[t];
+    gs[t] = gi[t];
     if (has_next) {
-      double* orow = gO + a * n;
-      if (v0) __stcs(orow + c0, -fma(ga, xn0, xa * gn0));
-      if (v1) __stcs(orow + c1, -fma(ga, xn1, xa * gn1));
+      xn[t] = xi[n + t];
+      gn[t] = gi[n + t];
     }
+  }
+  __syncwarp();
+  double* gD = P.gD + P.d_off[rr.inst] + (long long)i * n * n;
+  const bool pairs = (n % 2 == 0) && ((reinterpret_cast<uintptr_t>(gD) & 15) == 0);
+  if (pairs) adj_block<2>(gD, n, xs, gs, nullptr, nullptr, false, lane);
+  else adj_block<1>(gD, n, xs, gs, nullptr, nullptr, false, lane);
+  if (has_next) {
+    double* gO = P.gO + P.o_off[rr.inst] + (long long)i * n * n;
+    if ((n % 2 == 0) && ((reinterpret_cast<uintptr_t>(gO) & 15) == 0)) adj_block<2>(gO, n, xs, gs, xn, gn, true, lane);
+    else adj_block<1>(gO, n, xs, gs, xn, gn, true, lane);
   }
 }
 

@@ -76,3 +76,23 @@ def cond_estimate(D, O, b, maxit=20000):
     from oracle import bt_oracle as orc
     res = orc.pcg(D, O, b, lambda r: r, 1e-12, maxit)
     return orc.lanczos_cond(res.alphas, res.betas)
+
+
+def ill_conditioned(inst, row, decades, seed):
+    """Congruence S' = P^T S P with P = I except P_row = V diag(s) V^T
+    (V orthogonal, s spanning `decades` decades): S' stays SPD, D'_row gets
+    kappa ~ 10^(2 decades) kappa(D_row), and the preconditioned spectrum is
+    unchanged (the preconditioner of Sec. 4.1 transforms with P)."""
+    n = inst.n
+    rng = np.random.default_rng(seed)
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    Pm = V @ np.diag(np.logspace(0, -decades, n)) @ V.T
+    D, O = inst.D.copy(), inst.O.copy()
+    D[row] = Pm.T @ D[row] @ Pm
+    D[row] = 0.5 * (D[row] + D[row].T)
+    if row > 0:
+        O[row - 1] = O[row - 1] @ Pm
+    if row < inst.N - 1:
+        O[row] = Pm.T @ O[row]
+    from paper_2503_15269_gb300 import workloads as wl
+    return wl.Instance(D=D, O=O, b=inst.b)

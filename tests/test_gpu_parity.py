@@ -19,7 +19,7 @@ from oracle import bt_oracle as orc
 from paper_2503_15269_gb300 import binding as bb
 from paper_2503_15269_gb300 import workloads as wl
 
-from _util import Single, dev, host, maxrel, rel
+from _util import Single, dev, host, ill_conditioned, maxrel, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -211,29 +211,10 @@ def test_not_spd_reports_block_mixed():
         s.close()
 
 
-def _ill_conditioned(inst, row, decades, seed):
-    """Congruence S' = P^T S P with P = I except P_row = V diag(s) V^T
-    (V orthogonal, s spanning `decades` decades): S' stays SPD, D'_row gets
-    kappa ~ 10^(2 decades) kappa(D_row), and the preconditioned spectrum is
-    unchanged (the preconditioner of Sec. 4.1 transforms with P)."""
-    n = inst.n
-    rng = np.random.default_rng(seed)
-    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
-    Pm = V @ np.diag(np.logspace(0, -decades, n)) @ V.T
-    D, O = inst.D.copy(), inst.O.copy()
-    D[row] = Pm.T @ D[row] @ Pm
-    D[row] = 0.5 * (D[row] + D[row].T)
-    if row > 0:
-        O[row - 1] = O[row - 1] @ Pm
-    if row < inst.N - 1:
-        O[row] = Pm.T @ O[row]
-    return wl.Instance(D=D, O=O, b=inst.b)
-
-
 def test_mixed_ill_conditioned_block_solve():
     # kappa(D_5) ~ 1e4, smallest pivot ratio ~ 8e-3: the float32 factor is
     # kept; refinement reaches the direct solve
-    inst = _ill_conditioned(wl.small_llt(71, 12, 8), 5, 2, 72)
+    inst = ill_conditioned(wl.small_llt(71, 12, 8), 5, 2, 72)
     assert np.linalg.eigvalsh(orc.assemble(inst.D, inst.O)).min() > 0
     xref = orc.direct_solve(inst.D, inst.O, inst.b)
     with Single(inst, m=2, alpha=[1.0, 7.0], precision=bb.BT_MIXED) as s:
@@ -251,7 +232,7 @@ def test_mixed_ill_conditioned_block_apply(decades):
     # it at float32 rounding.  (A float32 copy of such an S cannot carry its
     # smallest eigen-directions -- kappa(S) u32 > 1 -- so mixed refinement
     # is not expected to converge on it; only the apply is checked.)
-    inst = _ill_conditioned(wl.small_llt(71, 12, 8), 5, decades, 72)
+    inst = ill_conditioned(wl.small_llt(71, 12, 8), 5, decades, 72)
     r = np.random.default_rng(73).standard_normal((inst.N, inst.n))
     ref = orc.apply_opt(orc.opt_blocks(inst.D, inst.O), r, [1.0])
     with Single(inst, m=1, precision=bb.BT_MIXED) as s:
