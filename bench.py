@@ -631,14 +631,16 @@ def other_workload(a):
         # latency-bound single instances: microseconds per solve and per PCG
         # iteration (one persistent launch per solve, setup excluded)
         rows = []
-        for name, inst, prec, tol in (("LL^T N=16 n=6", wl.config0(), bb.BT_FP64, 1e-10),
-                                      ("LQR N=128 n=12", wl.config1(), bb.BT_FP64, 1e-8),
-                                      ("LQR N=128 n=12", wl.config1(), bb.BT_MIXED, 1e-8)):
+        # group -1: the shared-memory engine, 1: the persistent kernel on one CTA, 0: automatic
+        for name, inst, prec, tol, grp in (("LL^T N=16 n=6", wl.config0(), bb.BT_FP64, 1e-10, 0),
+                                           ("LL^T N=16 n=6", wl.config0(), bb.BT_FP64, 1e-10, 1),
+                                           ("LQR N=128 n=12", wl.config1(), bb.BT_FP64, 1e-8, 0),
+                                           ("LQR N=128 n=12", wl.config1(), bb.BT_MIXED, 1e-8, 0)):
             dD = torch.tensor(inst.D, device=dev)
             dO = torch.tensor(inst.O, device=dev)
             db = torch.tensor(inst.b.reshape(-1), device=dev)
             dx = torch.zeros_like(db)
-            p, keep = bb.make_params(m=M, alpha=ALPHA, precision=prec)
+            p, keep = bb.make_params(m=M, alpha=ALPHA, precision=prec, group_ctas=grp)
             st, h = bb.bt_setup(inst.N, inst.n, dD, dO, p)
             assert st == bb.BT_OK, bb.status_string(st)
             for _ in range(a.warmup):
@@ -652,9 +654,12 @@ def other_workload(a):
             torch.cuda.synchronize()
             us = 1e3 * e0.elapsed_time(e1) / a.steps
             bb.bt_destroy(h)
+            # group_ctas 0 picks the shared-memory engine for float64 instances whose
+            # blocks fit one CTA (here LL^T N = 16, n = 6), the persistent kernel otherwise
+            engine = {0: "automatic", 1: "persistent kernel, 1 CTA"}[grp]
             rows.append({"instance": name, "precision": "f64" if prec == bb.BT_FP64 else "f32+f64", "tol": tol,
-                         "us_per_solve": us, "iters": it, "us_per_iter": us / max(it, 1)})
-        emit({"metric": "microseconds per single-instance solve (latency-bound rows)", "value": rows[-1]["us_per_solve"],
+                         "engine": engine, "us_per_solve": us, "iters": it, "us_per_iter": us / max(it, 1)})
+        emit({"metric": "microseconds per single-instance solve (latency-bound rows)", "value": rows[0]["us_per_solve"],
               "unit": "us", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "higher_is_better": False,
               "data": "synthetic (seeded)", "config": {"workload": "single instances, one persistent launch each"},
               "rows": rows})

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libbt.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["bt_api.cu", "bt_pcg.cu", "bt_pcg_gen.cu", "bt_pcg_mf.cu", "bt_setup.cu", "bt_noalloc.cu", "bt_mrhs.cu", "bt_lqr.cu"]
+SOURCES = ["bt_api.cu", "bt_pcg.cu", "bt_pcg_gen.cu", "bt_pcg_mf.cu", "bt_setup.cu", "bt_noalloc.cu", "bt_mrhs.cu", "bt_lqr.cu", "bt_small.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]
