@@ -633,8 +633,10 @@ def other_workload(a):
         rows = []
         # group -1: the shared-memory engine, 1: the persistent kernel on one CTA, 0: automatic
         for name, inst, prec, tol, grp in (("LL^T N=16 n=6", wl.config0(), bb.BT_FP64, 1e-10, 0),
+                                           ("LL^T N=16 n=6", wl.config0(), bb.BT_FP64, 1e-10, -8),
                                            ("LL^T N=16 n=6", wl.config0(), bb.BT_FP64, 1e-10, 1),
                                            ("LQR N=128 n=12", wl.config1(), bb.BT_FP64, 1e-8, 0),
+                                           ("LQR N=128 n=12", wl.config1(), bb.BT_FP64, 1e-8, 32),
                                            ("LQR N=128 n=12", wl.config1(), bb.BT_MIXED, 1e-8, 0)):
             dD = torch.tensor(inst.D, device=dev)
             dO = torch.tensor(inst.O, device=dev)
@@ -655,13 +657,15 @@ def other_workload(a):
             us = 1e3 * e0.elapsed_time(e1) / a.steps
             bb.bt_destroy(h)
             # group_ctas 0 picks the shared-memory engine for float64 instances whose
-            # blocks fit one CTA (here LL^T N = 16, n = 6), the persistent kernel otherwise
-            engine = {0: "automatic", 1: "persistent kernel, 1 CTA"}[grp]
+            # blocks fit one CTA (LL^T N = 16, n = 6) or a cluster of 8 (LQR N = 128,
+            # n = 12), the persistent kernel otherwise; -8 asks for a cluster of 8
+            engine = {0: "automatic", -8: "shared-memory engine, cluster of 8",
+                      1: "persistent kernel, 1 CTA", 32: "persistent kernel, 32 CTAs"}[grp]
             rows.append({"instance": name, "precision": "f64" if prec == bb.BT_FP64 else "f32+f64", "tol": tol,
                          "engine": engine, "us_per_solve": us, "iters": it, "us_per_iter": us / max(it, 1)})
         emit({"metric": "microseconds per single-instance solve (latency-bound rows)", "value": rows[0]["us_per_solve"],
               "unit": "us", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "higher_is_better": False,
-              "data": "synthetic (seeded)", "config": {"workload": "single instances, one persistent launch each"},
+              "data": "synthetic (seeded)", "config": {"workload": "single instances, one launch each (setup excluded)"},
               "rows": rows})
         return
     adjoint_workload(a, bb, wl, torch, dev)

@@ -105,12 +105,15 @@ typedef struct bt_params {
   int ctas_per_sm;     /* persistent CTAs per SM; 0 = autotuned/default.           */
   int group_ctas;      /* single-instance solves: CTAs of the persistent kernel that
                           split the block rows (>= 1); 0 = automatic: float64
-                          instances whose seven block arrays fit in one CTA's shared
-                          memory (about 200 KB, e.g. N = 16, n = 6) run on the
-                          shared-memory engine (one CTA, every block loaded once per
-                          solve), others take a CTA count chosen from N; -1 = the
-                          shared-memory engine (BT_ERR_ARG from setup where it does
-                          not fit).                                                 */
+                          instances whose block arrays fit in the shared memory of
+                          one CTA (about 200 KB, e.g. N = 16, n = 6) or of a cluster
+                          of 2, 4 or 8 CTAs (e.g. N = 128, n = 12 on 8) run on the
+                          shared-memory engine (every block loaded once per solve,
+                          halo rows read from the neighbouring CTAs' shared
+                          memory), others take a CTA count chosen from N;
+                          -1, -2, -4, -8 = the shared-memory engine on a cluster of
+                          that many CTAs (BT_ERR_ARG from setup where it does not
+                          fit, or leaves a CTA fewer than two block rows).        */
   int stage_kb;        /* shared-memory pipeline stage size in KiB; 0 = default.   */
   int h_matrix_free;   /* 1: apply H_opt = H_J^2 matrix-free, H_J v = -D^-1 (O_{i-1}^T
                           v_{i-1} + O_i v_{i+1}) from the D^-1 and O blocks the handle
@@ -312,9 +315,10 @@ bt_status bt_alpha_chebyshev(int m, double rho, double* alpha);
 /* bt_autotune -- choose the persistent kernel's launch shape for this handle
  * by timing its own solves of b (DEVICE, packed as for the solve calls):
  * batched handles try stage sizes of 64, 72 and 80 KiB, single-instance
- * handles two mappings: the shared-memory engine (where it fits; reported
- * as *group_ctas = -1) and the persistent kernel with 1, N/16, N/8, N/4 and
- * N/2 CTAs per instance (shapes that do not fit are skipped); each candidate
+ * handles two mappings: the shared-memory engine on clusters of 1, 2, 4 and
+ * 8 CTAs (where they fit; reported as *group_ctas = -C) and the persistent
+ * kernel with 1, N/16, N/8, N/4 and N/2 CTAs per instance (shapes that do
+ * not fit are skipped); each candidate
  * runs one untimed and `trials` timed
  * solves (CUDA events on the handle's stream) and the fastest stays
  * configured for later calls (a captured CUDA graph is dropped).  x (DEVICE)

@@ -23,11 +23,11 @@ extern "C" cudaError_t bt_launch_setup(const bt::SetupParams* P, int mixed, int 
 extern "C" cudaError_t bt_launch_adjoint(const bt::AdjParams* P, cudaStream_t st);
 namespace bt { struct MParams; }
 extern "C" int bt_mrhs_smem_bytes(int n, int tc);
-extern "C" int bt_small_fits(int N, int n, int bs64);
+extern "C" int bt_small_cluster(int N, int n, int bs64, int want);
 extern "C" cudaError_t bt_small_launch(const double* const* blk64, int N, int n, int bs64, int m, const double* alpha,
                                        const double* b, double* x, int use_x0, double tol, int maxit,
                                        long long budget, double* hist, int hist_len, int* iters, int* status,
-                                       int* outer, double* resid, double* errval, cudaStream_t st);
+                                       int* outer, double* resid, double* errval, int C, cudaStream_t st);
 extern "C" int bt_mrhs_tc_supported(int n);
 extern "C" cudaError_t bt_mrhs_occupancy(int smem, int tc, int* blocks);
 extern "C" cudaError_t bt_mrhs_images(int N, int n, int m, const float* const* blk32, int bs32, float* const* img,
@@ -70,7 +70,7 @@ struct bt_ctx {
   double *F64 = nullptr, *K64 = nullptr;
   float *F32 = nullptr, *K32 = nullptr;
   int variant = 0;  // persistent kernel: 0 stored H_opt, 1 general member, 2 matrix-free H_opt
-  int small = 0;    // single float64 instance solved by the shared-memory engine (bt_small.cu)
+  int small = 0;    // single float64 instance on the shared-memory engine (bt_small.cu): its cluster size, 0 = off
   double* hist = nullptr;  // caller's per-iteration history buffer (bt_set_history), or null
   int hist_len = 0;
   bt::InstDesc* d_inst = nullptr;
@@ -194,7 +194,7 @@ bt_status check_params(const bt_params* p, double* alpha_out) {
       if (alpha_out[j] != 1.0) return BT_ERR_PARAM;
   if (p->precision != BT_FP64 && p->precision != BT_MIXED) return BT_ERR_PARAM;
   if (p->tol_inner < 0.0 || p->tol_inner >= 1.0) return BT_ERR_PARAM;
-  if (p->max_outer < 0 || p->cycle_budget < 0 || p->ctas_per_sm < 0 || p->group_ctas < -1 || p->stage_kb < 0)
+  if (p->max_outer < 0 || p->cycle_budget < 0 || p->ctas_per_sm < 0 || p->group_ctas < -8 || p->stage_kb < 0)
     return BT_ERR_PARAM;
   // the matrix-free H applies H_opt = H_J^2: the optimum only
   if (p->h_matrix_free != 0 && (p->h_matrix_free != 1 || p->a != 1.0)) return BT_ERR_PARAM;
@@ -253,18 +253,22 @@ bt_status read_setup_status(bt_ctx* h) {
 // Launch shape of the persistent kernel for a stage size and (single
 // instance) a CTA count; 0 = the defaults.  Sets stages, stage and vector-slot
 // bytes, dynamic shared memory, grid and group size; allocates nothing.
-// Whether a single-instance handle can use the shared-memory engine: float64,
-// the optimum with stored H blocks, every block in one CTA's shared memory.
-bool small_eligible(const bt_ctx* h) {
-  return !h->batched && !h->mixed && h->variant == 0 && h->B == 1 &&
-         bt_small_fits(h->N[0], h->n[0], (int)rup((long long)h->n[0] * h->n[0], 2));
+// The cluster size of the shared-memory engine for a single-instance handle
+// (float64, the optimum with stored H blocks): `want` CTAs (want > 0), or the
+// smallest cluster whose CTAs hold the blocks (want = 0); 0 where none does.
+int small_cluster(const bt_ctx* h, int want) {
+  if (h->batched || h->mixed || h->variant != 0 || h->B != 1) return 0;
+  return bt_small_cluster(h->N[0], h->n[0], (int)rup((long long)h->n[0] * h->n[0], 2), want);
 }
 
 bt_status configure(bt_ctx* h, int stage_kb, int group_ctas) {
-  // single instances: group_ctas -1 asks for the shared-memory engine, 0 takes
-  // it where eligible; both fall back to the persistent kernel's shape rules
-  h->small = (group_ctas <= 0 && small_eligible(h)) ? 1 : 0;
-  if (group_ctas == -1 && !h->small) return BT_ERR_ARG;
+  // single instances: group_ctas -C asks for the shared-memory engine on a
+  // cluster of C CTAs, 0 takes it (smallest cluster) where eligible; the
+  // persistent kernel's shape is configured either way
+  if (group_ctas < 0 && group_ctas != -1 && group_ctas != -2 && group_ctas != -4 && group_ctas != -8)
+    return BT_ERR_ARG;
+  h->small = group_ctas <= 0 ? small_cluster(h, -group_ctas) : 0;
+  if (group_ctas < 0 && !h->small) return BT_ERR_ARG;
   if (group_ctas < 0) group_ctas = 0;
   const bool mixed = h->mixed != 0;
   const bool general = h->variant == 1;
@@ -593,15 +597,14 @@ bt_status bt_autotune(bt_handle h, const double* b, double* x, double tol, int m
       }
       std::fclose(f);
       if (hit_kb >= 0 && configure(h, hit_kb, h->batched ? 0 : hit_g) == BT_OK) {
-        if (!h->batched && hit_g >= 1) h->small = 0;  // a recorded CTA count means the persistent kernel
         if (h->graph) cudaGraphExecDestroy(h->graph);
         if (h->graph_src) cudaGraphDestroy(h->graph_src);
         h->graph = nullptr;
         h->graph_src = nullptr;
         h->prm.stage_kb = hit_kb;
-        h->prm.group_ctas = h->batched ? 0 : (h->small ? -1 : h->G);
+        h->prm.group_ctas = h->batched ? 0 : (h->small ? -h->small : h->G);
         if (stage_kb) *stage_kb = h->stage_bytes / 1024;
-        if (group_ctas) *group_ctas = h->small ? -1 : h->G;
+        if (group_ctas) *group_ctas = h->small ? -h->small : h->G;
         const bt_status o = h->batched ? bt_pcg_solve_batched_async(h, b, x, tol, maxit, nullptr, nullptr)
                                        : bt_pcg_solve_async(h, b, x, tol, maxit, nullptr, nullptr);
         if (o != BT_OK) return o;
@@ -615,7 +618,8 @@ bt_status bt_autotune(bt_handle h, const double* b, double* x, double tol, int m
   if (h->batched) {
     for (int kb : {64, 72, 80}) cand.push_back({kb, 0});
   } else {
-    if (small_eligible(h)) cand.push_back({h->prm.stage_kb, -1});
+    for (int C = 1; C <= 8; C *= 2)
+      if (small_cluster(h, C)) cand.push_back({h->prm.stage_kb, -C});
     const int N = h->N[0];
     std::vector<int> gs = {1, N / 16, N / 8, N / 4, N / 2};
     for (int g : gs)
@@ -647,7 +651,6 @@ bt_status bt_autotune(bt_handle h, const double* b, double* x, double tol, int m
   bt_status out = BT_OK;
   for (size_t i = 0; i < cand.size() && out == BT_OK; ++i) {
     if (configure(h, cand[i].first, cand[i].second) != BT_OK) continue;  // shape does not fit: skip
-    if (cand[i].second >= 1) h->small = 0;  // time the persistent kernel itself
     if ((out = solve()) != BT_OK) break;                                  // untimed
     cudaEventRecord(e0, st);
     for (int t = 0; t < trials && out == BT_OK; ++t) out = solve();
@@ -665,9 +668,8 @@ bt_status bt_autotune(bt_handle h, const double* b, double* x, double tol, int m
   }
   const bt_status cs = configure(h, cand[best].first, cand[best].second);
   if (cs != BT_OK) return cs;
-  if (cand[best].second >= 1) h->small = 0;
   h->prm.stage_kb = cand[best].first;
-  h->prm.group_ctas = h->batched ? 0 : (h->small ? -1 : h->G);
+  h->prm.group_ctas = h->batched ? 0 : (h->small ? -h->small : h->G);
   if (cache && *cache) {
     if (FILE* f = std::fopen(cache, "a")) {
       std::fprintf(f, "{\"key\": \"%s\", \"stage_kb\": %d, \"group_ctas\": %d}\n", key.c_str(),
@@ -676,7 +678,7 @@ bt_status bt_autotune(bt_handle h, const double* b, double* x, double tol, int m
     }
   }
   if (stage_kb) *stage_kb = h->stage_bytes / 1024;
-  if (group_ctas) *group_ctas = h->small ? -1 : h->G;
+  if (group_ctas) *group_ctas = h->small ? -h->small : h->G;
   if (out != BT_OK) return out;
   // leave x with a solve in the chosen shape
   if ((out = solve()) != BT_OK) return out;
@@ -953,7 +955,7 @@ static bt_status solve_launch(bt_handle h, const double* b, double* x, double to
                                    h->prm.use_x0, tol, maxit,
                                    h->prm.cycle_budget > 0 ? h->prm.cycle_budget : (1ll << 34), h->hist,
                                    h->hist_len, h->d_iters, h->d_status, h->d_outer, h->d_resid, h->d_errval,
-                                   h->stream));
+                                   h->small, h->stream));
   }
   bt::KParams P = base_kparams(h);
   P.op = bt::kOpSolve;

@@ -1,5 +1,6 @@
-// Small single instances (float64): the whole PCG of one instance in one CTA
-// with every block resident in shared memory.
+// Small single instances (float64): the whole PCG of one instance in one CTA,
+// or in one thread-block cluster of C CTAs, with every block resident in
+// shared memory.
 //
 // For an instance as small as N = 16 block rows of n = 6 (the seven float64
 // block arrays D, O, D^-1, E, Hd, Hu, Hl take 32 KB) the persistent kernel's
@@ -8,18 +9,34 @@
 // and every iteration runs from shared memory: block-tridiagonal SpMV
 // (Eq. 1), the preconditioner apply y0 = G r, y_j = H y_{j-1},
 // z = sum_j alpha_j y_j (Sec. 4.1-4.2 closed form), textbook PCG on the
-// float64 user vectors with a fixed-order block reduction for the dots.
+// float64 user vectors with a fixed-order reduction for the dots.
+//
+// A larger instance (LQR N = 128, n = 12: 1.1 MB of float64 blocks) splits
+// its block rows over a cluster of C CTAs (rows [c N / C, (c + 1) N / C) in
+// CTA c, at least two rows each): each CTA holds the blocks of its rows (and
+// the two rows above, whose O, E, Hl its rows read) and its rows of every
+// vector; the one or two halo rows a sweep reads from a neighbour come from
+// that CTA's shared memory through the cluster's distributed shared memory,
+// after a cluster barrier that makes them final.  A dot product sums each
+// CTA's total, then the C totals in rank order, so every CTA holds the same
+// bitwise result and takes the same decisions.
+//
 // Results and statuses are those of the persistent kernel's float64 path
 // (recursive residual test ||r|| <= tol ||b||, x0 = 0 or the caller's).
+#include <cooperative_groups.h>
+
 #include <cstdint>
 
 #include "../../include/bt.h"
 #include "bt_common.cuh"
 
+namespace cg = cooperative_groups;
+
 namespace bt {
 
 constexpr int kSmallThreads = 256;
-constexpr int kSmallMaxBytes = 200 * 1024;  // shared memory the engine may take
+constexpr int kSmallMaxBytes = 200 * 1024;  // shared memory one CTA may take
+constexpr int kSmallMaxCluster = 8;         // portable cluster size
 
 struct SmallParams {
   const double *D, *O, *Dinv, *E, *Hd, *Hu, *Hl;  // library slots (column-major, stride bs)
@@ -37,124 +54,234 @@ struct SmallParams {
   double *resid, *errval;
 };
 
-// Shared-memory floats of the engine: seven block arrays of N slots and eight
-// vectors of N n doubles, plus the reduction scratch.
-__host__ __device__ inline long long small_bytes(int N, int n, int bs) {
-  return (7ll * N * bs + 8ll * N * n) * 8 + 64 * 8;
+// first block row of CTA c of C
+__host__ __device__ inline int small_row0(int N, int C, int c) { return (int)((long long)c * N / C); }
+
+// Largest per-CTA row count and block-slot count over the C CTAs (a CTA keeps
+// the slots of rows max(0, s - 2) .. e - 1); every CTA uses the same layout.
+__host__ __device__ inline void small_extent(int N, int C, int& rows_max, int& slots_max) {
+  rows_max = slots_max = 0;
+  for (int c = 0; c < C; ++c) {
+    const int s = small_row0(N, C, c), e = small_row0(N, C, c + 1);
+    const int lo = s >= 2 ? s - 2 : 0;
+    rows_max = rows_max > e - s ? rows_max : e - s;
+    slots_max = slots_max > e - lo ? slots_max : e - lo;
+  }
 }
 
+// Shared memory of one CTA: seven block arrays, eight vectors, scratch.
+__host__ __device__ inline long long small_bytes(int N, int n, int bs, int C) {
+  int rows_max, slots_max;
+  small_extent(N, C, rows_max, slots_max);
+  return (7ll * slots_max * bs + 8ll * rows_max * n) * 8 + 64 * 8;
+}
+
+// Whether C CTAs can hold the instance: every CTA two rows at least (the halo
+// of the H sweep then sits in the neighbouring CTA), the shared memory cap.
+__host__ __device__ inline bool small_fits_c(int N, int n, int bs, int C) {
+  if (N < 1 || n < 1 || C < 1 || C > kSmallMaxCluster) return false;
+  if (C > 1 && N < 2 * C) return false;
+  return small_bytes(N, n, bs, C) <= kSmallMaxBytes;
+}
+
+// CL: launched as a cluster of C > 1 CTAs (distributed shared memory and
+// cluster barriers); else one CTA, with none of that code.
+template <bool CL>
 struct Small {
   const SmallParams& P;
-  double *D, *O, *Dinv, *E, *Hd, *Hu, *Hl;
-  double* red;  // [32] warp partials + broadcast
-  int N, n, bs, tid, nel;
+  double *D, *O, *Dinv, *E, *Hd, *Hu, *Hl;  // local slots: block row i at (i - lo) * bs
+  double* vbase;                            // eight vectors of rows_max * n (local rows)
+  double* red;                              // [64] scratch: warp sums, totals, cluster slots
+  int N, n, bs, tid, C, rank, s, e, lo, nel, rows_max;
+  int s_prev, s_next;  // first rows of the neighbouring CTAs
+  int rpar = 0;        // parity of the cluster-sum slot
 
   __device__ Small(const SmallParams& P_, double* sm) : P(P_) {
     N = P.N;
     n = P.n;
     bs = P.bs;
     tid = threadIdx.x;
-    nel = N * n;
-    const long long A = (long long)N * bs;
+    C = 1;
+    rank = 0;
+    if constexpr (CL) {
+      C = (int)cg::this_cluster().num_blocks();
+      rank = (int)cg::this_cluster().block_rank();
+    }
+    s = small_row0(N, C, rank);
+    e = small_row0(N, C, rank + 1);
+    s_prev = rank > 0 ? small_row0(N, C, rank - 1) : 0;
+    s_next = e;
+    lo = s >= 2 ? s - 2 : 0;
+    nel = (e - s) * n;
+    int slots_max;
+    small_extent(N, C, rows_max, slots_max);
+    const long long A = (long long)slots_max * bs;
     D = sm; O = D + A; Dinv = O + A; E = Dinv + A; Hd = E + A; Hu = Hd + A; Hl = Hu + A;
-    red = Hl + A + 8ll * nel;
+    vbase = Hl + A;
+    red = vbase + 8ll * rows_max * n;
   }
-  __device__ double* vec(int k) { return Hl + (long long)N * bs + (long long)k * nel; }
+  __device__ double* vec(int k) { return vbase + (long long)k * rows_max * n; }
+  __device__ const double* slot(const double* M, int i) { return M + (long long)(i - lo) * bs; }
 
-  // sum over the CTA, fixed order: a shuffle tree within each warp, then one
-  // over the warps' sums (float64 adds are slow here; no serial chains)
-  __device__ double reduce(double v) {
+  // row r (0 <= r < N) of vector v: local, or a neighbour's (same offsets in
+  // every CTA of the cluster)
+  __device__ const double* row(const double* v, int r) {
+    if constexpr (CL) {
+      if (r < s || r >= e) {
+        double* w = const_cast<double*>(v);
+        if (r < s) return cg::this_cluster().map_shared_rank(w, rank - 1) + (long long)(r - s_prev) * n;
+        return cg::this_cluster().map_shared_rank(w, rank + 1) + (long long)(r - s_next) * n;
+      }
+    }
+    return v + (long long)(r - s) * n;
+  }
+
+  // every CTA's writes before it are visible to the whole cluster after it
+  __device__ void csync() {
+    if constexpr (CL) cg::this_cluster().sync();
+    else __syncthreads();
+  }
+
+  // v[0..K) summed over the CTA (shuffle tree in each warp, then over the
+  // warps) and then over the cluster in rank order: the same bits in every CTA
+  template <int K>
+  __device__ void reduceK(double (&v)[K]) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __syncthreads();  // red free (the previous broadcast was read)
-    if ((tid & 31) == 0) red[tid >> 5] = v;
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int q = 0; q < K; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    __syncthreads();  // scratch free (the previous totals were read)
+    if ((tid & 31) == 0)
+#pragma unroll
+      for (int q = 0; q < K; ++q) red[8 * q + (tid >> 5)] = v[q];
     __syncthreads();
     if (tid < 32) {
-      double w = tid < kSmallThreads / 32 ? red[tid] : 0.0;
+      double w[K];
 #pragma unroll
-      for (int o = kSmallThreads / 64; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-      if (tid == 0) red[32] = w;
+      for (int q = 0; q < K; ++q) w[q] = tid < kSmallThreads / 32 ? red[8 * q + tid] : 0.0;
+#pragma unroll
+      for (int o = kSmallThreads / 64; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < K; ++q) w[q] += __shfl_xor_sync(0xffffffffu, w[q], o);
+      if (tid == 0)
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+          red[16 + q] = w[q];
+          red[20 + 2 * rpar + q] = w[q];  // this CTA's totals for the cluster sum
+        }
     }
+    if constexpr (CL) {
+      cg::this_cluster().sync();
+      if (tid == 0) {
+        double t[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q) t[q] = 0.0;
+        for (int c = 0; c < C; ++c) {
+          const double* rc = cg::this_cluster().map_shared_rank(red, c);
+#pragma unroll
+          for (int q = 0; q < K; ++q) t[q] += rc[20 + 2 * rpar + q];
+        }
+#pragma unroll
+        for (int q = 0; q < K; ++q) red[16 + q] = t[q];
+      }
+    }
+    // a CTA's slot of parity p is rewritten two sums later, after the next
+    // sum's cluster barrier: every CTA has read it by then
+    rpar ^= 1;
     __syncthreads();
-    return red[32];
+#pragma unroll
+    for (int q = 0; q < K; ++q) v[q] = red[16 + q];
+  }
+  __device__ void reduce2(double a, double b, double& ra, double& rb) {
+    double v[2] = {a, b};
+    reduceK<2>(v);
+    ra = v[0];
+    rb = v[1];
+  }
+  __device__ double reduce(double a) {
+    double v[1] = {a};
+    reduceK<1>(v);
+    return v[0];
   }
 
-  // out = (block row of M) v for every element (i, a); kind 0: S, 1: G, 2: H
+  // out = (block row of M) v for this CTA's elements (i, a); kind 0: S, 1: G, 2: H
   __device__ void sweep(int kind, const double* v, double* out) {
-    for (int e = tid; e < nel; e += kSmallThreads) {
-      const int i = e / n, a = e - i * n;
-      const double* vi = v + i * n;
+    for (int el = tid; el < nel; el += kSmallThreads) {
+      const int li = el / n, a = el - li * n;
+      const int i = s + li;
+      const double* vi = v + (long long)li * n;
       double acc = 0.0;
-      const double* M0 = (kind == 0 ? D : (kind == 1 ? Dinv : Hd)) + (long long)i * bs;
+      const double* M0 = slot(kind == 0 ? D : (kind == 1 ? Dinv : Hd), i);
       for (int c = 0; c < n; ++c) acc = fma(M0[c * n + a], vi[c], acc);
       if (kind == 0 || kind == 1) {
         const double* M = kind == 0 ? O : E;
         const double sg = kind == 0 ? 1.0 : -1.0;  // G's off-diagonal blocks are -E_i, -E_{i-1}^T
         double t = 0.0;
         if (i + 1 < N) {  // (i, i+1): O_i / E_i
-          const double* Mi = M + (long long)i * bs;
-          const double* vn = vi + n;
+          const double* Mi = slot(M, i);
+          const double* vn = row(v, i + 1);
           for (int c = 0; c < n; ++c) t = fma(Mi[c * n + a], vn[c], t);
         }
         if (i >= 1) {  // (i, i-1): O_{i-1}^T / E_{i-1}^T
-          const double* Mp = M + (long long)(i - 1) * bs;
-          const double* vp = vi - n;
+          const double* Mp = slot(M, i - 1);
+          const double* vp = row(v, i - 1);
           for (int c = 0; c < n; ++c) t = fma(Mp[a * n + c], vp[c], t);
         }
         acc = fma(sg, t, acc);
       } else {
         if (i + 2 < N) {  // (i, i+2): Hu_i
-          const double* Mi = Hu + (long long)i * bs;
-          const double* vn = vi + 2 * n;
+          const double* Mi = slot(Hu, i);
+          const double* vn = row(v, i + 2);
           for (int c = 0; c < n; ++c) acc = fma(Mi[c * n + a], vn[c], acc);
         }
         if (i >= 2) {  // (i, i-2): Hl_{i-2}
-          const double* Mp = Hl + (long long)(i - 2) * bs;
-          const double* vp = vi - 2 * n;
+          const double* Mp = slot(Hl, i - 2);
+          const double* vp = row(v, i - 2);
           for (int c = 0; c < n; ++c) acc = fma(Mp[c * n + a], vp[c], acc);
         }
       }
-      out[e] = acc;
+      out[el] = acc;
     }
   }
 
-  // z = M^-1 r (y0 = G r, y_j = H y_{j-1}, z = y0 + sum_{j>0} alpha_j y_j); returns r . z
+  // z = M^-1 r (y0 = G r, y_j = H y_{j-1}, z = y0 + sum_{j>0} alpha_j y_j); returns r . z.
+  // r must be final in every CTA (a cluster barrier since its last write).
   __device__ double precond(const double* r, double* z, double* y0, double* ya, double* yb) {
     sweep(1, r, P.m == 1 ? z : y0);
-    __syncthreads();
     if (P.m > 1) {
       const double* yin = y0;
       for (int j = 1; j < P.m; ++j) {
+        csync();  // yin final in every CTA (the H sweep reads two rows of the neighbours)
         double* yout = (j & 1) ? ya : yb;
         sweep(2, yin, yout);
-        __syncthreads();
         yin = yout;
         const double aj = P.alpha[j];
-        for (int e = tid; e < nel; e += kSmallThreads) z[e] = fma(aj, yout[e], j == 1 ? y0[e] : z[e]);
-        __syncthreads();
+        for (int el = tid; el < nel; el += kSmallThreads) z[el] = fma(aj, yout[el], j == 1 ? y0[el] : z[el]);
       }
     }
     double t = 0.0;
-    for (int e = tid; e < nel; e += kSmallThreads) t = fma(r[e], z[e], t);
+    for (int el = tid; el < nel; el += kSmallThreads) t = fma(r[el], z[el], t);
     return reduce(t);
   }
 };
 
+template <bool CL>
 __global__ void __launch_bounds__(kSmallThreads, 1) bt_small_kernel(const __grid_constant__ SmallParams P) {
   extern __shared__ __align__(16) double smd[];
-  Small Sm(P, smd);
+  Small<CL> Sm(P, smd);
   const int tid = threadIdx.x;
   const long long deadline = clock64() + P.budget;
-  // load the blocks (all N slots of the seven arrays) once
+  // load the blocks of this CTA's rows (and the two rows above) once
   {
-    const long long A = (long long)P.N * P.bs;
+    const long long off = (long long)Sm.lo * P.bs, cnt = (long long)(Sm.e - Sm.lo) * P.bs;
     const double* src[7] = {P.D, P.O, P.Dinv, P.E, P.Hd, P.Hu, P.Hl};
     double* dst[7] = {Sm.D, Sm.O, Sm.Dinv, Sm.E, Sm.Hd, Sm.Hu, Sm.Hl};
     const int na = P.m > 1 ? 7 : 4;
     for (int k = 0; k < na; ++k)
-      for (long long t = tid; t < A; t += kSmallThreads) dst[k][t] = __ldg(src[k] + t);
+      for (long long t = tid; t < cnt; t += kSmallThreads) dst[k][t] = __ldg(src[k] + off + t);
   }
   const int nel = Sm.nel;
+  const long long g0 = (long long)Sm.s * P.n;  // this CTA's first element in the user vectors
   double* x = Sm.vec(0);
   double* r = Sm.vec(1);
   double* p = Sm.vec(2);
@@ -163,28 +290,28 @@ __global__ void __launch_bounds__(kSmallThreads, 1) bt_small_kernel(const __grid
   double* y0 = Sm.vec(5);
   double* ya = Sm.vec(6);
   double* yb = Sm.vec(7);
-  double* const hist = (P.hist && tid == 0) ? P.hist : nullptr;
+  double* const hist = (P.hist && tid == 0 && Sm.rank == 0) ? P.hist : nullptr;
   auto record = [&](int idx, int field, double v) {
     if (hist && idx >= 0 && idx < P.hist_len) hist[(size_t)idx * 3 + field] = v;
   };
   // r0 = b - S x0 (or b with x0 = 0)
   double bb = 0.0;
-  for (int e = tid; e < nel; e += kSmallThreads) {
-    const double bv = P.b[e];
+  for (int el = tid; el < nel; el += kSmallThreads) {
+    const double bv = P.b[g0 + el];
     bb = fma(bv, bv, bb);
-    x[e] = P.use_x0 ? P.x[e] : 0.0;
-    r[e] = bv;
+    x[el] = P.use_x0 ? P.x[g0 + el] : 0.0;
+    r[el] = bv;
   }
-  __syncthreads();
+  Sm.csync();  // x final in every CTA
   if (P.use_x0) {
     Sm.sweep(0, x, q);
-    __syncthreads();
-    for (int e = tid; e < nel; e += kSmallThreads) r[e] -= q[e];
+    for (int el = tid; el < nel; el += kSmallThreads) r[el] -= q[el];
   }
-  const double nb = sqrt(Sm.reduce(bb));
   double rr_loc = 0.0;
-  for (int e = tid; e < nel; e += kSmallThreads) rr_loc = fma(r[e], r[e], rr_loc);
-  double rr = Sm.reduce(rr_loc);
+  for (int el = tid; el < nel; el += kSmallThreads) rr_loc = fma(r[el], r[el], rr_loc);
+  double bbt, rr;
+  Sm.reduce2(bb, rr_loc, bbt, rr);  // also makes r final in every CTA
+  const double nb = sqrt(bbt);
   int status = kOK, it = 0;
   double errv = 0.0;
   const double nrhs = P.use_x0 ? nb : sqrt(rr);
@@ -193,23 +320,31 @@ __global__ void __launch_bounds__(kSmallThreads, 1) bt_small_kernel(const __grid
     status = kErrNonfinite;
   } else if (nrhs > 0.0 && !(rr <= thr2)) {
     double rho = Sm.precond(r, z, y0, ya, yb);
-    for (int e = tid; e < nel; e += kSmallThreads) p[e] = z[e];
-    __syncthreads();
+    for (int el = tid; el < nel; el += kSmallThreads) p[el] = z[el];
     for (int k = 1;; ++k) {
       if (k > P.maxit) {
         status = kErrNoConv;
         it = P.maxit;
         break;
       }
-      if (clock64() > deadline) {
+      Sm.csync();  // p final in every CTA
+      Sm.sweep(0, p, q);
+      double t = 0.0;
+      for (int el = tid; el < nel; el += kSmallThreads) t = fma(p[el], q[el], t);
+      // the cycle budget: rank 0's clock decides for the cluster, through the sum
+      double pq, late = 0.0;
+      if constexpr (CL) {
+        Sm.reduce2(t, (tid == 0 && Sm.rank == 0 && clock64() > deadline) ? 1.0 : 0.0, pq, late);
+      } else {
+        if (tid == 0) Sm.red[24] = clock64() > deadline ? 1.0 : 0.0;  // read after the sum's barriers
+        pq = Sm.reduce(t);
+        late = Sm.red[24];
+      }
+      if (late > 0.0) {
         status = kErrTimeout;
         it = k - 1;
         break;
       }
-      Sm.sweep(0, p, q);
-      double t = 0.0;
-      for (int e = tid; e < nel; e += kSmallThreads) t = fma(p[e], q[e], t);
-      const double pq = Sm.reduce(t);
       if (!isfinite(pq)) {
         status = kErrNonfinite;
         it = k - 1;
@@ -225,13 +360,13 @@ __global__ void __launch_bounds__(kSmallThreads, 1) bt_small_kernel(const __grid
       record(k - 1, 1, al);
       record(k - 1, 2, 0.0);
       t = 0.0;
-      for (int e = tid; e < nel; e += kSmallThreads) {
-        x[e] = fma(al, p[e], x[e]);
-        const double rv = fma(-al, q[e], r[e]);
-        r[e] = rv;
+      for (int el = tid; el < nel; el += kSmallThreads) {
+        x[el] = fma(al, p[el], x[el]);
+        const double rv = fma(-al, q[el], r[el]);
+        r[el] = rv;
         t = fma(rv, rv, t);
       }
-      rr = Sm.reduce(t);
+      rr = Sm.reduce(t);  // also makes r final in every CTA
       it = k;
       record(k - 1, 0, sqrt(rr) / nrhs);
       if (!isfinite(rr)) {
@@ -243,32 +378,37 @@ __global__ void __launch_bounds__(kSmallThreads, 1) bt_small_kernel(const __grid
       const double be = rz / rho;
       record(k - 1, 2, be);
       rho = rz;
-      for (int e = tid; e < nel; e += kSmallThreads) p[e] = fma(be, p[e], z[e]);
-      __syncthreads();
+      for (int el = tid; el < nel; el += kSmallThreads) p[el] = fma(be, p[el], z[el]);
     }
   }
-  __syncthreads();
-  for (int e = tid; e < nel; e += kSmallThreads) P.x[e] = x[e];
-  if (tid == 0) {
+  for (int el = tid; el < nel; el += kSmallThreads) P.x[g0 + el] = x[el];
+  if (tid == 0 && Sm.rank == 0) {
     *P.iters = it;
     *P.status = status;
     *P.outer = 0;
     *P.resid = status == kErrBreakdown ? errv : (nb > 0 ? sqrt(rr) / nb : 0.0);
     *P.errval = errv;
   }
+  // no CTA leaves while a neighbour may still read its shared memory
+  Sm.csync();
 }
 
 }  // namespace bt
 
-// Whether an instance of this shape fits the engine (shared memory).
-extern "C" int bt_small_fits(int N, int n, int bs64) {
-  return N >= 1 && n >= 1 && bt::small_bytes(N, n, bs64) <= bt::kSmallMaxBytes;
+// The cluster size of the engine for an instance of this shape: 1 where one
+// CTA holds it, else the smallest of 2, 4, 8 that does; 0 where none does.
+// want > 0 asks for exactly that size (0 if it does not fit).
+extern "C" int bt_small_cluster(int N, int n, int bs64, int want) {
+  if (want > 0) return bt::small_fits_c(N, n, bs64, want) ? want : 0;
+  for (int C = 1; C <= bt::kSmallMaxCluster; C *= 2)
+    if (bt::small_fits_c(N, n, bs64, C)) return C;
+  return 0;
 }
 
 extern "C" cudaError_t bt_small_launch(const double* const* blk64, int N, int n, int bs64, int m, const double* alpha,
                                        const double* b, double* x, int use_x0, double tol, int maxit,
                                        long long budget, double* hist, int hist_len, int* iters, int* status,
-                                       int* outer, double* resid, double* errval, cudaStream_t st) {
+                                       int* outer, double* resid, double* errval, int C, cudaStream_t st) {
   bt::SmallParams P{};
   P.D = blk64[0]; P.O = blk64[1]; P.Dinv = blk64[2]; P.E = blk64[3];
   P.Hd = blk64[4]; P.Hu = blk64[5]; P.Hl = blk64[6];
@@ -277,9 +417,30 @@ extern "C" cudaError_t bt_small_launch(const double* const* blk64, int N, int n,
   P.b = b; P.x = x; P.use_x0 = use_x0; P.tol = tol; P.maxit = maxit; P.budget = budget;
   P.hist = hist; P.hist_len = hist_len;
   P.iters = iters; P.status = status; P.outer = outer; P.resid = resid; P.errval = errval;
-  const int smem = (int)bt::small_bytes(N, n, bs64);
-  cudaError_t e = cudaFuncSetAttribute(bt::bt_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (!bt::small_fits_c(N, n, bs64, C)) return cudaErrorInvalidValue;
+  const int smem = (int)bt::small_bytes(N, n, bs64, C);
+  if (C == 1) {
+    cudaError_t e =
+        cudaFuncSetAttribute(bt::bt_small_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    bt::bt_small_kernel<false><<<1, bt::kSmallThreads, smem, st>>>(P);
+    return cudaGetLastError();
+  }
+  cudaError_t e = cudaFuncSetAttribute(bt::bt_small_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  bt::bt_small_kernel<<<1, bt::kSmallThreads, smem, st>>>(P);
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)C);
+  cfg.blockDim = dim3(bt::kSmallThreads);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, bt::bt_small_kernel<true>, P);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

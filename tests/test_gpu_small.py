@@ -1,8 +1,8 @@
-"""The shared-memory engine for small float64 single instances (one CTA,
-every block resident): against the oracle's PCG (iterations within 1,
-solution within 1e-10), against the persistent kernel, status paths,
-history recording, eligibility and the autotuner's choice between the two
-mappings."""
+"""The shared-memory engine for small float64 single instances (one CTA, or a
+cluster of 2, 4 or 8 CTAs sharing the block rows, every block resident):
+against the oracle's PCG (iterations within 1, solution within 1e-10),
+against the persistent kernel, status paths, history recording,
+eligibility and the autotuner's choice between the two mappings."""
 import numpy as np
 import pytest
 import torch
@@ -15,7 +15,7 @@ from _util import Single, dev, host, rel
 
 pytestmark = pytest.mark.gpu
 
-SMALL, PERSISTENT = -1, 1  # group_ctas: shared-memory engine, persistent kernel on one CTA
+SMALL, PERSISTENT = -1, 1  # group_ctas: shared-memory engine (one CTA), persistent kernel on one CTA
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -56,6 +56,70 @@ def test_small_engine_matches_oracle_and_persistent(N, n, m, alpha):
     assert rel(x, out[PERSISTENT][1]) <= 1e-10
 
 
+def test_config1_float64_on_a_cluster_matches_oracle():
+    """LQR N = 128, n = 12 (1.1 MB of float64 blocks): the engine on a cluster
+    of 8 CTAs (16 block rows each), as the automatic choice picks it."""
+    inst = wl.config1()
+    alpha = [1.0, 7.0]
+    ref = orc.pcg_opt(inst.D, inst.O, inst.b, alpha, 1e-10, 2000)
+    for g in (-8, 0):
+        with Single(inst, m=2, alpha=alpha, group_ctas=g) as s:
+            s.ok()
+            st, it, x = s.solve(inst.b, 1e-10, 2000)
+        assert st == bb.BT_OK
+        assert abs(it - ref.iters) <= 1
+        assert rel(x, ref.x) <= 1e-10
+
+
+# ragged row splits (N not a multiple of C; two rows in some CTAs), every H
+# sweep reading two halo rows from a neighbour
+@pytest.mark.parametrize("N,n,C", [(4, 6, 2), (9, 5, 4), (17, 8, 8), (16, 6, 8), (50, 12, 4), (33, 16, 8)])
+@pytest.mark.parametrize("m,alpha", [(1, [1.0]), (2, [1.0, 7.0]), (3, [1.0, 2.0, 3.0])])
+def test_cluster_engine_matches_oracle_and_persistent(N, n, C, m, alpha):
+    inst = wl.small_llt(95, N, n)
+    ref = orc.pcg_opt(inst.D, inst.O, inst.b, alpha, 1e-11, 2000)
+    out = {}
+    for g in (-C, PERSISTENT):
+        with Single(inst, m=m, alpha=alpha, group_ctas=g) as s:
+            s.ok()
+            st, it, x = s.solve(inst.b, 1e-11, 2000)
+            assert st == bb.BT_OK
+            out[g] = (it, x)
+    it, x = out[-C]
+    assert abs(it - ref.iters) <= 1
+    assert rel(x, ref.x) <= 1e-10
+    assert rel(x, out[PERSISTENT][1]) <= 1e-10
+
+
+def test_cluster_engine_status_paths_and_initial_guess():
+    inst = wl.small_llt(96, 24, 6)
+    xr = orc.direct_solve(inst.D, inst.O, inst.b)
+    with Single(inst, m=2, alpha=[1.0, 7.0], group_ctas=-4, use_x0=True) as s:
+        s.ok()
+        st, it, x = s.solve(np.zeros_like(inst.b), 1e-10, 100, x0=np.zeros_like(inst.b))
+        assert st == bb.BT_OK and it == 0 and np.all(x == 0)
+        st, it, x = s.solve(inst.b, 1e-14, 3, x0=np.zeros_like(inst.b))
+        assert st == bb.BT_ERR_NO_CONVERGENCE and it == 3
+        b = inst.b.copy()
+        b[20, 2] = np.inf
+        st, it, x = s.solve(b, 1e-10, 100, x0=np.zeros_like(inst.b))
+        assert st == bb.BT_ERR_NONFINITE
+        x0 = xr + 1e-3 * np.random.default_rng(5).standard_normal(xr.shape)
+        st, it, x = s.solve(inst.b, 1e-12, 300, x0=x0)
+        assert st == bb.BT_OK
+        ref = orc.pcg_opt(inst.D, inst.O, inst.b, [1.0, 7.0], 1e-12, 300, x0=x0)
+        assert abs(it - ref.iters) <= 1 and rel(x, xr) <= 1e-9
+
+
+def test_cluster_engine_rejects_too_few_rows_per_cta():
+    inst = wl.small_llt(97, 10, 4)  # 8 CTAs would hold one row each
+    p, keep = bb.make_params(m=2, alpha=[1.0, 7.0], group_ctas=-8)
+    st, h = bb.bt_setup(inst.N, inst.n, dev(inst.D), dev(inst.O), p)
+    assert st == bb.BT_ERR_ARG
+    if h:
+        bb.bt_destroy(h)
+
+
 def test_small_engine_status_paths():
     inst = wl.small_llt(91, 12, 5)
     with Single(inst, m=2, alpha=[1.0, 7.0], group_ctas=SMALL) as s:
@@ -93,7 +157,7 @@ def test_small_engine_initial_guess():
 def test_small_engine_history_matches_persistent():
     inst = wl.small_llt(93, 16, 6)
     hists = {}
-    for g in (SMALL, PERSISTENT):
+    for g in (SMALL, -4, PERSISTENT):
         hist = torch.zeros(64 * 3, dtype=torch.float64, device="cuda")
         with Single(inst, m=2, alpha=[1.0, 7.0], group_ctas=g) as s:
             s.ok()
@@ -101,9 +165,10 @@ def test_small_engine_history_matches_persistent():
             st, it, x = s.solve(inst.b, 1e-10, 64)
             assert st == bb.BT_OK
         hists[g] = (it, host(hist).reshape(64, 3))
-    it = min(hists[SMALL][0], hists[PERSISTENT][0])
-    a, b = hists[SMALL][1][:it], hists[PERSISTENT][1][:it]
-    assert np.allclose(a, b, rtol=1e-8, atol=1e-14)
+    it = min(h[0] for h in hists.values())
+    for g in (SMALL, -4):
+        a, b = hists[g][1][:it], hists[PERSISTENT][1][:it]
+        assert np.allclose(a, b, rtol=1e-8, atol=1e-14), g
 
 
 def test_small_engine_rejected_where_it_does_not_fit():
@@ -121,7 +186,7 @@ def test_autotune_chooses_between_the_mappings():
         s.ok()
         x = dev(np.zeros(inst.N * inst.n))
         st, kb, g = bb.bt_autotune(s.h, dev(inst.b.reshape(-1)), x, 1e-10, 500, 3)
-        assert st == bb.BT_OK and (g == -1 or g >= 1)
+        assert st == bb.BT_OK and (g in (-1, -2, -4, -8) or g >= 1)
         ref = orc.pcg_opt(inst.D, inst.O, inst.b, [1.0, 7.0], 1e-10, 500)
         assert rel(host(x).reshape(inst.N, inst.n), ref.x) <= 1e-10
         st, it, x2 = s.solve(inst.b, 1e-10, 500)
