@@ -23,11 +23,12 @@ extern "C" cudaError_t bt_launch_setup(const bt::SetupParams* P, int mixed, int 
 extern "C" cudaError_t bt_launch_adjoint(const bt::AdjParams* P, cudaStream_t st);
 namespace bt { struct MParams; }
 extern "C" int bt_mrhs_smem_bytes(int n, int tc);
-extern "C" int bt_small_cluster(int N, int n, int bs64, int want);
-extern "C" cudaError_t bt_small_launch(const double* const* blk64, int N, int n, int bs64, int m, const double* alpha,
-                                       const double* b, double* x, int use_x0, double tol, int maxit,
-                                       long long budget, double* hist, int hist_len, int* iters, int* status,
-                                       int* outer, double* resid, double* errval, int C, cudaStream_t st);
+extern "C" int bt_small_cluster(int N, int n, int bs64, int bs32, int want);
+extern "C" cudaError_t bt_small_launch(const double* const* blk64, const float* const* blk32, int N, int n, int bs64,
+                                       int bs32, int m, const double* alpha, const double* b, double* x, int use_x0,
+                                       double tol, double tol_inner, int max_outer, int maxit, long long budget,
+                                       double* hist, int hist_len, int* iters, int* status, int* outer,
+                                       double* resid, double* errval, int scal64, int C, cudaStream_t st);
 extern "C" int bt_mrhs_tc_supported(int n);
 extern "C" cudaError_t bt_mrhs_occupancy(int smem, int tc, int* blocks);
 extern "C" cudaError_t bt_mrhs_images(int N, int n, int m, const float* const* blk32, int bs32, float* const* img,
@@ -254,11 +255,13 @@ bt_status read_setup_status(bt_ctx* h) {
 // instance) a CTA count; 0 = the defaults.  Sets stages, stage and vector-slot
 // bytes, dynamic shared memory, grid and group size; allocates nothing.
 // The cluster size of the shared-memory engine for a single-instance handle
-// (float64, the optimum with stored H blocks): `want` CTAs (want > 0), or the
-// smallest cluster whose CTAs hold the blocks (want = 0); 0 where none does.
+// (the optimum with stored H blocks, float64 or mixed): `want` CTAs (want >
+// 0), or the smallest cluster whose CTAs hold the blocks (want = 0); 0 where
+// none does.
 int small_cluster(const bt_ctx* h, int want) {
-  if (h->batched || h->mixed || h->variant != 0 || h->B != 1) return 0;
-  return bt_small_cluster(h->N[0], h->n[0], (int)rup((long long)h->n[0] * h->n[0], 2), want);
+  if (h->batched || h->variant != 0 || h->B != 1) return 0;
+  const int n = h->n[0];
+  return bt_small_cluster(h->N[0], n, (int)rup((long long)n * n, 2), h->mixed ? bt::slot32(n) : 0, want);
 }
 
 bt_status configure(bt_ctx* h, int stage_kb, int group_ctas) {
@@ -950,12 +953,14 @@ static bt_status solve_launch(bt_handle h, const double* b, double* x, double to
   if (!(tol >= 0.0) || maxit < 0) return BT_ERR_ARG;
   if (h->small) {
     const double* blk[7] = {h->D64, h->O64, h->Dinv64, h->E64, h->Hd64, h->Hu64, h->Hl64};
+    const float* blk32[7] = {h->D32, h->O32, h->Dinv32, h->E32, h->Hd32, h->Hu32, h->Hl32};
     const int n = h->n[0];
-    return cuda_st(bt_small_launch(blk, h->N[0], n, (int)rup((long long)n * n, 2), h->prm.m, h->alpha, b, x,
-                                   h->prm.use_x0, tol, maxit,
+    return cuda_st(bt_small_launch(blk, h->mixed ? blk32 : nullptr, h->N[0], n, (int)rup((long long)n * n, 2),
+                                   bt::slot32(n), h->prm.m, h->alpha, b, x, h->prm.use_x0, tol, h->prm.tol_inner,
+                                   h->prm.max_outer > 0 ? h->prm.max_outer : 30, maxit,
                                    h->prm.cycle_budget > 0 ? h->prm.cycle_budget : (1ll << 34), h->hist,
                                    h->hist_len, h->d_iters, h->d_status, h->d_outer, h->d_resid, h->d_errval,
-                                   h->small, h->stream));
+                                   h->prm.mixed_strict_fp64, h->small, h->stream));
   }
   bt::KParams P = base_kparams(h);
   P.op = bt::kOpSolve;

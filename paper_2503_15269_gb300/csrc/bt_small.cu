@@ -40,6 +40,13 @@ constexpr int kSmallMaxCluster = 8;         // portable cluster size
 
 struct SmallParams {
   const double *D, *O, *Dinv, *E, *Hd, *Hu, *Hl;  // library slots (column-major, stride bs)
+  // mixed handles: the float32 slots (stride bs32) of all seven arrays; D, O
+  // above are then the float64 copies the refinement residual uses
+  const float *D32, *O32, *Dinv32, *E32, *Hd32, *Hu32, *Hl32;
+  int bs32;
+  double tol_inner;  // mixed: 0 = automatic (as the persistent kernel)
+  int max_outer;
+  int scal64;        // mixed: divide the inner step scalars in float64 (else float32, as the persistent kernel)
   int N, n, bs, m;
   double alpha[kMaxM];
   const double* b;
@@ -76,12 +83,22 @@ __host__ __device__ inline long long small_bytes(int N, int n, int bs, int C) {
   return (7ll * slots_max * bs + 8ll * rows_max * n) * 8 + 64 * 8;
 }
 
+// Mixed handles: float64 D, O and the float64 solution and refinement
+// residual, then the seven float32 block arrays and eight float32 vectors.
+__host__ __device__ inline long long small_bytes_mixed(int N, int n, int bs64, int bs32, int C) {
+  int rows_max, slots_max;
+  small_extent(N, C, rows_max, slots_max);
+  return (2ll * slots_max * bs64 + 2ll * rows_max * n + 64) * 8 + (7ll * slots_max * bs32 + 8ll * rows_max * n) * 4;
+}
+
 // Whether C CTAs can hold the instance: every CTA two rows at least (the halo
 // of the H sweep then sits in the neighbouring CTA), the shared memory cap.
-__host__ __device__ inline bool small_fits_c(int N, int n, int bs, int C) {
+// bs32 > 0: a mixed handle.
+__host__ __device__ inline bool small_fits_c(int N, int n, int bs, int C, int bs32 = 0) {
   if (N < 1 || n < 1 || C < 1 || C > kSmallMaxCluster) return false;
   if (C > 1 && N < 2 * C) return false;
-  return small_bytes(N, n, bs, C) <= kSmallMaxBytes;
+  const long long b = bs32 > 0 ? small_bytes_mixed(N, n, bs, bs32, C) : small_bytes(N, n, bs, C);
+  return b <= kSmallMaxBytes;
 }
 
 // CL: launched as a cluster of C > 1 CTAs (distributed shared memory and
@@ -121,14 +138,14 @@ struct Small {
     red = vbase + 8ll * rows_max * n;
   }
   __device__ double* vec(int k) { return vbase + (long long)k * rows_max * n; }
-  __device__ const double* slot(const double* M, int i) { return M + (long long)(i - lo) * bs; }
 
   // row r (0 <= r < N) of vector v: local, or a neighbour's (same offsets in
   // every CTA of the cluster)
-  __device__ const double* row(const double* v, int r) {
+  template <typename T>
+  __device__ const T* row(const T* v, int r) {
     if constexpr (CL) {
       if (r < s || r >= e) {
-        double* w = const_cast<double*>(v);
+        T* w = const_cast<T*>(v);
         if (r < s) return cg::this_cluster().map_shared_rank(w, rank - 1) + (long long)(r - s_prev) * n;
         return cg::this_cluster().map_shared_rank(w, rank + 1) + (long long)(r - s_next) * n;
       }
@@ -204,64 +221,78 @@ struct Small {
     return v[0];
   }
 
-  // out = (block row of M) v for this CTA's elements (i, a); kind 0: S, 1: G, 2: H
-  __device__ void sweep(int kind, const double* v, double* out) {
+  // out = (block row of M) v for this CTA's elements (i, a); kind 0: S, 1: G,
+  // 2: H; blk = D, O, D^-1, E, Hd, Hu, Hl local slots of stride `sb` (block row
+  // i at (i - lo) sb), element type T, accumulation in T
+  template <typename T>
+  __device__ void sweepT(int kind, const T* const* blk, int sb, const T* v, T* out) {
+    const auto slotT = [&](int k, int i) { return blk[k] + (long long)(i - lo) * sb; };
     for (int el = tid; el < nel; el += kSmallThreads) {
       const int li = el / n, a = el - li * n;
       const int i = s + li;
-      const double* vi = v + (long long)li * n;
-      double acc = 0.0;
-      const double* M0 = slot(kind == 0 ? D : (kind == 1 ? Dinv : Hd), i);
+      const T* vi = v + (long long)li * n;
+      T acc = T(0);
+      const T* M0 = slotT(kind == 0 ? 0 : (kind == 1 ? 2 : 4), i);
       for (int c = 0; c < n; ++c) acc = fma(M0[c * n + a], vi[c], acc);
       if (kind == 0 || kind == 1) {
-        const double* M = kind == 0 ? O : E;
-        const double sg = kind == 0 ? 1.0 : -1.0;  // G's off-diagonal blocks are -E_i, -E_{i-1}^T
-        double t = 0.0;
+        const int km = kind == 0 ? 1 : 3;
+        const T sg = kind == 0 ? T(1) : T(-1);  // G's off-diagonal blocks are -E_i, -E_{i-1}^T
+        T t = T(0);
         if (i + 1 < N) {  // (i, i+1): O_i / E_i
-          const double* Mi = slot(M, i);
-          const double* vn = row(v, i + 1);
+          const T* Mi = slotT(km, i);
+          const T* vn = row(v, i + 1);
           for (int c = 0; c < n; ++c) t = fma(Mi[c * n + a], vn[c], t);
         }
         if (i >= 1) {  // (i, i-1): O_{i-1}^T / E_{i-1}^T
-          const double* Mp = slot(M, i - 1);
-          const double* vp = row(v, i - 1);
+          const T* Mp = slotT(km, i - 1);
+          const T* vp = row(v, i - 1);
           for (int c = 0; c < n; ++c) t = fma(Mp[a * n + c], vp[c], t);
         }
         acc = fma(sg, t, acc);
       } else {
         if (i + 2 < N) {  // (i, i+2): Hu_i
-          const double* Mi = slot(Hu, i);
-          const double* vn = row(v, i + 2);
+          const T* Mi = slotT(5, i);
+          const T* vn = row(v, i + 2);
           for (int c = 0; c < n; ++c) acc = fma(Mi[c * n + a], vn[c], acc);
         }
         if (i >= 2) {  // (i, i-2): Hl_{i-2}
-          const double* Mp = slot(Hl, i - 2);
-          const double* vp = row(v, i - 2);
+          const T* Mp = slotT(6, i - 2);
+          const T* vp = row(v, i - 2);
           for (int c = 0; c < n; ++c) acc = fma(Mp[c * n + a], vp[c], acc);
         }
       }
       out[el] = acc;
     }
   }
+  __device__ void sweep(int kind, const double* v, double* out) {
+    const double* const blk[7] = {D, O, Dinv, E, Hd, Hu, Hl};
+    sweepT<double>(kind, blk, bs, v, out);
+  }
 
-  // z = M^-1 r (y0 = G r, y_j = H y_{j-1}, z = y0 + sum_{j>0} alpha_j y_j); returns r . z.
-  // r must be final in every CTA (a cluster barrier since its last write).
-  __device__ double precond(const double* r, double* z, double* y0, double* ya, double* yb) {
-    sweep(1, r, P.m == 1 ? z : y0);
+  // z = M^-1 r (y0 = G r, y_j = H y_{j-1}, z = y0 + sum_{j>0} alpha_j y_j);
+  // returns r . z (products and sum in float64).  r must be final in every CTA
+  // (a cluster barrier since its last write).
+  template <typename T>
+  __device__ double precondT(const T* const* blk, int sb, const T* r, T* z, T* y0, T* ya, T* yb) {
+    sweepT<T>(1, blk, sb, r, P.m == 1 ? z : y0);
     if (P.m > 1) {
-      const double* yin = y0;
+      const T* yin = y0;
       for (int j = 1; j < P.m; ++j) {
         csync();  // yin final in every CTA (the H sweep reads two rows of the neighbours)
-        double* yout = (j & 1) ? ya : yb;
-        sweep(2, yin, yout);
+        T* yout = (j & 1) ? ya : yb;
+        sweepT<T>(2, blk, sb, yin, yout);
         yin = yout;
-        const double aj = P.alpha[j];
+        const T aj = (T)P.alpha[j];
         for (int el = tid; el < nel; el += kSmallThreads) z[el] = fma(aj, yout[el], j == 1 ? y0[el] : z[el]);
       }
     }
     double t = 0.0;
-    for (int el = tid; el < nel; el += kSmallThreads) t = fma(r[el], z[el], t);
+    for (int el = tid; el < nel; el += kSmallThreads) t = fma((double)r[el], (double)z[el], t);
     return reduce(t);
+  }
+  __device__ double precond(const double* r, double* z, double* y0, double* ya, double* yb) {
+    const double* const blk[7] = {D, O, Dinv, E, Hd, Hu, Hl};
+    return precondT<double>(blk, bs, r, z, y0, ya, yb);
   }
 };
 
@@ -393,40 +424,226 @@ __global__ void __launch_bounds__(kSmallThreads, 1) bt_small_kernel(const __grid
   Sm.csync();
 }
 
+// Mixed handles: float32 PCG inside float64 iterative refinement, with the
+// persistent kernel's outer rules -- r64 = b - S x in float64 (D, O in
+// float64), stop when ||r64|| <= tol ||b||, else an inner float32 PCG on
+// r64 / ||r64|| to the inner tolerance (the caller's, else sqrt(tol) in
+// [1e-6, 1e-4], loosened to what the remaining factor needs), x += ||r64|| d.
+// The dots are summed in float64; the inner step scalars are divided in
+// float32 (their float32 use) unless the strict float64 split asks for float64.
+template <bool CL>
+__global__ void __launch_bounds__(kSmallThreads, 1) bt_small_mixed_kernel(const __grid_constant__ SmallParams P) {
+  extern __shared__ __align__(16) double smd[];
+  Small<CL> Sm(P, smd);
+  const int tid = threadIdx.x, n = P.n;
+  const long long deadline = clock64() + P.budget;
+  int rows_max, slots_max;
+  small_extent(P.N, Sm.C, rows_max, slots_max);
+  const long long A64 = (long long)slots_max * P.bs, A32 = (long long)slots_max * P.bs32;
+  const long long V = (long long)rows_max * n;
+  double* D64 = smd;
+  double* O64 = D64 + A64;
+  double* x = O64 + A64;  // the float64 solution (this CTA's rows)
+  double* r64 = x + V;    // the refinement residual
+  Sm.red = r64 + V;       // [64]
+  float* f = reinterpret_cast<float*>(Sm.red + 64);
+  float* blk32[7];
+  for (int k = 0; k < 7; ++k) blk32[k] = f + k * A32;
+  float* fv = f + 7 * A32;
+  float* xin = fv;
+  float* r = fv + V;
+  float* p = fv + 2 * V;
+  float* q = fv + 3 * V;
+  float* z = fv + 4 * V;
+  float* y0 = fv + 5 * V;
+  float* ya = fv + 6 * V;
+  float* yb = fv + 7 * V;
+  {
+    const long long o64 = (long long)Sm.lo * P.bs, c64 = (long long)(Sm.e - Sm.lo) * P.bs;
+    const long long o32 = (long long)Sm.lo * P.bs32, c32 = (long long)(Sm.e - Sm.lo) * P.bs32;
+    for (long long t = tid; t < c64; t += kSmallThreads) {
+      D64[t] = __ldg(P.D + o64 + t);
+      O64[t] = __ldg(P.O + o64 + t);
+    }
+    const float* src[7] = {P.D32, P.O32, P.Dinv32, P.E32, P.Hd32, P.Hu32, P.Hl32};
+    const int na = P.m > 1 ? 7 : 4;
+    for (int k = 0; k < na; ++k)
+      for (long long t = tid; t < c32; t += kSmallThreads) blk32[k][t] = __ldg(src[k] + o32 + t);
+  }
+  const double* const blk64[7] = {D64, O64, nullptr, nullptr, nullptr, nullptr, nullptr};
+  const float* const cblk32[7] = {blk32[0], blk32[1], blk32[2], blk32[3], blk32[4], blk32[5], blk32[6]};
+  const int nel = Sm.nel;
+  const long long g0 = (long long)Sm.s * n;
+  double* const hist = (P.hist && tid == 0 && Sm.rank == 0) ? P.hist : nullptr;
+  auto record = [&](int idx, int field, double v) {
+    if (hist && idx >= 0 && idx < P.hist_len) hist[(size_t)idx * 3 + field] = v;
+  };
+  double bb = 0.0;
+  for (int el = tid; el < nel; el += kSmallThreads) {
+    const double bv = P.b[g0 + el];
+    bb = fma(bv, bv, bb);
+    x[el] = P.use_x0 ? P.x[g0 + el] : 0.0;
+  }
+  const double nb = sqrt(Sm.reduce(bb));  // also makes x final in every CTA
+  int status = kOK, iters = 0, outer = 0;
+  double resid = 0.0, errv = 0.0;
+  if (!isfinite(nb)) {
+    status = kErrNonfinite;
+  } else if (nb == 0.0) {
+    for (int el = tid; el < nel; el += kSmallThreads) x[el] = 0.0;
+  } else {
+    double nr = nb;
+    for (outer = 0;; ++outer) {
+      const bool have_r64 = outer > 0 || P.use_x0;
+      if (have_r64) {
+        Sm.template sweepT<double>(0, blk64, P.bs, x, r64);
+        double t = 0.0;
+        for (int el = tid; el < nel; el += kSmallThreads) {
+          const double rv = P.b[g0 + el] - r64[el];
+          r64[el] = rv;
+          t = fma(rv, rv, t);
+        }
+        nr = sqrt(Sm.reduce(t));
+        if (!isfinite(nr)) {
+          status = kErrNonfinite;
+          break;
+        }
+      }
+      resid = nr / nb;
+      if (nr <= P.tol * nb) {
+        status = kOK;
+        break;
+      }
+      if (outer >= P.max_outer || iters >= P.maxit) {
+        status = kErrNoConv;
+        break;
+      }
+      double t_in = P.tol_inner > 0.0 ? P.tol_inner : fmin(1e-4, fmax(1e-6, sqrt(P.tol)));
+      const double need = 0.5 * P.tol * nb / nr;
+      if (need > t_in) t_in = need;
+      if (t_in > 0.5) t_in = 0.5;
+      // inner float32 PCG on S d = rhs / nr from d = 0
+      const double scale = 1.0 / nr;
+      double t = 0.0;
+      for (int el = tid; el < nel; el += kSmallThreads) {
+        const float rv = (float)((have_r64 ? r64[el] : P.b[g0 + el]) * scale);
+        r[el] = rv;
+        xin[el] = 0.f;
+        t = fma((double)rv, (double)rv, t);
+      }
+      const double rr0 = Sm.reduce(t);  // also makes r final in every CTA
+      const double thr2 = t_in * t_in * rr0;
+      const int maxit_in = P.maxit - iters;
+      int it = 0, ist = kOK;
+      double rr = rr0;
+      if (rr0 > 0.0 && !(rr0 <= thr2)) {
+        double rho = Sm.template precondT<float>(cblk32, P.bs32, r, z, y0, ya, yb);
+        for (int el = tid; el < nel; el += kSmallThreads) p[el] = z[el];
+        for (int k = 1;; ++k) {
+          if (k > maxit_in) {
+            ist = kErrNoConv;
+            it = maxit_in;
+            break;
+          }
+          Sm.csync();  // p final in every CTA
+          Sm.template sweepT<float>(0, cblk32, P.bs32, p, q);
+          double tq = 0.0;
+          for (int el = tid; el < nel; el += kSmallThreads) tq = fma((double)p[el], (double)q[el], tq);
+          double pq, late = 0.0;
+          if constexpr (CL) {
+            Sm.reduce2(tq, (tid == 0 && Sm.rank == 0 && clock64() > deadline) ? 1.0 : 0.0, pq, late);
+          } else {
+            if (tid == 0) Sm.red[24] = clock64() > deadline ? 1.0 : 0.0;  // read after the sum's barriers
+            pq = Sm.reduce(tq);
+            late = Sm.red[24];
+          }
+          if (late > 0.0) {
+            ist = kErrTimeout;
+            it = k - 1;
+            break;
+          }
+          if (!isfinite(pq)) {
+            ist = kErrNonfinite;
+            it = k - 1;
+            break;
+          }
+          if (!(pq > 0.0)) {
+            ist = kErrBreakdown;
+            it = k - 1;
+            errv = pq;
+            break;
+          }
+          const double al = P.scal64 ? rho / pq : (double)__fdiv_rn((float)rho, (float)pq);
+          const float alf = (float)al;
+          record(iters + k - 1, 1, al);
+          record(iters + k - 1, 2, 0.0);
+          double tr = 0.0;
+          for (int el = tid; el < nel; el += kSmallThreads) {
+            xin[el] = fmaf(alf, p[el], xin[el]);
+            const float rv = fmaf(-alf, q[el], r[el]);
+            r[el] = rv;
+            tr = fma((double)rv, (double)rv, tr);
+          }
+          rr = Sm.reduce(tr);  // also makes r final in every CTA
+          it = k;
+          record(iters + k - 1, 0, sqrt(rr / rr0));
+          if (!isfinite(rr)) {
+            ist = kErrNonfinite;
+            break;
+          }
+          if (rr <= thr2) break;
+          const double rz = Sm.template precondT<float>(cblk32, P.bs32, r, z, y0, ya, yb);
+          const double be = P.scal64 ? rz / rho : (double)__fdiv_rn((float)rz, (float)rho);
+          record(iters + k - 1, 2, be);
+          rho = rz;
+          const float bef = (float)be;
+          for (int el = tid; el < nel; el += kSmallThreads) p[el] = fmaf(bef, p[el], z[el]);
+        }
+      }
+      iters += it;
+      if (ist == kErrBreakdown || ist == kErrNonfinite || ist == kErrTimeout) {
+        status = ist;
+        break;
+      }
+      for (int el = tid; el < nel; el += kSmallThreads) x[el] = fma(nr, (double)xin[el], x[el]);
+      Sm.csync();  // x final in every CTA before the next residual
+    }
+  }
+  for (int el = tid; el < nel; el += kSmallThreads) P.x[g0 + el] = x[el];
+  if (tid == 0 && Sm.rank == 0) {
+    *P.iters = iters;
+    *P.status = status;
+    *P.outer = outer;
+    *P.resid = status == kErrBreakdown ? errv : resid;
+    *P.errval = errv;
+  }
+  Sm.csync();  // no CTA leaves while a neighbour may still read its shared memory
+}
+
 }  // namespace bt
 
-// The cluster size of the engine for an instance of this shape: 1 where one
-// CTA holds it, else the smallest of 2, 4, 8 that does; 0 where none does.
-// want > 0 asks for exactly that size (0 if it does not fit).
-extern "C" int bt_small_cluster(int N, int n, int bs64, int want) {
-  if (want > 0) return bt::small_fits_c(N, n, bs64, want) ? want : 0;
+// The cluster size of the engine for an instance of this shape (bs32 > 0: a
+// mixed handle): 1 where one CTA holds it, else the smallest of 2, 4, 8 that
+// does; 0 where none does.  want > 0 asks for exactly that size (0 if it does
+// not fit).
+extern "C" int bt_small_cluster(int N, int n, int bs64, int bs32, int want) {
+  if (want > 0) return bt::small_fits_c(N, n, bs64, want, bs32) ? want : 0;
   for (int C = 1; C <= bt::kSmallMaxCluster; C *= 2)
-    if (bt::small_fits_c(N, n, bs64, C)) return C;
+    if (bt::small_fits_c(N, n, bs64, C, bs32)) return C;
   return 0;
 }
 
-extern "C" cudaError_t bt_small_launch(const double* const* blk64, int N, int n, int bs64, int m, const double* alpha,
-                                       const double* b, double* x, int use_x0, double tol, int maxit,
-                                       long long budget, double* hist, int hist_len, int* iters, int* status,
-                                       int* outer, double* resid, double* errval, int C, cudaStream_t st) {
-  bt::SmallParams P{};
-  P.D = blk64[0]; P.O = blk64[1]; P.Dinv = blk64[2]; P.E = blk64[3];
-  P.Hd = blk64[4]; P.Hu = blk64[5]; P.Hl = blk64[6];
-  P.N = N; P.n = n; P.bs = bs64; P.m = m;
-  for (int j = 0; j < bt::kMaxM; ++j) P.alpha[j] = j < m ? alpha[j] : 0.0;
-  P.b = b; P.x = x; P.use_x0 = use_x0; P.tol = tol; P.maxit = maxit; P.budget = budget;
-  P.hist = hist; P.hist_len = hist_len;
-  P.iters = iters; P.status = status; P.outer = outer; P.resid = resid; P.errval = errval;
-  if (!bt::small_fits_c(N, n, bs64, C)) return cudaErrorInvalidValue;
-  const int smem = (int)bt::small_bytes(N, n, bs64, C);
+template <bool MIX>
+static cudaError_t small_launch(const bt::SmallParams& P, int smem, int C, cudaStream_t st) {
   if (C == 1) {
-    cudaError_t e =
-        cudaFuncSetAttribute(bt::bt_small_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const auto kern = MIX ? bt::bt_small_mixed_kernel<false> : bt::bt_small_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    bt::bt_small_kernel<false><<<1, bt::kSmallThreads, smem, st>>>(P);
+    kern<<<1, bt::kSmallThreads, smem, st>>>(P);
     return cudaGetLastError();
   }
-  cudaError_t e = cudaFuncSetAttribute(bt::bt_small_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const auto kern = MIX ? bt::bt_small_mixed_kernel<true> : bt::bt_small_kernel<true>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)C);
@@ -440,7 +657,37 @@ extern "C" cudaError_t bt_small_launch(const double* const* blk64, int N, int n,
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, bt::bt_small_kernel<true>, P);
+  e = cudaLaunchKernelEx(&cfg, kern, P);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
+}
+
+// blk64: D, O, D^-1, E, Hd, Hu, Hl float64 slots (stride bs64; a mixed handle
+// passes its float64 D, O only) and blk32 the float32 slots (stride bs32) of a
+// mixed handle, else null.
+extern "C" cudaError_t bt_small_launch(const double* const* blk64, const float* const* blk32, int N, int n, int bs64,
+                                       int bs32, int m, const double* alpha, const double* b, double* x, int use_x0,
+                                       double tol, double tol_inner, int max_outer, int maxit, long long budget,
+                                       double* hist, int hist_len, int* iters, int* status, int* outer,
+                                       double* resid, double* errval, int scal64, int C, cudaStream_t st) {
+  const bool mix = blk32 != nullptr;
+  bt::SmallParams P{};
+  P.D = blk64[0]; P.O = blk64[1]; P.Dinv = blk64[2]; P.E = blk64[3];
+  P.Hd = blk64[4]; P.Hu = blk64[5]; P.Hl = blk64[6];
+  if (mix) {
+    P.D32 = blk32[0]; P.O32 = blk32[1]; P.Dinv32 = blk32[2]; P.E32 = blk32[3];
+    P.Hd32 = blk32[4]; P.Hu32 = blk32[5]; P.Hl32 = blk32[6];
+  }
+  P.bs32 = bs32;
+  P.tol_inner = tol_inner;
+  P.max_outer = max_outer;
+  P.scal64 = scal64;
+  P.N = N; P.n = n; P.bs = bs64; P.m = m;
+  for (int j = 0; j < bt::kMaxM; ++j) P.alpha[j] = j < m ? alpha[j] : 0.0;
+  P.b = b; P.x = x; P.use_x0 = use_x0; P.tol = tol; P.maxit = maxit; P.budget = budget;
+  P.hist = hist; P.hist_len = hist_len;
+  P.iters = iters; P.status = status; P.outer = outer; P.resid = resid; P.errval = errval;
+  if (!bt::small_fits_c(N, n, bs64, C, mix ? bs32 : 0)) return cudaErrorInvalidValue;
+  const int smem = (int)(mix ? bt::small_bytes_mixed(N, n, bs64, bs32, C) : bt::small_bytes(N, n, bs64, C));
+  return mix ? small_launch<true>(P, smem, C, st) : small_launch<false>(P, smem, C, st);
 }

@@ -57,7 +57,7 @@ def test_single_autotune_keeps_parity(precision):
         db, x = dev(inst.b.reshape(-1)), dev(np.zeros(inst.b.size))
         st, kb, g = bb.bt_autotune(s.h, db, x, 1e-10, 2000, 1)
         # the persistent kernel on 1 .. N/2 CTAs, or (float64) the shared-memory engine on a cluster
-        shapes = {1, 128 // 16, 128 // 8, 128 // 4, 128 // 2} | ({-8} if precision == bb.BT_FP64 else set())
+        shapes = {1, 128 // 16, 128 // 8, 128 // 4, 128 // 2, -1, -2, -4, -8}
         assert st == bb.BT_OK and g in shapes
         st, it, xs = s.solve(inst.b, 1e-10, 2000)
     assert st == bb.BT_OK

@@ -1,5 +1,6 @@
-"""The shared-memory engine for small float64 single instances (one CTA, or a
-cluster of 2, 4 or 8 CTAs sharing the block rows, every block resident):
+"""The shared-memory engine for small single instances, float64 and mixed
+(one CTA, or a cluster of 2, 4 or 8 CTAs sharing the block rows, every block
+resident):
 against the oracle's PCG (iterations within 1, solution within 1e-10),
 against the persistent kernel, status paths, history recording,
 eligibility and the autotuner's choice between the two mappings."""
@@ -191,3 +192,52 @@ def test_autotune_chooses_between_the_mappings():
         assert rel(host(x).reshape(inst.N, inst.n), ref.x) <= 1e-10
         st, it, x2 = s.solve(inst.b, 1e-10, 500)
         assert st == bb.BT_OK and abs(it - ref.iters) <= 1
+
+
+@pytest.mark.parametrize("g", [0, -8])
+def test_config1_mixed_on_the_shared_memory_engine(g):
+    """LQR N = 128, n = 12, float32 PCG inside float64 refinement on the
+    shared-memory engine (the automatic choice takes the smallest cluster that
+    holds the float32 and float64 blocks): the true residual to tol and the
+    solution within cond * tol of the oracle's direct solve, as the
+    persistent kernel's mixed path."""
+    inst = wl.config1()
+    xr = orc.direct_solve(inst.D, inst.O, inst.b)
+    out = {}
+    for gg in (g, 32):
+        with Single(inst, m=2, alpha=[1.0, 7.0], precision=bb.BT_MIXED, group_ctas=gg) as s:
+            s.ok()
+            st, it, x = s.solve(inst.b, 1e-10, 2000)
+            info = s.info()
+        assert st == bb.BT_OK
+        res = np.linalg.norm(orc.spmv(inst.D, inst.O, x) - inst.b) / np.linalg.norm(inst.b)
+        assert res <= 1e-10 and info[2] <= 1e-10
+        assert rel(x, xr) <= 1e-7
+        out[gg] = (it, info[1])
+    # the same refinement structure as the persistent kernel (outer steps)
+    assert out[g][1] == out[32][1] and abs(out[g][0] - out[32][0]) <= 4
+
+
+@pytest.mark.parametrize("N,n,g", [(16, 6, -1), (9, 12, -1), (40, 8, -2), (17, 16, -8)])
+def test_mixed_small_engine_matches_direct_solve(N, n, g):
+    inst = wl.small_llt(98, N, n)
+    with Single(inst, m=2, alpha=[1.0, 7.0], precision=bb.BT_MIXED, group_ctas=g) as s:
+        s.ok()
+        st, it, x = s.solve(inst.b, 1e-12, 3000)
+        assert st == bb.BT_OK
+        # zero right-hand side and the outer-step limit
+        st0, it0, x0 = s.solve(np.zeros_like(inst.b), 1e-12, 100)
+        assert st0 == bb.BT_OK and it0 == 0 and np.all(x0 == 0)
+    assert rel(x, orc.direct_solve(inst.D, inst.O, inst.b)) <= 1e-8
+
+
+def test_mixed_small_engine_outer_limit_and_nonfinite():
+    inst = wl.small_llt(99, 12, 6)
+    with Single(inst, m=2, alpha=[1.0, 7.0], precision=bb.BT_MIXED, group_ctas=-1, max_outer=1) as s:
+        s.ok()
+        st, it, x = s.solve(inst.b, 1e-14, 3000)
+        assert st == bb.BT_ERR_NO_CONVERGENCE and s.info()[1] == 1
+        b = inst.b.copy()
+        b[2, 3] = np.nan
+        st, it, x = s.solve(b, 1e-10, 100)
+        assert st == bb.BT_ERR_NONFINITE

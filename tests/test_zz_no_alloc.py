@@ -60,7 +60,11 @@ def two_calls(precision, tol):
     first = wl.config1()                 # N = 128, n = 12
     second = wl.small_llt(7, 37, 9)      # different shape: odd N, odd n
     for inst in (first, second):
-        st_a, it_a, x_a = allocating_solve(inst, params, tol, 2000)
+        # the allocating path on the persistent kernel at the shape the
+        # no-allocation entry takes (one CTA up to N = 32, else N / 4)
+        g = 1 if inst.N <= 32 else inst.N // 4
+        p_alloc, keep_a = bb.make_params(m=2, alpha=[1.0, 7.0], precision=precision, group_ctas=g)
+        st_a, it_a, x_a = allocating_solve(inst, p_alloc, tol, 2000)
         st_b, it_b, x_b = noalloc_solve(inst, params, tol, 2000, x_init=np.full(inst.N * inst.n, 3.0))
         assert st_a == bb.BT_OK and st_b == bb.BT_OK
         assert abs(it_a - it_b) <= 1
