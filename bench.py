@@ -637,7 +637,8 @@ def other_workload(a):
                                            ("LL^T N=16 n=6", wl.config0(), bb.BT_FP64, 1e-10, 1),
                                            ("LQR N=128 n=12", wl.config1(), bb.BT_FP64, 1e-8, 0),
                                            ("LQR N=128 n=12", wl.config1(), bb.BT_FP64, 1e-8, 32),
-                                           ("LQR N=128 n=12", wl.config1(), bb.BT_MIXED, 1e-8, 0)):
+                                           ("LQR N=128 n=12", wl.config1(), bb.BT_MIXED, 1e-8, 0),
+                                           ("LQR N=128 n=12", wl.config1(), bb.BT_MIXED, 1e-8, 32)):
             dD = torch.tensor(inst.D, device=dev)
             dO = torch.tensor(inst.O, device=dev)
             db = torch.tensor(inst.b.reshape(-1), device=dev)
@@ -656,9 +657,9 @@ def other_workload(a):
             torch.cuda.synchronize()
             us = 1e3 * e0.elapsed_time(e1) / a.steps
             bb.bt_destroy(h)
-            # group_ctas 0 picks the shared-memory engine for float64 instances whose
-            # blocks fit one CTA (LL^T N = 16, n = 6) or a cluster of 8 (LQR N = 128,
-            # n = 12), the persistent kernel otherwise; -8 asks for a cluster of 8
+            # group_ctas 0 picks the shared-memory engine for instances whose blocks
+            # fit one CTA (LL^T N = 16, n = 6) or a cluster (LQR N = 128, n = 12: 8
+            # CTAs), the persistent kernel otherwise; -8 asks for a cluster of 8
             engine = {0: "automatic", -8: "shared-memory engine, cluster of 8",
                       1: "persistent kernel, 1 CTA", 32: "persistent kernel, 32 CTAs"}[grp]
             rows.append({"instance": name, "precision": "f64" if prec == bb.BT_FP64 else "f32+f64", "tol": tol,
