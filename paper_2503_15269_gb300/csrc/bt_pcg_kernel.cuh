@@ -224,6 +224,66 @@ __device__ __forceinline__ T dtr1(const T* __restrict__ M, int a, const T* __res
   return (s0 + s1) + (s2 + s3);
 }
 
+// Four outputs (a .. a+3) of M v, M float32 column-major NB x NB, a % 4 == 0:
+// one 128-bit load per column step of M and one per four entries of v.
+template <int NB>
+__device__ __forceinline__ float4 dcol4(const float* __restrict__ M, int a, const float* __restrict__ v) {
+  float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;
+#pragma unroll
+  for (int c = 0; c < NB; c += 4) {
+    const float4 vv = *reinterpret_cast<const float4*>(v + c);
+    const float4 m0 = *reinterpret_cast<const float4*>(M + c * NB + a);
+    const float4 m1 = *reinterpret_cast<const float4*>(M + (c + 1) * NB + a);
+    const float4 m2 = *reinterpret_cast<const float4*>(M + (c + 2) * NB + a);
+    const float4 m3 = *reinterpret_cast<const float4*>(M + (c + 3) * NB + a);
+    s0 = make_float4(fmaf(m0.x, vv.x, s0.x), fmaf(m0.y, vv.x, s0.y), fmaf(m0.z, vv.x, s0.z), fmaf(m0.w, vv.x, s0.w));
+    s1 = make_float4(fmaf(m1.x, vv.y, s1.x), fmaf(m1.y, vv.y, s1.y), fmaf(m1.z, vv.y, s1.z), fmaf(m1.w, vv.y, s1.w));
+    s0 = make_float4(fmaf(m2.x, vv.z, s0.x), fmaf(m2.y, vv.z, s0.y), fmaf(m2.z, vv.z, s0.z), fmaf(m2.w, vv.z, s0.w));
+    s1 = make_float4(fmaf(m3.x, vv.w, s1.x), fmaf(m3.y, vv.w, s1.y), fmaf(m3.z, vv.w, s1.z), fmaf(m3.w, vv.w, s1.w));
+  }
+  return make_float4(s0.x + s1.x, s0.y + s1.y, s0.z + s1.z, s0.w + s1.w);
+}
+
+// Start offset of the column walk of dtr2 for the column pair p = a / 2:
+// pair p reads words 2 p NB + 4 q (and NB more), bank group (p NB / 2 + q)
+// mod 8, so the 8 lanes of a 128-bit phase need distinct (p NB / 2 + rot)
+// mod 8: NB = 4 mod 8 repeats every 4 pairs, NB = 8 mod 16 every 2, and
+// NB = 0 mod 16 at once.
+template <int NB>
+__device__ __forceinline__ int tr2_rot(int p) {
+  if constexpr (NB % 8 == 4) return (p >> 2) & 1;
+  else if constexpr (NB % 16 == 8) return (p >> 1) & 3;
+  else return p & 7;
+}
+
+// Two outputs (a, a+1) of M^T v, M float32 column-major NB x NB, a even:
+// columns a and a+1 of M (contiguous) dotted with v.
+template <int NB>
+__device__ __forceinline__ float2 dtr2(const float* __restrict__ M, int a, const float* __restrict__ v) {
+  constexpr int Q = NB / 4;
+  const float* c0 = M + a * NB;
+  const float* c1 = c0 + NB;
+  const int rot = tr2_rot<NB>(a >> 1) % Q;
+  float x0 = 0.f, x1 = 0.f, y0 = 0.f, y1 = 0.f;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    int qq = q + rot;
+    if (qq >= Q) qq -= Q;
+    const float4 w = *reinterpret_cast<const float4*>(v + 4 * qq);
+    const float4 m0 = *reinterpret_cast<const float4*>(c0 + 4 * qq);
+    const float4 m1 = *reinterpret_cast<const float4*>(c1 + 4 * qq);
+    x0 = fmaf(m0.x, w.x, x0);
+    x1 = fmaf(m0.y, w.y, x1);
+    y0 = fmaf(m1.x, w.x, y0);
+    y1 = fmaf(m1.y, w.y, y1);
+    x0 = fmaf(m0.z, w.z, x0);
+    x1 = fmaf(m0.w, w.w, x1);
+    y0 = fmaf(m1.z, w.z, y0);
+    y1 = fmaf(m1.w, w.w, y1);
+  }
+  return make_float2(x0 + x1, y0 + y1);
+}
+
 // All block-vector products of one chunk: part1 = M1 v_i, part2 = M2 v_{i+k},
 // push = (M2^T v_i) for S and G, (Hl_i v_i) for H.  For H_ab (kKB2G) also
 // part3 = F_i v_{i+1} and push1 = K_i v_i (to row i+1).  NB = 0: runtime n.
@@ -338,7 +398,42 @@ __device__ __forceinline__ void chunk_products(const T* __restrict__ stg, int R,
     }
     return;
   }
-  if constexpr (NB > 0) {
+  if constexpr (NB > 0 && NB % 4 == 0 && NB <= 24 && sizeof(T) == 4) {
+    // float32 blocks up to n = 24: four outputs of a direct product per
+    // task, two of a transposed one (the push of S and G) -- half the tasks
+    // of the two-output form, whose per-task overhead weighs most on small
+    // blocks (n = 36 measured no faster this way)
+    constexpr int n = NB;
+    constexpr int q4 = NB / 4;
+    constexpr int hp = NB / 2;
+    const int nd4 = nr * q4;
+    const int np = (KIND == kKB2) ? (nr + h) * q4 : (nr + h) * hp;
+    const int ntask = 2 * nd4 + np;
+    for (int t = tid; t < ntask; t += kThreads) {
+      if (t < nd4) {
+        const int jj = t / q4, a = 4 * (t - jj * q4);
+        *reinterpret_cast<float4*>(part1 + jj * n + a) = dcol4<NB>(a0 + (size_t)jj * bse, a, vs + (r0 + jj - base) * n);
+      } else if (t < 2 * nd4) {
+        const int t2 = t - nd4;
+        const int jj = t2 / q4, a = 4 * (t2 - jj * q4);
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r0 + jj + k < N) {
+          const T* M2 = (KIND == kKB2) ? a1 + (size_t)jj * bse : a1 + (size_t)(jj + h) * bse;
+          o = dcol4<NB>(M2, a, vs + (r0 + jj + k - base) * n);
+        }
+        *reinterpret_cast<float4*>(part2 + jj * n + a) = o;
+      } else {
+        const int t3 = t - 2 * nd4;
+        if constexpr (KIND == kKB2) {
+          const int jj = t3 / q4, a = 4 * (t3 - jj * q4);
+          *reinterpret_cast<float4*>(push + jj * n + a) = dcol4<NB>(a2 + (size_t)jj * bse, a, vs + jj * n);
+        } else {
+          const int jj = t3 / hp, a = 2 * (t3 - jj * hp);
+          *reinterpret_cast<float2*>(push + jj * n + a) = dtr2<NB>(a1 + (size_t)jj * bse, a, vs + jj * n);
+        }
+      }
+    }
+  } else if constexpr (NB > 0) {
     constexpr int n = NB;
     constexpr int hp = NB / 2;
     const int nd2 = nr * hp;                          // pairs of direct outputs

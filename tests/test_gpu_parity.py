@@ -390,3 +390,40 @@ def test_batched_mixed_ragged_block_sizes(m, alpha):
         res = np.linalg.norm(orc.spmv(inst.D, inst.O, xs[k]) - inst.b) / np.linalg.norm(inst.b)
         assert res <= 1e-10, (k, inst.N, inst.n, res)
         assert rel(xs[k], orc.direct_solve(inst.D, inst.O, inst.b)) <= 1e-8, k
+
+
+def _ties(rng, shape, lo_exp, hi_exp):
+    """float64 values exactly halfway between two neighbouring float32 values,
+    or one float64 ulp either side of such a midpoint, over a spread of
+    binades (the cases round-to-nearest-even decides)."""
+    f = rng.uniform(1.0, 2.0, shape).astype(np.float32)
+    nxt = np.nextafter(f, np.float32(np.inf))
+    mid = (f.astype(np.float64) + nxt.astype(np.float64)) / 2
+    nudge = rng.integers(-1, 2, shape)
+    mid = np.where(nudge > 0, np.nextafter(mid, np.inf), np.where(nudge < 0, np.nextafter(mid, -np.inf), mid))
+    sign = np.where(rng.random(shape) < 0.5, -1.0, 1.0)
+    return sign * np.ldexp(mid, rng.integers(lo_exp, hi_exp, shape))
+
+
+@pytest.mark.parametrize("N,n", [(3, 12), (4, 5), (2, 36)])
+def test_fp32_block_copies_round_to_nearest_even(N, n):
+    """The float32 copies of D_i and O_i that a mixed handle streams equal the
+    IEEE round-to-nearest-even conversion of the caller's float64 blocks, bit
+    for bit: S_32 e_j read back through the float32 SpMV is column j of S
+    converted by numpy (a product with a unit vector adds only exact zeros)."""
+    rng = np.random.default_rng(700 + n)
+    D = np.zeros((N, n, n))
+    for i in range(N):
+        T = _ties(rng, (n, n), -40, -6)
+        D[i] = np.tril(T, -1) + np.tril(T, -1).T + np.diag(np.abs(_ties(rng, n, 6, 7)))
+    O = _ties(rng, (N - 1, n, n), -150, 8)  # reaches float32 subnormals
+    inst = wl.Instance(D=D, O=O, b=np.zeros((N, n)))
+    S = orc.assemble(D, O)
+    with Single(inst, m=1, precision=bb.BT_MIXED) as s:
+        s.ok()
+        for j in range(N * n):
+            e = np.zeros(N * n)
+            e[j] = 1.0
+            col = s.spmv(e.reshape(N, n), f32=True).reshape(-1)
+            want = S[:, j].astype(np.float32).astype(np.float64)
+            assert np.array_equal(col, want), j
