@@ -1018,13 +1018,19 @@ def alpha_choices(a, bb, wl, torch, dev):
 
 
 def lqr_pipeline(a, bb, wl, torch, dev):
-    """LQR problems end to end on the device: Schur-complement formation
-    (bt_lqr_schur, float64), refactor of a mixed handle, batched PCG to 1e-8
-    (a = 1, m = 2, alpha = (1, 7)) and dual-to-primal recovery
-    (bt_lqr_recover), for 1024 LQR problems with the shapes of the bench
-    batch (N ~ U{32..512}, n in {12, 24, 36}, m = n/3; dense SPD Q, R).
-    Each stage timed with CUDA events; the formation kernel's roofline is the
-    float64 rate (its FMA count per block row: 2n^3 + m^3/2 + n m^2 + n^2 m/2)."""
+    """LQR problems end to end on the device, for 1024 LQR problems with the
+    shapes of the bench batch (N ~ U{32..512}, n in {12, 24, 36}, m = n/3;
+    dense SPD Q, R), each stage timed with CUDA events, two ways:
+      fused:    bt_lqr_refactor (the Schur complement formed straight into the
+                mixed handle, D_k factored on chip, then E and H), batched PCG
+                to 1e-8 (a = 1, m = 2, alpha = (1, 7)), recovery (bt_lqr_recover);
+      two-step: bt_lqr_schur (D, O in the caller's layout), bt_refactor, the
+                same solve and recovery.
+    value is the fused pipeline.  The formation runs in double-float pairs on
+    the float32 pipe; its roofline counts pair FMAs per block row --
+    2n^3 + m^3/3 + (n m^2 + n^2 m)/2 for S, n^3/2 more for the fused factor
+    of D_k -- against the float32 issue rate divided by the 12 float32
+    instructions of one pair FMA."""
     import numpy as np
     shapes = wl.config2_shapes(1024)[:max(1, min(a.batch, 1024))]  # --batch: the first problems only
     probs = [wl.lqr_data(wl._rng(6, k), N, n, max(1, n // 3)) for k, (N, n) in enumerate(shapes)]
@@ -1046,9 +1052,10 @@ def lqr_pipeline(a, bb, wl, torch, dev):
     st, h = bb.bt_setup_batched(Ns, ns, d_off, o_off, dD, dO, p)
     assert st == bb.BT_OK, bb.status_string(st)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-    t = {"schur": 0.0, "refactor": 0.0, "solve": 0.0, "recover": 0.0}
+    t2 = {"schur": 0.0, "refactor": 0.0, "solve": 0.0, "recover": 0.0}
+    tf = {"lqr_refactor": 0.0, "solve": 0.0, "recover": 0.0}
 
-    def step(timed):
+    def step_two(timed):
         ev[0].record()
         st, _, _ = bb.bt_lqr_schur(Ns, ns, ms, dA, dB, dQ, dR, dq, dr, dc, dD, dO, dg)
         assert st == bb.BT_OK
@@ -1061,30 +1068,68 @@ def lqr_pipeline(a, bb, wl, torch, dev):
         ev[4].record()
         torch.cuda.synchronize()
         if timed:
-            for i, k in enumerate(t):
-                t[k] += ev[i].elapsed_time(ev[i + 1])
+            for i, k in enumerate(t2):
+                t2[k] += ev[i].elapsed_time(ev[i + 1])
+
+    def step_fused(timed):
+        ev[0].record()
+        st, _, _ = bb.bt_lqr_refactor(h, ms, dA, dB, dQ, dR, dq, dr, dc, dg)
+        assert st == bb.BT_OK
+        ev[1].record()
+        assert bb.bt_pcg_solve_batched_async(h, dg, dl, TOL, 5000) == bb.BT_OK
+        ev[2].record()
+        assert bb.bt_lqr_recover(Ns, ns, ms, dA, dB, dQ, dR, dq, dr, dl, dx, du) == bb.BT_OK
+        ev[3].record()
+        torch.cuda.synchronize()
+        if timed:
+            for i, k in enumerate(tf):
+                tf[k] += ev[i].elapsed_time(ev[i + 1])
 
     for _ in range(a.warmup):
-        step(False)
+        step_two(False)
     for _ in range(a.steps):
-        step(True)
+        step_two(True)
+    st, its2, sts = bb.bt_pcg_solve_batched(h, dg, dl, len(probs), TOL, 5000)
+    assert st == bb.BT_OK and (sts == 0).all()
+    for _ in range(a.warmup):
+        step_fused(False)
+    for _ in range(a.steps):
+        step_fused(True)
     st, its, sts = bb.bt_pcg_solve_batched(h, dg, dl, len(probs), TOL, 5000)
     assert st == bb.BT_OK and (sts == 0).all()
+    # formation alone (bt_lqr_schur) for its roofline
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        bb.bt_lqr_schur(Ns, ns, ms, dA, dB, dQ, dR, dq, dr, dc, dD, dO, dg)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_schur = e0.elapsed_time(e1) / a.steps
     bb.bt_destroy(h)
-    ms_step = {k: v / a.steps for k, v in t.items()}
-    tot = sum(ms_step.values())
-    fma = sum(int(N) * (2 * n ** 3 + m ** 3 / 2 + n * m * m + n * n * m / 2) for N, n, m in zip(Ns, ns, ms))
-    achieved = 2 * fma / (ms_step["schur"] / 1e3) / 1e12
-    peak_tf = 1.25  # GB300 nominal float64 (non-tensor) rate, TFLOP/s
-    emit({"metric": "LQR problems per second end to end on the device (formation, refactor, PCG to 1e-8, recovery)",
+    ms_two = {k: v / a.steps for k, v in t2.items()}
+    ms_fused = {k: v / a.steps for k, v in tf.items()}
+    tot = sum(ms_fused.values())
+    ddfma = sum(int(N) * (2 * n ** 3 + m ** 3 / 3 + (n * m * m + n * n * m) / 2) for N, n, m in zip(Ns, ns, ms))
+    achieved = 2 * ddfma / (ms_schur / 1e3) / 1e12
+    props = torch.cuda.get_device_properties(dev)
+    # float32 lanes per SM (4 x 32) x SMs x 2.07 GHz / 12 instructions per pair FMA x 2 flops
+    peak_tf = props.multi_processor_count * 128 * 2.07e9 / 12 * 2 / 1e12
+    emit({"metric": "LQR problems per second end to end on the device (formation fused with the refactor, "
+                    "PCG to 1e-8, recovery)",
           "value": len(probs) / (tot / 1e3), "unit": "problems/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
-          "ms_per_step": tot, "higher_is_better": True, "dtype": "f64 formation + f32/f64 solve",
+          "ms_per_step": tot, "higher_is_better": True, "dtype": "f32-pair formation + f32/f64 solve + f64 recovery",
           "data": "synthetic (seeded LQR, dense SPD Q and R)",
           "config": {"workload": f"{len(probs)} LQR problems, N~U{{32..512}}, n in {{12,24,36}}, m=n/3"},
-          "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-                       "frac": achieved / peak_tf, "traffic": None, "peak_source": "nominal float64 rate",
-                       "kernel": "k_lqr_schur", "flop_per_launch": 2 * fma},
-          "detail": {"ms": ms_step, "iters_mean": float(np.mean(its))}})
+          "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s (float64-equivalent)",
+                       "frac": achieved / peak_tf, "traffic": None,
+                       "peak_source": "float32 issue rate / 12 instructions per pair FMA (SMs x 128 lanes x 2.07 GHz)",
+                       "kernel": "k_lqr_schur (bt_lqr_schur alone)", "ms_per_launch": ms_schur,
+                       "flop_per_launch": 2 * ddfma},
+          "detail": {"ms_fused": ms_fused, "ms_two_step": ms_two,
+                     "formation_plus_refactor_ms": ms_fused["lqr_refactor"],
+                     "two_step_formation_plus_refactor_ms": ms_two["schur"] + ms_two["refactor"],
+                     "two_step_problems_per_s": len(probs) / (sum(ms_two.values()) / 1e3),
+                     "iters_mean": float(np.mean(its)), "iters_mean_two_step": float(np.mean(its2))}})
 
 
 def fp64_one_at_a_time(bb, torch, dev, stream, Ns, ns, d_off, o_off, v_off, dD, dO, db):

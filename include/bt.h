@@ -383,14 +383,43 @@ bt_status bt_ritz_rho(bt_handle h, const double* b, int iters, double* rho);
  * (A, Bm, R, r may be NULL when every N[k] = 1).  DEVICE outputs in exactly
  * the layout bt_setup_batched takes: D [sum N][n][n], O [sum (N-1)][n][n]
  * (d_off[k] = sum_{j<k} N_j n_j^2, o_off[k] = sum_{j<k} (N_j-1) n_j^2) and
- * gamma [sum N][n] (vec_off[k] = sum_{j<k} N_j n_j).  Float64 arithmetic;
- * one CTA per 16 knots of a problem.  Queued on `stream` (a cudaStream_t),
+ * gamma [sum N][n] (vec_off[k] = sum_{j<k} N_j n_j).  Arithmetic in
+ * double-float pairs (two float32 numbers with error-free products and sums,
+ * about 48 significand bits) on the float32 pipe, inputs split on load and
+ * every result rounded once to float64: agrees with a float64 formation to
+ * about 1e-13 relative to the block norms at these condition numbers.  One
+ * CTA per 16 knots of a problem.  Queued on `stream` (a cudaStream_t),
  * then synchronised: returns BT_ERR_NOT_SPD if some Q_k or R_k has a
  * non-positive Cholesky pivot (*bad_inst, *bad_row name the first one if
  * non-NULL; for R_k the row is k), BT_ERR_ARG on bad sizes or pointers. */
 bt_status bt_lqr_schur(int B, const int* N, const int* n, const int* m, const double* A, const double* Bm,
                        const double* Q, const double* R, const double* q, const double* r, const double* c,
                        double* D, double* O, double* gamma, void* stream, int* bad_inst, int* bad_row);
+
+/* bt_lqr_refactor -- bt_lqr_schur fused with the refactor of a handle: forms
+ * S and gamma of B LQR problems (the construction above) and writes S
+ * straight into h's block arrays (D, O in float64 and float32, the
+ * library's column-major slots), then factors every D_k from the float32
+ * copy just written (Sec. 4.3's block Cholesky, D_k^-1 = W^T W with
+ * W = L^-1; float64 for the blocks the float32 factor refuses, as in
+ * bt_refactor) and forms E and the H blocks (Sec. 4.1).  No D or O array
+ * passes through device memory in the caller's layout and nothing is copied
+ * into the library layout.  h must be a BT_MIXED handle of the optimum (a =
+ * 1, stored H blocks, not mixed_strict_fp64) created by bt_setup or
+ * bt_setup_batched with the problems' shapes: instance k has N[k] = h's N_k
+ * block rows and state size n[k] = h's n_k (<= 48); m (HOST, one entry per
+ * instance) gives the input sizes.  A, Bm, Q, R, q, r, c as for
+ * bt_lqr_schur (DEVICE); gamma (DEVICE, [sum N][n], h's vector packing)
+ * receives the right-hand sides.  Afterwards h holds exactly what
+ * bt_refactor of bt_lqr_schur's D and O leaves.  Synchronises h's stream;
+ * BT_ERR_NOT_SPD if some Q_k or R_k has a non-positive pivot (*bad_inst,
+ * *bad_row as for bt_lqr_schur; h's blocks are then unspecified until the
+ * next successful refactor) or some D_k is not SPD (bt_last_error names it),
+ * BT_ERR_STATE for a handle of another kind, BT_ERR_ARG on bad sizes or
+ * pointers. */
+bt_status bt_lqr_refactor(bt_handle h, const int* m, const double* A, const double* Bm, const double* Q,
+                          const double* R, const double* q, const double* r, const double* c, double* gamma,
+                          int* bad_inst, int* bad_row);
 
 /* bt_lqr_recover -- the primal solution of the QP above from the solution
  * lam of S lam = gamma: z = -G^-1 (g + C^T lam), i.e.

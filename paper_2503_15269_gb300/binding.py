@@ -93,6 +93,7 @@ def lib() -> C.CDLL:
         "bt_alpha_chebyshev": (C.c_int, [C.c_int, C.c_double, C.POINTER(C.c_double)]),
         "bt_lqr_schur": (C.c_int, [C.c_int, ip, ip, ip, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, vp, ip, ip]),
         "bt_lqr_recover": (C.c_int, [C.c_int, ip, ip, ip, dp, dp, dp, dp, dp, dp, dp, dp, dp, vp]),
+        "bt_lqr_refactor": (C.c_int, [H, ip, dp, dp, dp, dp, dp, dp, dp, dp, ip, ip]),
         "bt_device_bytes": (C.c_longlong, [H]),
         "bt_destroy": (None, [H]),
         "bt_status_string": (C.c_char_p, [C.c_int]),
@@ -323,6 +324,15 @@ def bt_lqr_schur(N, n, m, A, Bm, Q, R, q, r, c, D, O, gamma, stream=None):
     bi, br = C.c_int(-1), C.c_int(-1)
     st = lib().bt_lqr_schur(len(Na), Np, nP, mP, _optr(A), _optr(Bm), _ptr(Q), _optr(R), _ptr(q), _optr(r),
                             _ptr(c), _ptr(D), _optr(O), _ptr(gamma), _stream_ptr(stream), C.byref(bi), C.byref(br))
+    return st, bi.value, br.value
+
+
+def bt_lqr_refactor(h, m, A, Bm, Q, R, q, r, c, gamma):
+    """Returns (status, bad_instance, bad_row)."""
+    ma, mP = _iarr(m)
+    bi, br = C.c_int(-1), C.c_int(-1)
+    st = lib().bt_lqr_refactor(h, mP, _optr(A), _optr(Bm), _ptr(Q), _optr(R), _ptr(q), _optr(r), _ptr(c),
+                               _ptr(gamma), C.byref(bi), C.byref(br))
     return st, bi.value, br.value
 
 

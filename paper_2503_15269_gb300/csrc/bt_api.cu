@@ -20,6 +20,11 @@ extern "C" cudaError_t bt_launch_persistent(const bt::KParams* P, int grid, int 
 extern "C" int bt_persistent_smem_fixed(int variant);
 extern "C" cudaError_t bt_persistent_occupancy(int mt_is_float, int variant, int smem_bytes, int* blocks_per_sm);
 extern "C" cudaError_t bt_launch_setup(const bt::SetupParams* P, int mixed, int m, int maxn, cudaStream_t st);
+extern "C" bt_status bt_lqr_schur_handle(int B, const int* N, const int* n, const int* m, const double* A,
+                                         const double* Bm, const double* Q, const double* R, const double* q,
+                                         const double* r, const double* c, double* gamma, const bt::InstDesc* hinst,
+                                         double* hD64, double* hO64, float* hD32, float* hO32, float* hDinv32,
+                                         void* stream, int* bad_inst, int* bad_row);
 extern "C" cudaError_t bt_launch_adjoint(const bt::AdjParams* P, cudaStream_t st);
 namespace bt { struct MParams; }
 extern "C" int bt_mrhs_smem_bytes(int n, int tc);
@@ -919,6 +924,41 @@ bt_status bt_refactor(bt_handle h, const double* D, const double* O) {
   Range nvtx_range("bt_refactor");
   if (!h || !D || (h->maxN > 1 && !O)) return BT_ERR_ARG;
   return launch_setup_kernels(h, D, O);
+}
+
+bt_status bt_lqr_refactor(bt_handle h, const int* m, const double* A, const double* Bm, const double* Q,
+                          const double* R, const double* q, const double* r, const double* c, double* gamma,
+                          int* bad_inst, int* bad_row) {
+  Range nvtx_range("bt_lqr_refactor");
+  if (!h || !m || !gamma) return BT_ERR_ARG;
+  if (!h->mixed || h->variant != 0 || h->prm.mixed_strict_fp64) return BT_ERR_STATE;
+  if (h->maxn > 48) return BT_ERR_ARG;
+  cudaStream_t st = h->stream;
+  if (cudaMemsetAsync(h->d_fail_key, 0xff, sizeof(unsigned long long), st)) return BT_ERR_CUDA;
+  const bt_status s = bt_lqr_schur_handle(h->B, h->N.data(), h->n.data(), m, A, Bm, Q, R, q, r, c, gamma, h->d_inst,
+                                          h->D64, h->O64, h->D32, h->O32, h->Dinv32, st, bad_inst, bad_row);
+  if (s != BT_OK) return s;
+  // D_k^-1 from the float32 copy the formation left in the handle (float64
+  // refactor of refused rows, as in bt_refactor), then E and the H blocks
+  bt::SetupParams sp{};
+  sp.inst = h->d_inst;
+  sp.rows = h->d_rows;
+  sp.nrows = h->total_rows;
+  sp.D64 = h->D64; sp.O64 = h->O64; sp.Dinv64 = h->Dinv64; sp.E64 = h->E64;
+  sp.Hd64 = h->Hd64; sp.Hu64 = h->Hu64; sp.Hl64 = h->Hl64;
+  sp.D32 = h->D32; sp.O32 = h->O32; sp.Dinv32 = h->Dinv32; sp.E32 = h->E32;
+  sp.Hd32 = h->Hd32; sp.Hu32 = h->Hu32; sp.Hl32 = h->Hl32;
+  sp.fam_a = 1.0;
+  sp.want32 = 1;
+  sp.want64 = 1;
+  sp.fail_key = h->d_fail_key;
+  sp.fail_piv = h->d_fail_piv;
+  sp.retry = h->d_retry;
+  sp.segs = h->d_segs;
+  sp.nsegs = h->nsegs;
+  sp.copied = 1;
+  if (bt_status e = cuda_st(bt_launch_setup(&sp, 1, h->prm.m, h->maxn, st)); e != BT_OK) return e;
+  return read_setup_status(h);
 }
 
 bt_status bt_setup_status(bt_handle h) {

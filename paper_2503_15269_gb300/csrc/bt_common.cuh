@@ -142,6 +142,8 @@ struct SetupParams {
                             // float32 factor was refused (refactored in float64)
   const SegRef* segs;       // mixed only, optional: row segments for the fused E/H kernel
   long long nsegs;
+  int copied;               // mixed: D64, O64, D32, O32 already hold the blocks (written by the
+                            // LQR formation); the factor reads D from them and copies nothing
 };
 
 struct AdjParams {

@@ -16,17 +16,18 @@
 //     gamma_k = -(c_k + w_k - A_{k-1} w_{k-1} - B_{k-1} R_{k-1}^-1 r_{k-1}),
 //     x_k = -Q_k^-1 (q_k + lam_k - A_k^T lam_{k+1}),  u_k = -R_k^-1 (r_k - B_k^T lam_{k+1}).
 //
-// Float64 throughout (the blocks feed the float64 residual of the solver).
-// One CTA walks a segment of consecutive block rows of one instance and
-// carries A_{k-1}, P_{k-1}, w_{k-1} in shared memory from row to row, so each
-// row inverts one Q_k (Cholesky, W = L^-1, W^T W) and forms one n x n product
-// P_k and one symmetric A_{k-1} P_{k-1}.  Float64 issues at ~2 FMA per clock
-// per SM on GB300, so these kernels are bound by the float64 pipe.
+// The blocks feed the float64 residual of the solver, so they are formed to
+// float64 accuracy: the formation in double-float pairs on the float32 pipe
+// (float64 issues at ~2 FMA per clock per SM on GB300, 1/64 of float32),
+// the recovery in float64.  One CTA walks a segment of consecutive block
+// rows of one instance and carries row k-1's contribution to D_k and gamma_k
+// in shared memory from row to row.
 #include <algorithm>
 #include <vector>
 
 #include "../../include/bt.h"
 #include "bt_common.cuh"
+#include "bt_dd.cuh"
 
 namespace bt {
 
@@ -38,6 +39,7 @@ static_assert(kLqrThreads >= kLqrMax, "one thread per row of a block column");
 struct LqrDesc {
   int N, n, m, pad;
   long long oA, oB, oQ, oR, ov, ou;  // element offsets: A/O, Bm, Q/D, R, n-vectors, m-vectors
+  long long ot;                      // first task of k_lqr_winv (sum over earlier problems of 2 N - 1)
 };
 struct LqrSeg {
   int inst, a, b, pad;
@@ -48,6 +50,12 @@ struct LqrParams {
   const LqrSeg* segs;
   const double *A, *Bm, *Q, *R, *q, *r, *c, *lam;
   double *D, *O, *gamma, *x, *u;
+  dd *WQ, *WR;  // formation scratch: W = L^-1 of every Q_k, R_k (at the offsets of Q, R)
+  // optional: a mixed handle's block arrays, written by the formation
+  // (column-major slots at the handle's offsets) -- null when not attached
+  const InstDesc* hinst;
+  double *hD64, *hO64;
+  float *hD32, *hO32, *hDinv32;
   unsigned long long* fail_key;  // min over (inst << 32 | 2 * row + (R ? 1 : 0)) of refused blocks
 };
 
@@ -84,51 +92,6 @@ __device__ bool chol(double* M, int n, double* rinv) {
   return true;
 }
 
-// From the Cholesky factor in lower(M): M <- M^-1 = W^T W with W = L^-1.
-// W by right-looking forward substitution on the columns of I, two barriers
-// per row: row j of B (I minus the earlier updates) is scaled to W_j by
-// 1/L_jj, then the rows below take one FMA per element.
-__device__ void chol_inverse(double* M, double* W, int n, const double* rinv) {
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) W[t] = (t / n == t % n) ? 1.0 : 0.0;
-  for (int j = 0; j < n; ++j) {
-    __syncthreads();
-    if (threadIdx.x <= j) W[j * n + threadIdx.x] *= rinv[j];
-    __syncthreads();
-    const int cols = j + 1, rows = n - j - 1;
-    for (int t = threadIdx.x; t < rows * cols; t += blockDim.x) {
-      const int i = j + 1 + t / cols, c = t % cols;
-      W[i * n + c] = fma(-M[i * n + j], W[j * n + c], W[i * n + c]);
-    }
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-    const int i = t / n, j = t % n;
-    if (j > i) continue;
-    double acc = 0.0;
-    for (int r = i; r < n; ++r) acc = fma(W[r * n + i], W[r * n + j], acc);
-    M[i * n + j] = acc;
-    M[j * n + i] = acc;
-  }
-  __syncthreads();
-}
-
-// C (+)= X Y^T for X [rows x k], Y [cols x k] (row-major, leading dims k);
-// sym: C is symmetric, only j <= i is computed and mirrored.
-__device__ void gemm_nt(double* C, int ldc, const double* X, const double* Y, int rows, int cols, int k, double s,
-                        bool acc, bool sym) {
-  for (int t = threadIdx.x; t < rows * cols; t += blockDim.x) {
-    const int i = t / cols, j = t % cols;
-    if (sym && j > i) continue;
-    double v = 0.0;
-    for (int p = 0; p < k; ++p) v = fma(X[i * k + p], Y[j * k + p], v);
-    v *= s;
-    const double o = acc ? C[i * ldc + j] + v : v;
-    C[i * ldc + j] = o;
-    if (sym && j < i) C[j * ldc + i] = o;
-  }
-  __syncthreads();
-}
-
 __device__ void load(double* dst, const double* src, int cnt) {
   for (int t = threadIdx.x; t < cnt; t += blockDim.x) dst[t] = src[t];
 }
@@ -139,103 +102,307 @@ __device__ void refuse(const LqrParams& P, int inst, int row, int isR) {
 }
 
 // ---- formation ---------------------------------------------------------------
+// Double-float (bt_dd.cuh) throughout the O(n^3) work: float64 runs at 1/64
+// of the float32 rate here, and a pair of float32 numbers with error-free
+// products and sums carries about 48 significand bits.  The inputs are split
+// into pairs on load and the blocks rounded once to float64 on the store.
+//
+// Two kernels.  k_lqr_winv inverts the Cholesky factor of every Q_k and R_k,
+// one warp per matrix with no CTA barrier (the column-serial part of a
+// Cholesky is latency, so many independent matrices per SM hide it):
+//   Q_k = L L^T,  W = L^-1 (so Q_k^-1 = W^T W), likewise W_R for R_k,
+// into a scratch array of pairs.  k_lqr_schur then forms, per block row k,
+//   Y = W A_k^T,  O_k = -W^T Y (= -Q_k^-1 A_k^T),  t = W q_k,  w_k = W^T t,
+//   D_k = W^T W + C_{k-1},  gamma_k = -(c_k + w_k - g_{k-1}),
+// and for the next row, with V = W_R B_k^T and s = W_R r_k,
+//   C_k = Y^T Y + V^T V   (= A_k Q_k^-1 A_k^T + B_k R_k^-1 B_k^T),
+//   g_k = Y^T t + V^T s   (= A_k w_k + B_k R_k^-1 r_k),
+// from products only (every phase parallel over output elements).  With a
+// mixed handle attached it writes D and O in the handle's layout (float64
+// and float32 column-major slots) instead of, or besides, the caller's.
+
+constexpr int kWinvWarps = 4;
+
+// One warp: M (col-major pairs, n x n, element (i, j) at j n + i) <- the
+// float64 row-major block src; Cholesky factor L in the lower triangle by
+// columns (left-looking: lane = row, rows lane and lane + 32), rv[j] =
+// 1 / L_jj; then W = L^-1 by columns (lane = column), W(i, c) for i > c kept
+// in the upper triangle at index i n + c.  False (on every lane) if a pivot
+// is not positive.
+__device__ bool dd_warp_chol_inv(dd* M, dd* rv, const double* src, int n, int lane) {
+  constexpr unsigned FULL = 0xffffffffu;
+  for (int t = lane; t < n * n; t += 32) {
+    const int i = t / n, j = t - i * n;
+    M[j * n + i] = dd_from(src[t]);
+  }
+  __syncwarp();
+  for (int j = 0; j < n; ++j) {
+    dd dv[2] = {dd_make(0.f, 0.f), dd_make(0.f, 0.f)};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = lane + 32 * h;
+      if (i < n && i >= j) {  // d_i = M(i, j) - sum_{p<j} L(i, p) L(j, p), two interleaved sums
+        DDAcc a0, a1;
+        a0.init(M[j * n + i]);
+        a1.init0();
+        int p = 0;
+        for (; p + 1 < j; p += 2) {
+          a0.fms(M[p * n + i], M[p * n + j]);
+          a1.fms(M[(p + 1) * n + i], M[(p + 1) * n + j]);
+        }
+        if (p < j) a0.fms(M[p * n + i], M[p * n + j]);
+        dv[h] = dd_add(a0.value(), a1.value());
+      }
+    }
+    const dd own = (j < 32) ? dv[0] : dv[1];
+    const dd piv = dd_make(__shfl_sync(FULL, own.h, j & 31), __shfl_sync(FULL, own.l, j & 31));
+    if (!(piv.h > 0.f) || !isfinite(piv.h)) return false;
+    const dd s = dd_sqrt(piv);
+    const dd r = dd_rcp(s);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = lane + 32 * h;
+      if (i < n && i > j) M[j * n + i] = dd_mul(dv[h], r);
+    }
+    if (lane == (j & 31)) {
+      M[j * n + j] = s;
+      rv[j] = r;
+    }
+    __syncwarp();
+  }
+  // W(i, c) = -(1 / L_ii) sum_{p=c}^{i-1} L(i, p) W(p, c), W(c, c) = 1 / L_cc;
+  // a lane reads only its own column of W and the (read-only) lower triangle
+  for (int i = 1; i < n; ++i) {
+    const dd ri = rv[i];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = lane + 32 * h;
+      if (c < i) {
+        DDAcc a0, a1;
+        a0.init0();
+        a1.init0();
+        a0.fma(M[c * n + i], rv[c]);
+        int p = c + 1;
+        for (; p + 1 < i; p += 2) {
+          a0.fma(M[p * n + i], M[p * n + c]);
+          a1.fma(M[(p + 1) * n + i], M[(p + 1) * n + c]);
+        }
+        if (p < i) a0.fma(M[p * n + i], M[p * n + c]);
+        M[i * n + c] = dd_neg(dd_mul(dd_add(a0.value(), a1.value()), ri));
+      }
+    }
+  }
+  __syncwarp();
+  return true;
+}
+
+// Every Q_k and R_k of the batch: task t of instance k (desc[k].ot <= t <
+// desc[k+1].ot) is Q_{t - ot} for t - ot < N, else R_{t - ot - N}.  W is
+// stored row-major (lower triangle, zeros above) at the element offset of
+// its Q or R block.
+__global__ void __launch_bounds__(kWinvWarps * 32) k_lqr_winv(const __grid_constant__ LqrParams P, long long ntask,
+                                                               int B, int stride) {
+  extern __shared__ __align__(16) double lsm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long task = (long long)blockIdx.x * kWinvWarps + warp;
+  if (task >= ntask) return;
+  int lo = 0, hi = B - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (P.desc[mid].ot <= task) lo = mid;
+    else hi = mid - 1;
+  }
+  const LqrDesc d = P.desc[lo];
+  const long long rel = task - d.ot;
+  const bool isR = rel >= d.N;
+  const int row = (int)(isR ? rel - d.N : rel);
+  const int n = isR ? d.m : d.n;
+  const long long off = isR ? d.oR + (long long)row * n * n : d.oQ + (long long)row * n * n;
+  dd* M = reinterpret_cast<dd*>(lsm) + (size_t)warp * stride;
+  dd* rv = M + n * n;
+  if (!dd_warp_chol_inv(M, rv, (isR ? P.R : P.Q) + off, n, lane)) {
+    if (lane == 0) atomicMin(P.fail_key, ((unsigned long long)lo << 32) | (unsigned)(2 * row + (isR ? 1 : 0)));
+    return;
+  }
+  dd* dst = (isR ? P.WR : P.WQ) + off;
+  for (int t = lane; t < n * n; t += 32) {
+    const int i = t / n, c = t - i * n;
+    dst[t] = (i > c) ? M[t] : (i == c ? rv[i] : dd_make(0.f, 0.f));
+  }
+}
+
+// CTA-wide helpers of k_lqr_schur: every thread calls them; each ends with a
+// barrier.  Matrices are row-major pairs in shared memory.
+
+// Y = W X for W lower triangular (rows x rows) and X (rows x cols).
+__device__ void dd_trmm(dd* Y, const dd* W, const dd* X, int rows, int cols) {
+  for (int t = threadIdx.x; t < rows * cols; t += blockDim.x) {
+    const int i = t / cols, j = t - i * cols;
+    DDAcc a;
+    a.init0();
+    for (int p = 0; p <= i; ++p) a.fma(W[i * rows + p], X[p * cols + j]);
+    Y[t] = a.value();
+  }
+  __syncthreads();
+}
+
+// (X^T Z)(i, j) = sum_p X[p][i] Z[p][j] over the rows p of X and Z (both
+// rows x cols); tri: X is lower triangular, so p starts at i.
+__device__ __forceinline__ dd dd_tdot(const dd* X, const dd* Z, int rows, int cols, int i, int j, bool tri) {
+  DDAcc a;
+  a.init0();
+  for (int p = tri ? i : 0; p < rows; ++p) a.fma(X[p * cols + i], Z[p * cols + j]);
+  return a.value();
+}
+
+__device__ void load_dd(dd* dst, const double* src, int cnt) {
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) dst[t] = dd_from(src[t]);
+}
+
+__device__ void copy_dd(dd* dst, const dd* src, int cnt) {
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) dst[t] = src[t];
+}
+
+// dst (cols x rows) = src^T for src (rows x cols), row-major
+__device__ void load_dd_t(dd* dst, const double* src, int rows, int cols) {
+  for (int t = threadIdx.x; t < rows * cols; t += blockDim.x) {
+    const int i = t / cols, j = t - i * cols;
+    dst[j * rows + i] = dd_from(src[t]);
+  }
+}
+
 __global__ void __launch_bounds__(kLqrThreads) k_lqr_schur(const __grid_constant__ LqrParams P) {
   extern __shared__ __align__(16) double lsm[];
   const LqrSeg sg = P.segs[blockIdx.x];
   const LqrDesc d = P.desc[sg.inst];
-  const int n = d.n, m = d.m, N = d.N, nn = n * n;
-  double* Qi = lsm;             // Q_k^-1
-  double* Ak = Qi + nn;         // A_k
-  double* Pk = Ak + nn;         // P_k = Q_k^-1 A_k^T
-  double* Ap = Pk + nn;         // A_{k-1}
-  double* Pp = Ap + nn;         // P_{k-1}
-  double* Wd = Pp + nn;         // inverse scratch, then the D accumulator
-  double* Ri = Wd + nn;         // R_{k-1}^-1  (m x m)
-  double* Rw = Ri + m * m;      // its scratch
-  double* Bk = Rw + m * m;      // B_{k-1}     (n x m)
-  double* Uk = Bk + n * m;      // B_{k-1} R_{k-1}^-1 (n x m)
-  double* wk = Uk + n * m;      // w_k = Q_k^-1 q_k
-  double* wp = wk + kLqrMax;    // w_{k-1}
-  double* rinv = wp + kLqrMax;  // reciprocal pivots
-  const double* Qb = P.Q + d.oQ;
-  const double* Ab = P.A + d.oA;
-  const double* qb = P.q + d.ov;
-  // Q_k^-1, A_k, P_k, w_k of row k into (Qi, Ak, Pk, wk); false if Q_k is refused
-  auto row_terms = [&](int k) -> bool {
-    load(Qi, Qb + (long long)k * nn, nn);
-    if (!chol(Qi, n, rinv)) return false;
-    chol_inverse(Qi, Wd, n, rinv);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      double v = 0.0;
-      for (int p = 0; p < n; ++p) v = fma(Qi[i * n + p], qb[(long long)k * n + p], v);
-      wk[i] = v;
-    }
-    if (k < N - 1) {
-      load(Ak, Ab + (long long)k * nn, nn);
-      __syncthreads();
-      gemm_nt(Pk, n, Qi, Ak, n, n, n, 1.0, false, false);  // Q_k^-1 A_k^T (Q_k^-1 symmetric)
+  const int n = d.n, m = d.m, N = d.N, nn = n * n, mm = m * m, mn = m * n;
+  const int tid = threadIdx.x;
+  dd* Wq = reinterpret_cast<dd*>(lsm);  // W = L^-1 of Q_k
+  dd* At = Wq + nn;                     // A_k^T
+  dd* Y = At + nn;                      // W A_k^T
+  dd* C = Y + nn;                       // carry C_{k-1} (lower), then D_k in place
+  dd* Wr = C + nn;                      // W_R of R_k
+  dd* Bt = Wr + mm;                     // B_k^T (m x n)
+  dd* V = Bt + mn;                      // W_R B_k^T
+  dd* vq = V + mn;                      // q_k, then w_k
+  dd* vt = vq + kLqrMax;                // t = W q_k
+  dd* vr = vt + kLqrMax;                // r_k
+  dd* vs = vr + kLqrMax;                // s = W_R r_k
+  dd* vg = vs + kLqrMax;                // g_{k-1}
+  const bool fused = P.hinst != nullptr;
+  const InstDesc hd = fused ? P.hinst[sg.inst] : InstDesc{};
+  for (int k = sg.a > 0 ? sg.a - 1 : 0; k < sg.b; ++k) {
+    const bool own = k >= sg.a;  // row a-1 of a later segment only rebuilds the carry
+    const bool hasA = k < N - 1;
+    copy_dd(Wq, P.WQ + d.oQ + (long long)k * nn, nn);
+    load_dd(vq, P.q + d.ov + (long long)k * n, n);
+    if (hasA) {
+      load_dd_t(At, P.A + d.oA + (long long)k * nn, n, n);
+      load_dd_t(Bt, P.Bm + d.oB + (long long)k * n * m, n, m);
+      copy_dd(Wr, P.WR + d.oR + (long long)k * mm, mm);
+      load_dd(vr, P.r + d.ou + (long long)k * m, m);
     }
     __syncthreads();
-    return true;
-  };
-  auto carry = [&]() {  // (Ak, Pk, wk) of row k become (Ap, Pp, wp)
-    for (int t = threadIdx.x; t < nn; t += blockDim.x) {
-      Ap[t] = Ak[t];
-      Pp[t] = Pk[t];
+    // t = W q_k, s = W_R r_k; then w_k = W^T t (into vq)
+    for (int i = tid; i < n + (hasA ? m : 0); i += blockDim.x) {
+      DDAcc a;
+      a.init0();
+      if (i < n) {
+        for (int p = 0; p <= i; ++p) a.fma(Wq[i * n + p], vq[p]);
+        vt[i] = a.value();
+      } else {
+        const int ir = i - n;
+        for (int p = 0; p <= ir; ++p) a.fma(Wr[ir * m + p], vr[p]);
+        vs[ir] = a.value();
+      }
     }
-    for (int t = threadIdx.x; t < n; t += blockDim.x) wp[t] = wk[t];
     __syncthreads();
-  };
-  if (sg.a > 0) {
-    if (!row_terms(sg.a - 1)) { refuse(P, sg.inst, sg.a - 1, 0); return; }
-    carry();
-  }
-  for (int k = sg.a; k < sg.b; ++k) {
-    if (!row_terms(k)) { refuse(P, sg.inst, k, 0); return; }
-    double* Dk = P.D + d.oQ + (long long)k * nn;
-    double* gk = P.gamma + d.ov + (long long)k * n;
-    const double* ck = P.c + d.ov + (long long)k * n;
-    if (k < N - 1) {
-      double* Ok = P.O + d.oA + (long long)k * nn;
-      for (int t = threadIdx.x; t < nn; t += blockDim.x) Ok[t] = -Pk[t];
+    for (int i = tid; i < n; i += blockDim.x) {
+      DDAcc a;
+      a.init0();
+      for (int p = i; p < n; ++p) a.fma(Wq[p * n + i], vt[p]);
+      vq[i] = a.value();
     }
-    if (k == 0) {
-      for (int t = threadIdx.x; t < nn; t += blockDim.x) Dk[t] = Qi[t];
-      for (int t = threadIdx.x; t < n; t += blockDim.x) gk[t] = -(ck[t] + wk[t]);
-    } else {
-      // D_k = Q_k^-1 + A_{k-1} P_{k-1} + (B R^-1) B^T over row k-1's input
-      for (int t = threadIdx.x; t < nn; t += blockDim.x) Wd[t] = Qi[t];
-      __syncthreads();
-      // A_{k-1} P_{k-1} = A_{k-1} Q^-1 A_{k-1}^T: symmetric; (A P)[i][j] = sum_p A[i][p] P[p][j]
-      for (int t = threadIdx.x; t < nn; t += blockDim.x) {
-        const int i = t / n, j = t % n;
+    if (hasA) {  // Y = W A_k^T, V = W_R B_k^T (one pass over both)
+      for (int t = tid; t < nn + mn; t += blockDim.x) {
+        DDAcc a;
+        a.init0();
+        if (t < nn) {
+          const int i = t / n, j = t - i * n;
+          for (int p = 0; p <= i; ++p) a.fma(Wq[i * n + p], At[p * n + j]);
+          Y[t] = a.value();
+        } else {
+          const int u = t - nn, i = u / n, j = u - i * n;
+          for (int p = 0; p <= i; ++p) a.fma(Wr[i * m + p], Bt[p * n + j]);
+          V[u] = a.value();
+        }
+      }
+    }
+    __syncthreads();
+    if (own) {
+      // O_k = -W^T Y: the handle's column-major slots when a handle is
+      // attached (consecutive threads down a column), else row-major
+      if (hasA) {
+        double* Oc = P.O ? P.O + d.oA + (long long)k * nn : nullptr;
+        double* O64 = fused ? P.hO64 + hd.off64 + (long long)k * hd.bs64 : nullptr;
+        float* O32 = fused ? P.hO32 + hd.off32 + (long long)k * hd.bs32 : nullptr;
+        for (int t = tid; t < nn; t += blockDim.x) {
+          const int hi_ = t / n, lo_ = t - hi_ * n;
+          const int a = fused ? lo_ : hi_, c = fused ? hi_ : lo_;  // element (a, c)
+          const dd o = dd_neg(dd_tdot(Wq, Y, n, n, a, c, true));
+          const double ov = dd_to(o);
+          if (Oc) Oc[a * n + c] = ov;
+          if (fused) {  // the float32 copy rounds the float64 value, as bt_refactor's does
+            O64[c * n + a] = ov;
+            O32[c * n + a] = (float)ov;
+          }
+        }
+      }
+      // D_k = W^T W + C_{k-1} (lower, in place), gamma_k
+      for (int t = tid; t < nn; t += blockDim.x) {
+        const int i = t / n, j = t - i * n;
         if (j > i) continue;
-        double v = 0.0;
-        for (int p = 0; p < n; ++p) v = fma(Ap[i * n + p], Pp[p * n + j], v);
-        Wd[i * n + j] += v;
-        if (j < i) Wd[j * n + i] += v;
+        dd v = dd_tdot(Wq, Wq, n, n, i, j, true);
+        if (k > 0) v = dd_add(v, C[t]);
+        C[t] = v;
+      }
+      for (int i = tid; i < n; i += blockDim.x) {
+        dd v = dd_add(dd_from(P.c[d.ov + (long long)k * n + i]), vq[i]);
+        if (k > 0) v = dd_add(v, dd_neg(vg[i]));
+        P.gamma[d.ov + (long long)k * n + i] = -dd_to(v);
       }
       __syncthreads();
-      const double* Rb = P.R + d.oR + (long long)(k - 1) * m * m;
-      load(Ri, Rb, m * m);
-      load(Bk, P.Bm + d.oB + (long long)(k - 1) * n * m, n * m);
-      if (!chol(Ri, m, rinv)) { refuse(P, sg.inst, k - 1, 1); return; }
-      chol_inverse(Ri, Rw, m, rinv);
-      // U = B R^-1 (R^-1 symmetric: U[i][j] = sum_p B[i][p] Ri[j][p])
-      gemm_nt(Uk, m, Bk, Ri, n, m, m, 1.0, false, false);
-      gemm_nt(Wd, n, Uk, Bk, n, n, m, 1.0, true, true);
-      for (int t = threadIdx.x; t < nn; t += blockDim.x) Dk[t] = Wd[t];
-      // gamma_k = -(c_k + w_k - A_{k-1} w_{k-1} - U r_{k-1})
-      const double* rp = P.r + d.ou + (long long)(k - 1) * m;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        double v = ck[i] + wk[i];
-        for (int p = 0; p < n; ++p) v = fma(-Ap[i * n + p], wp[p], v);
-        for (int p = 0; p < m; ++p) v = fma(-Uk[i * m + p], rp[p], v);
-        gk[i] = -v;
+      double* Dc = P.D ? P.D + d.oQ + (long long)k * nn : nullptr;
+      double* D64 = fused ? P.hD64 + hd.off64 + (long long)k * hd.bs64 : nullptr;
+      float* D32 = fused ? P.hD32 + hd.off32 + (long long)k * hd.bs32 : nullptr;
+      for (int t = tid; t < nn; t += blockDim.x) {  // symmetric: both layouts index alike
+        const int i = t / n, j = t - i * n;
+        const dd v = C[j > i ? j * n + i : t];
+        const double dv = dd_to(v);
+        if (Dc) Dc[t] = dv;
+        if (fused) {
+          D64[t] = dv;
+          D32[t] = (float)dv;
+        }
+      }
+      __syncthreads();
+    }
+    if (hasA) {
+      // C_k = Y^T Y + V^T V (lower), g_k = Y^T t + V^T s
+      for (int t = tid; t < nn; t += blockDim.x) {
+        const int i = t / n, j = t - i * n;
+        if (j > i) continue;
+        C[t] = dd_add(dd_tdot(Y, Y, n, n, i, j, false), dd_tdot(V, V, m, n, i, j, false));
+      }
+      for (int i = tid; i < n; i += blockDim.x) {
+        DDAcc a;
+        a.init0();
+        for (int p = 0; p < n; ++p) a.fma(Y[p * n + i], vt[p]);
+        for (int p = 0; p < m; ++p) a.fma(V[p * n + i], vs[p]);
+        vg[i] = a.value();
       }
     }
     __syncthreads();
-    carry();
   }
 }
 
@@ -303,30 +470,36 @@ __global__ void __launch_bounds__(kLqrThreads) k_lqr_recover(const __grid_consta
 
 namespace {
 
-int smem_schur(int n, int m) { return (6 * n * n + 2 * m * m + 2 * n * m + 3 * bt::kLqrMax) * 8; }
+int smem_schur(int n, int m) { return (4 * n * n + m * m + 2 * n * m + 5 * bt::kLqrMax) * 8; }
 int smem_recover(int n, int m) { return (std::max(n * n, m * m) + 2 * bt::kLqrMax) * 8; }
 
-// Host descriptors and segments; checks the shapes.
+// Host descriptors and segments; checks the shapes.  Also the task count of
+// k_lqr_winv and the element counts of Q and R (the sizes of its scratch).
 bt_status lqr_plan(int B, const int* N, const int* n, const int* m, std::vector<bt::LqrDesc>& desc,
-                   std::vector<bt::LqrSeg>& segs, int& maxn, int& maxm) {
+                   std::vector<bt::LqrSeg>& segs, int& maxn, int& maxm, long long& ntask, long long& nQ,
+                   long long& nR) {
   if (B < 1 || !N || !n || !m) return BT_ERR_ARG;
   desc.resize(B);
-  long long oA = 0, oB = 0, oQ = 0, oR = 0, ov = 0, ou = 0;
+  long long oA = 0, oB = 0, oQ = 0, oR = 0, ov = 0, ou = 0, ot = 0;
   maxn = maxm = 1;
   for (int k = 0; k < B; ++k) {
     if (N[k] < 1 || n[k] < 1 || n[k] > bt::kLqrMax || m[k] < 1 || m[k] > bt::kLqrMax) return BT_ERR_ARG;
     const long long Nk = N[k], nk = n[k], mk = m[k];
-    desc[k] = bt::LqrDesc{N[k], n[k], m[k], 0, oA, oB, oQ, oR, ov, ou};
+    desc[k] = bt::LqrDesc{N[k], n[k], m[k], 0, oA, oB, oQ, oR, ov, ou, ot};
     oA += (Nk - 1) * nk * nk;
     oB += (Nk - 1) * nk * mk;
     oQ += Nk * nk * nk;
     oR += (Nk - 1) * mk * mk;
     ov += Nk * nk;
     ou += (Nk - 1) * mk;
+    ot += 2 * Nk - 1;
     maxn = std::max(maxn, n[k]);
     maxm = std::max(maxm, m[k]);
     for (int a = 0; a < N[k]; a += bt::kLqrSeg) segs.push_back(bt::LqrSeg{k, a, std::min(N[k], a + bt::kLqrSeg), 0});
   }
+  ntask = ot;
+  nQ = oQ;
+  nR = oR;
   return BT_OK;
 }
 
@@ -335,28 +508,43 @@ bt_status lqr_run(bool schur, int B, const int* N, const int* n, const int* m, b
   std::vector<bt::LqrDesc> desc;
   std::vector<bt::LqrSeg> segs;
   int maxn = 0, maxm = 0;
-  bt_status s = lqr_plan(B, N, n, m, desc, segs, maxn, maxm);
+  long long ntask = 0, nQ = 0, nR = 0;
+  bt_status s = lqr_plan(B, N, n, m, desc, segs, maxn, maxm, ntask, nQ, nR);
   if (s != BT_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t bd = desc.size() * sizeof(bt::LqrDesc), bs = segs.size() * sizeof(bt::LqrSeg);
+  const size_t head = ((bd + bs + 8 + 255) / 256) * 256;
+  const size_t scratch = schur ? (size_t)(nQ + nR) * sizeof(bt::dd) : 0;
   char* buf = nullptr;
-  if (cudaMallocAsync((void**)&buf, bd + bs + 64, st) != cudaSuccess) return BT_ERR_ALLOC;
+  if (cudaMallocAsync((void**)&buf, head + scratch, st) != cudaSuccess) return BT_ERR_ALLOC;
   const auto ok = [](cudaError_t e) { return e == cudaSuccess; };
   bt_status out = BT_OK;
   unsigned long long key = ~0ull;
   P.desc = reinterpret_cast<const bt::LqrDesc*>(buf);
   P.segs = reinterpret_cast<const bt::LqrSeg*>(buf + bd);
   P.fail_key = reinterpret_cast<unsigned long long*>(buf + ((bd + bs + 7) / 8) * 8);
+  P.WQ = reinterpret_cast<bt::dd*>(buf + head);
+  P.WR = P.WQ + nQ;
   const int smem = schur ? smem_schur(maxn, maxm) : smem_recover(maxn, maxm);
   const void* fn = schur ? (const void*)bt::k_lqr_schur : (const void*)bt::k_lqr_recover;
+  const int maxd = std::max(maxn, maxm);
+  const int wstride = maxd * maxd + maxd;  // pairs per warp of k_lqr_winv: one block and its pivots
+  const int wsmem = bt::kWinvWarps * wstride * (int)sizeof(bt::dd);
   if (!ok(cudaMemcpyAsync(buf, desc.data(), bd, cudaMemcpyHostToDevice, st)) ||
       !ok(cudaMemcpyAsync(buf + bd, segs.data(), bs, cudaMemcpyHostToDevice, st)) ||
       !ok(cudaMemsetAsync(P.fail_key, 0xff, sizeof(unsigned long long), st)) ||
-      !ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) {
+      !ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) ||
+      (schur && !ok(cudaFuncSetAttribute(bt::k_lqr_winv, cudaFuncAttributeMaxDynamicSharedMemorySize, wsmem)))) {
     out = BT_ERR_CUDA;
   } else {
+    if (schur) {
+      const long long wgrid = (ntask + bt::kWinvWarps - 1) / bt::kWinvWarps;
+      bt::k_lqr_winv<<<(unsigned)wgrid, bt::kWinvWarps * 32, wsmem, st>>>(P, ntask, B, wstride);
+      if (!ok(cudaGetLastError())) out = BT_ERR_CUDA;
+    }
     void* args[] = {(void*)&P};
-    if (!ok(cudaLaunchKernel(fn, dim3((unsigned)segs.size()), dim3(bt::kLqrThreads), args, smem, st)) ||
+    if (out != BT_OK ||
+        !ok(cudaLaunchKernel(fn, dim3((unsigned)segs.size()), dim3(bt::kLqrThreads), args, smem, st)) ||
         !ok(cudaMemcpyAsync(&key, P.fail_key, sizeof(key), cudaMemcpyDeviceToHost, st)) ||
         !ok(cudaStreamSynchronize(st)))
       out = BT_ERR_CUDA;
@@ -370,6 +558,13 @@ bt_status lqr_run(bool schur, int B, const int* N, const int* n, const int* m, b
   return out;
 }
 
+bool any_long(int B, const int* N) {
+  if (B < 1 || !N) return false;
+  for (int k = 0; k < B; ++k)
+    if (N[k] > 1) return true;
+  return false;
+}
+
 }  // namespace
 
 extern "C" bt_status bt_lqr_schur(int B, const int* N, const int* n, const int* m, const double* A,
@@ -377,9 +572,28 @@ extern "C" bt_status bt_lqr_schur(int B, const int* N, const int* n, const int* 
                                   const double* r, const double* c, double* D, double* O, double* gamma,
                                   void* stream, int* bad_inst, int* bad_row) {
   if (!Q || !q || !c || !D || !gamma) return BT_ERR_ARG;
+  if (any_long(B, N) && (!A || !Bm || !R || !r || !O)) return BT_ERR_ARG;
   bt::LqrParams P{};
   P.A = A; P.Bm = Bm; P.Q = Q; P.R = R; P.q = q; P.r = r; P.c = c;
   P.D = D; P.O = O; P.gamma = gamma;
+  return lqr_run(true, B, N, n, m, P, stream, bad_inst, bad_row);
+}
+
+// The formation into a mixed handle's block arrays (D, O in float64 and
+// float32, D^-1 in float32; column-major slots at the handle's offsets), for
+// bt_lqr_refactor.  Shapes are the handle's; the caller checks them.
+extern "C" bt_status bt_lqr_schur_handle(int B, const int* N, const int* n, const int* m, const double* A,
+                                         const double* Bm, const double* Q, const double* R, const double* q,
+                                         const double* r, const double* c, double* gamma, const bt::InstDesc* hinst,
+                                         double* hD64, double* hO64, float* hD32, float* hO32, float* hDinv32,
+                                         void* stream, int* bad_inst, int* bad_row) {
+  if (!Q || !q || !c || !gamma || !hinst || !hD64 || !hD32 || !hDinv32) return BT_ERR_ARG;
+  if (any_long(B, N) && (!A || !Bm || !R || !r || !hO64 || !hO32)) return BT_ERR_ARG;
+  bt::LqrParams P{};
+  P.A = A; P.Bm = Bm; P.Q = Q; P.R = R; P.q = q; P.r = r; P.c = c;
+  P.gamma = gamma;
+  P.hinst = hinst;
+  P.hD64 = hD64; P.hO64 = hO64; P.hD32 = hD32; P.hO32 = hO32; P.hDinv32 = hDinv32;
   return lqr_run(true, B, N, n, m, P, stream, bad_inst, bad_row);
 }
 
@@ -387,6 +601,7 @@ extern "C" bt_status bt_lqr_recover(int B, const int* N, const int* n, const int
                                     const double* Bm, const double* Q, const double* R, const double* q,
                                     const double* r, const double* lambda, double* x, double* u, void* stream) {
   if (!Q || !q || !lambda || !x) return BT_ERR_ARG;
+  if (any_long(B, N) && (!A || !Bm || !R || !r || !u)) return BT_ERR_ARG;
   bt::LqrParams P{};
   P.A = A; P.Bm = Bm; P.Q = Q; P.R = R; P.q = q; P.r = r; P.lam = lambda;
   P.x = x; P.u = u;

@@ -31,16 +31,18 @@ __device__ void factor_row64(const SetupParams& P, long long gr, char* wsm) {
   const int n = d.n, i = rr.row, nn = n * n;
   double* A = reinterpret_cast<double*>(wsm);  // 16 maxn^2 + 512 bytes per warp
   double* T = A + nn;
-  const double* Du = P.D + P.d_off[rr.inst] + (long long)i * nn;
+  // the caller's D (row-major), or with P.copied the library's float64 copy
+  // (column-major: the same array for a symmetric D)
+  const double* Du = P.copied ? P.D64 + d.off64 + (long long)i * d.bs64 : P.D + P.d_off[rr.inst] + (long long)i * nn;
   const bool hasO = i < d.N - 1;
   for (int t = lane; t < nn; t += 32) A[t] = Du[t];
-  if (hasO) {
+  if (hasO && !P.copied) {
     const double* Ou = P.O + P.o_off[rr.inst] + (long long)i * nn;
     for (int t = lane; t < nn; t += 32) T[t] = Ou[t];
   }
   __syncwarp();
   const float inv_n = 1.0f / (float)n;
-  {
+  if (!P.copied) {
     double* D64 = P.D64 + d.off64 + (long long)i * d.bs64;
     double* O64 = P.O64 + d.off64 + (long long)i * d.bs64;
     float* D32 = P.want32 ? P.D32 + d.off32 + (long long)i * d.bs32 : nullptr;
@@ -282,10 +284,12 @@ __global__ void k_factor32(const __grid_constant__ SetupParams P, int wpc, int w
       __syncwarp();
     }
   };
-  if (i < d.N - 1)
-    copy_block(P.O + P.o_off[rr.inst] + (long long)i * nn, P.O64 + d.off64 + (long long)i * d.bs64,
-               P.O32 + d.off32 + (long long)i * d.bs32);
-  copy_block(P.D + P.d_off[rr.inst] + (long long)i * nn, P.D64 + d.off64 + (long long)i * d.bs64, D32);
+  if (!P.copied) {
+    if (i < d.N - 1)
+      copy_block(P.O + P.o_off[rr.inst] + (long long)i * nn, P.O64 + d.off64 + (long long)i * d.bs64,
+                 P.O32 + d.off32 + (long long)i * d.bs32);
+    copy_block(P.D + P.d_off[rr.inst] + (long long)i * nn, P.D64 + d.off64 + (long long)i * d.bs64, D32);
+  }
   float* out = P.Dinv32 + d.off32 + (long long)i * d.bs32;
   {
     int done = -1;  // -1: no register variant for this n

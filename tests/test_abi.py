@@ -82,3 +82,9 @@ def test_bad_arguments_rejected_without_a_gpu(built):
     assert lib.bt_lqr_schur(1, one, big, one, *args, None, None, None) == bb.BT_ERR_ARG
     assert lib.bt_lqr_schur(0, one, one, one, *args, None, None, None) == bb.BT_ERR_ARG
     assert lib.bt_lqr_recover(1, one, one, big, *((vp,) * 9), None) == bb.BT_ERR_ARG
+    assert lib.bt_lqr_refactor(None, one, *((vp,) * 8), None, None) == bb.BT_ERR_ARG
+    # knots beyond the first need the dynamics, inputs and input costs
+    two = (ctypes.c_int * 1)(2)
+    assert lib.bt_lqr_schur(1, two, one, one, None, None, vp, None, vp, None, vp, vp, vp, vp, None, None,
+                            None) == bb.BT_ERR_ARG
+    assert lib.bt_lqr_recover(1, two, one, one, None, None, vp, None, vp, None, vp, vp, vp, None) == bb.BT_ERR_ARG

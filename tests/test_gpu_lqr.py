@@ -163,3 +163,97 @@ def test_single_knot_problems_without_dynamics():
     for k, p in enumerate(probs):
         Dr, Or, gr = orc.lqr_schur(p.A, p.Bm, p.Q, p.R, p.q, p.r, p.c)
         assert maxrel(Ds[k], Dr) <= 1e-12 and maxrel(gs[k], gr) <= 1e-12
+
+
+def _offsets(probs):
+    cum = lambda xs: np.concatenate([[0], np.cumsum(xs)[:-1]]).astype(np.int64)
+    return (cum([p.N * p.n * p.n for p in probs]), cum([(p.N - 1) * p.n * p.n for p in probs]),
+            cum([p.N * p.n for p in probs]))
+
+
+FUSED = [(1, 5, 2), (12, 6, 2), (17, 12, 4), (33, 24, 8), (40, 36, 12), (3, 48, 48), (20, 36, 12), (9, 7, 3)]
+
+
+def test_lqr_refactor_matches_the_oracle():
+    """bt_lqr_refactor (formation straight into a mixed handle, D_k factored on
+    chip, then E and H) against the oracle: gamma as bt_lqr_schur gives it; the
+    handle's float64 S (through bt_spmv) to 1e-12; the preconditioner built from
+    its float32 blocks (bt_apply_precond) within the float32 bound of the
+    parity tests; and the solve of S lam = gamma against the oracle's direct
+    solve at the mixed path's 1e-8."""
+    probs = [wl.small_lqr(90 + k, N, n, m) for k, (N, n, m) in enumerate(FUSED)]
+    A, Bm, Q, R, q, r, c = _pack(probs)
+    Ns, ns, ms = [p.N for p in probs], [p.n for p in probs], [p.m for p in probs]
+    dA, dB, dQ, dR, dq, dr, dc = (dev(v) for v in (A, Bm, Q, R, q, r, c))
+    dD = dev(np.zeros(sum(p.N * p.n * p.n for p in probs)))
+    dO = dev(np.zeros(sum((p.N - 1) * p.n * p.n for p in probs)))
+    dg = dev(np.zeros(sum(p.N * p.n for p in probs)))
+    st, _, _ = bb.bt_lqr_schur(Ns, ns, ms, dA, dB, dQ, dR, dq, dr, dc, dD, dO, dg)
+    assert st == bb.BT_OK
+    d_off, o_off, v_off = _offsets(probs)
+    par, keep = bb.make_params(m=2, alpha=[1.0, 7.0], precision=bb.BT_MIXED)
+    # a handle set up from unrelated blocks: everything it solves with must
+    # come from the fused call
+    dz = dev(np.concatenate([np.tile(np.eye(p.n).reshape(-1), p.N) for p in probs]))
+    st, h = bb.bt_setup_batched(np.array(Ns, np.int32), np.array(ns, np.int32), d_off, o_off, dz,
+                                dev(np.zeros(max(1, dO.numel()))), par)
+    assert st == bb.BT_OK
+    try:
+        dg2 = dev(np.zeros(dg.numel()))
+        st, bi, br = bb.bt_lqr_refactor(h, ms, dA, dB, dQ, dR, dq, dr, dc, dg2)
+        assert st == bb.BT_OK, bb.status_string(st)
+        assert np.array_equal(host(dg2), host(dg))
+        rng = np.random.default_rng(11)
+        xv = rng.standard_normal(dg.numel())
+        y64 = dev(np.zeros(xv.size))
+        assert bb.bt_spmv(h, dev(xv), y64) == bb.BT_OK
+        z = dev(np.zeros(xv.size))
+        assert bb.bt_apply_precond(h, dev(xv), z) == bb.BT_OK
+        dl = dev(np.zeros(dg.numel()))
+        st, its, sts = bb.bt_pcg_solve_batched(h, dg2, dl, len(probs), 1e-12, 5000)
+        assert st == bb.BT_OK and (sts == 0).all()
+    finally:
+        bb.bt_destroy(h)
+    # the two-step path (bt_lqr_schur's D, O through bt_setup_batched) leaves the
+    # same handle: the same solve, bit for bit
+    st, h2 = bb.bt_setup_batched(np.array(Ns, np.int32), np.array(ns, np.int32), d_off, o_off, dD, dO, par)
+    assert st == bb.BT_OK
+    try:
+        dl2 = dev(np.zeros(dg.numel()))
+        st, its2, sts2 = bb.bt_pcg_solve_batched(h2, dg, dl2, len(probs), 1e-12, 5000)
+        assert st == bb.BT_OK and (sts2 == 0).all()
+    finally:
+        bb.bt_destroy(h2)
+    assert (its2 == its).all() and np.array_equal(host(dl2), host(dl))
+    ys, zs, ls, xs, gs = (_split(host(t) if not isinstance(t, np.ndarray) else t, [p.N * p.n for p in probs],
+                                 [(p.N, p.n) for p in probs]) for t in (y64, z, dl, xv, dg2))
+    for k, p in enumerate(probs):
+        Dr, Or, gr = orc.lqr_schur(p.A, p.Bm, p.Q, p.R, p.q, p.r, p.c)
+        assert maxrel(gs[k], gr) <= 1e-12, k
+        assert maxrel(ys[k], orc.spmv(Dr, Or, xs[k])) <= 1e-12, k
+        assert maxrel(zs[k], orc.apply_opt(orc.opt_blocks(Dr, Or), xs[k], [1.0, 7.0])) <= 2e-4, k
+        assert rel(ls[k], orc.direct_solve(Dr, Or, gr)) <= 1e-8, k
+
+
+def test_lqr_refactor_rejects_other_handles_and_reports_non_spd():
+    probs = [wl.small_lqr(95, 6, 4, 2), wl.small_lqr(96, 9, 4, 2)]
+    A, Bm, Q, R, q, r, c = _pack(probs)
+    Ns, ns, ms = [p.N for p in probs], [p.n for p in probs], [p.m for p in probs]
+    d_off, o_off, _ = _offsets(probs)
+    dz = dev(np.concatenate([np.tile(np.eye(p.n).reshape(-1), p.N) for p in probs]))
+    dO = dev(np.zeros(sum((p.N - 1) * p.n * p.n for p in probs)))
+    dg = dev(np.zeros(sum(p.N * p.n for p in probs)))
+    for prec in (bb.BT_FP64, bb.BT_MIXED):
+        par, keep = bb.make_params(m=2, alpha=[1.0, 7.0], precision=prec)
+        st, h = bb.bt_setup_batched(np.array(Ns, np.int32), np.array(ns, np.int32), d_off, o_off, dz, dO, par)
+        assert st == bb.BT_OK
+        try:
+            Qbad = Q.copy()
+            Qbad[(6 * 16) + 5 * 16:(6 * 16) + 6 * 16] = -np.eye(4).reshape(-1)  # Q_5 of problem 1
+            st, bi, br = bb.bt_lqr_refactor(h, ms, dev(A), dev(Bm), dev(Qbad), dev(R), dev(q), dev(r), dev(c), dg)
+            if prec == bb.BT_FP64:
+                assert st == bb.BT_ERR_STATE
+            else:
+                assert st == bb.BT_ERR_NOT_SPD and (bi, br) == (1, 5)
+        finally:
+            bb.bt_destroy(h)
