@@ -1022,8 +1022,10 @@ def lqr_pipeline(a, bb, wl, torch, dev):
     shapes of the bench batch (N ~ U{32..512}, n in {12, 24, 36}, m = n/3;
     dense SPD Q, R), each stage timed with CUDA events, two ways:
       fused:    bt_lqr_refactor (the Schur complement formed straight into the
-                mixed handle, D_k factored on chip, then E and H), batched PCG
-                to 1e-8 (a = 1, m = 2, alpha = (1, 7)), recovery (bt_lqr_recover);
+                mixed handle, D_k factored from there, then E and H), batched
+                PCG to 1e-8 (a = 1, m = 2, alpha = (1, 7)), recovery from the
+                factors of Q_k and R_k the formation kept
+                (bt_lqr_recover_factored);
       two-step: bt_lqr_schur (D, O in the caller's layout), bt_refactor, the
                 same solve and recovery.
     value is the fused pipeline.  The formation runs in double-float pairs on
@@ -1078,7 +1080,7 @@ def lqr_pipeline(a, bb, wl, torch, dev):
         ev[1].record()
         assert bb.bt_pcg_solve_batched_async(h, dg, dl, TOL, 5000) == bb.BT_OK
         ev[2].record()
-        assert bb.bt_lqr_recover(Ns, ns, ms, dA, dB, dQ, dR, dq, dr, dl, dx, du) == bb.BT_OK
+        assert bb.bt_lqr_recover_factored(h, ms, dA, dB, dq, dr, dl, dx, du) == bb.BT_OK
         ev[3].record()
         torch.cuda.synchronize()
         if timed:
@@ -1117,7 +1119,7 @@ def lqr_pipeline(a, bb, wl, torch, dev):
     emit({"metric": "LQR problems per second end to end on the device (formation fused with the refactor, "
                     "PCG to 1e-8, recovery)",
           "value": len(probs) / (tot / 1e3), "unit": "problems/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
-          "ms_per_step": tot, "higher_is_better": True, "dtype": "f32-pair formation + f32/f64 solve + f64 recovery",
+          "ms_per_step": tot, "higher_is_better": True, "dtype": "f32-pair formation and recovery + f32/f64 solve",
           "data": "synthetic (seeded LQR, dense SPD Q and R)",
           "config": {"workload": f"{len(probs)} LQR problems, N~U{{32..512}}, n in {{12,24,36}}, m=n/3"},
           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s (float64-equivalent)",

@@ -421,6 +421,19 @@ bt_status bt_lqr_refactor(bt_handle h, const int* m, const double* A, const doub
                           const double* R, const double* q, const double* r, const double* c, double* gamma,
                           int* bad_inst, int* bad_row);
 
+/* bt_lqr_recover_factored -- bt_lqr_recover for the problems of the last
+ * successful bt_lqr_refactor on h, from the factors that call formed and h
+ * keeps (W = L^-1 of every Q_k and R_k, in double-float pairs): per knot
+ *     x_k = -W^T W (q_k + lam_k - A_k^T lam_{k+1}),
+ *     u_k = -W_R^T W_R (r_k - B_k^T lam_{k+1}),
+ * two triangular products each instead of a Cholesky factorization.  Q and
+ * R must be those of that call (they are not read again); m (HOST) must
+ * equal its m, else BT_ERR_STATE (also before any bt_lqr_refactor).  A, Bm,
+ * q, r, lambda (DEVICE) and the outputs x, u (DEVICE) as for
+ * bt_lqr_recover.  Synchronises h's stream. */
+bt_status bt_lqr_recover_factored(bt_handle h, const int* m, const double* A, const double* Bm, const double* q,
+                                  const double* r, const double* lambda, double* x, double* u);
+
 /* bt_lqr_recover -- the primal solution of the QP above from the solution
  * lam of S lam = gamma: z = -G^-1 (g + C^T lam), i.e.
  *     x_k = -Q_k^-1 (q_k + lam_k - A_k^T lam_{k+1})  (no A term at k = N-1),

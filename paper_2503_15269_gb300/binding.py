@@ -94,6 +94,7 @@ def lib() -> C.CDLL:
         "bt_lqr_schur": (C.c_int, [C.c_int, ip, ip, ip, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, vp, ip, ip]),
         "bt_lqr_recover": (C.c_int, [C.c_int, ip, ip, ip, dp, dp, dp, dp, dp, dp, dp, dp, dp, vp]),
         "bt_lqr_refactor": (C.c_int, [H, ip, dp, dp, dp, dp, dp, dp, dp, dp, ip, ip]),
+        "bt_lqr_recover_factored": (C.c_int, [H, ip, dp, dp, dp, dp, dp, dp, dp]),
         "bt_device_bytes": (C.c_longlong, [H]),
         "bt_destroy": (None, [H]),
         "bt_status_string": (C.c_char_p, [C.c_int]),
@@ -334,6 +335,12 @@ def bt_lqr_refactor(h, m, A, Bm, Q, R, q, r, c, gamma):
     st = lib().bt_lqr_refactor(h, mP, _optr(A), _optr(Bm), _ptr(Q), _optr(R), _ptr(q), _optr(r), _ptr(c),
                                _ptr(gamma), C.byref(bi), C.byref(br))
     return st, bi.value, br.value
+
+
+def bt_lqr_recover_factored(h, m, A, Bm, q, r, lam, x, u) -> int:
+    ma, mP = _iarr(m)
+    return lib().bt_lqr_recover_factored(h, mP, _optr(A), _optr(Bm), _ptr(q), _optr(r), _ptr(lam), _ptr(x),
+                                         _optr(u))
 
 
 def bt_lqr_recover(N, n, m, A, Bm, Q, R, q, r, lam, x, u, stream=None) -> int:

@@ -24,7 +24,12 @@ extern "C" bt_status bt_lqr_schur_handle(int B, const int* N, const int* n, cons
                                          const double* Bm, const double* Q, const double* R, const double* q,
                                          const double* r, const double* c, double* gamma, const bt::InstDesc* hinst,
                                          double* hD64, double* hO64, float* hD32, float* hO32, float* hDinv32,
-                                         void* stream, int* bad_inst, int* bad_row);
+                                         void* stream, int* bad_inst, int* bad_row, void* buf, size_t buf_bytes,
+                                         size_t* need);
+extern "C" size_t bt_lqr_handle_bytes(int B, const int* N, const int* n, const int* m);
+extern "C" bt_status bt_lqr_recover_w_run(int B, const int* N, const int* n, const int* m, const double* A,
+                                          const double* Bm, const double* q, const double* r, const double* lambda,
+                                          double* x, double* u, const void* buf, void* stream);
 extern "C" cudaError_t bt_launch_adjoint(const bt::AdjParams* P, cudaStream_t st);
 namespace bt { struct MParams; }
 extern "C" int bt_mrhs_smem_bytes(int n, int tc);
@@ -111,6 +116,10 @@ struct bt_ctx {
   void* mr_vec[16] = {};
   int mr_G = 0, mr_smem = 0, mr_outer = 0;
   float* mr_img[9] = {};  // block images of the tensor-core many-RHS engine
+  void* lqr_buf = nullptr;  // bt_lqr_refactor's scratch (kept after its first call): the W factors
+  size_t lqr_bytes = 0;
+  bool lqr_valid = false;   // the W factors belong to the last bt_lqr_refactor
+  std::vector<int> lqr_m;   // its input sizes
   std::vector<double> mr_resid;
 };
 
@@ -177,6 +186,9 @@ void free_all(bt_ctx* h) {
   h->graph_src = nullptr;
   for (void* p : h->allocs) cudaFree(p);
   h->allocs.clear();
+  if (h->lqr_buf) cudaFree(h->lqr_buf);
+  h->lqr_buf = nullptr;
+  h->lqr_bytes = 0;
 }
 
 bt_status check_params(const bt_params* p, double* alpha_out) {
@@ -935,8 +947,30 @@ bt_status bt_lqr_refactor(bt_handle h, const int* m, const double* A, const doub
   if (h->maxn > 48) return BT_ERR_ARG;
   cudaStream_t st = h->stream;
   if (cudaMemsetAsync(h->d_fail_key, 0xff, sizeof(unsigned long long), st)) return BT_ERR_CUDA;
+  // the formation's scratch (W = L^-1 of every Q_k and R_k) is kept by the
+  // handle: no allocation per call, and bt_lqr_recover_factored reads it
+  const size_t need = bt_lqr_handle_bytes(h->B, h->N.data(), h->n.data(), m);
+  if (need == 0) return BT_ERR_ARG;
+  h->lqr_valid = false;
+  if (need > h->lqr_bytes) {
+    if (h->lqr_buf) {
+      cudaStreamSynchronize(st);
+      cudaFree(h->lqr_buf);
+      h->bytes -= h->lqr_bytes;
+    }
+    h->lqr_buf = nullptr;
+    h->lqr_bytes = 0;
+    if (cudaMalloc(&h->lqr_buf, need) != cudaSuccess) {
+      h->lqr_buf = nullptr;
+      cudaGetLastError();
+      return BT_ERR_ALLOC;
+    }
+    h->lqr_bytes = need;
+    h->bytes += need;
+  }
   const bt_status s = bt_lqr_schur_handle(h->B, h->N.data(), h->n.data(), m, A, Bm, Q, R, q, r, c, gamma, h->d_inst,
-                                          h->D64, h->O64, h->D32, h->O32, h->Dinv32, st, bad_inst, bad_row);
+                                          h->D64, h->O64, h->D32, h->O32, h->Dinv32, st, bad_inst, bad_row,
+                                          h->lqr_buf, h->lqr_bytes, nullptr);
   if (s != BT_OK) return s;
   // D_k^-1 from the float32 copy the formation left in the handle (float64
   // refactor of refused rows, as in bt_refactor), then E and the H blocks
@@ -958,7 +992,20 @@ bt_status bt_lqr_refactor(bt_handle h, const int* m, const double* A, const doub
   sp.nsegs = h->nsegs;
   sp.copied = 1;
   if (bt_status e = cuda_st(bt_launch_setup(&sp, 1, h->prm.m, h->maxn, st)); e != BT_OK) return e;
-  return read_setup_status(h);
+  const bt_status e = read_setup_status(h);
+  if (e == BT_OK) {
+    h->lqr_valid = true;
+    h->lqr_m.assign(m, m + h->B);
+  }
+  return e;
+}
+
+bt_status bt_lqr_recover_factored(bt_handle h, const int* m, const double* A, const double* Bm, const double* q,
+                                  const double* r, const double* lambda, double* x, double* u) {
+  Range nvtx_range("bt_lqr_recover_factored");
+  if (!h || !m) return BT_ERR_ARG;
+  if (!h->lqr_valid || !std::equal(h->lqr_m.begin(), h->lqr_m.end(), m)) return BT_ERR_STATE;
+  return bt_lqr_recover_w_run(h->B, h->N.data(), h->n.data(), m, A, Bm, q, r, lambda, x, u, h->lqr_buf, h->stream);
 }
 
 bt_status bt_setup_status(bt_handle h) {

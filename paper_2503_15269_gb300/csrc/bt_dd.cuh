@@ -115,13 +115,48 @@ __device__ __forceinline__ dd dd_rcp(dd a) {
   return fast_two_sum(x, __fmul_rn(x, e));
 }
 
-// float64 <-> pair.  The split is exact up to the 2^-48 rounding of the low
-// part; the merge rounds hi + lo once to float64.
-__device__ __forceinline__ dd dd_from(double x) {
-  const float h = __double2float_rn(x);
-  return dd_make(h, __double2float_rn(x - (double)h));
+// float64 <-> float32 conversions on the integer pipes.  A conversion
+// instruction runs on the float64 pipe (1/64 of the float32 rate here), and
+// the formation converts every input and output element, so these rebuild
+// the IEEE 754 encodings from the bits instead; values outside the normal
+// range of the narrower format take the hardware conversion.
+//
+// float -> double is exact: the sign, the exponent rebiased by 1023 - 127
+// and the 23 fraction bits shifted up by 29.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)f;  // zeros, subnormals, infinities, NaN
+  const unsigned long long b = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)(e + 896u) << 52) |
+                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)b);
 }
 
-__device__ __forceinline__ double dd_to(dd x) { return (double)x.h + (double)x.l; }
+// double -> float, round to nearest even: for a normal float result (biased
+// float64 exponent 897 .. 1150) the sign, the rebiased exponent and the top
+// 23 of the 52 fraction bits, plus one unit in the last place when the 29
+// dropped bits are above half, or exactly half with an odd kept part (a
+// carry out of the fraction moves into the exponent, reaching infinity from
+// the largest binade as IEEE rounding does).
+__device__ __forceinline__ float d2f_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  if (e - 897u > 253u) return __double2float_rn(x);
+  unsigned f = (hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1fffffffu;
+  f += (rem > 0x10000000u || (rem == 0x10000000u && (f & 1u))) ? 1u : 0u;
+  return __uint_as_float(f);
+}
+
+// float64 <-> pair: hi = fl32(x), lo = fl32(x - hi) (x - hi is exact in
+// float64), so hi + lo is within 2^-48 of x; the merge rounds hi + lo once to
+// float64.  One float64 operation each.
+__device__ __forceinline__ dd dd_from(double x) {
+  const float h = d2f_rn(x);
+  return dd_make(h, d2f_rn(x - f2d_exact(h)));
+}
+
+__device__ __forceinline__ double dd_to(dd x) { return f2d_exact(x.h) + f2d_exact(x.l); }
 
 }  // namespace bt

@@ -40,6 +40,7 @@ struct LqrDesc {
   int N, n, m, pad;
   long long oA, oB, oQ, oR, ov, ou;  // element offsets: A/O, Bm, Q/D, R, n-vectors, m-vectors
   long long ot;                      // first task of k_lqr_winv (sum over earlier problems of 2 N - 1)
+  long long okn;                     // first knot (sum over earlier problems of N)
 };
 struct LqrSeg {
   int inst, a, b, pad;
@@ -234,25 +235,48 @@ __global__ void __launch_bounds__(kWinvWarps * 32) k_lqr_winv(const __grid_const
 // CTA-wide helpers of k_lqr_schur: every thread calls them; each ends with a
 // barrier.  Matrices are row-major pairs in shared memory.
 
-// Y = W X for W lower triangular (rows x rows) and X (rows x cols).
-__device__ void dd_trmm(dd* Y, const dd* W, const dd* X, int rows, int cols) {
-  for (int t = threadIdx.x; t < rows * cols; t += blockDim.x) {
-    const int i = t / cols, j = t - i * cols;
-    DDAcc a;
-    a.init0();
-    for (int p = 0; p <= i; ++p) a.fma(W[i * rows + p], X[p * cols + j]);
-    Y[t] = a.value();
+// (X^T Z)(i, j) = sum_p X[p][i] Z[p][j] over the rows p of X and Z (both
+// rows x cols); tri: X is lower triangular, so p starts at i.  Two
+// interleaved sums (the two_sum chain of one sum is serial).
+__device__ __forceinline__ dd dd_tdot(const dd* X, const dd* Z, int rows, int cols, int i, int j, bool tri) {
+  DDAcc a0, a1;
+  a0.init0();
+  a1.init0();
+  int p = tri ? i : 0;
+  const dd* x = X + (long long)p * cols + i;
+  const dd* z = Z + (long long)p * cols + j;
+  for (; p + 1 < rows; p += 2, x += 2 * cols, z += 2 * cols) {
+    a0.fma(x[0], z[0]);
+    a1.fma(x[cols], z[cols]);
   }
-  __syncthreads();
+  if (p < rows) a0.fma(x[0], z[0]);
+  return dd_add(a0.value(), a1.value());
 }
 
-// (X^T Z)(i, j) = sum_p X[p][i] Z[p][j] over the rows p of X and Z (both
-// rows x cols); tri: X is lower triangular, so p starts at i.
-__device__ __forceinline__ dd dd_tdot(const dd* X, const dd* Z, int rows, int cols, int i, int j, bool tri) {
-  DDAcc a;
-  a.init0();
-  for (int p = tri ? i : 0; p < rows; ++p) a.fma(X[p * cols + i], Z[p * cols + j]);
-  return a.value();
+// (W X)(i, j) = sum_{p <= i} W[i][p] X[p][j] for W lower triangular (ld w)
+// and X with cols columns, two interleaved sums.
+__device__ __forceinline__ dd dd_lmul(const dd* W, int w, const dd* X, int cols, int i, int j) {
+  DDAcc a0, a1;
+  a0.init0();
+  a1.init0();
+  const dd* wr = W + (long long)i * w;
+  const dd* x = X + j;
+  int p = 0;
+  for (; p + 1 <= i; p += 2, x += 2 * cols) {
+    a0.fma(wr[p], x[0]);
+    a1.fma(wr[p + 1], x[cols]);
+  }
+  if (p <= i) a0.fma(wr[p], x[0]);
+  return dd_add(a0.value(), a1.value());
+}
+
+// Element t of the lower triangle in row order: (i, j) with j <= i.
+__device__ __forceinline__ void tri_ij(int t, int& i, int& j) {
+  int r = __float2int_rz((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  if ((r + 1) * (r + 2) / 2 <= t) ++r;  // guard the float estimate
+  if (r * (r + 1) / 2 > t) --r;
+  i = r;
+  j = t - r * (r + 1) / 2;
 }
 
 __device__ void load_dd(dd* dst, const double* src, int cnt) {
@@ -291,6 +315,8 @@ __global__ void __launch_bounds__(kLqrThreads) k_lqr_schur(const __grid_constant
   dd* vg = vs + kLqrMax;                // g_{k-1}
   const bool fused = P.hinst != nullptr;
   const InstDesc hd = fused ? P.hinst[sg.inst] : InstDesc{};
+  const float inv_n = 1.0f / (float)n;
+  const int ntri = n * (n + 1) / 2;
   for (int k = sg.a > 0 ? sg.a - 1 : 0; k < sg.b; ++k) {
     const bool own = k >= sg.a;  // row a-1 of a later segment only rebuilds the carry
     const bool hasA = k < N - 1;
@@ -325,46 +351,47 @@ __global__ void __launch_bounds__(kLqrThreads) k_lqr_schur(const __grid_constant
     }
     if (hasA) {  // Y = W A_k^T, V = W_R B_k^T (one pass over both)
       for (int t = tid; t < nn + mn; t += blockDim.x) {
-        DDAcc a;
-        a.init0();
         if (t < nn) {
-          const int i = t / n, j = t - i * n;
-          for (int p = 0; p <= i; ++p) a.fma(Wq[i * n + p], At[p * n + j]);
-          Y[t] = a.value();
+          const int i = qdiv(t, inv_n), j = t - i * n;
+          Y[t] = dd_lmul(Wq, n, At, n, i, j);
         } else {
-          const int u = t - nn, i = u / n, j = u - i * n;
-          for (int p = 0; p <= i; ++p) a.fma(Wr[i * m + p], Bt[p * n + j]);
-          V[u] = a.value();
+          const int u = t - nn, i = qdiv(u, inv_n), j = u - i * n;
+          V[u] = dd_lmul(Wr, m, Bt, n, i, j);
         }
       }
     }
     __syncthreads();
     if (own) {
-      // O_k = -W^T Y: the handle's column-major slots when a handle is
-      // attached (consecutive threads down a column), else row-major
+      // O_k = -W^T Y, one row of O per run of threads (the same triangular
+      // length across a warp); for a handle it goes through At (free once Y
+      // is formed) so that the column-major slots are written coalesced
       if (hasA) {
         double* Oc = P.O ? P.O + d.oA + (long long)k * nn : nullptr;
-        double* O64 = fused ? P.hO64 + hd.off64 + (long long)k * hd.bs64 : nullptr;
-        float* O32 = fused ? P.hO32 + hd.off32 + (long long)k * hd.bs32 : nullptr;
         for (int t = tid; t < nn; t += blockDim.x) {
-          const int hi_ = t / n, lo_ = t - hi_ * n;
-          const int a = fused ? lo_ : hi_, c = fused ? hi_ : lo_;  // element (a, c)
+          const int a = qdiv(t, inv_n), c = t - a * n;  // element (a, c)
           const dd o = dd_neg(dd_tdot(Wq, Y, n, n, a, c, true));
-          const double ov = dd_to(o);
-          if (Oc) Oc[a * n + c] = ov;
-          if (fused) {  // the float32 copy rounds the float64 value, as bt_refactor's does
-            O64[c * n + a] = ov;
-            O32[c * n + a] = (float)ov;
+          if (Oc) Oc[t] = dd_to(o);
+          if (fused) At[t] = o;
+        }
+        if (fused) {
+          __syncthreads();
+          double* O64 = P.hO64 + hd.off64 + (long long)k * hd.bs64;
+          float* O32 = P.hO32 + hd.off32 + (long long)k * hd.bs32;
+          for (int t = tid; t < nn; t += blockDim.x) {  // t = c n + a
+            const int c = qdiv(t, inv_n), a = t - c * n;
+            const double ov = dd_to(At[a * n + c]);
+            O64[t] = ov;
+            O32[t] = d2f_rn(ov);  // the float32 copy rounds the float64 value, as bt_refactor's does
           }
         }
       }
       // D_k = W^T W + C_{k-1} (lower, in place), gamma_k
-      for (int t = tid; t < nn; t += blockDim.x) {
-        const int i = t / n, j = t - i * n;
-        if (j > i) continue;
+      for (int t = tid; t < ntri; t += blockDim.x) {
+        int i, j;
+        tri_ij(t, i, j);
         dd v = dd_tdot(Wq, Wq, n, n, i, j, true);
-        if (k > 0) v = dd_add(v, C[t]);
-        C[t] = v;
+        if (k > 0) v = dd_add(v, C[i * n + j]);
+        C[i * n + j] = v;
       }
       for (int i = tid; i < n; i += blockDim.x) {
         dd v = dd_add(dd_from(P.c[d.ov + (long long)k * n + i]), vq[i]);
@@ -376,23 +403,23 @@ __global__ void __launch_bounds__(kLqrThreads) k_lqr_schur(const __grid_constant
       double* D64 = fused ? P.hD64 + hd.off64 + (long long)k * hd.bs64 : nullptr;
       float* D32 = fused ? P.hD32 + hd.off32 + (long long)k * hd.bs32 : nullptr;
       for (int t = tid; t < nn; t += blockDim.x) {  // symmetric: both layouts index alike
-        const int i = t / n, j = t - i * n;
+        const int i = qdiv(t, inv_n), j = t - i * n;
         const dd v = C[j > i ? j * n + i : t];
         const double dv = dd_to(v);
         if (Dc) Dc[t] = dv;
         if (fused) {
           D64[t] = dv;
-          D32[t] = (float)dv;
+          D32[t] = d2f_rn(dv);
         }
       }
       __syncthreads();
     }
     if (hasA) {
       // C_k = Y^T Y + V^T V (lower), g_k = Y^T t + V^T s
-      for (int t = tid; t < nn; t += blockDim.x) {
-        const int i = t / n, j = t - i * n;
-        if (j > i) continue;
-        C[t] = dd_add(dd_tdot(Y, Y, n, n, i, j, false), dd_tdot(V, V, m, n, i, j, false));
+      for (int t = tid; t < ntri; t += blockDim.x) {
+        int i, j;
+        tri_ij(t, i, j);
+        C[i * n + j] = dd_add(dd_tdot(Y, Y, n, n, i, j, false), dd_tdot(V, V, m, n, i, j, false));
       }
       for (int i = tid; i < n; i += blockDim.x) {
         DDAcc a;
@@ -466,6 +493,78 @@ __global__ void __launch_bounds__(kLqrThreads) k_lqr_recover(const __grid_consta
   }
 }
 
+
+// Recovery from the factors the formation left (W = L^-1 of Q_k and R_k, in
+// pairs): one warp per knot k,
+//   v = q_k + lam_k - A_k^T lam_{k+1},   x_k = -W^T (W v),
+//   w = r_k - B_k^T lam_{k+1},           u_k = -W_R^T (W_R w),
+// v and w in float64, the two triangular products in pairs with W staged in
+// shared memory (row-major, lower); lane = row of W v and column of W^T t.
+// No factorization, so no pivot to refuse.
+constexpr int kRecWarps = 4;
+
+__device__ void warp_wtw(const dd* Wg, dd* W, dd* v, dd* t, int n, int lane, double* out) {
+  for (int e = lane; e < n * n; e += 32) W[e] = Wg[e];
+  __syncwarp();
+  for (int i = lane; i < n; i += 32) {  // t = W v
+    DDAcc a;
+    a.init0();
+    for (int p = 0; p <= i; ++p) a.fma(W[i * n + p], v[p]);
+    t[i] = a.value();
+  }
+  __syncwarp();
+  for (int i = lane; i < n; i += 32) {  // out = -W^T t
+    DDAcc a;
+    a.init0();
+    for (int p = i; p < n; ++p) a.fma(W[p * n + i], t[p]);
+    out[i] = -dd_to(a.value());
+  }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(kRecWarps * 32) k_lqr_recover_w(const __grid_constant__ LqrParams P, long long nknot,
+                                                                   int B, int maxd) {
+  extern __shared__ __align__(16) double lsm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long task = (long long)blockIdx.x * kRecWarps + warp;
+  if (task >= nknot) return;
+  int lo = 0, hi = B - 1;  // the problem: last k with desc[k].okn <= task
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (P.desc[mid].okn <= task) lo = mid;
+    else hi = mid - 1;
+  }
+  const LqrDesc d = P.desc[lo];
+  const int k = (int)(task - d.okn), n = d.n, m = d.m, N = d.N;
+  dd* W = reinterpret_cast<dd*>(lsm) + (size_t)warp * (maxd * maxd + 2 * maxd);
+  dd* v = W + maxd * maxd;
+  dd* t = v + maxd;
+  const double* lk = P.lam + d.ov + (long long)k * n;
+  const double* lk1 = lk + n;
+  // the right-hand sides in float64 (n^2 multiply-adds per knot, coalesced
+  // down the columns of A_k), split into pairs once
+  for (int i = lane; i < n; i += 32) {  // v = q_k + lam_k - A_k^T lam_{k+1}
+    double a = P.q[d.ov + (long long)k * n + i] + lk[i];
+    if (k < N - 1) {
+      const double* Ak = P.A + d.oA + (long long)k * n * n;
+      for (int p = 0; p < n; ++p) a = fma(-Ak[p * n + i], lk1[p], a);
+    }
+    v[i] = dd_from(a);
+  }
+  __syncwarp();
+  warp_wtw(P.WQ + d.oQ + (long long)k * n * n, W, v, t, n, lane, P.x + d.ov + (long long)k * n);
+  if (k < N - 1) {
+    for (int i = lane; i < m; i += 32) {  // w = r_k - B_k^T lam_{k+1}
+      double a = P.r[d.ou + (long long)k * m + i];
+      const double* Bk = P.Bm + d.oB + (long long)k * n * m;
+      for (int p = 0; p < n; ++p) a = fma(-Bk[p * m + i], lk1[p], a);
+      v[i] = dd_from(a);
+    }
+    __syncwarp();
+    warp_wtw(P.WR + d.oR + (long long)k * m * m, W, v, t, m, lane, P.u + d.ou + (long long)k * m);
+  }
+}
+
 }  // namespace bt
 
 namespace {
@@ -480,12 +579,12 @@ bt_status lqr_plan(int B, const int* N, const int* n, const int* m, std::vector<
                    long long& nR) {
   if (B < 1 || !N || !n || !m) return BT_ERR_ARG;
   desc.resize(B);
-  long long oA = 0, oB = 0, oQ = 0, oR = 0, ov = 0, ou = 0, ot = 0;
+  long long oA = 0, oB = 0, oQ = 0, oR = 0, ov = 0, ou = 0, ot = 0, okn = 0;
   maxn = maxm = 1;
   for (int k = 0; k < B; ++k) {
     if (N[k] < 1 || n[k] < 1 || n[k] > bt::kLqrMax || m[k] < 1 || m[k] > bt::kLqrMax) return BT_ERR_ARG;
     const long long Nk = N[k], nk = n[k], mk = m[k];
-    desc[k] = bt::LqrDesc{N[k], n[k], m[k], 0, oA, oB, oQ, oR, ov, ou, ot};
+    desc[k] = bt::LqrDesc{N[k], n[k], m[k], 0, oA, oB, oQ, oR, ov, ou, ot, okn};
     oA += (Nk - 1) * nk * nk;
     oB += (Nk - 1) * nk * mk;
     oQ += Nk * nk * nk;
@@ -493,6 +592,7 @@ bt_status lqr_plan(int B, const int* N, const int* n, const int* m, std::vector<
     ov += Nk * nk;
     ou += (Nk - 1) * mk;
     ot += 2 * Nk - 1;
+    okn += Nk;
     maxn = std::max(maxn, n[k]);
     maxm = std::max(maxm, m[k]);
     for (int a = 0; a < N[k]; a += bt::kLqrSeg) segs.push_back(bt::LqrSeg{k, a, std::min(N[k], a + bt::kLqrSeg), 0});
@@ -503,8 +603,18 @@ bt_status lqr_plan(int B, const int* N, const int* n, const int* m, std::vector<
   return BT_OK;
 }
 
+// Bytes of the device buffer a formation call uses: descriptors, segments
+// and the failure key, then the W scratch of k_lqr_winv.
+size_t lqr_head_bytes(size_t ndesc, size_t nsegs) {
+  return ((ndesc * sizeof(bt::LqrDesc) + nsegs * sizeof(bt::LqrSeg) + 8 + 255) / 256) * 256;
+}
+
+// pre, pre_bytes: a caller-owned device buffer to use instead of a
+// stream-ordered allocation (the handle-attached formation keeps one); with
+// pre_bytes too small (or pre null) the call allocates, and *need (if
+// non-null) receives the bytes it wanted.
 bt_status lqr_run(bool schur, int B, const int* N, const int* n, const int* m, bt::LqrParams P, void* stream,
-                  int* bad_inst, int* bad_row) {
+                  int* bad_inst, int* bad_row, char* pre = nullptr, size_t pre_bytes = 0, size_t* need = nullptr) {
   std::vector<bt::LqrDesc> desc;
   std::vector<bt::LqrSeg> segs;
   int maxn = 0, maxm = 0;
@@ -513,10 +623,12 @@ bt_status lqr_run(bool schur, int B, const int* N, const int* n, const int* m, b
   if (s != BT_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t bd = desc.size() * sizeof(bt::LqrDesc), bs = segs.size() * sizeof(bt::LqrSeg);
-  const size_t head = ((bd + bs + 8 + 255) / 256) * 256;
+  const size_t head = lqr_head_bytes(desc.size(), segs.size());
   const size_t scratch = schur ? (size_t)(nQ + nR) * sizeof(bt::dd) : 0;
-  char* buf = nullptr;
-  if (cudaMallocAsync((void**)&buf, head + scratch, st) != cudaSuccess) return BT_ERR_ALLOC;
+  if (need) *need = head + scratch;
+  const bool own_buf = !(pre && pre_bytes >= head + scratch);
+  char* buf = own_buf ? nullptr : pre;
+  if (own_buf && cudaMallocAsync((void**)&buf, head + scratch, st) != cudaSuccess) return BT_ERR_ALLOC;
   const auto ok = [](cudaError_t e) { return e == cudaSuccess; };
   bt_status out = BT_OK;
   unsigned long long key = ~0ull;
@@ -549,7 +661,7 @@ bt_status lqr_run(bool schur, int B, const int* N, const int* n, const int* m, b
         !ok(cudaStreamSynchronize(st)))
       out = BT_ERR_CUDA;
   }
-  cudaFreeAsync(buf, st);
+  if (own_buf) cudaFreeAsync(buf, st);
   if (out == BT_OK && key != ~0ull) {
     if (bad_inst) *bad_inst = (int)(key >> 32);
     if (bad_row) *bad_row = (int)((key & 0xffffffffu) >> 1);
@@ -580,13 +692,16 @@ extern "C" bt_status bt_lqr_schur(int B, const int* N, const int* n, const int* 
 }
 
 // The formation into a mixed handle's block arrays (D, O in float64 and
-// float32, D^-1 in float32; column-major slots at the handle's offsets), for
-// bt_lqr_refactor.  Shapes are the handle's; the caller checks them.
+// float32; column-major slots at the handle's offsets), for
+// bt_lqr_refactor, in the caller's device buffer (buf, buf_bytes) when it is
+// large enough; *need receives the bytes a call uses.  Shapes are the
+// handle's; the caller checks them.
 extern "C" bt_status bt_lqr_schur_handle(int B, const int* N, const int* n, const int* m, const double* A,
                                          const double* Bm, const double* Q, const double* R, const double* q,
                                          const double* r, const double* c, double* gamma, const bt::InstDesc* hinst,
                                          double* hD64, double* hO64, float* hD32, float* hO32, float* hDinv32,
-                                         void* stream, int* bad_inst, int* bad_row) {
+                                         void* stream, int* bad_inst, int* bad_row, void* buf, size_t buf_bytes,
+                                         size_t* need) {
   if (!Q || !q || !c || !gamma || !hinst || !hD64 || !hD32 || !hDinv32) return BT_ERR_ARG;
   if (any_long(B, N) && (!A || !Bm || !R || !r || !hO64 || !hO32)) return BT_ERR_ARG;
   bt::LqrParams P{};
@@ -594,7 +709,60 @@ extern "C" bt_status bt_lqr_schur_handle(int B, const int* N, const int* n, cons
   P.gamma = gamma;
   P.hinst = hinst;
   P.hD64 = hD64; P.hO64 = hO64; P.hD32 = hD32; P.hO32 = hO32; P.hDinv32 = hDinv32;
-  return lqr_run(true, B, N, n, m, P, stream, bad_inst, bad_row);
+  return lqr_run(true, B, N, n, m, P, stream, bad_inst, bad_row, static_cast<char*>(buf), buf_bytes, need);
+}
+
+// Bytes of the device buffer bt_lqr_schur_handle uses for these shapes (0 on
+// bad shapes): the handle allocates it once and keeps it, and the factors W
+// it holds serve bt_lqr_recover_factored.
+extern "C" size_t bt_lqr_handle_bytes(int B, const int* N, const int* n, const int* m) {
+  std::vector<bt::LqrDesc> desc;
+  std::vector<bt::LqrSeg> segs;
+  int maxn = 0, maxm = 0;
+  long long ntask = 0, nQ = 0, nR = 0;
+  if (lqr_plan(B, N, n, m, desc, segs, maxn, maxm, ntask, nQ, nR) != BT_OK) return 0;
+  return lqr_head_bytes(desc.size(), segs.size()) + (size_t)(nQ + nR) * sizeof(bt::dd);
+}
+
+// The recovery from the W factors in buf (left there by bt_lqr_schur_handle
+// for the same shapes).  Synchronises.
+extern "C" bt_status bt_lqr_recover_w_run(int B, const int* N, const int* n, const int* m, const double* A,
+                                          const double* Bm, const double* q, const double* r, const double* lambda,
+                                          double* x, double* u, const void* buf, void* stream) {
+  if (!q || !lambda || !x || !buf) return BT_ERR_ARG;
+  if (any_long(B, N) && (!A || !Bm || !r || !u)) return BT_ERR_ARG;
+  std::vector<bt::LqrDesc> desc;
+  std::vector<bt::LqrSeg> segs;
+  int maxn = 0, maxm = 0;
+  long long ntask = 0, nQ = 0, nR = 0;
+  bt_status s = lqr_plan(B, N, n, m, desc, segs, maxn, maxm, ntask, nQ, nR);
+  if (s != BT_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const long long nknot = desc.back().okn + desc.back().N;
+  bt::LqrParams P{};
+  P.A = A; P.Bm = Bm; P.q = q; P.r = r; P.lam = lambda; P.x = x; P.u = u;
+  P.WQ = reinterpret_cast<bt::dd*>(const_cast<char*>(static_cast<const char*>(buf)) +
+                                   lqr_head_bytes(desc.size(), segs.size()));
+  P.WR = P.WQ + nQ;
+  const size_t bd = desc.size() * sizeof(bt::LqrDesc);
+  char* dbuf = nullptr;
+  if (cudaMallocAsync((void**)&dbuf, bd, st) != cudaSuccess) return BT_ERR_ALLOC;
+  P.desc = reinterpret_cast<const bt::LqrDesc*>(dbuf);
+  const int maxd = std::max(maxn, maxm);
+  const int smem = bt::kRecWarps * (maxd * maxd + 2 * maxd) * (int)sizeof(bt::dd);
+  const auto ok = [](cudaError_t e) { return e == cudaSuccess; };
+  bt_status out = BT_OK;
+  if (!ok(cudaMemcpyAsync(dbuf, desc.data(), bd, cudaMemcpyHostToDevice, st)) ||
+      !ok(cudaFuncSetAttribute(bt::k_lqr_recover_w, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+    out = BT_ERR_CUDA;
+  else {
+    bt::k_lqr_recover_w<<<(unsigned)((nknot + bt::kRecWarps - 1) / bt::kRecWarps), bt::kRecWarps * 32, smem, st>>>(
+        P, nknot, B, maxd);
+    if (!ok(cudaGetLastError())) out = BT_ERR_CUDA;
+  }
+  cudaFreeAsync(dbuf, st);
+  if (!ok(cudaStreamSynchronize(st)) && out == BT_OK) out = BT_ERR_CUDA;
+  return out;
 }
 
 extern "C" bt_status bt_lqr_recover(int B, const int* N, const int* n, const int* m, const double* A,

@@ -212,8 +212,25 @@ def test_lqr_refactor_matches_the_oracle():
         dl = dev(np.zeros(dg.numel()))
         st, its, sts = bb.bt_pcg_solve_batched(h, dg2, dl, len(probs), 1e-12, 5000)
         assert st == bb.BT_OK and (sts == 0).all()
+        # primal recovery from the factors the formation kept, against the
+        # oracle and against the factorizing recovery
+        dx = dev(np.zeros(dg.numel()))
+        du = dev(np.zeros(sum((p.N - 1) * p.m for p in probs)))
+        assert bb.bt_lqr_recover_factored(h, [mm + 1 for mm in ms], dA, dB, dq, dr, dl, dx, du) == bb.BT_ERR_STATE
+        assert bb.bt_lqr_recover_factored(h, ms, dA, dB, dq, dr, dl, dx, du) == bb.BT_OK
+        dx2, du2 = dev(np.zeros(dg.numel())), dev(np.zeros(du.numel()))
+        assert bb.bt_lqr_recover(Ns, ns, ms, dA, dB, dQ, dR, dq, dr, dl, dx2, du2) == bb.BT_OK
     finally:
         bb.bt_destroy(h)
+    assert maxrel(host(dx), host(dx2)) <= 1e-12 and maxrel(host(du), host(du2)) <= 1e-12
+    xs = _split(host(dx), [p.N * p.n for p in probs], [(p.N, p.n) for p in probs])
+    us = _split(host(du), [(p.N - 1) * p.m for p in probs], [(p.N - 1, p.m) for p in probs])
+    lams = _split(host(dl), [p.N * p.n for p in probs], [(p.N, p.n) for p in probs])
+    for k, p in enumerate(probs):
+        xr, ur = orc.lqr_recover(p.A, p.Bm, p.Q, p.R, p.q, p.r, lams[k])
+        assert maxrel(xs[k], xr) <= 1e-12, k
+        if p.N > 1:
+            assert maxrel(us[k], ur) <= 1e-12, k
     # the two-step path (bt_lqr_schur's D, O through bt_setup_batched) leaves the
     # same handle: the same solve, bit for bit
     st, h2 = bb.bt_setup_batched(np.array(Ns, np.int32), np.array(ns, np.int32), d_off, o_off, dD, dO, par)
@@ -248,6 +265,10 @@ def test_lqr_refactor_rejects_other_handles_and_reports_non_spd():
         st, h = bb.bt_setup_batched(np.array(Ns, np.int32), np.array(ns, np.int32), d_off, o_off, dz, dO, par)
         assert st == bb.BT_OK
         try:
+            dx = dev(np.zeros(dg.numel()))
+            du = dev(np.zeros(sum((p.N - 1) * p.m for p in probs)))
+            # no formation on this handle yet: no factors to recover from
+            assert bb.bt_lqr_recover_factored(h, ms, dev(A), dev(Bm), dev(q), dev(r), dg, dx, du) == bb.BT_ERR_STATE
             Qbad = Q.copy()
             Qbad[(6 * 16) + 5 * 16:(6 * 16) + 6 * 16] = -np.eye(4).reshape(-1)  # Q_5 of problem 1
             st, bi, br = bb.bt_lqr_refactor(h, ms, dev(A), dev(Bm), dev(Qbad), dev(R), dev(q), dev(r), dev(c), dg)
