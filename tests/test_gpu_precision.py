@@ -67,9 +67,15 @@ def test_strict_split_apply_on_ill_conditioned_blocks(decades):
 
 
 def test_noalloc_strict_split_matches_allocating_path():
+    """The no-allocation entry against the allocating path on the same engine
+    and shape (the persistent kernel on N / 4 CTAs; a single instance would
+    otherwise go to the shared-memory engine, whose float32 sums run in
+    another order)."""
     inst = wl.config1()
     p, keep = bb.make_params(m=2, alpha=[1.0, 7.0], precision=bb.BT_MIXED, mixed_strict_fp64=True)
-    st, h = bb.bt_setup(inst.N, inst.n, dev(inst.D), dev(inst.O), p)
+    pa, keep_a = bb.make_params(m=2, alpha=[1.0, 7.0], precision=bb.BT_MIXED, mixed_strict_fp64=True,
+                                group_ctas=inst.N // 4)
+    st, h = bb.bt_setup(inst.N, inst.n, dev(inst.D), dev(inst.O), pa)
     assert st == bb.BT_OK
     try:
         xa = dev(np.zeros(inst.N * inst.n))
