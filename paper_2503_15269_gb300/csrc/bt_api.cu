@@ -1261,7 +1261,7 @@ bt_status bt_pcg_solve_multi(bt_handle h, const double* B, double* X, int nrhs, 
   if (tc) {
     if (!h->mr_img[8]) {
       for (int i = 0; i < 9; ++i) {
-        bt_status s2 = dalloc(h, &h->mr_img[i], (size_t)N * n * n);
+        bt_status s2 = dalloc(h, &h->mr_img[i], (size_t)N * n * n * 2);  // [hi | lo] TF32 parts
         if (s2 != BT_OK) return s2;
       }
     }

@@ -529,8 +529,8 @@ __device__ __forceinline__ float comp(const float4& v, int i) { return i == 0 ? 
 
 // Shared memory of the tensor-core sweeps (floats, from kTcBase: the column
 // sums' scratch and the SIMT exchange tiles are idle during a sweep):
-//   bimg  [2][3][2][n n]  per column buffer and block: [hi | lo] B images (the
-//                         bulk copy lands in hi, the split writes lo)
+//   bimg  [2][3][2][n n]  per column buffer and block: [hi | lo] B images (one
+//                         bulk copy of the block's [hi | lo] image)
 //   aimg  [2][64 n]       [hi; lo] A image of the column's vector row
 //   ring  [3][n 64]       raw vector rows (columns c .. c + 2)
 //   stage [2][n 64]       the finished row, [n][64]: x_hi and x_lo partial sums
@@ -591,12 +591,13 @@ __device__ void msweep_tc(MSolver& Sv, int phase, const float* v_in, const float
   const auto issue = [&](int c, int buf) {  // kTcIssuer
     unsigned bytes = (unsigned)vb * 4u;
     for (int r = 0; r < 3; ++r)
-      if (role_ok(c, r)) bytes += (unsigned)bb * 4u;
+      if (role_ok(c, r)) bytes += (unsigned)bb * 8u;
     mbar_arrive_expect_tx(full + buf, bytes);
     for (int r = 0; r < 3; ++r) {
       if (!role_ok(c, r)) continue;
-      const float* src = r == 0 ? img0 + (size_t)c * bb : (r == 1 ? img1 + (size_t)c * bb : img2 + (size_t)(c - k) * bb);
-      bulk_g2s(bptr(buf, r), src, (unsigned)bb * 4u, full + buf);
+      const size_t blk = r == 2 ? (size_t)(c - k) : (size_t)c;
+      const float* src = (r == 0 ? img0 : (r == 1 ? img1 : img2)) + blk * 2 * bb;
+      bulk_g2s(bptr(buf, r), src, (unsigned)bb * 8u, full + buf);  // [hi | lo]
     }
     bulk_g2s(slot(c), v_in + (size_t)c * vb, (unsigned)vb * 4u, full + buf);
   };
@@ -628,19 +629,8 @@ __device__ void msweep_tc(MSolver& Sv, int phase, const float* v_in, const float
         bad = true;
         break;
       }
-      // split the blocks (hi in place, lo beside) and the vector row (transposed
-      // into the A image: one right-hand side j and four k per task)
-      for (int r = 0; r < 3; ++r) {
-        if (!role_ok(c, r)) continue;
-        float4* h4 = reinterpret_cast<float4*>(bptr(buf, r));
-        float4* l4 = h4 + bb / 4;
-        for (int q = tid; q < bb / 4; q += kMThreads) {
-          float4 h, l;
-          split4(h4[q], h, l);
-          h4[q] = h;
-          l4[q] = l;
-        }
-      }
+      // split the vector row (transposed into the A image: one right-hand side
+      // j and four k per task); the blocks arrive split ([hi | lo] images)
       const float* xr = slot(c);
       for (int q = tid; q < 16 * n; q += kMThreads) {
         const int j = q & 63, k4 = q >> 6;
@@ -1181,8 +1171,13 @@ __global__ void k_mrhs_image(const float* src, int bs32, float* dst, int N, int 
   const long long i = t / bb;
   const int w = (int)(t - i * bb);
   const int a = w / n, b = w - (w / n) * n;
-  const float v = trans ? src[i * bs32 + (long long)a * n + b] : src[i * bs32 + (long long)b * n + a];
-  dst[i * bb + ((a >> 3) * (n >> 2) + (b >> 2)) * 32 + (a & 7) * 4 + (b & 3)] = sign * v;
+  const float v = sign * (trans ? src[i * bs32 + (long long)a * n + b] : src[i * bs32 + (long long)b * n + a]);
+  // [hi | lo] TF32 parts of block row i, 2 n^2 floats: the B operand of the
+  // sweep's MMAs as it lands in shared memory
+  const float h = tf32_round(v);
+  const long long o = i * 2 * bb + ((a >> 3) * (n >> 2) + (b >> 2)) * 32 + (a & 7) * 4 + (b & 3);
+  dst[o] = h;
+  dst[o + bb] = tf32_round(v - h);
 }
 
 }  // namespace bt
