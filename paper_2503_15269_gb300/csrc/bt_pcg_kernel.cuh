@@ -734,26 +734,40 @@ struct Solver {
     if (fail) return;
     // vector rows written so far are read by bulk copies after this barrier
     fence_proxy_async_global();
-    double* red = reinterpret_cast<double*>(sm + kSmRed);
     double* bc = reinterpret_cast<double*>(sm + kSmBc);
     int* ctl = reinterpret_cast<int*>(sm + kSmCtl);
-    const int lane = tid & 31, w = tid >> 5;
+    // Sum of the 3 x kThreads partials as a fixed tree spread over the
+    // warps: every float64 add holds an SM sub-partition's float64 pipe for
+    // ~64 cycles, so the adds go where the pipes are idle (four partials
+    // per thread on 3 x 64 threads, then one warp per quantity) instead of
+    // a shuffle tree in every warp and a serial sum on one thread.  The
+    // vector staging buffers are free between sweeps.
+    static_assert(kThreads % 64 == 0 && kThreads >= 192, "three quantities of 64 threads");
+    double* tr = reinterpret_cast<double*>(sm + kSmVs);  // [3][kThreads] then [3][64]
+    static_assert((3 * kThreads + 3 * 64) * 8 <= 2 * kVsElems * 8, "reduction scratch fits the staging buffers");
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {  // v[3] is set below (timeout flag)
-      double x = v[i];
-      // a sweep leaves the partials it does not produce at exactly zero: skip
-      // their float64 shuffle sums (the test is an integer one: |bits| != 0)
-      if (__any_sync(0xffffffffu, (__double_as_longlong(x) << 1) != 0)) {
+    for (int i = 0; i < 3; ++i) tr[i * kThreads + tid] = v[i];  // v[3] is set below (timeout flag)
+    __syncthreads();
+    if (tid < 3 * 64) {
+      const int q = tid >> 6, j = tid & 63;
+      const double* a = tr + q * kThreads + j;
+      double s4 = 0.0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      }
-      if (lane == 0) red[w * 4 + i] = x;
+      for (int k = 0; k < kThreads / 64; k += 2) s4 += a[64 * k] + a[64 * (k + 1)];
+      tr[3 * kThreads + q * 64 + j] = s4;
+    }
+    __syncthreads();
+    if (tid < 3 * 32) {
+      const int q = tid >> 5, lane = tid & 31;
+      const double* b = tr + 3 * kThreads + q * 64;
+      double x = b[lane] + b[lane + 32];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) bc[q] = x;
     }
     __syncthreads();
     if (tid == 0) {
-      double t[4] = {0, 0, 0, 0};
-      for (int ww = 0; ww < kThreads / 32; ++ww)
-        for (int i = 0; i < 3; ++i) t[i] += red[ww * 4 + i];
+      double t[4] = {bc[0], bc[1], bc[2], 0.0};
       t[3] = (clock64() > deadline) ? 1.0 : 0.0;
       int bad = 0;
       if (G > 1) {
