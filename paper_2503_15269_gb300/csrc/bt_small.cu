@@ -189,17 +189,22 @@ struct Small {
     }
     if constexpr (CL) {
       cg::this_cluster().sync();
-      if (tid == 0) {
+      if (tid < 32) {  // lane c reads CTA c's totals (one remote load each), then a fixed tree
         double t[K];
 #pragma unroll
         for (int q = 0; q < K; ++q) t[q] = 0.0;
-        for (int c = 0; c < C; ++c) {
-          const double* rc = cg::this_cluster().map_shared_rank(red, c);
+        if (tid < C) {
+          const double* rc = cg::this_cluster().map_shared_rank(red, tid);
 #pragma unroll
-          for (int q = 0; q < K; ++q) t[q] += rc[20 + 2 * rpar + q];
+          for (int q = 0; q < K; ++q) t[q] = rc[20 + 2 * rpar + q];
         }
 #pragma unroll
-        for (int q = 0; q < K; ++q) red[16 + q] = t[q];
+        for (int o = 4; o > 0; o >>= 1)  // C <= 8
+#pragma unroll
+          for (int q = 0; q < K; ++q) t[q] += __shfl_xor_sync(0xffffffffu, t[q], o);
+        if (tid == 0)
+#pragma unroll
+          for (int q = 0; q < K; ++q) red[16 + q] = t[q];
       }
     }
     // a CTA's slot of parity p is rewritten two sums later, after the next
@@ -289,6 +294,31 @@ struct Small {
     double t = 0.0;
     for (int el = tid; el < nel; el += kSmallThreads) t = fma((double)r[el], (double)z[el], t);
     return reduce(t);
+  }
+  // The same, summing another partial (`other`, e.g. r . r) in the same
+  // reduction: one sum per iteration fewer when the convergence test waits
+  // for the preconditioner (the z of the last iteration is then formed and
+  // not used).
+  template <typename T>
+  __device__ double precond2T(const T* const* blk, int sb, const T* r, T* z, T* y0, T* ya, T* yb, double other,
+                              double& other_sum) {
+    sweepT<T>(1, blk, sb, r, P.m == 1 ? z : y0);
+    if (P.m > 1) {
+      const T* yin = y0;
+      for (int j = 1; j < P.m; ++j) {
+        csync();
+        T* yout = (j & 1) ? ya : yb;
+        sweepT<T>(2, blk, sb, yin, yout);
+        yin = yout;
+        const T aj = (T)P.alpha[j];
+        for (int el = tid; el < nel; el += kSmallThreads) z[el] = fma(aj, yout[el], j == 1 ? y0[el] : z[el]);
+      }
+    }
+    double t = 0.0;
+    for (int el = tid; el < nel; el += kSmallThreads) t = fma((double)r[el], (double)z[el], t);
+    double rz;
+    reduce2(t, other, rz, other_sum);
+    return rz;
   }
   __device__ double precond(const double* r, double* z, double* y0, double* ya, double* yb) {
     const double* const blk[7] = {D, O, Dinv, E, Hd, Hu, Hl};
@@ -397,7 +427,9 @@ __global__ void __launch_bounds__(kSmallThreads, 1) bt_small_kernel(const __grid
         r[el] = rv;
         t = fma(rv, rv, t);
       }
-      rr = Sm.reduce(t);  // also makes r final in every CTA
+      Sm.csync();  // r final in every CTA (the G sweep reads neighbouring rows)
+      const double* const blk64[7] = {Sm.D, Sm.O, Sm.Dinv, Sm.E, Sm.Hd, Sm.Hu, Sm.Hl};
+      const double rz = Sm.template precond2T<double>(blk64, P.bs, r, z, y0, ya, yb, t, rr);  // r.z and r.r
       it = k;
       record(k - 1, 0, sqrt(rr) / nrhs);
       if (!isfinite(rr)) {
@@ -405,7 +437,6 @@ __global__ void __launch_bounds__(kSmallThreads, 1) bt_small_kernel(const __grid
         break;
       }
       if (rr <= thr2) break;
-      const double rz = Sm.precond(r, z, y0, ya, yb);
       const double be = rz / rho;
       record(k - 1, 2, be);
       rho = rz;
@@ -584,7 +615,8 @@ __global__ void __launch_bounds__(kSmallThreads, 1) bt_small_mixed_kernel(const 
             r[el] = rv;
             tr = fma((double)rv, (double)rv, tr);
           }
-          rr = Sm.reduce(tr);  // also makes r final in every CTA
+          Sm.csync();  // r final in every CTA (the G sweep reads neighbouring rows)
+          const double rz = Sm.template precond2T<float>(cblk32, P.bs32, r, z, y0, ya, yb, tr, rr);  // r.z and r.r
           it = k;
           record(iters + k - 1, 0, sqrt(rr / rr0));
           if (!isfinite(rr)) {
@@ -592,7 +624,6 @@ __global__ void __launch_bounds__(kSmallThreads, 1) bt_small_mixed_kernel(const 
             break;
           }
           if (rr <= thr2) break;
-          const double rz = Sm.template precondT<float>(cblk32, P.bs32, r, z, y0, ya, yb);
           const double be = P.scal64 ? rz / rho : (double)__fdiv_rn((float)rz, (float)rho);
           record(iters + k - 1, 2, be);
           rho = rz;
