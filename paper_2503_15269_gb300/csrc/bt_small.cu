@@ -163,10 +163,14 @@ struct Small {
   // warps) and then over the cluster in rank order: the same bits in every CTA
   template <int K>
   __device__ void reduceK(double (&v)[K]) {
+    // warps past the CTA's elements hold exact zeros: no float64 adds for
+    // them (each float64 add holds a sub-partition's pipe for ~64 cycles)
+    if ((tid & ~31) < nel) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
+      for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-      for (int q = 0; q < K; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+        for (int q = 0; q < K; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    }
     __syncthreads();  // scratch free (the previous totals were read)
     if ((tid & 31) == 0)
 #pragma unroll
