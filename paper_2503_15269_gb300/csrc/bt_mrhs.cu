@@ -144,7 +144,6 @@ struct MSolver {
   long long deadline;
   int bar_count;
   bool fail;
-  double* colbuf;   // smem [kJ] scratch for reduced values
   double* colred;   // smem scratch for the cross-CTA column sums ([kMThreads / kJ][kJ])
   // tensor-core engine: TMEM base address, and the counts behind the mbarrier
   // phases (identical in every thread): columns whose data was waited for /
@@ -194,8 +193,14 @@ struct MSolver {
       const int g0 = q * G / kQ, g1 = (q + 1) * G / kQ;
       const double* src = P.red + (size_t)par * G * kJ + j;
       double t = 0.0;
-#pragma unroll 8
-      for (int gg = g0; gg < g1; ++gg) t += __ldcg(src + (size_t)gg * kJ);
+      for (int b0 = g0; b0 < g1; b0 += 16) {  // 16 loads in flight, then the adds in slot order
+        double v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) v[u] = (b0 + u < g1) ? __ldcg(src + (size_t)(b0 + u) * kJ) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+          if (b0 + u < g1) t += v[u];
+      }
       part[q * kJ + j] = t;
       __syncthreads();
       if (threadIdx.x < kJ) {
@@ -208,10 +213,29 @@ struct MSolver {
     __syncthreads();
   }
 
+  // Grid barrier alone (no values): the arrival count of grid_reduce.
+  // Bounded.
   __device__ void barrier() {
-    double* cv = colbuf;
-    if (threadIdx.x < kJ) cv[threadIdx.x] = 0.0;
-    grid_reduce(cv);
+    if (fail) return;
+    __syncthreads();
+    int* flag = reinterpret_cast<int*>(sm);
+    ++bar_count;  // the reductions' slot parity counts these barriers too
+    if (threadIdx.x == 0) {
+      __threadfence();  // publishes the CTA's global writes before the arrival
+      atomicAdd(P.bar, 1u);
+      const unsigned target = (unsigned)G * (unsigned)bar_count;
+      int bad = 0;
+      while (ld_acquire_u32(P.bar) < target) {
+        if (ld_volatile_i32(P.abort_flag) || clock64() > deadline) {
+          bad = 1;
+          break;
+        }
+      }
+      if (bad) atomicExch(P.abort_flag, 1);
+      flag[0] = bad;
+    }
+    __syncthreads();
+    if (flag[0]) fail = true;
   }
 };
 
@@ -529,7 +553,7 @@ __device__ __forceinline__ float comp(const float4& v, int i) { return i == 0 ? 
 
 // Shared memory of the tensor-core sweeps (floats, from kTcBase: the column
 // sums' scratch and the SIMT exchange tiles are idle during a sweep):
-//   bimg  [2][3][2][n n]  per column buffer and block: [hi | lo] B images (one
+//   bimg  [2][3][2][n n]  per column buffer, blocks of rows c - k, c, c + k: [hi | lo] B images (one
 //                         bulk copy of the block's [hi | lo] image)
 //   aimg  [2][64 n]       [hi; lo] A image of the column's vector row
 //   ring  [3][n 64]       raw vector rows (columns c .. c + 2)
@@ -580,7 +604,16 @@ __device__ void msweep_tc(MSolver& Sv, int phase, const float* v_in, const float
   float* pbuf = xbuf + vb;
   uint64_t* full = reinterpret_cast<uint64_t*>(Sv.sm + kTcBarOff);
   uint64_t* mbar = full + 2;
-  const auto bptr = [&](int buf, int role) { return bimg + (size_t)(buf * 3 + role) * 2 * bb; };
+  // images in the order role 2, 0, 1 (rows c - k, c, c + k): the blocks of
+  // rows c - k and c are adjacent, one B operand of N = 4n
+  const auto bptr = [&](int buf, int role) { return bimg + (size_t)(buf * 3 + (role + 1) % 3) * 2 * bb; };
+  // TMEM slot of row t: t m mod S with m k = 1 (mod S), so that rows c - k,
+  // c, c + k sit in consecutive slots (mod S)
+  const int mslot = (k == 1) ? 1 : 3;
+  const auto tslot = [&](int t) { return (t * mslot) % S; };
+  // rows c - k and c share one MMA of N = 4n when their slots are adjacent in
+  // TMEM (not wrapped) and a slot is exactly the 2n columns of a row
+  const bool can_merge = slot_cols == 2 * n;
   const auto slot = [&](int r) { return ring + (size_t)(r % 3) * vb; };
   // role 0: row c (block (c, c)); 1: row c + k; 2: row c - k
   const auto target = [&](int c, int role) { return role == 0 ? c : (role == 1 ? c + k : c - k); };
@@ -649,7 +682,7 @@ __device__ void msweep_tc(MSolver& Sv, int phase, const float* v_in, const float
       tc_fence_after();
       const int warp = tid >> 5, lane = tid & 31, q = warp & 3;
       if (warp < 8) {  // lanes 0-63: x_hi terms of column j = lane + 32 q; 64-127: x_lo terms
-        const unsigned base = Sv.tmem + (unsigned)((t % S) * slot_cols) + ((unsigned)(32 * q) << 16);
+        const unsigned base = Sv.tmem + (unsigned)(tslot(t) * slot_cols) + ((unsigned)(32 * q) << 16);
         float* st = stage + (q >> 1) * vb + 32 * (q & 1) + lane;
         for (int ch = warp >> 2; ch < n / 8; ch += 2) {
           float v[8], w[8];
@@ -673,12 +706,25 @@ __device__ void msweep_tc(MSolver& Sv, int phase, const float* v_in, const float
         // descriptors of K step 0; step ks starts 256 ks bytes later (16 ks in
         // the address field)
         const uint64_t da = tc_desc(smem_u32(aimg), 128, sbo);  // [x_hi; x_lo]
+        // rows c - k and c both accumulate (row c - k had its first product
+        // from column c - 2k, row c from column c - k, which exists when row
+        // c - k does)
+        const bool merge = can_merge && role_ok(c, 2) && role_ok(c, 0) && tslot(c - k) != S - 1;
+        if (merge) {
+          const unsigned id2 = tc_idesc(4 * n);
+          const unsigned d = Sv.tmem + (unsigned)(tslot(c - k) * slot_cols);
+          const uint64_t db = tc_desc(smem_u32(bptr(buf, 2)), 128, sbo);  // [Q2_hi | Q2_lo | Q0_hi | Q0_lo]
+          for (int ks = 0; ks < n / 8; ++ks) {
+            const uint64_t o = 16ull * (unsigned)ks;
+            tc_mma(d, da + o, db + o, id2, 1u);
+          }
+        }
         for (int r = 0; r < 3; ++r) {
-          if (!role_ok(c, r)) continue;
+          if (!role_ok(c, r) || (merge && r != 1)) continue;
           const int tr = target(c, r);
           // the first product into a row: role 1, or role 0 when column c - k does not exist
           const bool first = (r == 1) || (r == 0 && c - k < 0);
-          const unsigned d = Sv.tmem + (unsigned)((tr % S) * slot_cols);
+          const unsigned d = Sv.tmem + (unsigned)(tslot(tr) * slot_cols);
           const uint64_t db = tc_desc(smem_u32(bptr(buf, r)), 128, sbo);  // [Q_hi | Q_lo]
           for (int ks = 0; ks < n / 8; ++ks) {
             const uint64_t o = 16ull * (unsigned)ks;
@@ -828,7 +874,6 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
   float* alpf = reinterpret_cast<float*>(col + 12 * kJ);  // float copies of alpha_j, beta_j
   float* betf = alpf + kJ;
   double* scratch = reinterpret_cast<double*>(smem + kMSmScratch);
-  Sv.colbuf = colR;
   Sv.colred = scratch;
   const int n = P.n;
   const int tid = threadIdx.x;

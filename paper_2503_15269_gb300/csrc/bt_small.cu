@@ -160,36 +160,44 @@ struct Small {
   }
 
   // v[0..K) summed over the CTA (shuffle tree in each warp, then over the
-  // warps) and then over the cluster in rank order: the same bits in every CTA
-  template <int K>
-  __device__ void reduceK(double (&v)[K]) {
-    // warps past the CTA's elements hold exact zeros: no float64 adds for
-    // them (each float64 add holds a sub-partition's pipe for ~64 cycles)
+  // warps) and then over the cluster in rank order: the same bits in every CTA.
+  // post(red) runs on thread 0 once the totals are in red[16 .. 16 + K), before
+  // the barrier that publishes them: the step scalars are formed there, by one
+  // thread, and read by the others from red[26 ..) (float64 work repeated by
+  // every warp would queue on the float64 pipes, each float64 instruction
+  // holding a sub-partition's pipe for ~64 cycles).
+  template <int K, class Post>
+  __device__ void reduceK(double (&v)[K], Post post) {
+    // warps past the CTA's elements hold exact zeros: no float64 adds for them
     if ((tid & ~31) < nel) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
         for (int q = 0; q < K; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
     }
-    __syncthreads();  // scratch free (the previous totals were read)
+    __syncthreads();  // scratch free (the previous totals and scalars were read)
     if ((tid & 31) == 0)
 #pragma unroll
       for (int q = 0; q < K; ++q) red[8 * q + (tid >> 5)] = v[q];
     __syncthreads();
     if (tid < 32) {
+      const int aw = (nel + 31) >> 5;  // warps holding elements; the others' sums are zeros
       double w[K];
 #pragma unroll
       for (int q = 0; q < K; ++q) w[q] = tid < kSmallThreads / 32 ? red[8 * q + tid] : 0.0;
 #pragma unroll
       for (int o = kSmallThreads / 64; o > 0; o >>= 1)
+        if (o < aw)  // a level that would only add zeros is skipped (the same bits)
 #pragma unroll
-        for (int q = 0; q < K; ++q) w[q] += __shfl_xor_sync(0xffffffffu, w[q], o);
-      if (tid == 0)
+          for (int q = 0; q < K; ++q) w[q] += __shfl_xor_sync(0xffffffffu, w[q], o);
+      if (tid == 0) {
 #pragma unroll
         for (int q = 0; q < K; ++q) {
           red[16 + q] = w[q];
           red[20 + 2 * rpar + q] = w[q];  // this CTA's totals for the cluster sum
         }
+        if constexpr (!CL) post(red);
+      }
     }
     if constexpr (CL) {
       cg::this_cluster().sync();
@@ -203,12 +211,15 @@ struct Small {
           for (int q = 0; q < K; ++q) t[q] = rc[20 + 2 * rpar + q];
         }
 #pragma unroll
-        for (int o = 4; o > 0; o >>= 1)  // C <= 8
+        for (int o = 4; o > 0; o >>= 1)  // C <= 8; levels over lanes >= C only add zeros
+          if (o < C)
 #pragma unroll
-          for (int q = 0; q < K; ++q) t[q] += __shfl_xor_sync(0xffffffffu, t[q], o);
-        if (tid == 0)
+            for (int q = 0; q < K; ++q) t[q] += __shfl_xor_sync(0xffffffffu, t[q], o);
+        if (tid == 0) {
 #pragma unroll
           for (int q = 0; q < K; ++q) red[16 + q] = t[q];
+          post(red);  // every CTA's thread 0 on the same totals: the same decisions
+        }
       }
     }
     // a CTA's slot of parity p is rewritten two sums later, after the next
@@ -217,6 +228,10 @@ struct Small {
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < K; ++q) v[q] = red[16 + q];
+  }
+  template <int K>
+  __device__ void reduceK(double (&v)[K]) {
+    reduceK<K>(v, [](double*) {});
   }
   __device__ void reduce2(double a, double b, double& ra, double& rb) {
     double v[2] = {a, b};
@@ -302,10 +317,10 @@ struct Small {
   // The same, summing another partial (`other`, e.g. r . r) in the same
   // reduction: one sum per iteration fewer when the convergence test waits
   // for the preconditioner (the z of the last iteration is then formed and
-  // not used).
-  template <typename T>
+  // not used).  post: as in reduceK, on the totals (r . z, other).
+  template <typename T, class Post>
   __device__ double precond2T(const T* const* blk, int sb, const T* r, T* z, T* y0, T* ya, T* yb, double other,
-                              double& other_sum) {
+                              double& other_sum, Post post) {
     sweepT<T>(1, blk, sb, r, P.m == 1 ? z : y0);
     if (P.m > 1) {
       const T* yin = y0;
@@ -320,9 +335,10 @@ struct Small {
     }
     double t = 0.0;
     for (int el = tid; el < nel; el += kSmallThreads) t = fma((double)r[el], (double)z[el], t);
-    double rz;
-    reduce2(t, other, rz, other_sum);
-    return rz;
+    double v[2] = {t, other};
+    reduceK<2>(v, post);
+    other_sum = v[1];
+    return v[0];
   }
   __device__ double precond(const double* r, double* z, double* y0, double* ya, double* yb) {
     const double* const blk[7] = {D, O, Dinv, E, Hd, Hu, Hl};
@@ -396,34 +412,37 @@ __global__ void __launch_bounds__(kSmallThreads, 1) bt_small_kernel(const __grid
       Sm.sweep(0, p, q);
       double t = 0.0;
       for (int el = tid; el < nel; el += kSmallThreads) t = fma(p[el], q[el], t);
-      // the cycle budget: rank 0's clock decides for the cluster, through the sum
-      double pq, late = 0.0;
-      if constexpr (CL) {
-        Sm.reduce2(t, (tid == 0 && Sm.rank == 0 && clock64() > deadline) ? 1.0 : 0.0, pq, late);
-      } else {
-        if (tid == 0) Sm.red[24] = clock64() > deadline ? 1.0 : 0.0;  // read after the sum's barriers
-        pq = Sm.reduce(t);
-        late = Sm.red[24];
+      // thread 0 checks p.q and the cycle budget (rank 0's clock decides for a
+      // cluster, through the sum) and divides alpha = rho / p.q
+      double pq;
+      {
+        constexpr int K = CL ? 2 : 1;
+        double v[K];
+        v[0] = t;
+        if constexpr (CL) v[K - 1] = (tid == 0 && Sm.rank == 0 && clock64() > deadline) ? 1.0 : 0.0;
+        Sm.template reduceK<K>(v, [&](double* rd) {
+          const double pqv = rd[16];
+          bool late;
+          if constexpr (CL) late = rd[16 + K - 1] > 0.0;
+          else late = clock64() > deadline;
+          const int c = late ? kErrTimeout : (!isfinite(pqv) ? kErrNonfinite : (!(pqv > 0.0) ? kErrBreakdown : kOK));
+          rd[26] = c == kOK ? rho / pqv : 0.0;
+          reinterpret_cast<int*>(rd + 28)[0] = c;
+        });
+        pq = v[0];
       }
-      if (late > 0.0) {
-        status = kErrTimeout;
+      const int c_pq = reinterpret_cast<const int*>(Sm.red + 28)[0];
+      if (c_pq != kOK) {
+        status = c_pq;
         it = k - 1;
+        if (c_pq == kErrBreakdown) errv = pq;
         break;
       }
-      if (!isfinite(pq)) {
-        status = kErrNonfinite;
-        it = k - 1;
-        break;
+      const double al = Sm.red[26];
+      if (hist) {
+        record(k - 1, 1, al);
+        record(k - 1, 2, 0.0);
       }
-      if (!(pq > 0.0)) {
-        status = kErrBreakdown;
-        it = k - 1;
-        errv = pq;
-        break;
-      }
-      const double al = rho / pq;
-      record(k - 1, 1, al);
-      record(k - 1, 2, 0.0);
       t = 0.0;
       for (int el = tid; el < nel; el += kSmallThreads) {
         x[el] = fma(al, p[el], x[el]);
@@ -433,16 +452,23 @@ __global__ void __launch_bounds__(kSmallThreads, 1) bt_small_kernel(const __grid
       }
       Sm.csync();  // r final in every CTA (the G sweep reads neighbouring rows)
       const double* const blk64[7] = {Sm.D, Sm.O, Sm.Dinv, Sm.E, Sm.Hd, Sm.Hu, Sm.Hl};
-      const double rz = Sm.template precond2T<double>(blk64, P.bs, r, z, y0, ya, yb, t, rr);  // r.z and r.r
+      // r.z and r.r; thread 0 tests r.r and divides beta = r.z / rho
+      const double rz = Sm.template precond2T<double>(blk64, P.bs, r, z, y0, ya, yb, t, rr, [&](double* rd) {
+        const double rzv = rd[16], rrv = rd[17];
+        const int c = !isfinite(rrv) ? 1 : (rrv <= thr2 ? 2 : 0);
+        rd[27] = c == 0 ? rzv / rho : 0.0;
+        reinterpret_cast<int*>(rd + 28)[1] = c;
+      });
       it = k;
-      record(k - 1, 0, sqrt(rr) / nrhs);
-      if (!isfinite(rr)) {
+      if (hist) record(k - 1, 0, sqrt(rr) / nrhs);
+      const int c_rr = reinterpret_cast<const int*>(Sm.red + 28)[1];
+      if (c_rr == 1) {
         status = kErrNonfinite;
         break;
       }
-      if (rr <= thr2) break;
-      const double be = rz / rho;
-      record(k - 1, 2, be);
+      if (c_rr == 2) break;
+      const double be = Sm.red[27];
+      if (hist) record(k - 1, 2, be);
       rho = rz;
       for (int el = tid; el < nel; el += kSmallThreads) p[el] = fma(be, p[el], z[el]);
     }
@@ -584,34 +610,37 @@ __global__ void __launch_bounds__(kSmallThreads, 1) bt_small_mixed_kernel(const 
           Sm.template sweepT<float>(0, cblk32, P.bs32, p, q);
           double tq = 0.0;
           for (int el = tid; el < nel; el += kSmallThreads) tq = fma((double)p[el], (double)q[el], tq);
-          double pq, late = 0.0;
-          if constexpr (CL) {
-            Sm.reduce2(tq, (tid == 0 && Sm.rank == 0 && clock64() > deadline) ? 1.0 : 0.0, pq, late);
-          } else {
-            if (tid == 0) Sm.red[24] = clock64() > deadline ? 1.0 : 0.0;  // read after the sum's barriers
-            pq = Sm.reduce(tq);
-            late = Sm.red[24];
+          // thread 0: the checks and alpha (as in the float64 kernel)
+          double pq;
+          {
+            constexpr int K = CL ? 2 : 1;
+            double v[K];
+            v[0] = tq;
+            if constexpr (CL) v[K - 1] = (tid == 0 && Sm.rank == 0 && clock64() > deadline) ? 1.0 : 0.0;
+            Sm.template reduceK<K>(v, [&](double* rd) {
+              const double pqv = rd[16];
+              bool late;
+              if constexpr (CL) late = rd[16 + K - 1] > 0.0;
+              else late = clock64() > deadline;
+              const int c = late ? kErrTimeout : (!isfinite(pqv) ? kErrNonfinite : (!(pqv > 0.0) ? kErrBreakdown : kOK));
+              rd[26] = c != kOK ? 0.0 : (P.scal64 ? rho / pqv : (double)__fdiv_rn((float)rho, (float)pqv));
+              reinterpret_cast<int*>(rd + 28)[0] = c;
+            });
+            pq = v[0];
           }
-          if (late > 0.0) {
-            ist = kErrTimeout;
+          const int c_pq = reinterpret_cast<const int*>(Sm.red + 28)[0];
+          if (c_pq != kOK) {
+            ist = c_pq;
             it = k - 1;
+            if (c_pq == kErrBreakdown) errv = pq;
             break;
           }
-          if (!isfinite(pq)) {
-            ist = kErrNonfinite;
-            it = k - 1;
-            break;
-          }
-          if (!(pq > 0.0)) {
-            ist = kErrBreakdown;
-            it = k - 1;
-            errv = pq;
-            break;
-          }
-          const double al = P.scal64 ? rho / pq : (double)__fdiv_rn((float)rho, (float)pq);
+          const double al = Sm.red[26];
           const float alf = (float)al;
-          record(iters + k - 1, 1, al);
-          record(iters + k - 1, 2, 0.0);
+          if (hist) {
+            record(iters + k - 1, 1, al);
+            record(iters + k - 1, 2, 0.0);
+          }
           double tr = 0.0;
           for (int el = tid; el < nel; el += kSmallThreads) {
             xin[el] = fmaf(alf, p[el], xin[el]);
@@ -620,16 +649,23 @@ __global__ void __launch_bounds__(kSmallThreads, 1) bt_small_mixed_kernel(const 
             tr = fma((double)rv, (double)rv, tr);
           }
           Sm.csync();  // r final in every CTA (the G sweep reads neighbouring rows)
-          const double rz = Sm.template precond2T<float>(cblk32, P.bs32, r, z, y0, ya, yb, tr, rr);  // r.z and r.r
+          // r.z and r.r; thread 0 tests r.r and divides beta
+          const double rz = Sm.template precond2T<float>(cblk32, P.bs32, r, z, y0, ya, yb, tr, rr, [&](double* rd) {
+            const double rzv = rd[16], rrv = rd[17];
+            const int c = !isfinite(rrv) ? 1 : (rrv <= thr2 ? 2 : 0);
+            rd[27] = c != 0 ? 0.0 : (P.scal64 ? rzv / rho : (double)__fdiv_rn((float)rzv, (float)rho));
+            reinterpret_cast<int*>(rd + 28)[1] = c;
+          });
           it = k;
-          record(iters + k - 1, 0, sqrt(rr / rr0));
-          if (!isfinite(rr)) {
+          if (hist) record(iters + k - 1, 0, sqrt(rr / rr0));
+          const int c_rr = reinterpret_cast<const int*>(Sm.red + 28)[1];
+          if (c_rr == 1) {
             ist = kErrNonfinite;
             break;
           }
-          if (rr <= thr2) break;
-          const double be = P.scal64 ? rz / rho : (double)__fdiv_rn((float)rz, (float)rho);
-          record(iters + k - 1, 2, be);
+          if (c_rr == 2) break;
+          const double be = Sm.red[27];
+          if (hist) record(iters + k - 1, 2, be);
           rho = rz;
           const float bef = (float)be;
           for (int el = tid; el < nel; el += kSmallThreads) p[el] = fmaf(bef, p[el], z[el]);
