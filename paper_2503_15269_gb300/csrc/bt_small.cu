@@ -29,6 +29,7 @@
 
 #include "../../include/bt.h"
 #include "bt_common.cuh"
+#include "bt_dd.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -159,45 +160,27 @@ struct Small {
     else __syncthreads();
   }
 
-  // v[0..K) summed over the CTA (shuffle tree in each warp, then over the
-  // warps) and then over the cluster in rank order: the same bits in every CTA.
-  // post(red) runs on thread 0 once the totals are in red[16 .. 16 + K), before
-  // the barrier that publishes them: the step scalars are formed there, by one
-  // thread, and read by the others from red[26 ..) (float64 work repeated by
-  // every warp would queue on the float64 pipes, each float64 instruction
-  // holding a sub-partition's pipe for ~64 cycles).
+  // Float64 cost model of this engine: on this part a float64 warp
+  // instruction costs the SM about the same time whatever the number of its
+  // active lanes and whichever warps issue it (measured: the sweeps run no
+  // faster with the elements spread over four warps instead of three), so
+  // the sums and step scalars below are built from the fewest float64
+  // instructions, on as few warps as possible.
+  //
+  // Totals of the CTA (thread 0's w[q]) -> over the cluster in rank order
+  // (the same bits in every CTA) -> post(red) on thread 0 once the totals are
+  // in red[16 .. 16 + K), before the barrier that publishes them: the step
+  // scalars are formed there, by one thread, and read by the others from
+  // red[26 ..).
   template <int K, class Post>
-  __device__ void reduceK(double (&v)[K], Post post) {
-    // warps past the CTA's elements hold exact zeros: no float64 adds for them
-    if ((tid & ~31) < nel) {
+  __device__ void finishK(const double (&w)[K], double (&v)[K], Post post) {
+    if (tid == 0) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int q = 0; q < K; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
-    }
-    __syncthreads();  // scratch free (the previous totals and scalars were read)
-    if ((tid & 31) == 0)
-#pragma unroll
-      for (int q = 0; q < K; ++q) red[8 * q + (tid >> 5)] = v[q];
-    __syncthreads();
-    if (tid < 32) {
-      const int aw = (nel + 31) >> 5;  // warps holding elements; the others' sums are zeros
-      double w[K];
-#pragma unroll
-      for (int q = 0; q < K; ++q) w[q] = tid < kSmallThreads / 32 ? red[8 * q + tid] : 0.0;
-#pragma unroll
-      for (int o = kSmallThreads / 64; o > 0; o >>= 1)
-        if (o < aw)  // a level that would only add zeros is skipped (the same bits)
-#pragma unroll
-          for (int q = 0; q < K; ++q) w[q] += __shfl_xor_sync(0xffffffffu, w[q], o);
-      if (tid == 0) {
-#pragma unroll
-        for (int q = 0; q < K; ++q) {
-          red[16 + q] = w[q];
-          red[20 + 2 * rpar + q] = w[q];  // this CTA's totals for the cluster sum
-        }
-        if constexpr (!CL) post(red);
+      for (int q = 0; q < K; ++q) {
+        red[16 + q] = w[q];
+        red[20 + 2 * rpar + q] = w[q];  // this CTA's totals for the cluster sum
       }
+      if constexpr (!CL) post(red);
     }
     if constexpr (CL) {
       cg::this_cluster().sync();
@@ -229,6 +212,90 @@ struct Small {
 #pragma unroll
     for (int q = 0; q < K; ++q) v[q] = red[16 + q];
   }
+
+  // v[0..K) (one partial per thread) summed over the CTA (shuffle tree in
+  // each warp with elements, then over those warps) and over the cluster.
+  template <int K, class Post>
+  __device__ void reduceK(double (&v)[K], Post post) {
+    // warps past the CTA's elements hold exact zeros: no float64 adds for them
+    if ((tid & ~31) < nel) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < K; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    }
+    __syncthreads();  // scratch free (the previous totals and scalars were read)
+    if ((tid & 31) == 0)
+#pragma unroll
+      for (int q = 0; q < K; ++q) red[8 * q + (tid >> 5)] = v[q];
+    __syncthreads();
+    double w[K];
+    if (tid < 32) {
+      const int aw = (nel + 31) >> 5;  // warps holding elements; the others' sums are zeros
+#pragma unroll
+      for (int q = 0; q < K; ++q) w[q] = tid < kSmallThreads / 32 ? red[8 * q + tid] : 0.0;
+#pragma unroll
+      for (int o = kSmallThreads / 64; o > 0; o >>= 1)
+        if (o < aw)  // a level that would only add zeros is skipped (the same bits)
+#pragma unroll
+          for (int q = 0; q < K; ++q) w[q] += __shfl_xor_sync(0xffffffffu, w[q], o);
+    }
+    finishK<K>(w, v, post);
+  }
+
+  // v[q] + sum over the CTA's elements of a[q][el] b[q][el] (a[q] null: v[q]
+  // alone; v[q] is taken from thread 0), then over the cluster and post() as
+  // above.  All on warp 0: lane l forms the float64 products of elements
+  // l, l + 32, ... in one fma chain, then a shuffle tree -- for 96 elements
+  // 3 + 5 float64 instructions per sum instead of 1 + 5 on each of three
+  // warps and a tree over the warps.
+  //
+  // Float32 vectors (the mixed kernel): the same on the float32 pipe, every
+  // product split exactly (x y = p + e, e = fma(x, y, -p)) and summed as a
+  // double-float pair (error-free two_sum of the high parts, the low parts
+  // and rounding errors summed in float32: within about nel 2^-48 of the
+  // exact sum), merged into float64 once by lane 0.
+  template <int K, typename T, class Post>
+  __device__ void dotK(const T* const (&a)[K], const T* const (&b)[K], double (&v)[K], Post post) {
+    __syncthreads();  // the vectors are final in this CTA; the previous scalars were read
+    double w[K];
+    if (tid < 32) {
+      if constexpr (sizeof(T) == 8) {
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+          w[q] = tid == 0 ? v[q] : 0.0;
+          if (a[q])
+            for (int el = tid; el < nel; el += 32) w[q] = fma(a[q][el], b[q][el], w[q]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+          if (o < nel)  // lanes >= nel hold zeros (no level for them)
+#pragma unroll
+            for (int q = 0; q < K; ++q)
+              if (a[q]) w[q] += __shfl_xor_sync(0xffffffffu, w[q], o);
+      } else {
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+          w[q] = tid == 0 ? v[q] : 0.0;
+          if (!a[q]) continue;
+          dd acc = dd_make(0.f, 0.f);
+          for (int el = tid; el < nel; el += 32) {
+            const float x = a[q][el], y = b[q][el];
+            const float pr = __fmul_rn(x, y);
+            const float er = __fmaf_rn(x, y, -pr);
+            const dd t = two_sum(acc.h, pr);
+            acc = dd_make(t.h, __fadd_rn(acc.l, __fadd_rn(t.l, er)));
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1)
+            if (o < nel)
+              acc = dd_add(acc, dd_make(__shfl_xor_sync(0xffffffffu, acc.h, o), __shfl_xor_sync(0xffffffffu, acc.l, o)));
+          if (tid == 0) w[q] += f2d_exact(acc.h) + f2d_exact(acc.l);
+        }
+      }
+    }
+    finishK<K>(w, v, post);
+  }
   template <int K>
   __device__ void reduceK(double (&v)[K]) {
     reduceK<K>(v, [](double*) {});
@@ -259,20 +326,25 @@ struct Small {
       const T* M0 = slotT(kind == 0 ? 0 : (kind == 1 ? 2 : 4), i);
       for (int c = 0; c < n; ++c) acc = fma(M0[c * n + a], vi[c], acc);
       if (kind == 0 || kind == 1) {
+        // one fma chain over the three blocks (the fewest float64
+        // instructions); G's off-diagonal blocks are -E_i, -E_{i-1}^T
         const int km = kind == 0 ? 1 : 3;
-        const T sg = kind == 0 ? T(1) : T(-1);  // G's off-diagonal blocks are -E_i, -E_{i-1}^T
-        T t = T(0);
         if (i + 1 < N) {  // (i, i+1): O_i / E_i
           const T* Mi = slotT(km, i);
           const T* vn = row(v, i + 1);
-          for (int c = 0; c < n; ++c) t = fma(Mi[c * n + a], vn[c], t);
+          if (kind == 0)
+            for (int c = 0; c < n; ++c) acc = fma(Mi[c * n + a], vn[c], acc);
+          else
+            for (int c = 0; c < n; ++c) acc = fma(-Mi[c * n + a], vn[c], acc);
         }
         if (i >= 1) {  // (i, i-1): O_{i-1}^T / E_{i-1}^T
           const T* Mp = slotT(km, i - 1);
           const T* vp = row(v, i - 1);
-          for (int c = 0; c < n; ++c) t = fma(Mp[a * n + c], vp[c], t);
+          if (kind == 0)
+            for (int c = 0; c < n; ++c) acc = fma(Mp[a * n + c], vp[c], acc);
+          else
+            for (int c = 0; c < n; ++c) acc = fma(-Mp[a * n + c], vp[c], acc);
         }
-        acc = fma(sg, t, acc);
       } else {
         if (i + 2 < N) {  // (i, i+2): Hu_i
           const T* Mi = slotT(5, i);
@@ -314,13 +386,13 @@ struct Small {
     for (int el = tid; el < nel; el += kSmallThreads) t = fma((double)r[el], (double)z[el], t);
     return reduce(t);
   }
-  // The same, summing another partial (`other`, e.g. r . r) in the same
-  // reduction: one sum per iteration fewer when the convergence test waits
-  // for the preconditioner (the z of the last iteration is then formed and
-  // not used).  post: as in reduceK, on the totals (r . z, other).
+  // The same, with r . r summed beside r . z: one sum per iteration fewer
+  // when the convergence test waits for the preconditioner (the z of the
+  // last iteration is then formed and not used).  post: as in finishK, on the
+  // totals (r . z, r . r).
   template <typename T, class Post>
-  __device__ double precond2T(const T* const* blk, int sb, const T* r, T* z, T* y0, T* ya, T* yb, double other,
-                              double& other_sum, Post post) {
+  __device__ double precond2T(const T* const* blk, int sb, const T* r, T* z, T* y0, T* ya, T* yb, double& rr,
+                              Post post) {
     sweepT<T>(1, blk, sb, r, P.m == 1 ? z : y0);
     if (P.m > 1) {
       const T* yin = y0;
@@ -333,11 +405,11 @@ struct Small {
         for (int el = tid; el < nel; el += kSmallThreads) z[el] = fma(aj, yout[el], j == 1 ? y0[el] : z[el]);
       }
     }
-    double t = 0.0;
-    for (int el = tid; el < nel; el += kSmallThreads) t = fma((double)r[el], (double)z[el], t);
-    double v[2] = {t, other};
-    reduceK<2>(v, post);
-    other_sum = v[1];
+    const T* const a[2] = {r, r};
+    const T* const b[2] = {z, r};
+    double v[2] = {0.0, 0.0};
+    dotK<2, T>(a, b, v, post);
+    rr = v[1];
     return v[0];
   }
   __device__ double precond(const double* r, double* z, double* y0, double* ya, double* yb) {
@@ -410,17 +482,22 @@ __global__ void __launch_bounds__(kSmallThreads, 1) bt_small_kernel(const __grid
       }
       Sm.csync();  // p final in every CTA
       Sm.sweep(0, p, q);
-      double t = 0.0;
-      for (int el = tid; el < nel; el += kSmallThreads) t = fma(p[el], q[el], t);
-      // thread 0 checks p.q and the cycle budget (rank 0's clock decides for a
-      // cluster, through the sum) and divides alpha = rho / p.q
+      // p.q; thread 0 checks it and the cycle budget (rank 0's clock decides
+      // for a cluster, through the sum) and divides alpha = rho / p.q
       double pq;
       {
         constexpr int K = CL ? 2 : 1;
         double v[K];
-        v[0] = t;
-        if constexpr (CL) v[K - 1] = (tid == 0 && Sm.rank == 0 && clock64() > deadline) ? 1.0 : 0.0;
-        Sm.template reduceK<K>(v, [&](double* rd) {
+        const double* a[K];
+        const double* b[K];
+        v[0] = 0.0;
+        a[0] = p;
+        b[0] = q;
+        if constexpr (CL) {
+          v[K - 1] = (tid == 0 && Sm.rank == 0 && clock64() > deadline) ? 1.0 : 0.0;
+          a[K - 1] = b[K - 1] = nullptr;
+        }
+        Sm.template dotK<K, double>(a, b, v, [&](double* rd) {
           const double pqv = rd[16];
           bool late;
           if constexpr (CL) late = rd[16 + K - 1] > 0.0;
@@ -443,17 +520,14 @@ __global__ void __launch_bounds__(kSmallThreads, 1) bt_small_kernel(const __grid
         record(k - 1, 1, al);
         record(k - 1, 2, 0.0);
       }
-      t = 0.0;
       for (int el = tid; el < nel; el += kSmallThreads) {
         x[el] = fma(al, p[el], x[el]);
-        const double rv = fma(-al, q[el], r[el]);
-        r[el] = rv;
-        t = fma(rv, rv, t);
+        r[el] = fma(-al, q[el], r[el]);
       }
       Sm.csync();  // r final in every CTA (the G sweep reads neighbouring rows)
       const double* const blk64[7] = {Sm.D, Sm.O, Sm.Dinv, Sm.E, Sm.Hd, Sm.Hu, Sm.Hl};
       // r.z and r.r; thread 0 tests r.r and divides beta = r.z / rho
-      const double rz = Sm.template precond2T<double>(blk64, P.bs, r, z, y0, ya, yb, t, rr, [&](double* rd) {
+      const double rz = Sm.template precond2T<double>(blk64, P.bs, r, z, y0, ya, yb, rr, [&](double* rd) {
         const double rzv = rd[16], rrv = rd[17];
         const int c = !isfinite(rrv) ? 1 : (rrv <= thr2 ? 2 : 0);
         rd[27] = c == 0 ? rzv / rho : 0.0;
@@ -608,16 +682,22 @@ __global__ void __launch_bounds__(kSmallThreads, 1) bt_small_mixed_kernel(const 
           }
           Sm.csync();  // p final in every CTA
           Sm.template sweepT<float>(0, cblk32, P.bs32, p, q);
-          double tq = 0.0;
-          for (int el = tid; el < nel; el += kSmallThreads) tq = fma((double)p[el], (double)q[el], tq);
-          // thread 0: the checks and alpha (as in the float64 kernel)
+          // p.q (float64 products and sums); thread 0: the checks and alpha
+          // (as in the float64 kernel)
           double pq;
           {
             constexpr int K = CL ? 2 : 1;
             double v[K];
-            v[0] = tq;
-            if constexpr (CL) v[K - 1] = (tid == 0 && Sm.rank == 0 && clock64() > deadline) ? 1.0 : 0.0;
-            Sm.template reduceK<K>(v, [&](double* rd) {
+            const float* a[K];
+            const float* b[K];
+            v[0] = 0.0;
+            a[0] = p;
+            b[0] = q;
+            if constexpr (CL) {
+              v[K - 1] = (tid == 0 && Sm.rank == 0 && clock64() > deadline) ? 1.0 : 0.0;
+              a[K - 1] = b[K - 1] = nullptr;
+            }
+            Sm.template dotK<K, float>(a, b, v, [&](double* rd) {
               const double pqv = rd[16];
               bool late;
               if constexpr (CL) late = rd[16 + K - 1] > 0.0;
@@ -641,16 +721,13 @@ __global__ void __launch_bounds__(kSmallThreads, 1) bt_small_mixed_kernel(const 
             record(iters + k - 1, 1, al);
             record(iters + k - 1, 2, 0.0);
           }
-          double tr = 0.0;
           for (int el = tid; el < nel; el += kSmallThreads) {
             xin[el] = fmaf(alf, p[el], xin[el]);
-            const float rv = fmaf(-alf, q[el], r[el]);
-            r[el] = rv;
-            tr = fma((double)rv, (double)rv, tr);
+            r[el] = fmaf(-alf, q[el], r[el]);
           }
           Sm.csync();  // r final in every CTA (the G sweep reads neighbouring rows)
           // r.z and r.r; thread 0 tests r.r and divides beta
-          const double rz = Sm.template precond2T<float>(cblk32, P.bs32, r, z, y0, ya, yb, tr, rr, [&](double* rd) {
+          const double rz = Sm.template precond2T<float>(cblk32, P.bs32, r, z, y0, ya, yb, rr, [&](double* rd) {
             const double rzv = rd[16], rrv = rd[17];
             const int c = !isfinite(rrv) ? 1 : (rrv <= thr2 ? 2 : 0);
             rd[27] = c != 0 ? 0.0 : (P.scal64 ? rzv / rho : (double)__fdiv_rn((float)rzv, (float)rho));
