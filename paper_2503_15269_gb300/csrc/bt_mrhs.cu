@@ -569,7 +569,7 @@ constexpr int kTcBarOff = 64;  // bytes: full[2], mma, TMEM slot (in the flag wo
 // into rows c - k, c, c + k (k = 2 for H, else 1).  Per block and K step one
 // MMA with A = [x_hi; x_lo] (M = 128) and B = [Q_hi | Q_lo] (N = 2n) forms the
 // four partial products of x^T Q^T into the row's TMEM accumulator (2k + 1 of
-// them, row t in slot t % (2k + 1), 2n columns each).  Step c of the loop:
+// them, 2n columns each).  Step c of the loop:
 //   the finalize threads start copying the input (and `pre`) tiles of row
 //   t = c - 1 - k; wait for column c's data (issued two steps earlier); split
 //   it into TF32 parts; read row t (complete since column c - 1's MMAs, the
@@ -581,8 +581,15 @@ constexpr int kTcBarOff = 64;  // bytes: full[2], mma, TMEM slot (in the flag wo
 // column contributes to the owned rows only.  One thread (kTcIssuer) issues
 // the bulk copies and the MMAs; warps 0-7 read TMEM; the finalize tiles run on
 // threads < 4n.
+// `fd` (A sweep): the p update folded in -- the split forms p = z + beta p_old
+// from the copied p_old row and the z row (staged by cp.async into the `pre`
+// tile buffer, free in this sweep, one column ahead by the threads with no
+// finalize tile), writes p of the owned rows to fd.pout and feeds the MMAs
+// with it; the finalize reads its p tile from fd.pout.  Halo columns form
+// their p the same way (p_old and z of the neighbours are not rewritten
+// during the sweep).
 template <typename Fin>
-__device__ void msweep_tc(MSolver& Sv, int phase, const float* v_in, const float* pre, Fin fin) {
+__device__ void msweep_tc(MSolver& Sv, int phase, const float* v_in, const float* pre, Fin fin, const Fold& fd) {
   const MParams& P = Sv.P;
   const int n = Sv.n, N = Sv.N, s = Sv.s, e = Sv.e;
   __syncthreads();
@@ -641,6 +648,18 @@ __device__ void msweep_tc(MSolver& Sv, int phase, const float* v_in, const float
   }
   Sv.iss = Sv.gcol + min(2, c_hi - c_lo);
   const int a0 = 4 * (tid >> 4), j0 = 4 * (tid & 15);  // finalize tile of threads < 4n
+  const bool fold = fd.z != nullptr && phase == MP_A;
+  const float* fin_src = fold ? fd.pout : v_in;  // the finalize's input tile
+  // threads with neither a finalize tile nor the copy / MMA issue
+  const int sp0 = (4 * n + 31) / 32 * 32, spn = kTcIssuer - sp0;
+  // z row cc into pbuf (threads sp0 .. kTcIssuer - 1)
+  const auto stage_z = [&](int cc) {
+    if (tid >= sp0 && tid < kTcIssuer) {
+      for (int f = tid - sp0; f < vb / 4; f += spn) cp16(pbuf + 4 * f, fd.z + (size_t)cc * vb + 4 * f);
+      cp_commit();
+    }
+  };
+  if (fold && c_lo < c_hi) stage_z(c_lo);
   bool bad = false;
   for (int c = c_lo; c <= e + k; ++c) {  // step e + k finishes row e - 1
     const bool proc = c < c_hi;
@@ -651,12 +670,13 @@ __device__ void msweep_tc(MSolver& Sv, int phase, const float* v_in, const float
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         const size_t g = (size_t)t * vb + (size_t)(a0 + r) * kJ + j0;
-        cp16(xbuf + (a0 + r) * kJ + j0, v_in + g);
+        cp16(xbuf + (a0 + r) * kJ + j0, fin_src + g);
         if (pre) cp16(pbuf + (a0 + r) * kJ + j0, pre + g);
       }
       cp_commit();
     }
     if (proc) {
+      if (fold && tid >= sp0 && tid < kTcIssuer) cp_wait<0>();  // this thread's part of z row c
       const bool ok = mbar_wait(full + buf, (unsigned)((Sv.gcol >> 1) & 1), Sv.deadline);
       if (__syncthreads_or(!ok)) {
         bad = true;
@@ -665,12 +685,26 @@ __device__ void msweep_tc(MSolver& Sv, int phase, const float* v_in, const float
       // split the vector row (transposed into the A image: one right-hand side
       // j and four k per task); the blocks arrive split ([hi | lo] images)
       const float* xr = slot(c);
+      const bool own_c = c >= s && c < e;
       for (int q = tid; q < 16 * n; q += kMThreads) {
         const int j = q & 63, k4 = q >> 6;
+        float4 x = make_float4(xr[(4 * k4) * kJ + j], xr[(4 * k4 + 1) * kJ + j], xr[(4 * k4 + 2) * kJ + j],
+                               xr[(4 * k4 + 3) * kJ + j]);
+        if (fold) {  // p = z + beta_j p_old
+          const float bj = fd.beta[j];
+          const float* zr = pbuf + (4 * k4) * kJ + j;
+          x = make_float4(fmaf(bj, x.x, zr[0]), fmaf(bj, x.y, zr[kJ]), fmaf(bj, x.z, zr[2 * kJ]),
+                          fmaf(bj, x.w, zr[3 * kJ]));
+          if (own_c) {
+            float* po = fd.pout + (size_t)c * vb + (size_t)(4 * k4) * kJ + j;
+            po[0] = x.x;
+            po[kJ] = x.y;
+            po[2 * kJ] = x.z;
+            po[3 * kJ] = x.w;
+          }
+        }
         float4 h, l;
-        split4(make_float4(xr[(4 * k4) * kJ + j], xr[(4 * k4 + 1) * kJ + j], xr[(4 * k4 + 2) * kJ + j],
-                           xr[(4 * k4 + 3) * kJ + j]),
-               h, l);
+        split4(x, h, l);
         const int off = ((j >> 3) * nk4 + k4) * 32 + (j & 7) * 4;
         *reinterpret_cast<float4*>(aimg + off) = h;
         *reinterpret_cast<float4*>(aimg + vb + off) = l;
@@ -698,6 +732,8 @@ __device__ void msweep_tc(MSolver& Sv, int phase, const float* v_in, const float
       tc_fence_before();
       __syncthreads();
     }
+    // the z row of the next column into pbuf (the split of this one has read it)
+    if (fold && proc && c + 1 < c_hi) stage_z(c + 1);
     if (proc) {
       if (tid == kTcIssuer) {
         tc_fence_after();
@@ -781,7 +817,7 @@ __device__ void msweep_tc(MSolver& Sv, int phase, const float* v_in, const float
 template <bool TC, typename Fin>
 __device__ __forceinline__ void msweep(MSolver& Sv, int phase, const float* v_in, const float* pre, Fin fin,
                                        const Fold& fd = Fold{nullptr, nullptr, nullptr}) {
-  if constexpr (TC) msweep_tc(Sv, phase, v_in, pre, fin);
+  if constexpr (TC) msweep_tc(Sv, phase, v_in, pre, fin, fd);
   else msweep32(Sv, phase, v_in, pre, fin, fd);
 }
 
@@ -881,7 +917,7 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
   const size_t vb = (size_t)n * kJ;
   const int J = kJ;
   const int m = P.m;
-  const bool fold = !TC && 4 * n <= kMHalf;  // p update folded into the A sweep (the k-split layout)
+  const bool fold = TC || 4 * n <= kMHalf;  // p update folded into the A sweep (SIMT: the k-split layout)
 
   // ||b_j||^2 and x64 = 0 over the owned rows
   {
