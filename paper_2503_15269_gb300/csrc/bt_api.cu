@@ -113,7 +113,7 @@ struct bt_ctx {
   cudaGraphExec_t graph = nullptr;
   cudaGraph_t graph_src = nullptr;
   // many-right-hand-side workspace (allocated on the first bt_pcg_solve_multi)
-  void* mr_vec[16] = {};
+  void* mr_vec[17] = {};
   int mr_G = 0, mr_smem = 0, mr_outer = 0;
   float* mr_img[9] = {};  // block images of the tensor-core many-RHS engine
   void* lqr_buf = nullptr;  // bt_lqr_refactor's scratch (kept after its first call): the W factors
@@ -1222,7 +1222,7 @@ bt_status bt_pcg_solve_multi(bt_handle h, const double* B, double* X, int nrhs, 
   const int N = h->N[0], n = h->n[0];
   if (n % 4 != 0 || n > 64) return BT_ERR_ARG;  // 16 row groups of 4 at most (BT_MAX_BLOCK)
   const int kJ = 64;
-  if (!h->mr_vec[15]) {  // the last entry: a partly allocated workspace is allocated again
+  if (!h->mr_vec[16]) {  // the last entry: a partly allocated workspace is allocated again
     const size_t cnt = (size_t)N * n * kJ;
     bt_status s;
     double* d = nullptr;
@@ -1251,6 +1251,8 @@ bt_status bt_pcg_solve_multi(bt_handle h, const double* B, double* X, int nrhs, 
     h->mr_vec[14] = res_d;
     if ((s = dalloc(h, &f, cnt)) != BT_OK) return s;  // second p buffer
     h->mr_vec[15] = f;
+    if ((s = dalloc(h, &f, cnt)) != BT_OK) return s;  // second r buffer
+    h->mr_vec[16] = f;
   }
   // engine: tensor cores (3xTF32) where supported, unless the caller asks for SIMT
   const int tc_ok = bt_mrhs_tc_supported(n);

@@ -55,6 +55,7 @@ struct MParams {
   // float32 vectors [N][n][J]
   float *Xin, *R, *P, *Q, *Y0, *Ya, *Yb, *Z;
   float* P2;            // second p buffer: the A sweep writes the new p there (n <= 48)
+  float* R2;            // second r buffer: the tensor-core B1 sweep writes the new r there (m >= 2)
   double* red;          // [2][G][kJ]
   unsigned* bar;
   int* abort_flag;
@@ -297,6 +298,7 @@ struct Fold {
   const float* z;
   float* pout;
   const float* beta;
+  int sq;  // tensor-core B1 fold: sum (new r)^2 over the owned rows, this thread's part to the column scratch
 };
 
 // Float32 sweeps: the vector rows a row job reads (i-k, i, i+k) come from a
@@ -587,7 +589,10 @@ constexpr int kTcBarOff = 64;  // bytes: full[2], mma, TMEM slot (in the flag wo
 // finalize tile), writes p of the owned rows to fd.pout and feeds the MMAs
 // with it; the finalize reads its p tile from fd.pout.  Halo columns form
 // their p the same way (p_old and z of the neighbours are not rewritten
-// during the sweep).
+// during the sweep).  `fd` (B1 sweep): the r update r = r_old - alpha q folded
+// in the same way (fd.z = q, fd.beta = alpha); with fd.sq each thread sums the
+// new r^2 of its column (tid % 64) over the owned rows and leaves the sum in
+// the column scratch, [tid / 64][tid % 64], when the sweep ends.
 template <typename Fin>
 __device__ void msweep_tc(MSolver& Sv, int phase, const float* v_in, const float* pre, Fin fin, const Fold& fd) {
   const MParams& P = Sv.P;
@@ -648,10 +653,11 @@ __device__ void msweep_tc(MSolver& Sv, int phase, const float* v_in, const float
   }
   Sv.iss = Sv.gcol + min(2, c_hi - c_lo);
   const int a0 = 4 * (tid >> 4), j0 = 4 * (tid & 15);  // finalize tile of threads < 4n
-  const bool fold = fd.z != nullptr && phase == MP_A;
+  const bool fold = fd.z != nullptr && (phase == MP_A || phase == MP_B1);
   const float* fin_src = fold ? fd.pout : v_in;  // the finalize's input tile
   // threads with neither a finalize tile nor the copy / MMA issue
   const int sp0 = (4 * n + 31) / 32 * 32, spn = kTcIssuer - sp0;
+  Accum<float> sqa;  // fd.sq: this thread's sum of the new r^2
   // z row cc into pbuf (threads sp0 .. kTcIssuer - 1)
   const auto stage_z = [&](int cc) {
     if (tid >= sp0 && tid < kTcIssuer) {
@@ -690,17 +696,27 @@ __device__ void msweep_tc(MSolver& Sv, int phase, const float* v_in, const float
         const int j = q & 63, k4 = q >> 6;
         float4 x = make_float4(xr[(4 * k4) * kJ + j], xr[(4 * k4 + 1) * kJ + j], xr[(4 * k4 + 2) * kJ + j],
                                xr[(4 * k4 + 3) * kJ + j]);
-        if (fold) {  // p = z + beta_j p_old
+        if (fold) {
           const float bj = fd.beta[j];
           const float* zr = pbuf + (4 * k4) * kJ + j;
-          x = make_float4(fmaf(bj, x.x, zr[0]), fmaf(bj, x.y, zr[kJ]), fmaf(bj, x.z, zr[2 * kJ]),
-                          fmaf(bj, x.w, zr[3 * kJ]));
+          if (phase == MP_A)  // p = z + beta_j p_old
+            x = make_float4(fmaf(bj, x.x, zr[0]), fmaf(bj, x.y, zr[kJ]), fmaf(bj, x.z, zr[2 * kJ]),
+                            fmaf(bj, x.w, zr[3 * kJ]));
+          else  // r = r_old - alpha_j q
+            x = make_float4(fmaf(-bj, zr[0], x.x), fmaf(-bj, zr[kJ], x.y), fmaf(-bj, zr[2 * kJ], x.z),
+                            fmaf(-bj, zr[3 * kJ], x.w));
           if (own_c) {
             float* po = fd.pout + (size_t)c * vb + (size_t)(4 * k4) * kJ + j;
             po[0] = x.x;
             po[kJ] = x.y;
             po[2 * kJ] = x.z;
             po[3 * kJ] = x.w;
+            if (fd.sq) {
+              sqa.add(x.x * x.x);
+              sqa.add(x.y * x.y);
+              sqa.add(x.z * x.z);
+              sqa.add(x.w * x.w);
+            }
           }
         }
         float4 h, l;
@@ -812,6 +828,8 @@ __device__ void msweep_tc(MSolver& Sv, int phase, const float* v_in, const float
     if (tid == 0) atomicExch(P.abort_flag, 1);
   }
   __syncthreads();
+  // the column scratch overlaps the sweep's buffers, idle now
+  if (fold && fd.sq) Sv.colred[(tid / kJ) * kJ + tid % kJ] = sqa.value();
 }
 
 template <bool TC, typename Fin>
@@ -918,6 +936,7 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
   const int J = kJ;
   const int m = P.m;
   const bool fold = TC || 4 * n <= kMHalf;  // p update folded into the A sweep (SIMT: the k-split layout)
+  const bool foldr = TC && m >= 2;  // r update folded into the B1 sweep (tensor cores, with H sweeps)
 
   // ||b_j||^2 and x64 = 0 over the owned rows
   {
@@ -998,12 +1017,17 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
             }
       Sv.barrier();
     }
-    // z0 = M^-1 r0 ; rho = r.z
-    auto apply_precond = [&](double* rzout) {
+    float* Rc = P.R;   // the current r
+    float* Rn = P.R2;  // where a B1 sweep with the r update folded in writes the new r
+    // z0 = M^-1 r0 ; rho = r.z.  fr (foldr): the B1 sweep first forms
+    // r = r_old - alpha q (r.r per column reduced after it, the barrier before
+    // the H sweeps); returns true when no column remains active (the H sweeps
+    // are then skipped).
+    auto apply_precond = [&](double* rzout, bool fr) -> bool {
       // r.z per column, summed in the finalize of the sweep that completes z
       Accum<float> pa[4];
       // B1: y0 = G r (r is the staged centre block of this sweep)
-      msweep<TC>(Sv, MP_B1, P.R, nullptr, [&](int row, int a0, int j0, float (&o)[4][4], const float* xc, const float4*, int) {
+      msweep<TC>(Sv, MP_B1, Rc, nullptr, [&](int row, int a0, int j0, float (&o)[4][4], const float* xc, const float4*, int) {
         for (int r = 0; r < 4; ++r) {
           const size_t idx = (size_t)row * vb + (size_t)(a0 + r) * J + j0;
           const float4 y = make_float4(o[r][0], o[r][1], o[r][2], o[r][3]);
@@ -1017,14 +1041,35 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
             pa[3].add(rv.w * y.w);
           }
         }
-      });
+      }, fr ? Fold{P.Q, Rn, alpf, 1} : Fold{nullptr, nullptr, nullptr, 0});
+      if (fr) {
+        float* t = Rc;  // the r just formed is the current one
+        Rc = Rn;
+        Rn = t;
+        // r.r per column (the sweep left each thread's part in the scratch),
+        // then over the grid
+        __syncthreads();
+        if (tid < kJ) {
+          double sum = 0.0;
+          for (int a = 0; a < kMThreads / kJ; ++a) sum += scratch[a * kJ + tid];
+          colR[tid] = sum;
+        }
+        __syncthreads();
+        Sv.grid_reduce(colR);
+        if (tid < J) {
+          rrv[tid] = colR[tid];
+          if (actv[tid] > 0.0 && rrv[tid] <= tin[tid]) actv[tid] = 0.0;  // converged column
+        }
+        __syncthreads();
+        if (!__syncthreads_or(tid < J && actv[tid] > 0.0)) return true;
+      }
       for (int jp = 1; jp < m && !Sv.fail; ++jp) {
-        Sv.barrier();
+        if (!(fr && jp == 1)) Sv.barrier();  // (fr: the r.r reduction was the barrier)
         const float* yin = (jp == 1) ? P.Y0 : ((jp - 1) % 2 == 1 ? P.Ya : P.Yb);
         float* yout = (jp % 2 == 1) ? P.Ya : P.Yb;
         const float aj = P.alpha[jp];
         const bool lastj = (jp == m - 1);
-        msweep<TC>(Sv, MP_B2, yin, lastj ? P.R : nullptr,
+        msweep<TC>(Sv, MP_B2, yin, lastj ? Rc : nullptr,
                  [&](int row, int a0, int j0, float (&o)[4][4], const float* yc, const float4* rpf, int rst) {
           for (int r = 0; r < 4; ++r) {
             const size_t idx = (size_t)row * vb + (size_t)(a0 + r) * J + j0;
@@ -1052,8 +1097,9 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
       Sv.grid_reduce(colR);
       if (tid < J) rzout[tid] = colR[tid];
       __syncthreads();
+      return false;
     };
-    apply_precond(rho);
+    apply_precond(rho, false);
     // p = z; beta = 0 (with the folded update the first A sweep forms
     // z + 0 p from this copy)
     float* Pc = P.P;   // the current p (the old one while an A sweep folds the update in)
@@ -1109,53 +1155,77 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
         if (actv[tid] > 0.0) itc[tid] += 1.0;
       }
       __syncthreads();
-      // x += alpha p, r -= alpha q, rr per column: the owned rows are one
-      // contiguous range of float4s; thread t takes every kMThreads-th (so
-      // always column group t % 16) and loads a batch of kVB before storing.
-      {
-        Accum<float> pa[4];
+      if (foldr) {
+        // x += alpha p over the owned rows (no other CTA reads them: no
+        // barrier); r and r.r are formed in the B1 sweep
         const float4 al = *reinterpret_cast<const float4*>(alpf + 4 * (tid & 15));
         const float4* Pp = reinterpret_cast<const float4*>(Pc);
-        const float4* Qp = reinterpret_cast<const float4*>(P.Q);
         float4* Xp = reinterpret_cast<float4*>(P.Xin);
-        float4* Rp = reinterpret_cast<float4*>(P.R);
         const size_t f1 = (size_t)Sv.e * vb / 4;
         for (size_t f = (size_t)Sv.s * vb / 4 + tid; f < f1; f += (size_t)kVB * kMThreads) {
-          float4 pp[kVB], qq[kVB], xx[kVB], rr[kVB];
+          float4 pp[kVB], xx[kVB];
 #pragma unroll
           for (int b = 0; b < kVB; ++b) {
             const size_t g = f + (size_t)b * kMThreads;
-            if (g < f1) { pp[b] = Pp[g]; qq[b] = Qp[g]; xx[b] = Xp[g]; rr[b] = Rp[g]; }
+            if (g < f1) { pp[b] = Pp[g]; xx[b] = Xp[g]; }
           }
 #pragma unroll
           for (int b = 0; b < kVB; ++b) {
             const size_t g = f + (size_t)b * kMThreads;
-            if (g < f1) {
+            if (g < f1)
               Xp[g] = make_float4(fmaf(al.x, pp[b].x, xx[b].x), fmaf(al.y, pp[b].y, xx[b].y),
                                   fmaf(al.z, pp[b].z, xx[b].z), fmaf(al.w, pp[b].w, xx[b].w));
-              const float4 rv = make_float4(fmaf(-al.x, qq[b].x, rr[b].x), fmaf(-al.y, qq[b].y, rr[b].y),
-                                            fmaf(-al.z, qq[b].z, rr[b].z), fmaf(-al.w, qq[b].w, rr[b].w));
-              Rp[g] = rv;
-              pa[0].add(rv.x * rv.x);
-              pa[1].add(rv.y * rv.y);
-              pa[2].add(rv.z * rv.z);
-              pa[3].add(rv.w * rv.w);
-            }
           }
         }
-        double pr[4];
-        widen(pa, pr);
-        cta_col_reduce(pr, scratch, colR, kMThreads / 16);
-        Sv.grid_reduce(colR);
-        if (tid < J) {
-          rrv[tid] = colR[tid];
-          if (actv[tid] > 0.0 && rrv[tid] <= tin[tid]) actv[tid] = 0.0;  // converged column
+      } else {
+        // x += alpha p, r -= alpha q, rr per column: the owned rows are one
+        // contiguous range of float4s; thread t takes every kMThreads-th (so
+        // always column group t % 16) and loads a batch of kVB before storing.
+        {
+          Accum<float> pa[4];
+          const float4 al = *reinterpret_cast<const float4*>(alpf + 4 * (tid & 15));
+          const float4* Pp = reinterpret_cast<const float4*>(Pc);
+          const float4* Qp = reinterpret_cast<const float4*>(P.Q);
+          float4* Xp = reinterpret_cast<float4*>(P.Xin);
+          float4* Rp = reinterpret_cast<float4*>(Rc);
+          const size_t f1 = (size_t)Sv.e * vb / 4;
+          for (size_t f = (size_t)Sv.s * vb / 4 + tid; f < f1; f += (size_t)kVB * kMThreads) {
+            float4 pp[kVB], qq[kVB], xx[kVB], rr[kVB];
+#pragma unroll
+            for (int b = 0; b < kVB; ++b) {
+              const size_t g = f + (size_t)b * kMThreads;
+              if (g < f1) { pp[b] = Pp[g]; qq[b] = Qp[g]; xx[b] = Xp[g]; rr[b] = Rp[g]; }
+            }
+#pragma unroll
+            for (int b = 0; b < kVB; ++b) {
+              const size_t g = f + (size_t)b * kMThreads;
+              if (g < f1) {
+                Xp[g] = make_float4(fmaf(al.x, pp[b].x, xx[b].x), fmaf(al.y, pp[b].y, xx[b].y),
+                                    fmaf(al.z, pp[b].z, xx[b].z), fmaf(al.w, pp[b].w, xx[b].w));
+                const float4 rv = make_float4(fmaf(-al.x, qq[b].x, rr[b].x), fmaf(-al.y, qq[b].y, rr[b].y),
+                                              fmaf(-al.z, qq[b].z, rr[b].z), fmaf(-al.w, qq[b].w, rr[b].w));
+                Rp[g] = rv;
+                pa[0].add(rv.x * rv.x);
+                pa[1].add(rv.y * rv.y);
+                pa[2].add(rv.z * rv.z);
+                pa[3].add(rv.w * rv.w);
+              }
+            }
+          }
+          double pr[4];
+          widen(pa, pr);
+          cta_col_reduce(pr, scratch, colR, kMThreads / 16);
+          Sv.grid_reduce(colR);
+          if (tid < J) {
+            rrv[tid] = colR[tid];
+            if (actv[tid] > 0.0 && rrv[tid] <= tin[tid]) actv[tid] = 0.0;  // converged column
+          }
+          __syncthreads();
         }
-        __syncthreads();
+        const int still = __syncthreads_or(tid < J && actv[tid] > 0.0);
+        if (!still) break;
       }
-      const int still = __syncthreads_or(tid < J && actv[tid] > 0.0);
-      if (!still) break;
-      apply_precond(bet);   // bet temporarily holds the new r.z
+      if (apply_precond(bet, foldr)) break;  // bet temporarily holds the new r.z
       if (tid < J) {
         const double rzn = bet[tid];
         const double b = (actv[tid] > 0.0) ? rzn / rho[tid] : 0.0;
@@ -1322,7 +1392,7 @@ extern "C" cudaError_t bt_mrhs_images(int N, int n, int m, const float* const* b
 
 // Host launcher: fills the kernel parameters from plain pointers (the
 // workspace vector list is B64, X64, R64, Xin, R, P, Q, Y0, Ya, Yb, Z, red,
-// ctl, int results [iters | status | outer], double results [resid], P2;
+// ctl, int results [iters | status | outer], double results [resid], P2, R2;
 // img: the nine block images for the tensor-core engine, or null).
 extern "C" cudaError_t bt_mrhs_solve_launch(int N, int n, int m, const double* alpha, const float* const* blk32,
                                             const double* D64, const double* O64, int bs32, int bs64,
@@ -1353,6 +1423,7 @@ extern "C" cudaError_t bt_mrhs_solve_launch(int N, int n, int m, const double* a
   P.Yb = static_cast<float*>(vec[9]);
   P.Z = static_cast<float*>(vec[10]);
   P.P2 = static_cast<float*>(vec[15]);
+  P.R2 = static_cast<float*>(vec[16]);
   P.red = static_cast<double*>(vec[11]);
   int* ctl = static_cast<int*>(vec[12]);
   P.abort_flag = ctl + 1;
