@@ -915,7 +915,7 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
   double* col = reinterpret_cast<double*>(smem + kMSmScalars);
   double* colR = col + 0 * kJ;     // reduction buffer
   double* rho = col + 1 * kJ;
-  double* alp = col + 2 * kJ;
+  float* alpq = reinterpret_cast<float*>(col + 2 * kJ);  // float alpha of the previous iteration
   double* bet = col + 3 * kJ;
   double* actv = col + 4 * kJ;     // 1 active in the inner solve, 0 frozen
   double* nbv = col + 5 * kJ;      // ||b_j||
@@ -1115,6 +1115,39 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
       if (tid < J) betf[tid] = 0.f;
       Sv.barrier();
     }
+    // x += alpha p over the owned rows (the current p and alpha: Pc, alpf),
+    // or x += alpha' p' + alpha p (two): p' = Pn with alpha' = alpq first
+    bool x_pending = false;
+    auto x_update = [&](bool two) {
+      const float4 al = *reinterpret_cast<const float4*>(alpf + 4 * (tid & 15));
+      const float4 a2 = *reinterpret_cast<const float4*>(alpq + 4 * (tid & 15));
+      const float4* Pp = reinterpret_cast<const float4*>(Pc);
+      const float4* P2p = reinterpret_cast<const float4*>(Pn);
+      float4* Xp = reinterpret_cast<float4*>(P.Xin);
+      const size_t f1 = (size_t)Sv.e * vb / 4;
+      // loads of a batch of kVB before its stores: one latency per batch
+      for (size_t f = (size_t)Sv.s * vb / 4 + tid; f < f1; f += (size_t)kVB * kMThreads) {
+        float4 xx[kVB], pp[kVB], qq[kVB];
+#pragma unroll
+        for (int b = 0; b < kVB; ++b) {
+          const size_t g = min(f + (size_t)b * kMThreads, f1 - 1);  // clamped: loads stay in range
+          xx[b] = Xp[g];
+          pp[b] = Pp[g];
+          qq[b] = two ? P2p[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int b = 0; b < kVB; ++b) {
+          const size_t g = f + (size_t)b * kMThreads;
+          float4 x = xx[b];
+          if (two)
+            x = make_float4(fmaf(a2.x, qq[b].x, x.x), fmaf(a2.y, qq[b].y, x.y), fmaf(a2.z, qq[b].z, x.z),
+                            fmaf(a2.w, qq[b].w, x.w));
+          if (g < f1)
+            Xp[g] = make_float4(fmaf(al.x, pp[b].x, x.x), fmaf(al.y, pp[b].y, x.y), fmaf(al.z, pp[b].z, x.z),
+                                fmaf(al.w, pp[b].w, x.w));
+        }
+      }
+    };
     // inner iterations
     for (int kit = 1; !Sv.fail; ++kit) {
       const int anyact = __syncthreads_or(tid < J && actv[tid] > 0.0);
@@ -1144,38 +1177,27 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
       Sv.grid_reduce(colR);
       if (tid < J) {
         const double pq = colR[tid];
+        double a = 0.0;
         if (actv[tid] > 0.0) {
-          if (!isfinite(pq)) { actv[tid] = 0.0; outer_act[tid] = -1.0; alp[tid] = 0.0; }
-          else if (!(pq > 0.0)) { actv[tid] = 0.0; outer_act[tid] = -2.0; alp[tid] = 0.0; }
-          else alp[tid] = rho[tid] / pq;
-        } else {
-          alp[tid] = 0.0;
+          if (!isfinite(pq)) { actv[tid] = 0.0; outer_act[tid] = -1.0; }
+          else if (!(pq > 0.0)) { actv[tid] = 0.0; outer_act[tid] = -2.0; }
+          else a = rho[tid] / pq;
         }
-        alpf[tid] = (float)alp[tid];
+        alpq[tid] = alpf[tid];  // the previous iteration's alpha (paired x updates)
+        alpf[tid] = (float)a;
         if (actv[tid] > 0.0) itc[tid] += 1.0;
       }
       __syncthreads();
       if (foldr) {
         // x += alpha p over the owned rows (no other CTA reads them: no
-        // barrier); r and r.r are formed in the B1 sweep
-        const float4 al = *reinterpret_cast<const float4*>(alpf + 4 * (tid & 15));
-        const float4* Pp = reinterpret_cast<const float4*>(Pc);
-        float4* Xp = reinterpret_cast<float4*>(P.Xin);
-        const size_t f1 = (size_t)Sv.e * vb / 4;
-        for (size_t f = (size_t)Sv.s * vb / 4 + tid; f < f1; f += (size_t)kVB * kMThreads) {
-          float4 pp[kVB], xx[kVB];
-#pragma unroll
-          for (int b = 0; b < kVB; ++b) {
-            const size_t g = f + (size_t)b * kMThreads;
-            if (g < f1) { pp[b] = Pp[g]; xx[b] = Xp[g]; }
-          }
-#pragma unroll
-          for (int b = 0; b < kVB; ++b) {
-            const size_t g = f + (size_t)b * kMThreads;
-            if (g < f1)
-              Xp[g] = make_float4(fmaf(al.x, pp[b].x, xx[b].x), fmaf(al.y, pp[b].y, xx[b].y),
-                                  fmaf(al.z, pp[b].z, xx[b].z), fmaf(al.w, pp[b].w, xx[b].w));
-          }
+        // barrier); r and r.r are formed in the B1 sweep.  Two iterations per
+        // pass: an odd one leaves alpha_k p_k pending (p_k stays in Pc, then
+        // in Pn until the A sweep after next), an even one adds
+        // alpha_{k-1} p_{k-1} + alpha_k p_k (the same fma sequence)
+        if (kit & 1) x_pending = true;
+        else {
+          x_update(true);
+          x_pending = false;
         }
       } else {
         // x += alpha p, r -= alpha q, rr per column: the owned rows are one
@@ -1258,6 +1280,10 @@ __global__ void __launch_bounds__(kMThreads, 1) bt_mrhs_kernel(const __grid_cons
         }
         Sv.barrier();
       }
+    }
+    if (x_pending) {  // the last odd iteration's alpha p
+      x_update(false);
+      __syncthreads();  // x_in is read below with another thread mapping
     }
     // x64 += ||r64|| * x_in
     {
