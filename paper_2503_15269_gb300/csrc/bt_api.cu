@@ -98,6 +98,8 @@ struct bt_ctx {
   int* d_retry = nullptr;  // mixed: float64 refactor list (count + rows)
   bt::SegRef* d_segs = nullptr;  // mixed: row segments of the fused E/H kernel
   long long nsegs = 0;
+  long long* d_cls_idx = nullptr;  // mixed: canonical rows grouped by block-size class (float32 factor)
+  long long cls_lo[4] = {}, cls_hi[4] = {};
   char* d_ws = nullptr;
   long long ws_stride = 0, ws_vec = 0;
   int ws_slots = 0;
@@ -223,6 +225,15 @@ bt_status check_params(const bt_params* p, double* alpha_out) {
 
 inline long long rup(long long v, long long a) { return (v + a - 1) / a * a; }
 
+// The block-size classes of the float32 factor (mixed handles), or none.
+void set_classes(const bt_ctx* h, bt::SetupParams& sp) {
+  sp.cls_idx = h->d_cls_idx;
+  for (int c = 0; c < 4; ++c) {
+    sp.cls_lo[c] = h->cls_lo[c];
+    sp.cls_hi[c] = h->cls_hi[c];
+  }
+}
+
 // Queue the setup kernels (K0..K3) for D, O on the handle's stream.
 bt_status launch_setup_kernels(bt_ctx* h, const double* D, const double* O) {
   cudaStream_t st = h->stream;
@@ -249,6 +260,7 @@ bt_status launch_setup_kernels(bt_ctx* h, const double* D, const double* O) {
   sp.retry = h->prm.mixed_strict_fp64 ? nullptr : h->d_retry;
   sp.segs = h->d_segs;
   sp.nsegs = h->nsegs;
+  set_classes(h, sp);
   // the matrix-free variant forms no H blocks
   return cuda_st(bt_launch_setup(&sp, h->mixed ? 1 : 0, h->variant == 2 ? 1 : h->prm.m, h->maxn, st));
 }
@@ -432,7 +444,10 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
   ALLOC(h->d_errval, B);
   ALLOC(h->d_fail_key, 1);
   ALLOC(h->d_fail_piv, rows);
-  if (h->mixed) ALLOC(h->d_retry, rows + 1);
+  if (h->mixed) {
+    ALLOC(h->d_retry, rows + 1);
+    ALLOC(h->d_cls_idx, rows);
+  }
   // zero every block array once (padding slots must read as zero)
   auto z64 = [&](double* p) { if (p) cudaMemsetAsync(p, 0, off64 * sizeof(double), st); };
   auto z32 = [&](float* p) { if (p) cudaMemsetAsync(p, 0, off32 * sizeof(float), st); };
@@ -445,6 +460,23 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
     long long t = 0;
     for (int k = 0; k < B; ++k)
       for (int i = 0; i < h->N[k]; ++i) rr[t++] = bt::RowRef{k, i};
+  }
+  // mixed: the rows of each block-size class of the float32 factor
+  // (n = 12, 24, 36, other), canonical indices in instance order
+  std::vector<long long> cls_idx;
+  if (mixed) {
+    cls_idx.reserve(rows);
+    const auto cls_of = [](int n) { return n == 12 ? 0 : (n == 24 ? 1 : (n == 36 ? 2 : 3)); };
+    for (int c = 0; c < 4; ++c) {
+      h->cls_lo[c] = (long long)cls_idx.size();
+      long long t = 0;
+      for (int k = 0; k < B; ++k) {
+        if (cls_of(h->n[k]) == c)
+          for (int i = 0; i < h->N[k]; ++i) cls_idx.push_back(t + i);
+        t += h->N[k];
+      }
+      h->cls_hi[c] = (long long)cls_idx.size();
+    }
   }
   std::vector<bt::SegRef> segs;
   if (mixed) {
@@ -464,6 +496,8 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
       !ok(cudaMemcpyAsync(h->d_doff, h->d_off.data(), B * sizeof(long long), cudaMemcpyHostToDevice, st)) ||
       !ok(cudaMemcpyAsync(h->d_ooff, h->o_off.data(), B * sizeof(long long), cudaMemcpyHostToDevice, st)) ||
       (mixed && !ok(cudaMemcpyAsync(h->d_segs, segs.data(), segs.size() * sizeof(bt::SegRef),
+                                     cudaMemcpyHostToDevice, st))) ||
+      (mixed && !ok(cudaMemcpyAsync(h->d_cls_idx, cls_idx.data(), cls_idx.size() * sizeof(long long),
                                      cudaMemcpyHostToDevice, st))))
     return BT_ERR_CUDA;
   if (launch_setup_kernels(h, D, O) != BT_OK) return BT_ERR_CUDA;
@@ -990,6 +1024,7 @@ bt_status bt_lqr_refactor(bt_handle h, const int* m, const double* A, const doub
   sp.retry = h->d_retry;
   sp.segs = h->d_segs;
   sp.nsegs = h->nsegs;
+  set_classes(h, sp);
   sp.copied = 1;
   if (bt_status e = cuda_st(bt_launch_setup(&sp, 1, h->prm.m, h->maxn, st)); e != BT_OK) return e;
   const bt_status e = read_setup_status(h);

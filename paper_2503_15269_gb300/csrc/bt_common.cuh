@@ -144,6 +144,11 @@ struct SetupParams {
   long long nsegs;
   int copied;               // mixed: D64, O64, D32, O32 already hold the blocks (written by the
                             // LQR formation); the factor reads D from them and copies nothing
+  // mixed, optional: canonical row indices grouped by block-size class
+  // (0: n = 12, 1: 24, 2: 36, 3: any other n), class c at [cls_lo[c], cls_hi[c]);
+  // null: one float32 factor kernel over all rows
+  const long long* cls_idx;
+  long long cls_lo[4], cls_hi[4];
 };
 
 struct AdjParams {

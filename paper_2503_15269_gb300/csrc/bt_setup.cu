@@ -248,15 +248,17 @@ __device__ __forceinline__ bool factor_regs(const float* __restrict__ D32, float
 // pivot is at least lambda_min, the diagonal at most lambda_max); such rows
 // and non-positive or non-finite pivots go to the float64 retry list, so a
 // poorly conditioned block costs float64 time only where it occurs.
-__global__ void k_factor32(const __grid_constant__ SetupParams P, int wpc, int warp_bytes) {
-  extern __shared__ __align__(16) char smraw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long gr = (long long)blockIdx.x * wpc + warp;
-  if (gr >= P.nrows) return;
+// One row of k_factor32.  NB > 0: the register-resident factor for n = NB;
+// 0: the register variant chosen at run time for n in {12, 24, 36}, the
+// shared-memory walk otherwise; -1: the shared-memory walk only.  (A kernel
+// holding only one variant takes that variant's registers, not the largest
+// one's.)
+template <int NB>
+__device__ __forceinline__ void factor32_row(const SetupParams& P, long long gr, char* wsm, int warp_bytes,
+                                             int lane) {
   const RowRef rr = P.rows[gr];
   const InstDesc d = P.inst[rr.inst];
   const int n = d.n, i = rr.row, nn = n * n;
-  char* wsm = smraw + (size_t)warp * warp_bytes;
   float* A = reinterpret_cast<float*>(wsm);
   float* dv = reinterpret_cast<float*>(wsm + warp_bytes - 64 * sizeof(float));
   double* stg = reinterpret_cast<double*>(wsm);
@@ -293,11 +295,15 @@ __global__ void k_factor32(const __grid_constant__ SetupParams P, int wpc, int w
   float* out = P.Dinv32 + d.off32 + (long long)i * d.bs32;
   {
     int done = -1;  // -1: no register variant for this n
-    switch (n) {
-      case 12: done = factor_regs<12>(D32, out, lane) ? 1 : 0; break;
-      case 24: done = factor_regs<24>(D32, out, lane) ? 1 : 0; break;
-      case 36: done = factor_regs<36>(D32, out, lane) ? 1 : 0; break;
-      default: break;
+    if constexpr (NB > 0) {
+      done = factor_regs<NB>(D32, out, lane) ? 1 : 0;
+    } else if constexpr (NB == 0) {
+      switch (n) {
+        case 12: done = factor_regs<12>(D32, out, lane) ? 1 : 0; break;
+        case 24: done = factor_regs<24>(D32, out, lane) ? 1 : 0; break;
+        case 36: done = factor_regs<36>(D32, out, lane) ? 1 : 0; break;
+        default: break;
+      }
     }
     if (done == 0 && lane == 0) P.retry[1 + atomicAdd(P.retry, 1)] = (int)gr;
     if (done >= 0) return;
@@ -360,6 +366,25 @@ __global__ void k_factor32(const __grid_constant__ SetupParams P, int wpc, int w
     if (r0 < n) out[(long long)b * n + r0] = acc0;
     if (r1 < n) out[(long long)b * n + r1] = acc1;
   }
+}
+
+__global__ void k_factor32(const __grid_constant__ SetupParams P, int wpc, int warp_bytes) {
+  extern __shared__ __align__(16) char smraw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long gr = (long long)blockIdx.x * wpc + warp;
+  if (gr >= P.nrows) return;
+  factor32_row<0>(P, gr, smraw + (size_t)warp * warp_bytes, warp_bytes, lane);
+}
+
+// The rows of one block-size class (P.cls_idx[P.cls_lo[cls] ..
+// P.cls_hi[cls]), canonical row indices), with that class's variant only.
+template <int NB>
+__global__ void k_factor32_cls(const __grid_constant__ SetupParams P, int wpc, int warp_bytes, int cls) {
+  extern __shared__ __align__(16) char smraw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long li = P.cls_lo[cls] + (long long)blockIdx.x * wpc + warp;
+  if (li >= P.cls_hi[cls]) return;
+  factor32_row<NB>(P, P.cls_idx[li], smraw + (size_t)warp * warp_bytes, warp_bytes, lane);
 }
 
 // Small dense products in shared memory: matrices are row-major n x n.
@@ -860,8 +885,28 @@ static cudaError_t launch_setup_opt(const bt::SetupParams* P, int mixed, int m, 
     cudaFuncSetAttribute(bt::k_E<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_prod);
     cudaFuncSetAttribute(bt::k_H<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_prod);
     if ((err = cudaMemsetAsync(P->retry, 0, sizeof(int), st)) != cudaSuccess) return err;
-    bt::k_factor32<<<(unsigned)((nb + wpc32 - 1) / wpc32), 32 * wpc32, sm32, st>>>(*P, wpc32, per_warp32);
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if (P->cls_idx) {
+      // one launch per block-size class: each kernel holds one variant and
+      // takes its registers (n = 12 and 24 run at a higher occupancy than
+      // next to the n = 36 variant)
+      const auto launch_cls = [&](void (*kern)(bt::SetupParams, int, int, int), int c, int nbk) -> cudaError_t {
+        const long long cnt = P->cls_hi[c] - P->cls_lo[c];
+        if (cnt <= 0) return cudaSuccess;
+        const int q = nbk > 0 ? nbk : maxn;
+        const int pw = (4 * q * (q + 1) + 15) / 16 * 16 + 64 * (int)sizeof(float);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, wpc32 * pw);
+        if (e != cudaSuccess) return e;
+        kern<<<(unsigned)((cnt + wpc32 - 1) / wpc32), 32 * wpc32, wpc32 * pw, st>>>(*P, wpc32, pw, c);
+        return cudaGetLastError();
+      };
+      if ((err = launch_cls(bt::k_factor32_cls<12>, 0, 12)) != cudaSuccess) return err;
+      if ((err = launch_cls(bt::k_factor32_cls<24>, 1, 24)) != cudaSuccess) return err;
+      if ((err = launch_cls(bt::k_factor32_cls<36>, 2, 36)) != cudaSuccess) return err;
+      if ((err = launch_cls(bt::k_factor32_cls<-1>, 3, 0)) != cudaSuccess) return err;
+    } else {
+      bt::k_factor32<<<(unsigned)((nb + wpc32 - 1) / wpc32), 32 * wpc32, sm32, st>>>(*P, wpc32, per_warp32);
+      if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
     const long long rgrid = std::min<long long>((nb + wpc - 1) / wpc, 304);
     bt::k_factor_retry<<<(unsigned)rgrid, 32 * wpc, sm_fac, st>>>(*P, wpc, per_warp);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
