@@ -100,6 +100,7 @@ struct bt_ctx {
   long long nsegs = 0;
   long long* d_cls_idx = nullptr;  // mixed: canonical rows grouped by block-size class (float32 factor)
   long long cls_lo[4] = {}, cls_hi[4] = {};
+  long long seg_lo[4] = {}, seg_hi[4] = {};  // mixed: the E/H segments of each class (grouped in d_segs)
   char* d_ws = nullptr;
   long long ws_stride = 0, ws_vec = 0;
   int ws_slots = 0;
@@ -231,6 +232,8 @@ void set_classes(const bt_ctx* h, bt::SetupParams& sp) {
   for (int c = 0; c < 4; ++c) {
     sp.cls_lo[c] = h->cls_lo[c];
     sp.cls_hi[c] = h->cls_hi[c];
+    sp.seg_lo[c] = h->seg_lo[c];
+    sp.seg_hi[c] = h->seg_hi[c];
   }
 }
 
@@ -479,10 +482,17 @@ bt_status setup_common(bt_ctx* h, const double* D, const double* O) {
     }
   }
   std::vector<bt::SegRef> segs;
-  if (mixed) {
+  if (mixed) {  // grouped by block-size class, instance order within a class
     segs.reserve(h->nsegs);
-    for (int k = 0; k < B; ++k)
-      for (int a = 0; a < h->N[k]; a += kSegRows) segs.push_back(bt::SegRef{k, a, std::min(h->N[k], a + kSegRows), 0});
+    const auto cls_of = [](int n) { return n == 12 ? 0 : (n == 24 ? 1 : (n == 36 ? 2 : 3)); };
+    for (int c = 0; c < 4; ++c) {
+      h->seg_lo[c] = (long long)segs.size();
+      for (int k = 0; k < B; ++k)
+        if (cls_of(h->n[k]) == c)
+          for (int a = 0; a < h->N[k]; a += kSegRows)
+            segs.push_back(bt::SegRef{k, a, std::min(h->N[k], a + kSegRows), 0});
+      h->seg_hi[c] = (long long)segs.size();
+    }
   }
   std::vector<int> order(B);
   std::iota(order.begin(), order.end(), 0);

@@ -149,6 +149,7 @@ struct SetupParams {
   // null: one float32 factor kernel over all rows
   const long long* cls_idx;
   long long cls_lo[4], cls_hi[4];
+  long long seg_lo[4], seg_hi[4];  // with cls_idx: the segments of each class, grouped in segs
 };
 
 struct AdjParams {

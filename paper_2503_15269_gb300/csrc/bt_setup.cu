@@ -792,6 +792,24 @@ __global__ void __launch_bounds__(256, 2) k_EH(const __grid_constant__ SetupPara
   else eh_segment<1>(P, sg, want_h != 0, fsm);
 }
 
+// The segments of one block-size class (segments [P.seg_lo[cls],
+// P.seg_hi[cls]), grouped by class on the host) with one tile size: TS > 0
+// that tile, 0 the choice by n as in k_EH.  Each kernel takes its own
+// variant's registers and its class's shared memory.
+template <int TS>
+__global__ void __launch_bounds__(256, TS == 2 ? 4 : 2) k_EH_cls(const __grid_constant__ SetupParams P, int want_h, int cls) {
+  extern __shared__ __align__(16) float fsm[];
+  const SegRef sg = P.segs[P.seg_lo[cls] + blockIdx.x];
+  if constexpr (TS > 0) {
+    eh_segment<TS>(P, sg, want_h != 0, fsm);
+  } else {
+    const int n = P.inst[sg.inst].n;
+    if ((n & 3) == 0 && n >= 24) eh_segment<4>(P, sg, want_h != 0, fsm);
+    else if ((n & 1) == 0) eh_segment<2>(P, sg, want_h != 0, fsm);
+    else eh_segment<1>(P, sg, want_h != 0, fsm);
+  }
+}
+
 // ---------------------------------------------------------------- adjoint
 // gD_i = -g_i x_i^T, gO_i = -(g_i x_{i+1}^T + x_i g_{i+1}^T), caller layout
 // (row-major blocks).  One warp per block row: x_i, g_i, x_{i+1}, g_{i+1} are
@@ -914,6 +932,21 @@ static cudaError_t launch_setup_opt(const bt::SetupParams* P, int mixed, int m, 
     for (int q = 1; q <= maxn; ++q) maxbs = std::max(maxbs, bt::slot32(q));
     const int sm_eh = bt::kEHSlots * maxbs * (int)sizeof(float);
     if (P->segs && P->nsegs > 0 && sm_eh <= 200 * 1024) {
+      if (P->cls_idx) {  // the segments grouped by class: one launch per class
+        const auto launch_cls = [&](void (*kern)(bt::SetupParams, int, int), int c, int nbk) -> cudaError_t {
+          const long long cnt = P->seg_hi[c] - P->seg_lo[c];
+          if (cnt <= 0) return cudaSuccess;
+          const int smc = nbk > 0 ? bt::kEHSlots * bt::slot32(nbk) * (int)sizeof(float) : sm_eh;
+          cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smc);
+          if (e != cudaSuccess) return e;
+          kern<<<(unsigned)cnt, 256, smc, st>>>(*P, m >= 2 ? 1 : 0, c);
+          return cudaGetLastError();
+        };
+        if ((err = launch_cls(bt::k_EH_cls<2>, 0, 12)) != cudaSuccess) return err;
+        if ((err = launch_cls(bt::k_EH_cls<4>, 1, 24)) != cudaSuccess) return err;
+        if ((err = launch_cls(bt::k_EH_cls<4>, 2, 36)) != cudaSuccess) return err;
+        return launch_cls(bt::k_EH_cls<0>, 3, 0);
+      }
       cudaFuncSetAttribute(bt::k_EH, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_eh);
       bt::k_EH<<<(unsigned)P->nsegs, 256, sm_eh, st>>>(*P, m >= 2 ? 1 : 0);
       return cudaGetLastError();
