@@ -509,8 +509,10 @@ def main():
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}",
                        "graph": True},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            # per step: k_factor32, k_factor_retry, k_EH (refactor) and the persistent solve kernel
-            "gpu_launches": 4 * a.steps,
+            # per step: the float32 factor and the fused E/H kernel once per
+            # block-size class present (n = 12, 24, 36, other), k_factor_retry
+            # (refactor), and the persistent solve kernel
+            "gpu_launches": (2 * len({n if n in (12, 24, 36) else 0 for n in ns}) + 2) * a.steps,
             "roofline": roof,
             "err_vs_oracle": err,
             "cpu_baseline": cpu,
