@@ -795,9 +795,10 @@ __global__ void __launch_bounds__(256, 2) k_EH(const __grid_constant__ SetupPara
 // The segments of one block-size class (segments [P.seg_lo[cls],
 // P.seg_hi[cls]), grouped by class on the host) with one tile size: TS > 0
 // that tile, 0 the choice by n as in k_EH.  Each kernel takes its own
-// variant's registers and its class's shared memory.
-template <int TS>
-__global__ void __launch_bounds__(256, TS == 2 ? 4 : 2) k_EH_cls(const __grid_constant__ SetupParams P, int want_h, int cls) {
+// variant's registers and its class's shared memory; MINB CTAs per SM
+// (n = 12 and 24: four, their rings are small enough).
+template <int TS, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_EH_cls(const __grid_constant__ SetupParams P, int want_h, int cls) {
   extern __shared__ __align__(16) float fsm[];
   const SegRef sg = P.segs[P.seg_lo[cls] + blockIdx.x];
   if constexpr (TS > 0) {
@@ -942,10 +943,10 @@ static cudaError_t launch_setup_opt(const bt::SetupParams* P, int mixed, int m, 
           kern<<<(unsigned)cnt, 256, smc, st>>>(*P, m >= 2 ? 1 : 0, c);
           return cudaGetLastError();
         };
-        if ((err = launch_cls(bt::k_EH_cls<2>, 0, 12)) != cudaSuccess) return err;
-        if ((err = launch_cls(bt::k_EH_cls<4>, 1, 24)) != cudaSuccess) return err;
-        if ((err = launch_cls(bt::k_EH_cls<4>, 2, 36)) != cudaSuccess) return err;
-        return launch_cls(bt::k_EH_cls<0>, 3, 0);
+        if ((err = launch_cls(bt::k_EH_cls<2, 4>, 0, 12)) != cudaSuccess) return err;
+        if ((err = launch_cls(bt::k_EH_cls<4, 4>, 1, 24)) != cudaSuccess) return err;
+        if ((err = launch_cls(bt::k_EH_cls<4, 2>, 2, 36)) != cudaSuccess) return err;
+        return launch_cls(bt::k_EH_cls<0, 2>, 3, 0);
       }
       cudaFuncSetAttribute(bt::k_EH, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_eh);
       bt::k_EH<<<(unsigned)P->nsegs, 256, sm_eh, st>>>(*P, m >= 2 ? 1 : 0);
